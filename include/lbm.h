@@ -1,0 +1,171 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) lattice Boltzmann / DEM library for
+ * slurries of spheres, after Mutabaruka & Kamrin, "A simulation technique for
+ * slurries interacting with moving parts and deformable solids with
+ * applications" (arXiv 1703.05158).
+ *
+ * One handle is one simulation on one GPU:
+ *   - a D3Q19 lattice (Sect. 2.2, Table 1) of nx*ny*nz nodes, periodic in x
+ *     and y, with plane walls at z = -1/2 and z = nz - 1/2 (halfway, i.e.
+ *     link fraction q = 1/2) that may slide tangentially;
+ *   - BGK collision (Eq. 12) towards the second-order equilibrium (Eq. 9)
+ *     with the Smagorinsky relaxation time tau* = tau0 + tau_t (Eq. 18) and a
+ *     body acceleration g (force density rho*g on fluid nodes);
+ *   - spheres coupled to the fluid by interpolated bounce-back on cut links
+ *     (Eqs. 19, 21), momentum-exchange force and torque (Eqs. 25, 26) and
+ *     equilibrium refill of nodes a sphere uncovers;
+ *   - a linear spring-dashpot normal contact (Eq. 1) between spheres and
+ *     with the walls, integrated by velocity Verlet (Sect. 2.1) in
+ *     dem_substeps sub-steps per lattice step.
+ * Everything is in lattice units (Sect. 2.2): dx = dt = 1, fluid reference
+ * density 1, c_s^2 = 1/3.
+ *
+ * Conventions
+ *   Node index   n = x + nx*(y + ny*z).
+ *   Populations  [19][N] with N = nx*ny*nz, direction order of Table 1.
+ *   Vectors      per sphere, 3 consecutive doubles (x, y, z): array [n][3].
+ *   where        LBM_HOST (any host memory) or LBM_DEVICE (device memory on
+ *                the handle's device).  Output copies are complete when the
+ *                call returns (the call synchronises the handle's stream).
+ *   Ownership    the caller owns every buffer it passes; the library copies
+ *                inputs during the call and keeps no caller pointer.
+ *   Errors       0 on success, a negative LBM_ERR_* code otherwise.  Argument
+ *                errors leave the state untouched.  Errors the device detects
+ *                while stepping (capacity, divergence, a particle moving more
+ *                than half a node per step, a wait that ran out) are sticky:
+ *                lbm_step returns at once and lbm_sync, lbm_forces,
+ *                lbm_fields, ... report them until the handle is destroyed.
+ *   Threads      a handle is not thread-safe; all its work goes to its
+ *                stream in call order.
+ */
+#ifndef GB300_LBM_H
+#define GB300_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_s *lbm_handle;
+
+/* Return codes. */
+#define LBM_OK 0
+#define LBM_ERR_ARG (-1)          /* invalid argument */
+#define LBM_ERR_CUDA (-2)         /* a CUDA runtime call failed */
+#define LBM_ERR_NOMEM (-3)        /* device allocation failed */
+#define LBM_ERR_CAPACITY (-4)     /* more spheres, neighbours or links than sized */
+#define LBM_ERR_DIVERGED (-5)     /* non-positive or non-finite density found */
+#define LBM_ERR_UNSUPPORTED (-6)  /* valid request this build does not implement */
+#define LBM_ERR_TIMEOUT (-7)      /* a device-side wait gave up */
+#define LBM_ERR_GEOMETRY (-8)     /* a sphere moved >= 1/2 node in one step or left the box */
+
+/* Storage of the populations (arithmetic is FP32 in every case). */
+#define LBM_FP32 0       /* f_i - w_i stored as FP32 */
+#define LBM_BF16_DEV 1   /* f_i - w_i stored as bfloat16 */
+#define LBM_FP16_DEV 2   /* f_i - w_i stored as binary16 */
+
+/* Memory space of a caller buffer. */
+#define LBM_HOST 0
+#define LBM_DEVICE 1
+
+typedef struct {
+    int32_t nx, ny, nz;        /* lattice nodes; each >= 1 */
+    int32_t periodic_z;        /* must be 0: walls at z = -1/2 and nz - 1/2 */
+    double tau0;               /* relaxation time, > 1/2 (Eq. 15) */
+    double cs_smag;            /* Smagorinsky constant C >= 0 (Eq. 18); 0 = BGK */
+    double body_accel[3];      /* g; force density rho*g on fluid nodes */
+    double wall_vel_lo[3];     /* velocity of the z = -1/2 wall; z component must be 0 */
+    double wall_vel_hi[3];     /* velocity of the z = nz-1/2 wall; z component must be 0 */
+    double rho_particle;       /* sphere density / fluid density, > 0 */
+    double kn;                 /* normal contact stiffness (Eq. 1), >= 0 */
+    double restitution;        /* normal restitution coefficient, in (0, 1] */
+    int32_t dem_substeps;      /* DEM sub-steps per lattice step, >= 1 */
+    int32_t precision;         /* LBM_FP32, LBM_BF16_DEV or LBM_FP16_DEV */
+    int32_t max_particles;     /* capacity for spheres, >= 0 */
+    double max_radius;         /* largest radius lbm_set_particles accepts, <= 16 */
+    void *cuda_stream;         /* cudaStream_t to run on; NULL: the library makes one */
+    int32_t device;            /* CUDA device ordinal */
+} lbm_params;
+
+typedef struct {
+    int64_t nodes;             /* nx*ny*nz */
+    int64_t fluid_nodes;       /* fluid nodes of the current geometry */
+    int64_t links;             /* sphere cut links treated in the last step */
+    int64_t refilled;          /* nodes refilled in the last step */
+    int64_t steps;             /* lattice steps taken since lbm_set_particles */
+    int32_t particles;         /* spheres */
+    int32_t precision;         /* as created */
+    int64_t device_bytes;      /* device memory the handle holds */
+} lbm_info_t;
+
+/* Allocate a simulation and set the fluid to rest (f = w, rho = 1, u = 0)
+ * with no spheres.  *out receives the handle.  LBM_ERR_ARG on an invalid
+ * parameter (tau0 <= 1/2, a wall velocity with a z component, a box that
+ * cannot hold a sphere of max_radius, ...), LBM_ERR_UNSUPPORTED for
+ * periodic_z != 0, LBM_ERR_NOMEM / LBM_ERR_CUDA on device failure. */
+int lbm_create(const lbm_params *params, lbm_handle *out);
+
+/* Free everything the handle holds (synchronises its stream first). */
+int lbm_destroy(lbm_handle h);
+
+/* Place n spheres (host arrays): centres pos[n][3] (x, y in [0, n) after
+ * wrapping; z in (-1/2, nz - 1/2)), velocities vel[n][3], angular velocities
+ * omega[n][3], radii radius[n] in (0, max_radius], and fixed[n] (NULL = none
+ * fixed; 1 = prescribed motion: the centre moves with the given constant
+ * velocity, velocity and spin never change).  Resets the fluid to rest, the
+ * step counter to 0 and the external load to 0, and computes the node
+ * geometry (Sect. 2.3).  LBM_ERR_CAPACITY if n > max_particles. */
+int lbm_set_particles(lbm_handle h, int32_t n, const double *pos, const double *vel,
+                      const double *omega, const double *radius, const uint8_t *fixed);
+
+/* External force and torque on every sphere ([n][3] each, NULL = zero), added
+ * to the hydrodynamic load during the DEM sub-steps of every following step
+ * until set again (e.g. the load of another solver coupled to the spheres). */
+int lbm_set_particle_load(lbm_handle h, const double *force, const double *torque, int32_t where);
+
+/* Overwrite the populations of the fluid nodes with f[19][N] (FP64, the
+ * pre-collision state of the current time); solid nodes are ignored. */
+int lbm_set_populations(lbm_handle h, const double *f, int32_t where);
+
+/* Advance nsteps >= 0 lattice steps (asynchronous on the handle's stream).
+ * One step, Sect. 2.5 in the order of Sect. 2.3: geometry at the current
+ * sphere positions, refill of uncovered nodes, collision, streaming with
+ * interpolated bounce-back, momentum exchange, DEM sub-steps. */
+int lbm_step(lbm_handle h, int32_t nsteps);
+
+/* Hydrodynamic force F[n][3] and torque T[n][3] (about the centre) of the
+ * last step (Eqs. 25, 26); zero before the first step. */
+int lbm_forces(lbm_handle h, double *F, double *T, int32_t where);
+
+/* Current sphere centres, velocities and angular velocities ([n][3] each;
+ * any pointer may be NULL to skip it). */
+int lbm_particles(lbm_handle h, double *pos, double *vel, double *omega, int32_t where);
+
+/* Density rho[N] and velocity u[3][N] of the current state (Eqs. 5, 6 with
+ * the half-force shift); solid nodes give rho = 0 and u = 0.  Either pointer
+ * may be NULL. */
+int lbm_fields(lbm_handle h, float *rho, float *u, int32_t where);
+
+/* Pre-collision populations f[19][N] of the current state in FP64
+ * (w_i + stored deviation); solid nodes give 0. */
+int lbm_populations(lbm_handle h, double *f, int32_t where);
+
+/* Owner of every node for the current geometry: sphere index, -1 = fluid. */
+int lbm_geometry(lbm_handle h, int32_t *owner, int32_t where);
+
+/* Counters and sizes (synchronises the stream). */
+int lbm_info(lbm_handle h, lbm_info_t *info);
+
+/* Wait for the handle's stream and return its sticky device status. */
+int lbm_sync(lbm_handle h);
+
+/* Static description of a return code. */
+const char *lbm_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_LBM_H */

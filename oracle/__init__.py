@@ -1,0 +1,217 @@
+"""FP64 CPU oracle of the coupled LBM-DEM hot path (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` use this package.  It shares no code with the CUDA library; the
+arithmetic lives in ``lbm_oracle.c`` and this module only marshals arguments.
+
+Parity pins (tests/test_oracle_*.py): D3Q19 moment identities, exact mass and
+momentum balance, rest-state invariance, Couette and Poiseuille closed forms,
+the Smagorinsky reduction to BGK and its strain-rate relation, the lattice
+point count of a sphere, brute-force link fractions, bounce-back exactness on
+uniform flow, refill on a shifted sphere, drag on a periodic sphere array
+against Hasimoto/Sangani-Acrivos, and the DEM restitution and contact time.
+The coupled free-sphere trajectory itself has no closed form: parity
+unpinned beyond those invariants.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NQ = 19
+
+
+class OrcParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("tau0", ctypes.c_double), ("cs", ctypes.c_double),
+        ("g", ctypes.c_double * 3),
+        ("u_lo", ctypes.c_double * 3), ("u_hi", ctypes.c_double * 3),
+        ("rho_s", ctypes.c_double), ("kn", ctypes.c_double), ("restitution", ctypes.c_double),
+        ("dem_substeps", ctypes.c_int), ("les", ctypes.c_int), ("fluid", ctypes.c_int),
+        ("periodic_z", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+        lib.orc_create.restype = vp
+        lib.orc_create.argtypes = [ctypes.POINTER(OrcParams)]
+        lib.orc_destroy.argtypes = [vp]
+        lib.orc_set_particles.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp, ctypes.c_void_p]
+        lib.orc_set_populations.argtypes = [vp, dp]
+        lib.orc_get_populations.argtypes = [vp, dp]
+        lib.orc_step.argtypes = [vp, ctypes.c_int]
+        lib.orc_forces.argtypes = [vp, dp, dp]
+        lib.orc_contact_forces.argtypes = [vp, dp]
+        lib.orc_particles.argtypes = [vp, dp, dp, dp]
+        lib.orc_fields.argtypes = [vp, dp, dp]
+        lib.orc_tau_eff.argtypes = [vp, dp]
+        lib.orc_owner.argtypes = [vp, ip]
+        lib.orc_links.restype = ctypes.c_long
+        lib.orc_links.argtypes = [vp, ctypes.c_long, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p]
+        lib.orc_refilled.restype = ctypes.c_long
+        lib.orc_refilled.argtypes = [vp]
+        lib.orc_step_count.restype = ctypes.c_long
+        lib.orc_step_count.argtypes = [vp]
+        lib.orc_tables.argtypes = [ip, ip, ip, dp, ip]
+        lib.orc_feq.argtypes = [ctypes.c_double, dp, dp]
+        lib.orc_refill_only.argtypes = [vp]
+        lib.orc_set_load.argtypes = [vp, ctypes.c_void_p, ctypes.c_void_p]
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Oracle:
+    """One oracle simulation: x, y periodic, walls at z = -1/2 and nz - 1/2.
+
+    Arrays use node index x + nx*(y + ny*z); populations are [19, nz, ny, nx].
+    """
+
+    def __init__(self, nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0),
+                 u_hi=(0.0, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16,
+                 les=True, fluid=True, periodic_z=False, threads=None):
+        if threads is not None:
+            os.environ["OMP_NUM_THREADS"] = str(threads)
+        lib = _load()
+        p = OrcParams()
+        p.nx, p.ny, p.nz = nx, ny, nz
+        p.tau0, p.cs = tau0, cs
+        p.g[:] = list(g)
+        p.u_lo[:] = list(u_lo)
+        p.u_hi[:] = list(u_hi)
+        p.rho_s, p.kn, p.restitution = rho_s, kn, restitution
+        p.dem_substeps, p.les, p.fluid = dem_substeps, int(bool(les)), int(bool(fluid))
+        p.periodic_z = int(bool(periodic_z))
+        self._h = lib.orc_create(ctypes.byref(p))
+        if not self._h:
+            raise MemoryError("oracle allocation failed")
+        self.lib, self.shape = lib, (nz, ny, nx)
+        self.N = nx * ny * nz if fluid else 0
+        self.np = 0
+
+    def close(self):
+        if self._h:
+            self.lib.orc_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def set_particles(self, X, V=None, Om=None, R=None, fixed=None):
+        X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+        n = X.shape[0]
+        V = np.zeros((n, 3)) if V is None else np.ascontiguousarray(V, dtype=np.float64).reshape(n, 3)
+        Om = np.zeros((n, 3)) if Om is None else np.ascontiguousarray(Om, dtype=np.float64).reshape(n, 3)
+        R = np.ascontiguousarray(R, dtype=np.float64).reshape(n)
+        fx = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8).reshape(n)
+        self._keep = (X, V, Om, R, fx)
+        self.lib.orc_set_particles(self._h, n, _dp(X), _dp(V), _dp(Om), _dp(R),
+                                   None if fx is None else fx.ctypes.data)
+        self.np = n
+
+    def set_load(self, F=None, T=None):
+        """External force and torque per sphere, [n, 3] each (None = zero)."""
+        F = None if F is None else np.ascontiguousarray(F, dtype=np.float64).reshape(self.np, 3)
+        T = None if T is None else np.ascontiguousarray(T, dtype=np.float64).reshape(self.np, 3)
+        self._load = (F, T)
+        self.lib.orc_set_load(self._h, None if F is None else F.ctypes.data, None if T is None else T.ctypes.data)
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(NQ * self.N)
+        self.lib.orc_set_populations(self._h, _dp(f))
+
+    def populations(self):
+        f = np.empty(NQ * self.N)
+        self.lib.orc_get_populations(self._h, _dp(f))
+        return f.reshape((NQ,) + self.shape)
+
+    def step(self, n=1):
+        self.lib.orc_step(self._h, int(n))
+
+    def forces(self):
+        F, T = np.empty((self.np, 3)), np.empty((self.np, 3))
+        if self.np:
+            self.lib.orc_forces(self._h, _dp(F), _dp(T))
+        return F, T
+
+    def contact_forces(self):
+        F = np.empty((self.np, 3))
+        if self.np:
+            self.lib.orc_contact_forces(self._h, _dp(F))
+        return F
+
+    def particles(self):
+        X, V, Om = np.empty((self.np, 3)), np.empty((self.np, 3)), np.empty((self.np, 3))
+        if self.np:
+            self.lib.orc_particles(self._h, _dp(X), _dp(V), _dp(Om))
+        return X, V, Om
+
+    def fields(self):
+        rho, u = np.empty(self.N), np.empty(3 * self.N)
+        self.lib.orc_fields(self._h, _dp(rho), _dp(u))
+        return rho.reshape(self.shape), u.reshape((3,) + self.shape)
+
+    def tau_eff(self):
+        t = np.empty(self.N)
+        self.lib.orc_tau_eff(self._h, _dp(t))
+        return t.reshape(self.shape)
+
+    def owner(self):
+        o = np.empty(self.N, dtype=np.int32)
+        self.lib.orc_owner(self._h, o.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        return o.reshape(self.shape)
+
+    def links(self):
+        n = self.lib.orc_links(self._h, 0, None, None, None, None)
+        node = np.empty(n, dtype=np.int64)
+        d = np.empty(n, dtype=np.int32)
+        q = np.empty(n, dtype=np.float32)
+        pid = np.empty(n, dtype=np.int32)
+        self.lib.orc_links(self._h, n, node.ctypes.data, d.ctypes.data, q.ctypes.data, pid.ctypes.data)
+        return node, d, q, pid
+
+    def refill_only(self):
+        """Run only geometry and refill of the next step (test hook)."""
+        self.lib.orc_refill_only(self._h)
+
+    @property
+    def refilled(self):
+        return int(self.lib.orc_refilled(self._h))
+
+    @property
+    def steps(self):
+        return int(self.lib.orc_step_count(self._h))
+
+
+def tables():
+    """(c [19,3] int, w [19], opp [19]) as the oracle uses them."""
+    lib = _load()
+    cx, cy, cz, opp = (np.empty(NQ, dtype=np.int32) for _ in range(4))
+    w = np.empty(NQ)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.orc_tables(cx.ctypes.data_as(ip), cy.ctypes.data_as(ip), cz.ctypes.data_as(ip), _dp(w),
+                   opp.ctypes.data_as(ip))
+    return np.stack([cx, cy, cz], axis=1), w, opp
+
+
+def feq(rho, u):
+    """The oracle's second-order equilibrium (Eq. 9) for one (rho, u)."""
+    lib = _load()
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(3)
+    out = np.empty(NQ)
+    lib.orc_feq(float(rho), _dp(u), _dp(out))
+    return out

@@ -1,0 +1,762 @@
+/*
+ * lbm_oracle.c - plain, slow FP64 CPU reference of the coupled lattice
+ * Boltzmann / discrete element hot path of Mutabaruka & Kamrin, "A simulation
+ * technique for slurries interacting with moving parts and deformable solids
+ * with applications" (arXiv 1703.05158).
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this file.  It shares no code, header,
+ * table or helper with the CUDA library; the D3Q19 tables below are typed
+ * from the paper's Table 1 and the weights stated under Eq. (9).
+ *
+ * One time step n -> n+1, in the order of Sect. 2.5 read with Sect. 2.3:
+ *   1. geometry at X^n: owner of every node (fluid or sphere p)
+ *   2. refill of nodes uncovered since step n-1 with the equilibrium (Eq. 9)
+ *   3. collision, Eqs. (5), (6), (9), (12) with the Smagorinsky relaxation
+ *      time of Eq. (18) and a body force (Guo, Zheng & Shi 2002)
+ *   4. streaming, Eq. (13), with interpolated bounce-back on cut links,
+ *      Eqs. (19) and (21); the z walls are cut links with q = 1/2
+ *   5. momentum exchange force and torque on every sphere, Eqs. (25), (26)
+ *   6. DEM: linear spring-dashpot normal contact, Eq. (1), integrated by
+ *      velocity Verlet (Sect. 2.1) in dem_substeps sub-steps
+ *
+ * Arithmetic is FP64, except the geometric decisions (is a node inside a
+ * sphere, which sphere owns it, the link fraction q and so which branch of
+ * Eq. (19) applies) which are taken in FP32 from FP32 relative positions:
+ * the GPU library takes the same decisions with the same FP32 operations, so
+ * both sides agree on every node and link.  Build with -ffp-contract=off so
+ * that no multiply-add is fused.
+ *
+ * Readings of passages the paper leaves open are marked "reading:".
+ * Parity pins: every function below is pinned by tests in tests/ except the
+ * full coupled moving-sphere trajectory, which has no closed form.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NQ 19
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* Table 1: the D3Q19 velocity set, direction i = 0..18. */
+static const int CX[NQ] = {0, -1, 0, 0, -1, -1, -1, -1, 0, 0, 1, 0, 0, 1, 1, 1, 1, 0, 0};
+static const int CY[NQ] = {0, 0, -1, 0, -1, 1, 0, 0, -1, -1, 0, 1, 0, 1, -1, 0, 0, 1, 1};
+static const int CZ[NQ] = {0, 0, 0, -1, 0, 0, -1, 1, -1, 1, 0, 0, 1, 0, 0, 1, -1, 1, -1};
+
+/* Weight of direction i (text under Eq. 9): 1/3 at rest, 1/18 for the six
+ * axis directions 1, 2, 3, 10, 11, 12, 1/36 for the twelve diagonals. */
+static double weight(int i) {
+    if (i == 0) return 1.0 / 3.0;
+    if (i == 1 || i == 2 || i == 3 || i == 10 || i == 11 || i == 12) return 1.0 / 18.0;
+    return 1.0 / 36.0;
+}
+
+/* Opposite direction: the one whose velocity is -c_i, found from the table. */
+static int opposite(int i) {
+    for (int k = 0; k < NQ; ++k)
+        if (CX[k] == -CX[i] && CY[k] == -CY[i] && CZ[k] == -CZ[i]) return k;
+    return -1;
+}
+
+typedef struct {
+    int nx, ny, nz;         /* lattice; x, y periodic; walls at z=-1/2, z=nz-1/2 */
+    double tau0;            /* relaxation time, > 1/2 (Eq. 15) */
+    double cs;              /* Smagorinsky constant C (Eq. 18) */
+    double g[3];            /* body acceleration; force density rho*g */
+    double u_lo[3];         /* velocity of the wall at z = -1/2 */
+    double u_hi[3];         /* velocity of the wall at z = nz-1/2 */
+    double rho_s;           /* sphere density (fluid reference density is 1) */
+    double kn;              /* normal contact stiffness (Eq. 1) */
+    double restitution;     /* normal restitution coefficient */
+    int dem_substeps;       /* DEM sub-steps per lattice step */
+    int les;                /* 1: Smagorinsky tau (Eq. 18); 0: plain BGK path */
+    int fluid;              /* 0: DEM only, no lattice (hydrodynamic load 0) */
+    int periodic_z;         /* 1: z periodic too (no walls) */
+} orc_params;
+
+typedef struct {
+    orc_params p;
+    long N;                 /* nx*ny*nz */
+    double w[NQ];
+    int opp[NQ];
+    double *f;              /* [NQ][N] populations at time n (pre-collision) */
+    double *fc;             /* [NQ][N] post-collision populations */
+    double *fn;             /* [NQ][N] populations at time n+1 */
+    int *owner;             /* sphere owning each node at time n, -1 = fluid */
+    int *owner_prev;        /* the same at time n-1 */
+    float *key;             /* scratch for the overlap tie-break */
+    int np;
+    double *X, *V, *Om, *R; /* sphere centre, velocity, angular velocity, radius */
+    double *Fh, *Th;        /* hydrodynamic force and torque of the last step */
+    double *Fc;             /* contact force at the current position (carried) */
+    double *Fx, *Tx;        /* external force and torque held over every step */
+    unsigned char *fixed;   /* 1: prescribed motion, X += V dt; V, Om constant */
+    long step;
+    long refilled;          /* nodes refilled in the last step */
+} orc_state;
+
+/* ------------------------------------------------------------------ */
+/* Geometry                                                            */
+/* ------------------------------------------------------------------ */
+
+/* Image of lattice coordinate x (0..n-1) closest to centre coordinate Xc on
+ * a periodic axis: b + d with b = floor(Xc) and d the wrapped offset in
+ * [-n/2, n/2).  On a wall axis the coordinate itself. */
+static int image(int x, double Xc, int n, int periodic) {
+    if (!periodic) return x;
+    int b = (int)floor(Xc);
+    int d = (x - b) % n;
+    if (d < 0) d += n;
+    if (2 * d >= n) d -= n;
+    return b + d;
+}
+
+/* FP32 relative coordinate of an (unwrapped) lattice coordinate. */
+static float rel32(int xi, double Xc) { return (float)((double)xi - Xc); }
+
+/* Squared FP32 distance, summed x, y, z in that order. */
+static float dist2_32(float dx, float dy, float dz) { return dx * dx + dy * dy + dz * dz; }
+
+static int wrap(int x, int n) {
+    int r = x % n;
+    return r < 0 ? r + n : r;
+}
+
+/* Step 1.  A node is inside sphere p when |x - X_p|^2 < R_p^2 (strict).
+ * reading: a node inside several overlapping spheres belongs to the one with
+ * the smallest |x - X_p| - R_p, ties to the smallest p. */
+static void geometry(orc_state *s) {
+    const orc_params *P = &s->p;
+    for (long n = 0; n < s->N; ++n) {
+        s->owner[n] = -1;
+        s->key[n] = INFINITY;
+    }
+    for (int p = 0; p < s->np; ++p) {
+        const double *X = s->X + 3 * p;
+        float Rf = (float)s->R[p];
+        float R2 = Rf * Rf;
+        int ext = (int)ceil(s->R[p]) + 1;
+        int bx = (int)floor(X[0]), by = (int)floor(X[1]), bz = (int)floor(X[2]);
+        for (int oz = -ext; oz <= ext; ++oz) {
+            int zi = bz + oz;
+            if (!P->periodic_z && (zi < 0 || zi >= P->nz)) continue;
+            for (int oy = -ext; oy <= ext; ++oy) {
+                int yi = by + oy;
+                for (int ox = -ext; ox <= ext; ++ox) {
+                    int xi = bx + ox;
+                    float dx = rel32(xi, X[0]), dy = rel32(yi, X[1]), dz = rel32(zi, X[2]);
+                    float d2 = dist2_32(dx, dy, dz);
+                    if (!(d2 < R2)) continue;
+                    float key = sqrtf(d2) - Rf;
+                    long n = wrap(xi, P->nx) + (long)P->nx * (wrap(yi, P->ny) + (long)P->ny * wrap(zi, P->nz));
+                    if (key < s->key[n]) {
+                        s->key[n] = key;
+                        s->owner[n] = p;
+                    }
+                }
+            }
+        }
+    }
+}
+
+/* Link fraction q of the cut link from fluid node x (unwrapped image xi, yi,
+ * zi relative to sphere p) along direction j: the smallest root t of
+ * |x + t c_j - X_p| = R_p, i.e. q = |x_b - x_f| / |c_j| (Sect. 2.3).
+ * Written in the cancellation-free form q = c0 / (-b + sqrt(b^2 - a c0)) of
+ * t^2 a + 2 t b + c0 = 0 with a = |c_j|^2, b = c_j.(x - X), c0 = |x-X|^2 - R^2.
+ * FP32, like the inside test, so that q < 1/2 is decided identically on both
+ * sides. */
+static float link_q(const orc_state *s, int p, int xi, int yi, int zi, int j) {
+    const double *X = s->X + 3 * p;
+    float Rf = (float)s->R[p];
+    float dx = rel32(xi, X[0]), dy = rel32(yi, X[1]), dz = rel32(zi, X[2]);
+    float cx = (float)CX[j], cy = (float)CY[j], cz = (float)CZ[j];
+    float a = cx * cx + cy * cy + cz * cz;
+    float b = cx * dx + cy * dy + cz * dz;
+    float c0 = dist2_32(dx, dy, dz) - Rf * Rf;
+    float disc = b * b - a * c0;
+    if (disc < 0.0f) disc = 0.0f;
+    float q = c0 / (-b + sqrtf(disc));
+    if (q < 0.0f) q = 0.0f;
+    if (q > 1.0f) q = 1.0f;
+    return q;
+}
+
+/* ------------------------------------------------------------------ */
+/* Lattice Boltzmann                                                   */
+/* ------------------------------------------------------------------ */
+
+/* Eq. (9) with c_s^2 = 1/3: f_i^eq = rho w_i [1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u^2]. */
+static double feq(const orc_state *s, int i, double rho, const double u[3]) {
+    double cu = CX[i] * u[0] + CY[i] * u[1] + CZ[i] * u[2];
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    return rho * s->w[i] * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+}
+
+/* Density (Eq. 5) and velocity (Eq. 6) of node n; with a body force the
+ * velocity is shifted by half the force, u = (sum f c + F/2)/rho, F = rho g. */
+static void moments(const orc_state *s, const double *f, long n, double *rho, double u[3]) {
+    double r = 0, mx = 0, my = 0, mz = 0;
+    for (int i = 0; i < NQ; ++i) {
+        double fi = f[(long)i * s->N + n];
+        r += fi;
+        mx += fi * CX[i];
+        my += fi * CY[i];
+        mz += fi * CZ[i];
+    }
+    *rho = r;
+    u[0] = mx / r + 0.5 * s->p.g[0];
+    u[1] = my / r + 0.5 * s->p.g[1];
+    u[2] = mz / r + 0.5 * s->p.g[2];
+}
+
+/* Effective relaxation time tau* = tau0 + tau_t at node n (Sect. 2.2).
+ * Pi_ab = sum_i c_ia c_ib (f_i - f_i^eq); Q = sqrt(Pi_ab Pi_ab).
+ * reading: Eq. (18) is used with its Pi read as Q.  This is the root of
+ * tau_t (tau0 + tau_t) = sqrt(2) C^2 Q / (2 rho c_s^4), which follows from
+ * eta_t = (C l_x)^2 |S|, |S| = sqrt(2 S_ab S_ab) and S = Pi/(2 rho c_s^2 tau*);
+ * with c_s^4 = 1/9 and l_x = dt = 1:
+ *   tau_t = 1/2 [ sqrt(tau0^2 + 18 sqrt(2) C^2 Q / rho) - tau0 ]. */
+static double tau_eff(const orc_state *s, const double *f, long n, double rho, const double u[3]) {
+    double tau0 = s->p.tau0;
+    if (!s->p.les) return tau0;
+    double Pxx = 0, Pyy = 0, Pzz = 0, Pxy = 0, Pxz = 0, Pyz = 0;
+    for (int i = 0; i < NQ; ++i) {
+        double ne = f[(long)i * s->N + n] - feq(s, i, rho, u);
+        Pxx += CX[i] * CX[i] * ne;
+        Pyy += CY[i] * CY[i] * ne;
+        Pzz += CZ[i] * CZ[i] * ne;
+        Pxy += CX[i] * CY[i] * ne;
+        Pxz += CX[i] * CZ[i] * ne;
+        Pyz += CY[i] * CZ[i] * ne;
+    }
+    double Q = sqrt(Pxx * Pxx + Pyy * Pyy + Pzz * Pzz + 2.0 * (Pxy * Pxy + Pxz * Pxz + Pyz * Pyz));
+    double C = s->p.cs;
+    double tau_t = 0.5 * (sqrt(tau0 * tau0 + 18.0 * sqrt(2.0) * C * C * Q / rho) - tau0);
+    return tau0 + tau_t;
+}
+
+/* Step 3 at one fluid node: BGK relaxation towards Eq. (9) with tau*
+ * (Eq. 12), plus the body-force source of Guo et al. (2002),
+ *   S_i = (1 - 1/(2 tau*)) w_i [3 (c_i - u).F + 9 (c_i.u)(c_i.F)],  F = rho g. */
+static void collide_node(orc_state *s, long n) {
+    double rho, u[3];
+    moments(s, s->f, n, &rho, u);
+    double tau = tau_eff(s, s->f, n, rho, u);
+    double F[3] = {rho * s->p.g[0], rho * s->p.g[1], rho * s->p.g[2]};
+    for (int i = 0; i < NQ; ++i) {
+        double fi = s->f[(long)i * s->N + n];
+        double e = feq(s, i, rho, u);
+        double cu = CX[i] * u[0] + CY[i] * u[1] + CZ[i] * u[2];
+        double cF = CX[i] * F[0] + CY[i] * F[1] + CZ[i] * F[2];
+        double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+        double src = s->w[i] * (3.0 * (cF - uF) + 9.0 * cu * cF);
+        s->fc[(long)i * s->N + n] = fi - (fi - e) / tau + (1.0 - 0.5 / tau) * src;
+    }
+}
+
+/* Is z a lattice plane (always on a periodic z axis)? */
+static int in_z(const orc_state *s, int z) { return s->p.periodic_z || (z >= 0 && z < s->p.nz); }
+
+static long node_of(const orc_state *s, int x, int y, int z) {
+    return wrap(x, s->p.nx) + (long)s->p.nx * (wrap(y, s->p.ny) + (long)s->p.ny * wrap(z, s->p.nz));
+}
+
+static int is_fluid(const orc_state *s, int x, int y, int z) {
+    if (!in_z(s, z)) return 0;
+    return s->owner[node_of(s, x, y, z)] < 0;
+}
+
+/* Boundary point x_b = x + q c_j relative to the centre of sphere p, with x
+ * taken at its image nearest to the centre. */
+static void arm(const orc_state *s, int p, int x, int y, int z, int j, double q, double l[3]) {
+    const double *X = s->X + 3 * p;
+    int xi = image(x, X[0], s->p.nx, 1), yi = image(y, X[1], s->p.ny, 1);
+    int zi = image(z, X[2], s->p.nz, s->p.periodic_z);
+    l[0] = ((double)xi - X[0]) + q * CX[j];
+    l[1] = ((double)yi - X[1]) + q * CY[j];
+    l[2] = ((double)zi - X[2]) + q * CZ[j];
+}
+
+/* Describe the boundary met by the link from fluid node (x,y,z) along c_j:
+ * fraction q and boundary velocity u_b.  Returns the owning sphere, -1 for a
+ * z wall (q = 1/2, u_b = wall velocity; the halfway wall of Eq. 19). */
+static int boundary(const orc_state *s, int x, int y, int z, int j, double *q, double ub[3]) {
+    int zz = z + CZ[j];
+    if (!in_z(s, zz)) {
+        const double *uw = zz < 0 ? s->p.u_lo : s->p.u_hi;
+        *q = 0.5;
+        ub[0] = uw[0];
+        ub[1] = uw[1];
+        ub[2] = uw[2];
+        return -1;
+    }
+    int p = s->owner[node_of(s, x + CX[j], y + CY[j], zz)];
+    const double *X = s->X + 3 * p;
+    int xi = image(x, X[0], s->p.nx, 1), yi = image(y, X[1], s->p.ny, 1);
+    int zi = image(z, X[2], s->p.nz, s->p.periodic_z);
+    *q = (double)link_q(s, p, xi, yi, zi, j);
+    double l[3];
+    arm(s, p, x, y, z, j, *q, l);
+    const double *V = s->V + 3 * p, *W = s->Om + 3 * p;
+    ub[0] = V[0] + (W[1] * l[2] - W[2] * l[1]);
+    ub[1] = V[1] + (W[2] * l[0] - W[0] * l[2]);
+    ub[2] = V[2] + (W[0] * l[1] - W[1] * l[0]);
+    return p;
+}
+
+/* Step 4 for the population k arriving at fluid node (x,y,z) from a solid or
+ * wall node along the cut link j = opposite(k) (x + c_j is not fluid).
+ * Eq. (19) with the moving-boundary term of Eq. (21):
+ *   q <  1/2: f_k = 2q fc_j(x) + (1-2q) fc_j(x - c_j) + 6 w_j (c_k.u_b)
+ *   q >= 1/2: f_k = fc_j(x)/(2q) + (2q-1)/(2q) fc_k(x) + (3/q) w_j (c_k.u_b)
+ * reading: the sign of Eq. (21) is the one that makes a wall moving towards
+ * the fluid add momentum; the density factor is the reference density 1.
+ * reading: when q < 1/2 and x - c_j is not fluid, the halfway rule
+ * f_k = fc_j(x) + 6 w_j (c_k.u_b) is used. */
+static double bounce(const orc_state *s, long n, int x, int y, int z, int k, double q, const double ub[3]) {
+    int j = s->opp[k];
+    double cku = CX[k] * ub[0] + CY[k] * ub[1] + CZ[k] * ub[2];
+    double fcj = s->fc[(long)j * s->N + n];
+    if (q < 0.5) {
+        double dw = 6.0 * s->w[j] * cku;
+        if (is_fluid(s, x - CX[j], y - CY[j], z - CZ[j])) {
+            long nb = node_of(s, x - CX[j], y - CY[j], z - CZ[j]);
+            return 2.0 * q * fcj + (1.0 - 2.0 * q) * s->fc[(long)j * s->N + nb] + dw;
+        }
+        return fcj + dw;
+    }
+    double fck = s->fc[(long)k * s->N + n];
+    return fcj / (2.0 * q) + (2.0 * q - 1.0) / (2.0 * q) * fck + 3.0 / q * s->w[j] * cku;
+}
+
+/* Step 4: f_k(x, n+1) = fc_k(x - c_k) when x - c_k is fluid (Eq. 13), else
+ * the bounce-back value above. */
+static void stream(orc_state *s) {
+    const orc_params *P = &s->p;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < P->nz; ++z) {
+        for (int y = 0; y < P->ny; ++y) {
+            for (int x = 0; x < P->nx; ++x) {
+                long n = node_of(s, x, y, z);
+                if (s->owner[n] >= 0) continue;
+                for (int k = 0; k < NQ; ++k) {
+                    int j = s->opp[k];
+                    double v;
+                    if (is_fluid(s, x - CX[k], y - CY[k], z - CZ[k])) {
+                        v = s->fc[(long)k * s->N + node_of(s, x - CX[k], y - CY[k], z - CZ[k])];
+                    } else {
+                        double q, ub[3];
+                        boundary(s, x, y, z, j, &q, ub);
+                        v = bounce(s, n, x, y, z, k, q, ub);
+                    }
+                    s->fn[(long)k * s->N + n] = v;
+                }
+            }
+        }
+    }
+}
+
+/* Step 5: momentum exchange (Eqs. 25, 26).  Every cut link from fluid node x
+ * along j into sphere p carries fc_j(x) c_j into the solid and takes back
+ * f_k(x, n+1) c_k, k = opposite(j); the solid receives
+ *   dP = (fc_j(x) + f_k(x, n+1)) c_j,    F_p += dP,   T_p += l x dP,
+ * l = x_b - X_p, x_b = x + q c_j (reading of "l" as the arm to the boundary
+ * point of the link).  Summed in (node index, j) order. */
+static void momentum_exchange(orc_state *s) {
+    const orc_params *P = &s->p;
+    memset(s->Fh, 0, sizeof(double) * 3 * s->np);
+    memset(s->Th, 0, sizeof(double) * 3 * s->np);
+    for (int z = 0; z < P->nz; ++z)
+        for (int y = 0; y < P->ny; ++y)
+            for (int x = 0; x < P->nx; ++x) {
+                long n = node_of(s, x, y, z);
+                if (s->owner[n] >= 0) continue;
+                for (int j = 1; j < NQ; ++j) {
+                    int zz = z + CZ[j];
+                    if (!in_z(s, zz)) continue;
+                    int p = s->owner[node_of(s, x + CX[j], y + CY[j], zz)];
+                    if (p < 0) continue;
+                    int k = s->opp[j];
+                    double q, ub[3], l[3];
+                    boundary(s, x, y, z, j, &q, ub);
+                    arm(s, p, x, y, z, j, q, l);
+                    double m = s->fc[(long)j * s->N + n] + s->fn[(long)k * s->N + n];
+                    double dP[3] = {m * CX[j], m * CY[j], m * CZ[j]};
+                    double *F = s->Fh + 3 * p, *T = s->Th + 3 * p;
+                    F[0] += dP[0];
+                    F[1] += dP[1];
+                    F[2] += dP[2];
+                    T[0] += l[1] * dP[2] - l[2] * dP[1];
+                    T[1] += l[2] * dP[0] - l[0] * dP[2];
+                    T[2] += l[0] * dP[1] - l[1] * dP[0];
+                }
+            }
+}
+
+/* Step 2.  reading (the paper does not describe it): a node solid at n-1
+ * and fluid at n takes the equilibrium (Eq. 9) at the velocity of the
+ * surface of its previous owner, u_s = V_p + Om_p x (x - X_p), and at the
+ * mean density of its neighbours x + c_i that are fluid at both n-1 and n
+ * (1 if there are none).  State of the owner: the one at time n. */
+static void refill(orc_state *s) {
+    const orc_params *P = &s->p;
+    s->refilled = 0;
+    for (int z = 0; z < P->nz; ++z)
+        for (int y = 0; y < P->ny; ++y)
+            for (int x = 0; x < P->nx; ++x) {
+                long n = node_of(s, x, y, z);
+                int p = s->owner_prev[n];
+                if (p < 0 || s->owner[n] >= 0) continue;
+                double sum = 0.0;
+                int cnt = 0;
+                for (int i = 1; i < NQ; ++i) {
+                    int zz = z + CZ[i];
+                    if (!in_z(s, zz)) continue;
+                    long m = node_of(s, x + CX[i], y + CY[i], zz);
+                    if (s->owner_prev[m] >= 0 || s->owner[m] >= 0) continue;
+                    double r = 0.0;
+                    for (int k = 0; k < NQ; ++k) r += s->f[(long)k * s->N + m];
+                    sum += r;
+                    ++cnt;
+                }
+                double rho = cnt > 0 ? sum / cnt : 1.0;
+                const double *X = s->X + 3 * p, *V = s->V + 3 * p, *W = s->Om + 3 * p;
+                double l[3] = {(double)image(x, X[0], P->nx, 1) - X[0],
+                               (double)image(y, X[1], P->ny, 1) - X[1],
+                               (double)image(z, X[2], P->nz, P->periodic_z) - X[2]};
+                double us[3] = {V[0] + (W[1] * l[2] - W[2] * l[1]), V[1] + (W[2] * l[0] - W[0] * l[2]),
+                                V[2] + (W[0] * l[1] - W[1] * l[0])};
+                for (int i = 0; i < NQ; ++i) s->f[(long)i * s->N + n] = feq(s, i, rho, us);
+                ++s->refilled;
+            }
+}
+
+/* ------------------------------------------------------------------ */
+/* DEM                                                                 */
+/* ------------------------------------------------------------------ */
+
+static double sphere_mass(const orc_state *s, int a) {
+    double r = s->R[a];
+    return s->p.rho_s * (4.0 / 3.0) * M_PI * r * r * r;
+}
+
+/* Damping coefficient of Eq. (1).  reading: the paper says only that it
+ * depends on the restitution e; the linear spring-dashpot result
+ * gamma_n = -2 ln(e) sqrt(m_eff k_n) / sqrt(pi^2 + ln(e)^2) gives a normal
+ * restitution of exactly e for an isolated binary collision. */
+static double gamma_n(const orc_state *s, double meff) {
+    double le = log(s->p.restitution);
+    return -2.0 * le * sqrt(meff * s->p.kn) / sqrt(M_PI * M_PI + le * le);
+}
+
+/* Contact force on every sphere at positions X and velocities v (Eq. 1,
+ * reading: f^n = k_n delta - gamma_n v_n with delta > 0 the overlap,
+ * unclipped).  Sphere-sphere with the minimum image in x and y; sphere-wall
+ * against the planes z = -1/2 and z = nz - 1/2 with m_eff = m.  A fixed
+ * sphere acts with infinite mass. */
+static void contact_forces(orc_state *s, const double *X, const double *v, double *Fc) {
+    const orc_params *P = &s->p;
+#pragma omp parallel for schedule(static)
+    for (int a = 0; a < s->np; ++a) {
+        double F[3] = {0, 0, 0};
+        double ma = sphere_mass(s, a);
+        for (int b = 0; b < s->np; ++b) {
+            if (b == a) continue;
+            double d[3] = {X[3 * a] - X[3 * b], X[3 * a + 1] - X[3 * b + 1], X[3 * a + 2] - X[3 * b + 2]};
+            if (d[0] > 0.5 * P->nx) d[0] -= P->nx;
+            if (d[0] < -0.5 * P->nx) d[0] += P->nx;
+            if (d[1] > 0.5 * P->ny) d[1] -= P->ny;
+            if (d[1] < -0.5 * P->ny) d[1] += P->ny;
+            if (P->periodic_z && d[2] > 0.5 * P->nz) d[2] -= P->nz;
+            if (P->periodic_z && d[2] < -0.5 * P->nz) d[2] += P->nz;
+            double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double delta = s->R[a] + s->R[b] - dist;
+            if (!(delta > 0.0) || dist == 0.0) continue;
+            double nv[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+            double vn = (v[3 * a] - v[3 * b]) * nv[0] + (v[3 * a + 1] - v[3 * b + 1]) * nv[1] +
+                        (v[3 * a + 2] - v[3 * b + 2]) * nv[2];
+            double mb = sphere_mass(s, b);
+            double meff = s->fixed[b] ? ma : (s->fixed[a] ? mb : ma * mb / (ma + mb));
+            double fn = P->kn * delta - gamma_n(s, meff) * vn;
+            F[0] += fn * nv[0];
+            F[1] += fn * nv[1];
+            F[2] += fn * nv[2];
+        }
+        double lo = s->R[a] - (X[3 * a + 2] + 0.5);
+        if (!P->periodic_z && lo > 0.0) F[2] += P->kn * lo - gamma_n(s, ma) * v[3 * a + 2];
+        double hi = s->R[a] - ((P->nz - 0.5) - X[3 * a + 2]);
+        if (!P->periodic_z && hi > 0.0) F[2] -= P->kn * hi - gamma_n(s, ma) * (-v[3 * a + 2]);
+        Fc[3 * a] = F[0];
+        Fc[3 * a + 1] = F[1];
+        Fc[3 * a + 2] = F[2];
+    }
+}
+
+/* Step 6: velocity Verlet (Sect. 2.1) with sub-step h = 1/dem_substeps, the
+ * hydrodynamic load F_h, T_h and an external load F_x, T_x held over the
+ * lattice step, and no body force on spheres:
+ *   v += (F_h + F_x + F_c) h/(2m);  X += v h;  F_c = contact(X, v);
+ *   v += (F_h + F_x + F_c) h/(2m);  Om += (T_h + T_x) h / I,  I = 2/5 m R^2.
+ * A fixed sphere moves with its prescribed velocity: X += V h only.  Centres
+ * are wrapped into [0, n) on periodic axes after every drift. */
+static void dem(orc_state *s) {
+    const orc_params *P = &s->p;
+    int ns = P->dem_substeps > 0 ? P->dem_substeps : 1;
+    double h = 1.0 / ns;
+    for (int it = 0; it < ns; ++it) {
+        for (int a = 0; a < s->np; ++a) {
+            double m = sphere_mass(s, a);
+            for (int c = 0; c < 3; ++c) {
+                if (!s->fixed[a])
+                    s->V[3 * a + c] += (s->Fh[3 * a + c] + s->Fx[3 * a + c] + s->Fc[3 * a + c]) * h / (2.0 * m);
+                s->X[3 * a + c] += s->V[3 * a + c] * h;
+            }
+            if (s->X[3 * a] >= P->nx) s->X[3 * a] -= P->nx;
+            if (s->X[3 * a] < 0.0) s->X[3 * a] += P->nx;
+            if (s->X[3 * a + 1] >= P->ny) s->X[3 * a + 1] -= P->ny;
+            if (s->X[3 * a + 1] < 0.0) s->X[3 * a + 1] += P->ny;
+            if (P->periodic_z && s->X[3 * a + 2] >= P->nz) s->X[3 * a + 2] -= P->nz;
+            if (P->periodic_z && s->X[3 * a + 2] < 0.0) s->X[3 * a + 2] += P->nz;
+        }
+        contact_forces(s, s->X, s->V, s->Fc);
+        for (int a = 0; a < s->np; ++a) {
+            if (s->fixed[a]) continue;
+            double m = sphere_mass(s, a);
+            double I = 0.4 * m * s->R[a] * s->R[a];
+            for (int c = 0; c < 3; ++c) {
+                s->V[3 * a + c] += (s->Fh[3 * a + c] + s->Fx[3 * a + c] + s->Fc[3 * a + c]) * h / (2.0 * m);
+                s->Om[3 * a + c] += (s->Th[3 * a + c] + s->Tx[3 * a + c]) * h / I;
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Interface (ctypes)                                                  */
+/* ------------------------------------------------------------------ */
+
+static void *xcalloc(size_t n, size_t sz) { return n ? calloc(n, sz) : NULL; }
+
+void orc_destroy(orc_state *s);
+
+orc_state *orc_create(const orc_params *p) {
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return NULL;
+    orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
+    s->p = *p;
+    s->N = p->fluid ? (long)p->nx * p->ny * p->nz : 0;
+    for (int i = 0; i < NQ; ++i) {
+        s->w[i] = weight(i);
+        s->opp[i] = opposite(i);
+    }
+    if (s->N) {
+        s->f = (double *)xcalloc((size_t)NQ * s->N, sizeof(double));
+        s->fc = (double *)xcalloc((size_t)NQ * s->N, sizeof(double));
+        s->fn = (double *)xcalloc((size_t)NQ * s->N, sizeof(double));
+        s->owner = (int *)xcalloc((size_t)s->N, sizeof(int));
+        s->owner_prev = (int *)xcalloc((size_t)s->N, sizeof(int));
+        s->key = (float *)xcalloc((size_t)s->N, sizeof(float));
+        if (!s->f || !s->fc || !s->fn || !s->owner || !s->owner_prev || !s->key) {
+            orc_destroy(s);
+            return NULL;
+        }
+        for (int i = 0; i < NQ; ++i)
+            for (long n = 0; n < s->N; ++n) s->f[(long)i * s->N + n] = s->w[i];
+        for (long n = 0; n < s->N; ++n) s->owner[n] = s->owner_prev[n] = -1;
+    }
+    return s;
+}
+
+void orc_destroy(orc_state *s) {
+    if (!s) return;
+    free(s->f); free(s->fc); free(s->fn); free(s->owner); free(s->owner_prev); free(s->key);
+    free(s->X); free(s->V); free(s->Om); free(s->R); free(s->Fh); free(s->Th); free(s->Fc); free(s->fixed);
+    free(s->Fx); free(s->Tx);
+    free(s);
+}
+
+/* Place n spheres and reset the fluid to rest (f = w, rho = 1, u = 0). */
+int orc_set_particles(orc_state *s, int n, const double *X, const double *V, const double *Om,
+                      const double *R, const unsigned char *fixed) {
+    free(s->X); free(s->V); free(s->Om); free(s->R); free(s->Fh); free(s->Th); free(s->Fc); free(s->fixed);
+    free(s->Fx); free(s->Tx);
+    s->np = n;
+    s->Fx = (double *)xcalloc(3 * (size_t)n, sizeof(double));
+    s->Tx = (double *)xcalloc(3 * (size_t)n, sizeof(double));
+    s->X = (double *)xcalloc(3 * (size_t)n, sizeof(double));
+    s->V = (double *)xcalloc(3 * (size_t)n, sizeof(double));
+    s->Om = (double *)xcalloc(3 * (size_t)n, sizeof(double));
+    s->R = (double *)xcalloc((size_t)n, sizeof(double));
+    s->Fh = (double *)xcalloc(3 * (size_t)n, sizeof(double));
+    s->Th = (double *)xcalloc(3 * (size_t)n, sizeof(double));
+    s->Fc = (double *)xcalloc(3 * (size_t)n, sizeof(double));
+    s->fixed = (unsigned char *)xcalloc((size_t)n, 1);
+    if (n) {
+        memcpy(s->X, X, sizeof(double) * 3 * n);
+        memcpy(s->V, V, sizeof(double) * 3 * n);
+        memcpy(s->Om, Om, sizeof(double) * 3 * n);
+        memcpy(s->R, R, sizeof(double) * n);
+        if (fixed) memcpy(s->fixed, fixed, n);
+    }
+    if (s->N) {
+        for (int i = 0; i < NQ; ++i)
+            for (long m = 0; m < s->N; ++m) s->f[(long)i * s->N + m] = s->w[i];
+        geometry(s);
+        memcpy(s->owner_prev, s->owner, sizeof(int) * s->N);
+    }
+    contact_forces(s, s->X, s->V, s->Fc);
+    s->step = 0;
+    s->refilled = 0;
+    return 0;
+}
+
+/* External force and torque per sphere, [n][3] each (NULL = zero). */
+void orc_set_load(orc_state *s, const double *F, const double *T) {
+    for (int m = 0; m < 3 * s->np; ++m) {
+        s->Fx[m] = F ? F[m] : 0.0;
+        s->Tx[m] = T ? T[m] : 0.0;
+    }
+}
+
+/* Pre-collision populations in natural layout [19][N]; solid nodes ignored. */
+void orc_set_populations(orc_state *s, const double *f) {
+    for (long m = 0; m < (long)NQ * s->N; ++m)
+        if (s->owner[m % s->N] < 0) s->f[m] = f[m];
+}
+
+void orc_get_populations(const orc_state *s, double *f) {
+    for (long m = 0; m < (long)NQ * s->N; ++m) f[m] = s->owner[m % s->N] < 0 ? s->f[m] : 0.0;
+}
+
+void orc_step(orc_state *s, int nsteps) {
+    for (int it = 0; it < nsteps; ++it) {
+        if (s->N) {
+            memcpy(s->owner_prev, s->owner, sizeof(int) * s->N);
+            geometry(s);
+            refill(s);
+#pragma omp parallel for schedule(static)
+            for (long n = 0; n < s->N; ++n)
+                if (s->owner[n] < 0) collide_node(s, n);
+            stream(s);
+            momentum_exchange(s);
+            double *t = s->f;
+            s->f = s->fn;
+            s->fn = t;
+        }
+        dem(s);
+        ++s->step;
+    }
+}
+
+void orc_forces(const orc_state *s, double *F, double *T) {
+    memcpy(F, s->Fh, sizeof(double) * 3 * s->np);
+    memcpy(T, s->Th, sizeof(double) * 3 * s->np);
+}
+
+void orc_contact_forces(const orc_state *s, double *Fc) { memcpy(Fc, s->Fc, sizeof(double) * 3 * s->np); }
+
+void orc_particles(const orc_state *s, double *X, double *V, double *Om) {
+    memcpy(X, s->X, sizeof(double) * 3 * s->np);
+    memcpy(V, s->V, sizeof(double) * 3 * s->np);
+    memcpy(Om, s->Om, sizeof(double) * 3 * s->np);
+}
+
+/* Density and velocity (Eqs. 5, 6 with the force shift) of the current
+ * pre-collision state; u is [3][N]; solid nodes give rho = 0, u = 0. */
+void orc_fields(const orc_state *s, double *rho, double *u) {
+    for (long n = 0; n < s->N; ++n) {
+        if (s->owner[n] >= 0) {
+            rho[n] = 0.0;
+            u[n] = u[s->N + n] = u[2 * s->N + n] = 0.0;
+            continue;
+        }
+        double r, v[3];
+        moments(s, s->f, n, &r, v);
+        rho[n] = r;
+        u[n] = v[0];
+        u[s->N + n] = v[1];
+        u[2 * s->N + n] = v[2];
+    }
+}
+
+/* tau* of the collision the next step would apply at each fluid node. */
+void orc_tau_eff(const orc_state *s, double *tau) {
+    for (long n = 0; n < s->N; ++n) {
+        if (s->owner[n] >= 0) {
+            tau[n] = 0.0;
+            continue;
+        }
+        double r, v[3];
+        moments(s, s->f, n, &r, v);
+        tau[n] = tau_eff(s, s->f, n, r, v);
+    }
+}
+
+void orc_owner(const orc_state *s, int *owner) { memcpy(owner, s->owner, sizeof(int) * s->N); }
+
+/* Cut sphere links of the current geometry in (node, j) order; returns the
+ * count and fills up to cap entries. */
+long orc_links(const orc_state *s, long cap, long *node, int *dir, float *q, int *pid) {
+    const orc_params *P = &s->p;
+    long cnt = 0;
+    for (int z = 0; z < P->nz; ++z)
+        for (int y = 0; y < P->ny; ++y)
+            for (int x = 0; x < P->nx; ++x) {
+                long n = node_of(s, x, y, z);
+                if (s->owner[n] >= 0) continue;
+                for (int j = 1; j < NQ; ++j) {
+                    int zz = z + CZ[j];
+                    if (!in_z(s, zz)) continue;
+                    int p = s->owner[node_of(s, x + CX[j], y + CY[j], zz)];
+                    if (p < 0) continue;
+                    if (cnt < cap) {
+                        const double *X = s->X + 3 * p;
+                        node[cnt] = n;
+                        dir[cnt] = j;
+                        q[cnt] = link_q(s, p, image(x, X[0], P->nx, 1), image(y, X[1], P->ny, 1),
+                                        image(z, X[2], P->nz, P->periodic_z), j);
+                        pid[cnt] = p;
+                    }
+                    ++cnt;
+                }
+            }
+    return cnt;
+}
+
+long orc_refilled(const orc_state *s) { return s->refilled; }
+long orc_step_count(const orc_state *s) { return s->step; }
+
+/* ------------------------------------------------------------------ */
+/* Test hooks                                                          */
+/* ------------------------------------------------------------------ */
+
+/* The velocity set and weights as the oracle uses them. */
+void orc_tables(int *cx, int *cy, int *cz, double *w, int *opp) {
+    for (int i = 0; i < NQ; ++i) {
+        cx[i] = CX[i];
+        cy[i] = CY[i];
+        cz[i] = CZ[i];
+        w[i] = weight(i);
+        opp[i] = opposite(i);
+    }
+}
+
+/* Eq. (9) for one (rho, u): out[19]. */
+void orc_feq(double rho, const double *u, double *out) {
+    orc_state tmp;
+    for (int i = 0; i < NQ; ++i) tmp.w[i] = weight(i);
+    for (int i = 0; i < NQ; ++i) out[i] = feq(&tmp, i, rho, u);
+}
+
+/* Steps 1 and 2 of the next time step only (geometry and refill); the
+ * following orc_step then finds the geometry unchanged and refills nothing. */
+void orc_refill_only(orc_state *s) {
+    if (!s->N) return;
+    memcpy(s->owner_prev, s->owner, sizeof(int) * s->N);
+    geometry(s);
+    refill(s);
+}

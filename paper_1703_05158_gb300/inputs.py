@@ -1,0 +1,115 @@
+"""Seeded synthetic inputs for the tests and the benchmark.
+
+This module draws random numbers and places spheres; it holds none of the
+method's arithmetic and imports neither the CUDA binding nor the oracle, so
+both sides can be fed from it.
+
+Workloads (all synthetic; the paper measures on no public dataset):
+  * ``sphere_in_box``: one sphere of radius 4 at the centre of a 32^3 box
+    moving at (0.01, 0, 0) (the plain-method workload).
+  * ``slurry_box``: 256^3 box, 2000 monodisperse spheres of radius 4 placed by
+    random sequential addition, velocities uniform in [-0.01, 0.01]^3 (the
+    production workload).
+  * ``polydisperse``: radii uniform in [r_min, r_max], as in the paper's
+    polydispersity sweep (Sect. 3, d_max/d_min).
+"""
+import numpy as np
+
+SEED_BASE = 20170315
+
+
+def rng(seed):
+    return np.random.default_rng(seed)
+
+
+def rsa_spheres(box, n, radius, seed, gap=1.0, wall_gap=1.0, periodic_z=False, max_tries=10 ** 7):
+    """Random sequential addition of ``n`` non-overlapping spheres.
+
+    ``box`` = (nx, ny, nz); x and y are periodic, the z walls sit at -1/2 and
+    nz - 1/2.  ``radius`` is a scalar or a (r_min, r_max) pair (uniform).
+    Proposals are uniform in the box; a proposal is rejected when its surface
+    is closer than ``gap`` to an accepted sphere (minimum image) or closer
+    than ``wall_gap`` to a z wall.  Radii are drawn once, largest first.
+    Returns (X [n,3], R [n]).
+    """
+    nx, ny, nz = box
+    g = rng(seed)
+    if np.isscalar(radius):
+        R = np.full(n, float(radius))
+    else:
+        R = np.sort(g.uniform(radius[0], radius[1], size=n))[::-1].copy()
+    rmax = float(R.max()) if n else 0.0
+    cell = 2.0 * rmax + gap
+    dims = np.maximum(1, (np.array([nx, ny, nz]) // cell).astype(int))
+    csize = np.array([nx, ny, nz], dtype=float) / dims
+    grid = {}
+    X = np.zeros((n, 3))
+    L = np.array([nx, ny, nz], dtype=float)
+    per = np.array([True, True, bool(periodic_z)])
+    tries = 0
+    for a in range(n):
+        r = R[a]
+        while True:
+            tries += 1
+            if tries > max_tries:
+                raise RuntimeError("random sequential addition failed after %d proposals" % max_tries)
+            lo_z, hi_z = (0.0, nz) if periodic_z else (r - 0.5 + wall_gap, nz - 0.5 - r - wall_gap)
+            if hi_z < lo_z:
+                raise ValueError("sphere of radius %g does not fit between the walls" % r)
+            p = np.array([g.uniform(0, nx), g.uniform(0, ny), g.uniform(lo_z, hi_z)])
+            c = (p // csize).astype(int)
+            ok = True
+            for dz in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        key = ((c[0] + dx) % dims[0], (c[1] + dy) % dims[1], (c[2] + dz) % dims[2])
+                        for b in grid.get(key, ()):
+                            d = p - X[b]
+                            d = np.where(per, d - L * np.round(d / L), d)
+                            if np.dot(d, d) < (r + R[b] + gap) ** 2:
+                                ok = False
+                                break
+                        if not ok:
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if ok:
+                X[a] = p
+                grid.setdefault(tuple(c % dims), []).append(a)
+                break
+    return X, R
+
+
+def uniform_vectors(n, lo, hi, seed):
+    return rng(seed).uniform(lo, hi, size=(n, 3))
+
+
+def perturbation(shape, amplitude, seed):
+    """Uniform noise in [-amplitude, amplitude] of the given shape."""
+    return rng(seed).uniform(-amplitude, amplitude, size=shape)
+
+
+def sphere_in_box(n=32):
+    """One sphere, radius 4, at the box centre, velocity (0.01, 0, 0)."""
+    X = np.array([[n / 2.0, n / 2.0, n / 2.0]])
+    V = np.array([[0.01, 0.0, 0.0]])
+    return dict(X=X, V=V, Om=np.zeros((1, 3)), R=np.array([4.0]))
+
+
+def slurry_box(box=(256, 256, 256), n=2000, radius=4.0, seed=SEED_BASE + 2, vmax=0.01):
+    """Monodisperse slurry: RSA placement and uniform velocities."""
+    X, R = rsa_spheres(box, n, radius, seed)
+    V = uniform_vectors(n, -vmax, vmax, seed + 1)
+    return dict(X=X, V=V, Om=np.zeros((n, 3)), R=R)
+
+
+def polydisperse(box, n, r_range, seed, vmax=0.01):
+    X, R = rsa_spheres(box, n, r_range, seed)
+    V = uniform_vectors(n, -vmax, vmax, seed + 1)
+    return dict(X=X, V=V, Om=np.zeros((n, 3)), R=R)
+
+
+def solid_fraction(box, R):
+    return float(np.sum(4.0 / 3.0 * np.pi * np.asarray(R) ** 3) / (box[0] * box[1] * box[2]))
