@@ -12,7 +12,7 @@
 * Torque on a sphere spinning in place against Stokes, T = -8 pi mu R^3 Om.
   Periodic images raise it by O(phi) and the lattice sphere of radius 4 by
   about 5% (T/T_Stokes = 1.126, 1.071, 1.058 at L = 16, 24, 32); checked at
-  L = 24 within 10%.
+  L = 24 within 12%, per component of a spin about a skew axis.
 """
 import numpy as np
 import pytest
@@ -22,10 +22,10 @@ import oracle
 L, R = 16, 4.0
 
 
-def _run(tau, steps, g=0.0, Om=0.0, box=L):
+def _run(tau, steps, g=0.0, Om=(0.0, 0.0, 0.0), box=L):
     o = oracle.Oracle(box, box, box, tau0=tau, cs=0.0, g=(g, 0.0, 0.0), periodic_z=True, les=False)
     c = box / 2.0 - 0.5
-    o.set_particles([[c, c + 0.25, c - 0.25]], Om=[[0.0, 0.0, Om]], R=[R], fixed=[1])
+    o.set_particles([[c, c + 0.25, c - 0.25]], Om=[Om], R=[R], fixed=[1])
     o.step(steps)
     return o
 
@@ -57,12 +57,11 @@ def test_drag_periodic_array_hasimoto_sangani_acrivos():
 
 @pytest.mark.slow
 def test_torque_spinning_sphere():
-    tau, Om = 0.65, 1e-3
+    tau = 0.65
+    Om = np.array([1.0, -0.6, 0.8]) * 1e-3  # every component of the arm is exercised
     nu = (tau - 0.5) / 3.0
     o = _run(tau, 2000, Om=Om, box=24)
     F, T = o.forces()
     stokes = -8 * np.pi * nu * R ** 3 * Om
-    assert abs(T[0, 2] / stokes - 1.0) < 0.10, (T, stokes)
-    # the off-lattice centre breaks the lattice symmetry slightly
-    assert np.abs(T[0, :2]).max() < 1e-2 * abs(stokes)
-    assert np.abs(F).max() < 1e-2 * abs(stokes)
+    assert np.all(np.abs(T[0] / stokes - 1.0) < 0.12), (T, stokes)
+    assert np.abs(F).max() < 1e-2 * np.abs(stokes).max()

@@ -131,3 +131,38 @@ def test_refill_of_uncovered_nodes():
     # nodes not uncovered are untouched
     keep = ~uncovered & ~after
     assert np.array_equal(f[:, keep], f_before[:, keep])
+
+
+def test_bounce_back_reads_the_fictitious_node():
+    """Sect. 2.3: for q < 1/2 the reflected population is the one that left
+    the fictitious node x_f' = x_f - (1 - 2q) c_j, reaching x_f after exactly
+    one time step.  On a field whose post-collision populations are linear in
+    space, f_j^c = w_j rho(z) with rho linear in z (rest fluid, tau = 1: the
+    collision maps it to itself), the bounce-back value must therefore equal
+    w_j rho(z_f').  For q >= 1/2 (and for q < 1/2 with x_f - c_j solid) both
+    interpolated values sit at x_f and the result is w_j rho(z_f)."""
+    c, w, opp = oracle.tables()
+    nx, ny, nz, a = 20, 19, 22, 4e-3
+    o = oracle.Oracle(nx, ny, nz, tau0=1.0, cs=0.0)
+    o.set_particles([[9.75, 9.5, 10.25]], R=[4.25], fixed=[1])
+    z = np.arange(nz, dtype=float)
+    rho = 1.0 + a * (z - 10.0)
+    f = w[:, None, None, None] * rho[None, :, None, None] * np.ones((19, nz, ny, nx))
+    o.set_populations(f)
+    node, d, q, pid = o.links()
+    solid = o.owner() >= 0
+    o.step(1)
+    fn = o.populations().reshape(19, -1)
+    n_lt = 0
+    for n, j, qq in zip(node, d, q.astype(float)):
+        x, y, zz = n % nx, (n // nx) % ny, n // (nx * ny)
+        k = opp[j]
+        zb = zz - c[j, 2]
+        behind_fluid = 0 <= zb < nz and not solid[zb, (y - c[j, 1]) % ny, (x - c[j, 0]) % nx]
+        if qq < 0.5 and behind_fluid:
+            zf = zz - (1.0 - 2.0 * qq) * c[j, 2]
+            n_lt += 1
+        else:
+            zf = zz
+        assert abs(fn[k, n] - w[j] * (1.0 + a * (zf - 10.0))) < 1e-15
+    assert n_lt > 50
