@@ -1,0 +1,324 @@
+"""Benchmark: lattice updates per second of the coupled LBM-DEM step on GB300.
+
+Workload (synthetic): 256^3 D3Q19 box, periodic in x and y, walls in z with
+the top one sliding at 0.05; tau0 = 0.51, Smagorinsky C = 0.17; 2000 spheres
+of radius 4 placed by seeded random sequential addition (solid fraction
+0.032), velocities uniform in [-0.01, 0.01]^3, density ratio 2.5, k_n = 1e3,
+restitution 0.8, 16 DEM sub-steps per lattice step.  One step = geometry,
+refill, fused collide-stream, bounce-back + momentum exchange, DEM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16|fp16]
+  python bench.py --impl reference ...   # the FP64 CPU oracle, bounded sample
+
+Prints one JSON line (rank 0).  MLUPS counts every node of the box.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline at 256^3 + 2000 spheres; FP32 vs BF16-storage vs FP64 err"
+BOX = (256, 256, 256)
+NSPH = 2000
+NSPH_RUN = [NSPH]
+PHYS = dict(tau0=0.51, cs=0.17, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0), u_hi=(0.05, 0.0, 0.0), rho_s=2.5,
+            kn=1e3, restitution=0.8, dem_substeps=16)
+BYTES = {"fp32": 4, "bf16": 2, "fp16": 2}
+
+
+def workload_name(prec):
+    return "slurry box 256^3, 2000 spheres R=4, sliding lid 0.05, tau0=0.51, Cs=0.17, %s storage" % prec
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(prec):
+    """DRAM bytes per collide launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "stream_collide_256cubed_%s.md" % prec)
+    src = os.path.join(ROOT, "paper_1703_05158_gb300", "csrc", "lbm_collide.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        vals = dict(l.split(":", 1) for l in text.splitlines() if l.startswith(("traffic_bytes_per_launch:",
+                                                                                  "collide_source_sha256_16:")))
+        if vals.get("collide_source_sha256_16:".rstrip(":"), "").strip() != sha:
+            return None
+        return float(vals["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                s, m = float(f[1]), float(f[2])
+            except ValueError:
+                continue
+            sm.append(s)
+            mx = max(mx, m)
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        load = sorted(sm)[len(sm) // 4:] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(box, nsph, seed_offset=0):
+    from paper_1703_05158_gb300 import inputs
+
+    return inputs.slurry_box(box=box, n=nsph, seed=inputs.SEED_BASE + 2 + seed_offset)
+
+
+def cpu_baseline(steps=2):
+    """The oracle as it stands on the host cores, on the full workload for a
+    couple of steps (bounded sample)."""
+    import oracle
+
+    p = oracle_sample(BOX, NSPH)
+    o = oracle.Oracle(*BOX, **PHYS)
+    o.set_particles(p["X"], V=p["V"], Om=p["Om"], R=p["R"])
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    n = BOX[0] * BOX[1] * BOX[2]
+    return {"value": n * steps / dt / 1e6, "unit": "MLUPS", "cores": int(os.environ.get("OMP_NUM_THREADS",
+                                                                                        os.cpu_count())),
+            "kind": "oracle", "sample": "%d steps of the full 256^3 + 2000-sphere workload, FP64, %.1f s" % (steps, dt)}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle on the host, each step a bounded
+    sample of the workload (a 48^3 box at the same solid fraction: 13 spheres
+    of radius 4)."""
+    if rank != 0:
+        return
+    import oracle
+
+    box, nsph = (48, 48, 48), 13
+    p = oracle_sample(box, nsph, seed_offset=100)
+    o = oracle.Oracle(*box, **PHYS)
+    o.set_particles(p["X"], V=p["V"], Om=p["Om"], R=p["R"])
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    n = box[0] * box[1] * box[2]
+    val = n * args.steps / dt / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.precision), "sample": "48^3 box, 13 spheres R=4 per step"},
+            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": "48^3 box with 13 spheres (solid fraction of the workload), %d steps" %
+                                       args.steps},
+            "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1703_05158_gb300 import lbm
+
+    torch.cuda.set_device(local_rank)
+    dev = local_rank
+    stream = torch.cuda.Stream(device=dev)
+    p = oracle_sample(BOX, NSPH)
+    lat = lbm.Lattice(*BOX, precision=args.precision, max_particles=NSPH, max_radius=4.0,
+                      stream=ctypes_stream(stream), device=dev, **PHYS)
+    lat.set_particles(p["X"], V=p["V"], Om=p["Om"], R=p["R"])
+    N = BOX[0] * BOX[1] * BOX[2]
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # warm-up
+    lat.step(args.warmup)
+    lat.sync()
+    info = lat.info()
+
+    # timed region: events on the library's stream, phase profiler on
+    lat.profile(True)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with Clocks(dev) as clk:
+        start.record(stream)
+        lat.step(args.steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+    lat.sync()
+    ms = start.elapsed_time(end)
+    phases, psteps = lat.profile_read()
+    lat.profile(False)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * N * args.steps / (ms_max * 1e-3) / 1e6
+
+    # end to end through the public API with host buffers: every step uploads
+    # the external load (force, torque) from pinned host memory, steps, and
+    # reads the hydrodynamic force, torque and the centres back
+    n = NSPH
+    hF = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
+    hT = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
+    oF = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    oT = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    oX = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    ke = args.e2e_steps
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        lbm.lbm_set_particle_load(lat.h, hF, hT)
+        lbm.lbm_step(lat.h, 1)
+        lbm.lbm_forces(lat.h, oF, oT)
+        lbm.lbm_particles(lat.h, oX)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_val = world * N * ke / float(te.item()) / 1e6
+
+    if rank != 0:
+        return
+    s = BYTES[args.precision]
+    nf = info["fluid_nodes"]
+    walls = 2 * BOX[0] * BOX[1] * 5 * s
+    bytes_collide = nf * 2 * 19 * s + N * 1 + walls
+    collide_ms = phases["collide"] / max(psteps, 1)
+    achieved = bytes_collide / (collide_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = profiled_traffic(args.precision)
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(args.precision), "box": list(BOX), "spheres": NSPH,
+                   "radius": 4.0, "solid_fraction": round(float(np.sum(4 / 3 * np.pi * p["R"] ** 3)) / N, 4),
+                   "storage": args.precision, "fluid_nodes": nf, "links": info["links"],
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (populations %.2f GB)" % (19 * N * s / 1e9)},
+        "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": achieved, "peak": peak,
+                     "peak_kind": "%s hbm_gbs" % peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_collide,
+                     "avg_launch_ms": collide_ms},
+        "phases_ms_per_step": {k: v / max(psteps, 1) for k, v in phases.items()},
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_val, "unit": "MLUPS", "steps": ke,
+                "h2d_bytes_per_step": int(hF.numel() * 8 + hT.numel() * 8),
+                "d2h_bytes_per_step": int((oF.numel() + oT.numel() + oX.numel()) * 8)},
+        "gpu_launches": args.steps * (6 if NSPH_RUN[0] else 1),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    lat.close()
+
+
+def ctypes_stream(stream):
+    return stream.cuda_stream
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "fp16"], default="fp32")
+    ap.add_argument("--e2e-steps", type=int, default=300)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--box", type=int, default=256,
+                    help="cubic box edge for profiling runs; sphere count scaled to keep the solid fraction")
+    args = ap.parse_args()
+    if args.box != 256:
+        global BOX, NSPH
+        BOX = (args.box,) * 3
+        NSPH = int(round(2000 * (args.box / 256.0) ** 3))
+        NSPH_RUN[0] = NSPH
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

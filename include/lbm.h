@@ -158,6 +158,23 @@ int lbm_geometry(lbm_handle h, int32_t *owner, int32_t where);
 /* Counters and sizes (synchronises the stream). */
 int lbm_info(lbm_handle h, lbm_info_t *info);
 
+/* Phases of a step timed by the profiler. */
+#define LBM_PHASE_GEOMETRY 0  /* node geometry and refill */
+#define LBM_PHASE_COLLIDE 1   /* fused collide-stream kernel */
+#define LBM_PHASE_LINKS 2     /* bounce-back on sphere links and momentum exchange */
+#define LBM_PHASE_DEM 3       /* neighbour lists and DEM sub-steps */
+#define LBM_PHASES 4
+
+/* enable != 0: from now on record CUDA events on the handle's stream around
+ * each phase of every step and reset the totals; enable == 0: stop.  Adds no
+ * work on the device, only event records between kernels. */
+int lbm_profile(lbm_handle h, int32_t enable);
+
+/* Device time per phase, summed over the steps since profiling was enabled:
+ * ms[LBM_PHASES] in milliseconds, *steps the number of steps (either pointer
+ * may be NULL).  Synchronises the stream. */
+int lbm_profile_read(lbm_handle h, double *ms, int64_t *steps);
+
 /* Wait for the handle's stream and return its sticky device status. */
 int lbm_sync(lbm_handle h);
 

@@ -115,8 +115,13 @@ static int image(int x, double Xc, int n, int periodic) {
     return b + d;
 }
 
-/* FP32 relative coordinate of an (unwrapped) lattice coordinate. */
-static float rel32(int xi, double Xc) { return (float)((double)xi - Xc); }
+/* FP32 relative coordinate of an (unwrapped) lattice coordinate xi to the
+ * centre coordinate Xc: (float)(xi - b) - (float)(Xc - b) with b = floor(Xc).
+ * (Xc - b is exact in FP64; it is rounded to FP32 once per sphere.) */
+static float rel32(int xi, double Xc) {
+    double b = floor(Xc);
+    return (float)(xi - (int)b) - (float)(Xc - b);
+}
 
 /* Squared FP32 distance, summed x, y, z in that order. */
 static float dist2_32(float dx, float dy, float dz) { return dx * dx + dy * dy + dz * dz; }

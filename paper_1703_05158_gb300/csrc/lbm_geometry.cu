@@ -1,0 +1,185 @@
+// Node geometry and refill (Sect. 2.3), one CTA per sphere over its bounding
+// box.
+//
+// flag[n] (bit 0 = solid for every kernel that reads it):
+//   0 fluid
+//   1 solid, owner[n] = sphere of the current geometry
+//   3 solid at the previous geometry, not yet re-marked (the link kernel of
+//     the previous step turns its sphere's nodes from 1 to 3)
+//   2 fluid now, solid at the previous step (the refill turns 3 into 2; the
+//     collide kernel turns 2 into 0)
+//
+//   mark:   nodes inside sphere p at the current centre, unless a
+//           neighbouring sphere that also contains the node has a smaller
+//           |x - X| - R (ties to the smaller index) -> 1, owner p
+//   refill: nodes left at 3 take the equilibrium (Eq. 9) at the surface
+//           velocity of their previous sphere and at the mean density of the
+//           neighbours fluid before and after (flag 0), then become 2.
+//
+// Inside tests and keys are FP32 on relative coordinates
+// (float)(x - b) - (float)(X - b), b = floor(X), evaluated with
+// round-to-nearest intrinsics so that no multiply-add is contracted: the
+// same operations, in the same order, as the FP64 oracle uses for its
+// geometric decisions, so both sides classify every node identically.
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+// Per-sphere FP32 frame: integer base b = floor(X) and fraction X - b.
+struct Frame {
+    int b[3];
+    float fr[3];
+    float R, R2;
+};
+
+__device__ __forceinline__ Frame frame_of(const double *X, double R) {
+    Frame F;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double bb = floor(X[a]);
+        F.b[a] = (int)bb;
+        F.fr[a] = __double2float_rn(X[a] - bb);
+    }
+    F.R = __double2float_rn(R);
+    F.R2 = __fmul_rn(F.R, F.R);
+    return F;
+}
+
+__device__ __forceinline__ float rel(int o, float fr) { return __fsub_rn((float)o, fr); }
+
+__device__ __forceinline__ float dist2(float dx, float dy, float dz) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// Wrap a coordinate that is at most one box length outside [0, n).
+__device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
+// Offset of periodic coordinate x from base b, folded into [-n/2, n/2).
+__device__ __forceinline__ int fold(int x, int b, int n) {
+    int d = (x - b) % n;
+    if (d < 0) d += n;
+    if (2 * d >= n) d -= n;
+    return d;
+}
+
+__device__ __forceinline__ int ceil_r(double R) { return (int)ceil(R); }
+
+constexpr int MAX_NBR_SMEM = 64;
+
+__global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, uint8_t *__restrict__ flag,
+                                              int32_t *__restrict__ owner) {
+    const int p = blockIdx.x;
+    __shared__ Frame nf[MAX_NBR_SMEM];
+    __shared__ int nid[MAX_NBR_SMEM];
+    const int cnt = min(pt.nbr_cnt[p], MAX_NBR_SMEM);
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int q = pt.nbr[(long long)p * pt.max_nbr + t];
+        nid[t] = q;
+        nf[t] = frame_of(pt.X + 3 * q, pt.R[q]);
+    }
+    const Frame F = frame_of(pt.X + 3 * p, pt.R[p]);
+    __syncthreads();
+    const int e = ceil_r(pt.R[p]) + 1, B = 2 * e + 1;
+    for (int t = threadIdx.x; t < B * B * B; t += blockDim.x) {
+        const int oz = t / (B * B) - e, oy = (t / B) % B - e, ox = t % B - e;
+        const int z = F.b[2] + oz;
+        if (z < 0 || z >= L.nz) continue;
+        const float d2 = dist2(rel(ox, F.fr[0]), rel(oy, F.fr[1]), rel(oz, F.fr[2]));
+        if (!(d2 < F.R2)) continue;
+        const float key = __fsub_rn(__fsqrt_rn(d2), F.R);
+        const int x = wrapi(F.b[0] + ox, L.nx), y = wrapi(F.b[1] + oy, L.ny);
+        bool win = true;
+        for (int m = 0; m < cnt && win; ++m) {
+            const Frame &G = nf[m];
+            const float e2 = dist2(rel(fold(x, G.b[0], L.nx), G.fr[0]), rel(fold(y, G.b[1], L.ny), G.fr[1]),
+                                   rel(z - G.b[2], G.fr[2]));
+            if (!(e2 < G.R2)) continue;
+            const float k2 = __fsub_rn(__fsqrt_rn(e2), G.R);
+            if (k2 < key || (k2 == key && nid[m] < p)) win = false;
+        }
+        if (!win) continue;
+        const long long n = x + (long long)L.nx * (y + (long long)L.ny * z);
+        flag[n] = 1;
+        owner[n] = p;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_refill(const Lat L, const Parts pt, T *__restrict__ f,
+                                                uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
+                                                const int P, unsigned long long *__restrict__ ctr) {
+    const int p = blockIdx.x;
+    const double *Xg = pt.Xgeo + 3 * p;
+    const int e = ceil_r(pt.R[p]) + 1, B = 2 * e + 1;
+    const int bx = (int)floor(Xg[0]), by = (int)floor(Xg[1]), bz = (int)floor(Xg[2]);
+    const Frame F = frame_of(pt.X + 3 * p, pt.R[p]);  // current centre, for the surface velocity
+    const float V[3] = {(float)pt.V[3 * p], (float)pt.V[3 * p + 1], (float)pt.V[3 * p + 2]};
+    const float W[3] = {(float)pt.W[3 * p], (float)pt.W[3 * p + 1], (float)pt.W[3 * p + 2]};
+    for (int t = threadIdx.x; t < B * B * B; t += blockDim.x) {
+        const int z = bz + t / (B * B) - e;
+        if (z < 0 || z >= L.nz) continue;
+        const int y = wrapi(by + (t / B) % B - e, L.ny), x = wrapi(bx + t % B - e, L.nx);
+        const long long n = x + (long long)L.nx * (y + (long long)L.ny * z);
+        if (flag[n] != 3 || owner[n] != p) continue;
+        // mean density deviation of the neighbours fluid before and after
+        float sum = 0.f;
+        int cnt = 0;
+        for (int i = 1; i < Q; ++i) {
+            const int zz = z + rcz(i);
+            if (zz < 0 || zz >= L.nz) continue;
+            const int yy = wrapi(y + rcy(i), L.ny), xx = wrapi(x + rcx(i), L.nx);
+            const long long m = xx + (long long)L.nx * (yy + (long long)L.ny * zz);
+            if (flag[m] != 0) continue;
+            const Nbr nb(L, xx, yy);
+            const long long sm = m + L.plane;
+            float dr = 0.f;
+            for (int k = 0; k < Q; ++k) dr += Store<T>::ld(f + in_slot(L, nb, P, k, sm));
+            sum += dr;
+            ++cnt;
+        }
+        const float drho = cnt ? sum / (float)cnt : 0.f;
+        const float rho = 1.f + drho;
+        // surface velocity of the sphere at this node (current centre)
+        const float lx = rel(fold(x, F.b[0], L.nx), F.fr[0]);
+        const float ly = rel(fold(y, F.b[1], L.ny), F.fr[1]);
+        const float lz = rel(z - F.b[2], F.fr[2]);
+        const float ux = V[0] + (W[1] * lz - W[2] * ly);
+        const float uy = V[1] + (W[2] * lx - W[0] * lz);
+        const float uz = V[2] + (W[0] * ly - W[1] * lx);
+        const float uu = ux * ux + uy * uy + uz * uz;
+        const Nbr nb(L, x, y);
+        const long long s = n + L.plane;
+        for (int i = 0; i < Q; ++i) {
+            const float cu = rcx(i) * ux + rcy(i) * uy + rcz(i) * uz;
+            const float dq = (float)rw36(i) / 36.f * (drho + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * uu));
+            Store<T>::st(f + in_slot(L, nb, P, i, s), dq);
+        }
+        flag[n] = 2;
+        atomicAdd(ctr + 1, 1ull);
+    }
+}
+
+int launch_mark(lbm_s *h) {
+    k_mark<<<h->pt.np, 256, 0, h->stream>>>(h->L, h->pt, h->flag, h->owner);
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+int launch_refill(lbm_s *h, int parity) {
+    switch (h->precision) {
+        case LBM_FP32:
+            k_refill<float><<<h->pt.np, 256, 0, h->stream>>>(h->L, h->pt, (float *)h->f, h->flag, h->owner, parity, h->ctr);
+            break;
+        case LBM_BF16_DEV:
+            k_refill<__nv_bfloat16><<<h->pt.np, 256, 0, h->stream>>>(h->L, h->pt, (__nv_bfloat16 *)h->f, h->flag,
+                                                                      h->owner, parity, h->ctr);
+            break;
+        case LBM_FP16_DEV:
+            k_refill<__half><<<h->pt.np, 256, 0, h->stream>>>(h->L, h->pt, (__half *)h->f, h->flag, h->owner, parity,
+                                                               h->ctr);
+            break;
+        default: return LBM_ERR_ARG;
+    }
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+}  // namespace lbm

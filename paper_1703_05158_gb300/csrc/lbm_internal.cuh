@@ -1,0 +1,210 @@
+// Internal declarations of the GB300 LBM-DEM library (not part of the ABI).
+//
+// Lattice: D3Q19 in the direction order of Table 1 (Sect. 2.2); weights from
+// the text under Eq. (9).  Populations are stored as deviations d_i = f_i - w_i
+// from the rest equilibrium (so a fluid at rest is all zeros and the moment
+// sums lose no precision), one array per direction (SoA), x fastest, with one
+// ghost plane below z = 0 and one above z = nz-1 for the wall bounce-back.
+//
+// Streaming uses the one-array A-A pattern (Bailey et al. 2009):
+//   even step: node x reads its 19 slots i, collides, writes f^c_i into slot
+//              opp(i) of the same node;
+//   odd step:  node x reads slot opp(i) of x - c_i (= f^c_i of the neighbour),
+//              collides, writes f^c_i into slot i of x + c_i.
+// in_slot / post_slot below give, for each parity, where the pre-collision
+// population f_k(x) of the next step is read and where the post-collision
+// f^c_i(x) of a finished step sits.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+constexpr int Q = 19;
+
+// Table 1, direction i = 0..18.
+__host__ __device__ constexpr int cx(int i) {
+    constexpr int t[Q] = {0, -1, 0, 0, -1, -1, -1, -1, 0, 0, 1, 0, 0, 1, 1, 1, 1, 0, 0};
+    return t[i];
+}
+__host__ __device__ constexpr int cy(int i) {
+    constexpr int t[Q] = {0, 0, -1, 0, -1, 1, 0, 0, -1, -1, 0, 1, 0, 1, -1, 0, 0, 1, 1};
+    return t[i];
+}
+__host__ __device__ constexpr int cz(int i) {
+    constexpr int t[Q] = {0, 0, 0, -1, 0, 0, -1, 1, -1, 1, 0, 0, 1, 0, 0, 1, -1, 1, -1};
+    return t[i];
+}
+// Opposite direction: in Table 1 the pairs are (i, i+9) for i = 1..9.
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i <= 9 ? i + 9 : i - 9); }
+// 36 w_i: 12 at rest, 2 on the axes, 1 on the diagonals.
+__host__ __device__ constexpr int w36(int i) { return i == 0 ? 12 : (cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i) == 1 ? 2 : 1); }
+__host__ __device__ constexpr float wf(int i) { return (float)w36(i) / 36.0f; }
+
+// Runtime-indexed velocity components without memory: each table packed two
+// bits per direction into a 64-bit constant.
+__host__ __device__ constexpr unsigned long long pack_axis(int axis) {
+    unsigned long long r = 0;
+    for (int i = 0; i < Q; ++i)
+        r |= (unsigned long long)((axis == 0 ? cx(i) : (axis == 1 ? cy(i) : cz(i))) + 1) << (2 * i);
+    return r;
+}
+__device__ __forceinline__ int rcx(int i) { return (int)((pack_axis(0) >> (2 * i)) & 3ull) - 1; }
+__device__ __forceinline__ int rcy(int i) { return (int)((pack_axis(1) >> (2 * i)) & 3ull) - 1; }
+__device__ __forceinline__ int rcz(int i) { return (int)((pack_axis(2) >> (2 * i)) & 3ull) - 1; }
+__device__ __forceinline__ int ropp(int i) { return i == 0 ? 0 : (i <= 9 ? i + 9 : i - 9); }
+__device__ __forceinline__ int rw36(int i) {
+    return i == 0 ? 12 : (rcx(i) * rcx(i) + rcy(i) * rcy(i) + rcz(i) * rcz(i) == 1 ? 2 : 1);
+}
+
+// Device status bits (sticky, OR-ed by kernels).
+enum : int {
+    ST_DIVERGED = 1,
+    ST_NBR_OVERFLOW = 2,
+    ST_TIMEOUT = 4,
+    ST_FAST = 8,
+    ST_TILE = 16,
+};
+
+// Population storage: FP32, or a 16-bit float holding the deviation.
+template <typename T>
+struct Store;
+template <>
+struct Store<float> {
+    static __device__ __forceinline__ float ld(const float *p) { return *p; }
+    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+template <>
+struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+template <>
+struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+};
+
+// Lattice extents.  Storage index of node (x, y, z) is x + nx*(y + ny*(z+1)):
+// plane z = -1 and plane z = nz are the wall ghosts.  Slot i starts at i*S.
+struct Lat {
+    int nx, ny, nz;
+    long long plane;  // nx*ny
+    long long N;      // nx*ny*nz (flag / owner arrays, no ghosts)
+    long long S;      // slot stride in elements, >= plane*(nz+2), multiple of 64
+};
+
+// Offset of the storage index of x + (ox, oy, oz) from that of x, with x and y
+// periodic; z is never wrapped (the ghost planes absorb |oz| = 1 at the walls).
+struct Nbr {
+    int xm, xp;            // x offsets of -1 and +1
+    long long ym, yp, zp;  // y offsets of -1, +1; z offset of +1
+    __device__ __forceinline__ Nbr(const Lat &L, int x, int y) {
+        xm = x == 0 ? L.nx - 1 : -1;
+        xp = x == L.nx - 1 ? -(L.nx - 1) : 1;
+        ym = y == 0 ? (long long)L.nx * (L.ny - 1) : -(long long)L.nx;
+        yp = y == L.ny - 1 ? -(long long)L.nx * (L.ny - 1) : (long long)L.nx;
+        zp = L.plane;
+    }
+    __device__ __forceinline__ long long off(int ox, int oy, int oz) const {
+        return (ox < 0 ? xm : (ox > 0 ? xp : 0)) + (oy < 0 ? ym : (oy > 0 ? yp : 0)) + (long long)oz * zp;
+    }
+};
+
+// Slot (element index into the population array) holding the pre-collision
+// f_k(x) that the step of parity P reads; s is the storage index of x.
+__device__ __forceinline__ long long in_slot(const Lat &L, const Nbr &nb, int P, int k, long long s) {
+    return P == 0 ? (long long)k * L.S + s : (long long)ropp(k) * L.S + s + nb.off(-rcx(k), -rcy(k), -rcz(k));
+}
+// Slot holding the post-collision f^c_i(x) written by a finished step of parity P.
+__device__ __forceinline__ long long post_slot(const Lat &L, const Nbr &nb, int P, int i, long long s) {
+    return P == 0 ? (long long)ropp(i) * L.S + s : (long long)i * L.S + s + nb.off(rcx(i), rcy(i), rcz(i));
+}
+
+// Fluid parameters in FP32 for the kernels.
+struct Phys {
+    float tau0;
+    float smag;  // 18 sqrt(2) C^2 (Eq. 18 with c_s^4 = 1/9)
+    float g[3];
+    float ulo[3], uhi[3];
+};
+
+// Sphere state on the device.
+struct Parts {
+    int np;
+    double *X, *V, *W, *R;         // [np][3] x3, [np]
+    const uint8_t *fixed;          // [np]
+    double *Fh, *Th;               // hydrodynamic load of the last step
+    double *Fc;                    // contact force at the current position
+    double *Fx, *Tx;               // external load
+    double *Xgeo;                  // centres used by the current node geometry
+    float4 *Xf;                    // FP32 copy of centre and radius (neighbour search)
+    double *Xb[2], *Vh[2];         // DEM sub-step buffers
+    int *nbr, *nbr_cnt;            // neighbour lists [np][max_nbr]
+    int max_nbr;
+    double kn, ce, rho_s;          // ce = -2 ln e / sqrt(pi^2 + ln^2 e)
+    int substeps;
+    double skin;
+};
+
+}  // namespace lbm
+
+// Handle (opaque in the ABI).
+struct lbm_s {
+    lbm_params p;
+    lbm::Lat L;
+    lbm::Phys ph;
+    lbm::Parts pt;
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+    int precision;
+    size_t esize;  // bytes per stored population
+    void *f;       // populations
+    uint8_t *flag;  // 0 fluid, 1 solid, 3 solid at the previous geometry, 2 refilled (see lbm_geometry.cu)
+    int32_t *owner;
+    int *status;             // device status word
+    int *status_host;        // pinned mirror
+    unsigned *bar;           // DEM grid-barrier counter
+    unsigned long long *ctr; // [0] links, [1] refilled, [2] fluid-count scratch
+    int parity;              // parity of the next step
+    long long steps;
+    int sticky;              // first device error seen
+    int dem_blocks, dem_threads;  // cooperative fallback grid
+    int dem_cluster;              // CTAs of the one-cluster DEM kernel (0: use the fallback)
+    int tile_ext;            // half width of the per-sphere link tile
+    int link_cap;            // link-list capacity per sphere (shared memory)
+    size_t bytes;
+    // phase profiler: 5 events per step (before geometry, after each phase)
+    cudaEvent_t *ev;
+    int ev_cap, ev_used;     // capacity and used count, in steps
+    bool prof;
+    double prof_ms[4];
+    long long prof_steps;
+};
+
+// Launchers (one per translation unit).
+namespace lbm {
+int launch_stream_collide(lbm_s *h, int parity);
+int launch_mark(lbm_s *h);
+int launch_refill(lbm_s *h, int parity);
+int launch_links(lbm_s *h, int parity);
+int launch_neighbours(lbm_s *h);
+int launch_contact(lbm_s *h);
+int launch_dem(lbm_s *h);
+int launch_set_populations(lbm_s *h, const double *f_dev, int parity);
+int launch_get_populations(lbm_s *h, double *f_dev, int parity);
+int launch_fields(lbm_s *h, float *rho, float *u, int parity);
+int launch_owner(lbm_s *h, int32_t *owner);
+int launch_count_fluid(lbm_s *h);
+int dem_max_blocks(int threads, int *blocks_per_sm);
+int dem_cluster_setup(int max_particles);
+int link_capacity(double max_radius);
+size_t link_smem(int ext, int cap);
+int links_setup(int ext, int cap);
+}  // namespace lbm

@@ -1,0 +1,264 @@
+// Interpolated bounce-back on sphere links and momentum exchange (Sect. 2.3),
+// one CTA per sphere, run after the collide kernel of a step.
+//
+// The CTA stages a code per node of a cube around the sphere in shared
+// memory (0 fluid, 1 other solid or outside the box, 2 owned by this sphere).
+// Every pair (solid node s owned by the sphere, direction j) with x = s - c_j
+// fluid is a cut link.  Its fraction q is the smallest root of
+// |x + t c_j - X| = R in FP32, written as c0 / (-b + sqrt(b^2 - a c0)) and
+// evaluated with the same round-to-nearest operations as the oracle.  The
+// population k = opp(j) that x receives from the solid side is (Eq. 19 with
+// the moving-boundary term of Eq. 21, deviations from w throughout):
+//   q <  1/2, x - c_j fluid: 2q d^c_j(x) + (1-2q) d^c_j(x - c_j) + 6 w_j (c_k.u_b)
+//   q <  1/2, otherwise:     d^c_j(x) + 6 w_j (c_k.u_b)
+//   q >= 1/2:                d^c_j(x)/(2q) + (2q-1)/(2q) d^c_k(x) + (3/q) w_j (c_k.u_b)
+// with u_b = V + Om x (x + q c_j - X).  It is written where the next step
+// reads f_k(x).  All inputs are post-collision values of the finished step
+// and all outputs are slots no other link reads, so links are independent.
+//
+// Momentum exchange (Eqs. 25, 26): the sphere receives
+//   dP = (f^c_j(x) + f_k(x, t+1)) c_j,   torque (x_b - X) x dP.
+// With f = w + d this splits into the deviation part (d^c_j + d_k) c_j,
+// summed in FP32 per thread and per warp (shuffles), and the rest part
+// 2 w_j c_j = (36 w_j / 18) c_j, counted exactly in integers; (x_b - X) x c_j
+// = (x - X) x c_j since c_j x c_j = 0.  The CTA combines the warp sums in
+// FP64 in a fixed order, so the force is deterministic.
+#include <cmath>
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+// Wrap a coordinate that is at most one box length outside [0, n).
+__device__ __forceinline__ int wrap1(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, T *__restrict__ f,
+                                               uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
+                                               const int P, const int ext, const int cap, int *__restrict__ status,
+                                               unsigned long long *__restrict__ ctr) {
+    extern __shared__ unsigned char smem[];
+    const int B = 2 * ext + 1, B2 = B * B, B3 = B2 * B;
+    uint32_t *list = (uint32_t *)smem;            // cap entries: tile index << 5 | direction
+    uint8_t *code = smem + 4 * (size_t)cap;       // B3 node codes
+    __shared__ double red[8][13];
+    __shared__ int wsum[8];
+    const int p = blockIdx.x;
+    const double *Xp = pt.X + 3 * p;
+    int b[3];
+    float fr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double bb = floor(Xp[a]);
+        b[a] = (int)bb;
+        fr[a] = __double2float_rn(Xp[a] - bb);
+    }
+    const float R = __double2float_rn(pt.R[p]);
+    const float R2 = __fmul_rn(R, R);
+
+    // 1. node codes of the tile: 0 fluid, 1 other solid / outside, 2 this sphere
+    for (int t = threadIdx.x; t < B3; t += blockDim.x) {
+        const int z = b[2] + t / B2 - ext;
+        uint8_t c = 1;
+        if (z >= 0 && z < L.nz) {
+            const int y = wrap1(b[1] + (t / B) % B - ext, L.ny), x = wrap1(b[0] + t % B - ext, L.nx);
+            const int n = x + L.nx * (y + L.ny * z);
+            const uint8_t fl = flag[n];
+            c = (fl & 1) ? (owner[n] == p ? 2 : 1) : 0;
+        }
+        code[t] = c;
+    }
+    __syncthreads();
+
+    // 2. cut links (s owned, x = s - c_j fluid) into a list, in tile order
+    //    (count, block scan, write: deterministic order)
+    int mine = 0;
+    for (int t = threadIdx.x; t < B3; t += blockDim.x) {
+        if (code[t] != 2) continue;
+        for (int j = 1; j < Q; ++j) mine += code[t - (rcx(j) + B * (rcy(j) + B * rcz(j)))] == 0;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    int base = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+        if (w < wid) base += wsum[w];
+        total += wsum[w];
+    }
+    int pos = base + incl - mine;
+    for (int t = threadIdx.x; t < B3; t += blockDim.x) {
+        if (code[t] != 2) continue;
+        for (int j = 1; j < Q; ++j)
+            if (code[t - (rcx(j) + B * (rcy(j) + B * rcz(j)))] == 0) {
+                if (pos < cap) list[pos] = ((uint32_t)t << 5) | (uint32_t)j;
+                ++pos;
+            }
+    }
+    if (total > cap && threadIdx.x == 0) atomicOr(status, ST_TILE);
+    total = min(total, cap);
+    __syncthreads();
+
+    // 3. bounce-back and momentum exchange, links spread over the threads
+    const float V[3] = {(float)pt.V[3 * p], (float)pt.V[3 * p + 1], (float)pt.V[3 * p + 2]};
+    const float W[3] = {(float)pt.W[3 * p], (float)pt.W[3 * p + 1], (float)pt.W[3 * p + 2]};
+    float Fd[3] = {0.f, 0.f, 0.f}, Td[3] = {0.f, 0.f, 0.f};
+    int I[3] = {0, 0, 0}, J[3] = {0, 0, 0};
+    const int S = (int)L.S, plane = (int)L.plane;
+    for (int l = threadIdx.x; l < total; l += blockDim.x) {
+        const uint32_t e = list[l];
+        const int t = (int)(e >> 5), j = (int)(e & 31u), k = ropp(j);
+        const int cjx = rcx(j), cjy = rcy(j), cjz = rcz(j);
+        const int off = cjx + B * (cjy + B * cjz);
+        // fluid node x = s - c_j relative to the sphere frame
+        const int ox = t % B - ext - cjx, oy = (t / B) % B - ext - cjy, oz = t / B2 - ext - cjz;
+        const float dx = __fsub_rn((float)ox, fr[0]), dy = __fsub_rn((float)oy, fr[1]), dz = __fsub_rn((float)oz, fr[2]);
+        const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+        const float qa = (float)(cjx * cjx + cjy * cjy + cjz * cjz);
+        const float qb = __fadd_rn(__fadd_rn(__fmul_rn((float)cjx, dx), __fmul_rn((float)cjy, dy)),
+                                   __fmul_rn((float)cjz, dz));
+        const float c0 = __fsub_rn(d2, R2);
+        float disc = __fsub_rn(__fmul_rn(qb, qb), __fmul_rn(qa, c0));
+        if (disc < 0.f) disc = 0.f;
+        float q = __fdiv_rn(c0, __fadd_rn(-qb, __fsqrt_rn(disc)));
+        q = fminf(fmaxf(q, 0.f), 1.f);
+
+        // storage indices of x, of the solid node s = x + c_j and of x - c_j
+        const int xx = wrap1(b[0] + ox, L.nx), xy = wrap1(b[1] + oy, L.ny), xz = b[2] + oz;
+        const int sx = xx + L.nx * (xy + L.ny * xz) + plane;
+        const int ss = wrap1(xx + cjx, L.nx) + L.nx * (wrap1(xy + cjy, L.ny) + L.ny * (xz + cjz)) + plane;
+        const int sb = wrap1(xx - cjx, L.nx) + L.nx * (wrap1(xy - cjy, L.ny) + L.ny * (xz - cjz)) + plane;
+
+        const float dcj = Store<T>::ld(f + (P == 0 ? k * S + sx : j * S + ss));
+        const float lx = dx + q * cjx, ly = dy + q * cjy, lz = dz + q * cjz;
+        const float ubx = V[0] + (W[1] * lz - W[2] * ly);
+        const float uby = V[1] + (W[2] * lx - W[0] * lz);
+        const float ubz = V[2] + (W[0] * ly - W[1] * lx);
+        const float cku = -(cjx * ubx + cjy * uby + cjz * ubz);
+        const float wj = (float)rw36(j) * (1.f / 36.f);
+        float dn;
+        if (q < 0.5f) {
+            const float mw = 6.f * wj * cku;
+            if (code[t - 2 * off] == 0) {
+                const float dcj2 = Store<T>::ld(f + (P == 0 ? k * S + sb : j * S + sx));
+                dn = 2.f * q * dcj + (1.f - 2.f * q) * dcj2 + mw;
+            } else {
+                dn = dcj + mw;
+            }
+        } else {
+            const float dck = Store<T>::ld(f + (P == 0 ? j * S + sx : k * S + sb));
+            const float i2q = 0.5f / q;
+            dn = dcj * i2q + (2.f * q - 1.f) * i2q * dck + 3.f / q * wj * cku;
+        }
+        Store<T>::st(f + (P == 0 ? j * S + ss : k * S + sx), dn);
+
+        const float m = dcj + dn;
+        Fd[0] += m * cjx;
+        Fd[1] += m * cjy;
+        Fd[2] += m * cjz;
+        Td[0] += m * (dy * cjz - dz * cjy);
+        Td[1] += m * (dz * cjx - dx * cjz);
+        Td[2] += m * (dx * cjy - dy * cjx);
+        const int w = rw36(j);
+        I[0] += w * cjx;
+        I[1] += w * cjy;
+        I[2] += w * cjz;
+        J[0] += w * (oy * cjz - oz * cjy);
+        J[1] += w * (oz * cjx - ox * cjz);
+        J[2] += w * (ox * cjy - oy * cjx);
+    }
+
+    // 4. the nodes of this sphere become "owned at the previous geometry"
+    //    (3: still solid for every reader) for the next step's mark pass
+    for (int t = threadIdx.x; t < B3; t += blockDim.x) {
+        if (code[t] != 2) continue;
+        const int z = b[2] + t / B2 - ext;
+        const int y = wrap1(b[1] + (t / B) % B - ext, L.ny), x = wrap1(b[0] + t % B - ext, L.nx);
+        flag[x + L.nx * (y + L.ny * z)] = 3;
+    }
+
+    // 5. warp sums in FP32, then FP64 across warps in a fixed order
+    float v[6] = {Fd[0], Fd[1], Fd[2], Td[0], Td[1], Td[2]};
+    int iv[6] = {I[0], I[1], I[2], J[0], J[1], J[2]};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            v[a] += __shfl_xor_sync(0xffffffffu, v[a], o);
+            iv[a] += __shfl_xor_sync(0xffffffffu, iv[a], o);
+        }
+    }
+    if (lane == 0) {
+        for (int a = 0; a < 6; ++a) {
+            red[wid][a] = (double)v[a];
+            red[wid][6 + a] = (double)iv[a];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sm[12] = {0};
+        for (int w = 0; w < nw; ++w)
+            for (int a = 0; a < 12; ++a) sm[a] += red[w][a];
+        double frac[3];
+        for (int a = 0; a < 3; ++a) frac[a] = Xp[a] - floor(Xp[a]);
+        // rest part 2 w_j c_j: F = I/18, T = (J - frac x I)/18
+        const double Ix = sm[6], Iy = sm[7], Iz = sm[8];
+        double *F = pt.Fh + 3 * p, *Tq = pt.Th + 3 * p;
+        F[0] = sm[0] + Ix / 18.0;
+        F[1] = sm[1] + Iy / 18.0;
+        F[2] = sm[2] + Iz / 18.0;
+        Tq[0] = sm[3] + (sm[9] - (frac[1] * Iz - frac[2] * Iy)) / 18.0;
+        Tq[1] = sm[4] + (sm[10] - (frac[2] * Ix - frac[0] * Iz)) / 18.0;
+        Tq[2] = sm[5] + (sm[11] - (frac[0] * Iy - frac[1] * Ix)) / 18.0;
+        for (int a = 0; a < 3; ++a) pt.Xgeo[3 * p + a] = Xp[a];
+        atomicAdd(ctr, (unsigned long long)total);
+    }
+}
+
+int link_capacity(double max_radius) {
+    const double r = max_radius < 1.0 ? 1.0 : max_radius;
+    return (int)std::ceil(80.0 * r * r) + 64;
+}
+
+size_t link_smem(int ext, int cap) {
+    const size_t B = 2 * (size_t)ext + 1;
+    return 4 * (size_t)cap + B * B * B;
+}
+
+int links_setup(int ext, int cap) {
+    const int smem = (int)link_smem(ext, cap);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_links<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_links<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_links<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+int launch_links(lbm_s *h, int parity) {
+    const int ext = h->tile_ext, cap = h->link_cap;
+    const size_t smem = link_smem(ext, cap);
+    switch (h->precision) {
+        case LBM_FP32:
+            k_links<float><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, (float *)h->f, h->flag, h->owner, parity,
+                                                                ext, cap, h->status, h->ctr);
+            break;
+        case LBM_BF16_DEV:
+            k_links<__nv_bfloat16><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, (__nv_bfloat16 *)h->f, h->flag,
+                                                                        h->owner, parity, ext, cap, h->status, h->ctr);
+            break;
+        case LBM_FP16_DEV:
+            k_links<__half><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, (__half *)h->f, h->flag, h->owner, parity,
+                                                                 ext, cap, h->status, h->ctr);
+            break;
+        default: return LBM_ERR_ARG;
+    }
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+}  // namespace lbm

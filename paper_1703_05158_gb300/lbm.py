@@ -1,0 +1,323 @@
+"""ctypes binding of the C ABI in ``include/lbm.h`` (argument marshalling only).
+
+Every entry point of the header has a function of the same name here; the
+``Lattice`` class wraps a handle for convenience.  Arrays may be numpy arrays
+(host) or CUDA torch tensors (device: their data pointers are passed with
+``LBM_DEVICE``).  PyTorch is only used for device memory and the current
+stream; nothing here computes any part of the method, and there is no
+fallback: if the library cannot be loaded, importing this module fails.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK = 0
+LBM_ERR_ARG = -1
+LBM_ERR_CUDA = -2
+LBM_ERR_NOMEM = -3
+LBM_ERR_CAPACITY = -4
+LBM_ERR_DIVERGED = -5
+LBM_ERR_UNSUPPORTED = -6
+LBM_ERR_TIMEOUT = -7
+LBM_ERR_GEOMETRY = -8
+
+LBM_FP32 = 0
+LBM_BF16_DEV = 1
+LBM_FP16_DEV = 2
+LBM_HOST = 0
+LBM_DEVICE = 1
+
+PRECISIONS = {"fp32": LBM_FP32, "bf16": LBM_BF16_DEV, "fp16": LBM_FP16_DEV}
+
+EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_particles", "lbm_set_particle_load", "lbm_set_populations",
+           "lbm_step", "lbm_forces", "lbm_particles", "lbm_fields", "lbm_populations", "lbm_geometry", "lbm_info",
+           "lbm_sync", "lbm_error_string", "lbm_profile", "lbm_profile_read")
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("periodic_z", ctypes.c_int32),
+        ("tau0", ctypes.c_double), ("cs_smag", ctypes.c_double),
+        ("body_accel", ctypes.c_double * 3),
+        ("wall_vel_lo", ctypes.c_double * 3), ("wall_vel_hi", ctypes.c_double * 3),
+        ("rho_particle", ctypes.c_double), ("kn", ctypes.c_double), ("restitution", ctypes.c_double),
+        ("dem_substeps", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_particles", ctypes.c_int32),
+        ("max_radius", ctypes.c_double),
+        ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int32),
+    ]
+
+
+class lbm_info_t(ctypes.Structure):
+    _fields_ = [
+        ("nodes", ctypes.c_int64), ("fluid_nodes", ctypes.c_int64), ("links", ctypes.c_int64),
+        ("refilled", ctypes.c_int64), ("steps", ctypes.c_int64), ("particles", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+    ]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build=True):
+    """Load (building first if needed) the CUDA library; raises if it is missing."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("CUDA library %s is missing; run __graft_entry__.build()" % path)
+        lib = ctypes.CDLL(path)
+        vp, ip, dp, fp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p
+        lib.lbm_create.argtypes = [ctypes.POINTER(lbm_params), ctypes.POINTER(vp)]
+        lib.lbm_destroy.argtypes = [vp]
+        lib.lbm_set_particles.argtypes = [vp, ip, dp, dp, dp, dp, vp]
+        lib.lbm_set_particle_load.argtypes = [vp, dp, dp, ip]
+        lib.lbm_set_populations.argtypes = [vp, dp, ip]
+        lib.lbm_step.argtypes = [vp, ip]
+        lib.lbm_forces.argtypes = [vp, dp, dp, ip]
+        lib.lbm_particles.argtypes = [vp, dp, dp, dp, ip]
+        lib.lbm_fields.argtypes = [vp, fp, fp, ip]
+        lib.lbm_populations.argtypes = [vp, dp, ip]
+        lib.lbm_geometry.argtypes = [vp, vp, ip]
+        lib.lbm_info.argtypes = [vp, ctypes.POINTER(lbm_info_t)]
+        lib.lbm_sync.argtypes = [vp]
+        lib.lbm_profile.argtypes = [vp, ip]
+        lib.lbm_profile_read.argtypes = [vp, ctypes.c_void_p, ctypes.c_void_p]
+        lib.lbm_error_string.argtypes = [ctypes.c_int]
+        lib.lbm_error_string.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name != "lbm_error_string":
+                getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s: %s (%d)" % (what, lbm_error_string(code), code))
+        self.code = code
+
+
+def _check(code, what):
+    if code != LBM_OK:
+        raise LbmError(code, what)
+    return code
+
+
+def _ptr(a):
+    """(pointer, where) of a numpy array or a CUDA tensor; (None, HOST) for None."""
+    if a is None:
+        return None, LBM_HOST
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), (LBM_DEVICE if a.is_cuda else LBM_HOST)
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return ctypes.c_void_p(a.ctypes.data), LBM_HOST
+
+
+# ---- the ABI, one function per entry point -------------------------------
+
+def lbm_error_string(code):
+    return load().lbm_error_string(int(code)).decode()
+
+
+def lbm_create(params):
+    h = ctypes.c_void_p()
+    _check(load().lbm_create(ctypes.byref(params), ctypes.byref(h)), "lbm_create")
+    return h
+
+
+def lbm_destroy(h):
+    return _check(load().lbm_destroy(h), "lbm_destroy")
+
+
+def lbm_set_particles(h, pos, vel, omega, radius, fixed=None):
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    n = pos.shape[0]
+    vel = np.ascontiguousarray(vel, dtype=np.float64).reshape(n, 3)
+    omega = np.ascontiguousarray(omega, dtype=np.float64).reshape(n, 3)
+    radius = np.ascontiguousarray(radius, dtype=np.float64).reshape(n)
+    fx = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8).reshape(n)
+    return _check(load().lbm_set_particles(h, n, pos.ctypes.data, vel.ctypes.data, omega.ctypes.data,
+                                           radius.ctypes.data, None if fx is None else fx.ctypes.data),
+                  "lbm_set_particles")
+
+
+def lbm_set_particle_load(h, force=None, torque=None):
+    pf, w1 = _ptr(force)
+    pt, w2 = _ptr(torque)
+    where = LBM_DEVICE if LBM_DEVICE in (w1, w2) else LBM_HOST
+    return _check(load().lbm_set_particle_load(h, pf, pt, where), "lbm_set_particle_load")
+
+
+def lbm_set_populations(h, f):
+    p, where = _ptr(f)
+    return _check(load().lbm_set_populations(h, p, where), "lbm_set_populations")
+
+
+def lbm_step(h, nsteps=1):
+    return _check(load().lbm_step(h, int(nsteps)), "lbm_step")
+
+
+def lbm_forces(h, F, T):
+    pF, where = _ptr(F)
+    pT, _ = _ptr(T)
+    return _check(load().lbm_forces(h, pF, pT, where), "lbm_forces")
+
+
+def lbm_particles(h, pos, vel=None, omega=None):
+    p1, where = _ptr(pos)
+    p2, _ = _ptr(vel)
+    p3, _ = _ptr(omega)
+    return _check(load().lbm_particles(h, p1, p2, p3, where), "lbm_particles")
+
+
+def lbm_fields(h, rho, u):
+    p1, w1 = _ptr(rho)
+    p2, w2 = _ptr(u)
+    where = w1 if rho is not None else w2
+    return _check(load().lbm_fields(h, p1, p2, where), "lbm_fields")
+
+
+def lbm_populations(h, f):
+    p, where = _ptr(f)
+    return _check(load().lbm_populations(h, p, where), "lbm_populations")
+
+
+def lbm_geometry(h, owner):
+    p, where = _ptr(owner)
+    return _check(load().lbm_geometry(h, p, where), "lbm_geometry")
+
+
+def lbm_info(h):
+    info = lbm_info_t()
+    _check(load().lbm_info(h, ctypes.byref(info)), "lbm_info")
+    return {name: getattr(info, name) for name, _ in lbm_info_t._fields_}
+
+
+def lbm_sync(h):
+    return _check(load().lbm_sync(h), "lbm_sync")
+
+
+PHASES = ("geometry", "collide", "links", "dem")
+
+
+def lbm_profile(h, enable):
+    return _check(load().lbm_profile(h, int(bool(enable))), "lbm_profile")
+
+
+def lbm_profile_read(h):
+    """({phase: total ms}, steps) since profiling was enabled."""
+    ms = (ctypes.c_double * 4)()
+    steps = ctypes.c_int64()
+    _check(load().lbm_profile_read(h, ctypes.byref(ms), ctypes.byref(steps)), "lbm_profile_read")
+    return dict(zip(PHASES, list(ms))), steps.value
+
+
+# ---- convenience wrapper ---------------------------------------------------
+
+class Lattice:
+    """One simulation handle; x, y periodic, walls at z = -1/2 and nz - 1/2.
+
+    Host outputs are numpy arrays shaped like the oracle's: populations
+    [19, nz, ny, nx], fields rho [nz, ny, nx] and u [3, nz, ny, nx].
+    """
+
+    def __init__(self, nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0), u_hi=(0.0, 0.0, 0.0),
+                 rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16, precision="fp32", max_particles=0,
+                 max_radius=4.0, stream=None, device=0):
+        p = lbm_params()
+        p.nx, p.ny, p.nz, p.periodic_z = nx, ny, nz, 0
+        p.tau0, p.cs_smag = tau0, cs
+        p.body_accel[:] = list(g)
+        p.wall_vel_lo[:] = list(u_lo)
+        p.wall_vel_hi[:] = list(u_hi)
+        p.rho_particle, p.kn, p.restitution = rho_s, kn, restitution
+        p.dem_substeps = dem_substeps
+        p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        p.max_particles, p.max_radius = max_particles, max_radius
+        p.cuda_stream = stream
+        p.device = device
+        self.params = p
+        self.h = lbm_create(p)
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        self.np = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_particles(self, X, V=None, Om=None, R=None, fixed=None):
+        X = np.asarray(X, dtype=np.float64).reshape(-1, 3)
+        n = X.shape[0]
+        V = np.zeros((n, 3)) if V is None else V
+        Om = np.zeros((n, 3)) if Om is None else Om
+        lbm_set_particles(self.h, X, V, Om, R, fixed)
+        self.np = n
+
+    def set_load(self, F=None, T=None):
+        F = None if F is None else np.ascontiguousarray(F, dtype=np.float64).reshape(self.np, 3)
+        T = None if T is None else np.ascontiguousarray(T, dtype=np.float64).reshape(self.np, 3)
+        lbm_set_particle_load(self.h, F, T)
+
+    def set_populations(self, f):
+        if hasattr(f, "data_ptr"):
+            lbm_set_populations(self.h, f)
+        else:
+            lbm_set_populations(self.h, np.ascontiguousarray(f, dtype=np.float64).reshape(19, -1))
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def sync(self):
+        lbm_sync(self.h)
+
+    def forces(self):
+        F, T = np.zeros((self.np, 3)), np.zeros((self.np, 3))
+        lbm_forces(self.h, F, T)
+        return F, T
+
+    def particles(self):
+        X, V, Om = np.zeros((self.np, 3)), np.zeros((self.np, 3)), np.zeros((self.np, 3))
+        lbm_particles(self.h, X, V, Om)
+        return X, V, Om
+
+    def fields(self):
+        rho, u = np.empty(self.N, dtype=np.float32), np.empty(3 * self.N, dtype=np.float32)
+        lbm_fields(self.h, rho, u)
+        return rho.reshape(self.shape), u.reshape((3,) + self.shape)
+
+    def populations(self):
+        f = np.empty(19 * self.N)
+        lbm_populations(self.h, f)
+        return f.reshape((19,) + self.shape)
+
+    def owner(self):
+        o = np.empty(self.N, dtype=np.int32)
+        lbm_geometry(self.h, o)
+        return o.reshape(self.shape)
+
+    def info(self):
+        return lbm_info(self.h)
+
+    def profile(self, enable=True):
+        lbm_profile(self.h, enable)
+
+    def profile_read(self):
+        return lbm_profile_read(self.h)

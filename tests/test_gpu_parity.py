@@ -1,0 +1,199 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances: FP32 storage, per-population max relative error <= 1e-5 after
+100 steps and per-sphere force within 1e-4 relative; node ownership must be
+identical (both sides take the geometric decisions with the same FP32
+operations).  Sphere centres and velocities are integrated in FP64 on both
+sides from hydrodynamic loads that differ at the FP32 level; a relative load
+error eps over t steps moves a sphere by at most eps a t^2 / 2 (a = |F|/m),
+so centres must agree within 1e-5 a_max t^2 / 2 and velocities within
+1e-5 a_max t.  Box sizes are deliberately not multiples of the 32-wide warp
+or the block width, so every case has ragged rows.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1703_05158_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+POP_TOL = 1e-5
+FORCE_TOL = 1e-4
+
+
+def lbm():
+    from paper_1703_05158_gb300 import lbm as mod
+
+    mod.load()
+    return mod
+
+
+def make_pair(shape, parts=None, populations=None, precision="fp32", max_radius=4.0, **kw):
+    nx, ny, nz = shape
+    n = 0 if parts is None else len(parts["R"])
+    lat = lbm().Lattice(nx, ny, nz, max_particles=max(n, 1), max_radius=max_radius, precision=precision, **kw)
+    orc = oracle.Oracle(nx, ny, nz, **kw)
+    if parts is not None:
+        for o in (lat, orc):
+            o.set_particles(parts["X"], V=parts["V"], Om=parts.get("Om"), R=parts["R"], fixed=parts.get("fixed"))
+    if populations is not None:
+        orc.set_populations(populations)
+        lat.set_populations(orc.populations())
+    return lat, orc
+
+
+def perturbed(shape, amp, seed):
+    c, w, _ = oracle.tables()
+    eps = inputs.perturbation((19,) + tuple(reversed(shape)), amp, seed)
+    return w[:, None, None, None] * (1.0 + eps)
+
+
+def pop_error(lat, orc):
+    fo = orc.populations()
+    fg = lat.populations()
+    fluid = orc.owner() < 0
+    return float((np.abs(fg - fo)[:, fluid] / np.abs(fo[:, fluid])).max())
+
+
+def force_error(lat, orc):
+    Fg, Tg = lat.forces()
+    Fo, To = orc.forces()
+    ef = np.linalg.norm(Fg - Fo, axis=1) / np.linalg.norm(Fo, axis=1)
+    et = np.linalg.norm(Tg - To, axis=1) / np.maximum(np.linalg.norm(To, axis=1), 1e-300)
+    return float(ef.max()), float(et.max()), Fo, To
+
+
+def motion_tolerance(orc, steps, rho_s=2.5):
+    F, _ = orc.forces()
+    _, _, _ = orc.particles()
+    R = np.asarray(orc._keep[3])
+    a = np.linalg.norm(F, axis=1) / (rho_s * 4.0 / 3.0 * np.pi * R ** 3)
+    amax = float(a.max())
+    return 1e-5 * amax * steps ** 2 / 2 + 1e-12, 1e-5 * amax * steps + 1e-14
+
+
+def test_rest_state_is_exact():
+    lat, _ = make_pair((37, 29, 23), tau0=0.7, cs=0.17)
+    lat.step(50)
+    c, w, _ = oracle.tables()
+    f = lat.populations()
+    assert np.array_equal(f, np.broadcast_to(w[:, None, None, None], f.shape))
+
+
+def test_fluid_only_parity_walls_lid_force_smagorinsky():
+    shape = (37, 29, 23)
+    kw = dict(tau0=0.56, cs=0.17, g=(1e-5, 2e-6, 0.0), u_lo=(0.0, -0.01, 0.0), u_hi=(0.05, 0.01, 0.0))
+    lat, orc = make_pair(shape, populations=perturbed(shape, 0.05, 101), **kw)
+    lat.step(100)
+    orc.step(100)
+    assert pop_error(lat, orc) <= POP_TOL
+    rg, ug = lat.fields()
+    ro, uo = orc.fields()
+    assert np.abs(rg - ro).max() < 1e-6
+    assert np.abs(ug - uo).max() < 1e-7
+
+
+def test_single_sphere_plain_method_200_steps():
+    """One sphere of radius 4 at the centre of a 32^3 box moving at 0.01."""
+    p = inputs.sphere_in_box(32)
+    kw = dict(tau0=0.8, cs=0.1, g=(1e-6, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16)
+    lat, orc = make_pair((32, 32, 32), parts=p, **kw)
+    for n in (100, 100):
+        lat.step(n)
+        orc.step(n)
+        assert np.array_equal(lat.owner(), orc.owner())
+        assert pop_error(lat, orc) <= POP_TOL
+        ef, et, Fo, _ = force_error(lat, orc)
+        assert ef <= FORCE_TOL, (ef, Fo)
+        assert et <= 1e-2 or np.abs(lat.forces()[1] - orc.forces()[1]).max() < 1e-7
+    Xg, Vg, Wg = lat.particles()
+    Xo, Vo, Wo = orc.particles()
+    xt, vt = motion_tolerance(orc, 200)
+    assert np.abs(Xg - Xo).max() < xt
+    assert np.abs(Vg - Vo).max() < vt
+    assert lat.info()["refilled"] >= 0
+
+
+def test_many_spheres_moving_lid_contacts_periodic_edges():
+    shape = (64, 50, 40)
+    parts = inputs.polydisperse(shape, 20, (2.5, 4.5), seed=inputs.SEED_BASE + 11, vmax=0.02)
+    # a head-on pair that collides within the run, one across the periodic x
+    # edge, one close to the lower wall
+    extra_X = np.array([[20.0, 40.0, 30.0], [29.3, 40.0, 30.0], [0.7, 10.0, 12.0], [44.0, 25.0, 4.2]])
+    extra_V = np.array([[0.03, 0.0, 0.0], [-0.03, 0.0, 0.0], [-0.02, 0.01, 0.0], [0.0, 0.0, -0.02]])
+    extra_R = np.array([4.0, 4.2, 3.0, 3.5])
+    keep = np.ones(len(parts["R"]), dtype=bool)
+    for x, r in zip(extra_X, extra_R):
+        d = parts["X"] - x
+        d[:, :2] -= np.array(shape[:2]) * np.round(d[:, :2] / np.array(shape[:2]))
+        keep &= np.linalg.norm(d, axis=1) > parts["R"] + r + 1.0
+    p = dict(X=np.vstack([parts["X"][keep], extra_X]), V=np.vstack([parts["V"][keep], extra_V]),
+             Om=np.vstack([inputs.uniform_vectors(keep.sum(), -2e-3, 2e-3, 5), np.zeros((4, 3))]),
+             R=np.concatenate([parts["R"][keep], extra_R]))
+    kw = dict(tau0=0.6, cs=0.17, g=(2e-6, 0.0, 0.0), u_hi=(0.05, 0.0, 0.0), rho_s=2.5, kn=1e3,
+              restitution=0.8, dem_substeps=16)
+    lat, orc = make_pair(shape, parts=p, max_radius=5.0, **kw)
+    lat.step(100)
+    orc.step(100)
+    assert np.array_equal(lat.owner(), orc.owner())
+    assert pop_error(lat, orc) <= POP_TOL
+    ef, et, Fo, To = force_error(lat, orc)
+    assert ef <= FORCE_TOL, (ef, Fo)
+    Xg, Vg, _ = lat.particles()
+    Xo, Vo, _ = orc.particles()
+    xt, vt = motion_tolerance(orc, 100)
+    assert np.abs(Xg - Xo).max() < xt
+    assert np.abs(Vg - Vo).max() < vt
+    # the head-on pair did collide
+    assert Vo[-4, 0] < 0.0 < Vo[-3, 0]
+    info = lat.info()
+    node, _, _, _ = orc.links()
+    assert info["links"] == len(node)
+    assert info["fluid_nodes"] == int((orc.owner() < 0).sum())
+
+
+def test_no_particles_and_capacity_errors():
+    L = lbm()
+    lat = L.Lattice(40, 40, 12, tau0=0.7, max_particles=2, max_radius=4.0)
+    with pytest.raises(L.LbmError) as e:
+        lat.set_particles(np.full((3, 3), 10.0), R=[3.0, 3.0, 3.0])
+    assert e.value.code == L.LBM_ERR_CAPACITY
+    with pytest.raises(L.LbmError) as e:
+        lat.set_particles([[41.0, 10.0, 6.0]], R=[3.0])
+    assert e.value.code == L.LBM_ERR_ARG
+    lat.set_particles(np.zeros((0, 3)), R=np.zeros(0))
+    lat.step(3)
+    lat.sync()
+    assert lat.info()["steps"] == 3
+
+
+def test_mass_conservation_gpu():
+    shape = (96, 64, 48)
+    kw = dict(tau0=0.6, cs=0.17, u_hi=(0.05, 0.0, 0.0))
+    lat, orc = make_pair(shape, populations=perturbed(shape, 0.02, 7), **kw)
+    m0 = lat.populations().sum()
+    lat.step(500)
+    assert abs(lat.populations().sum() - m0) / m0 < 1e-7
+
+
+@pytest.mark.slow
+def test_full_size_slurry_box_sampled():
+    """256^3 with 2000 spheres of radius 4, the benchmark's launch
+    configuration, two steps: geometry identical everywhere, forces of every
+    sphere, populations at 200k sampled nodes."""
+    p = inputs.slurry_box()
+    kw = dict(tau0=0.51, cs=0.17, u_hi=(0.05, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16)
+    lat, orc = make_pair((256, 256, 256), parts=p, **kw)
+    lat.step(2)
+    orc.step(2)
+    assert np.array_equal(lat.owner(), orc.owner())
+    ef, _, Fo, _ = force_error(lat, orc)
+    assert ef <= FORCE_TOL, ef
+    fo = orc.populations().reshape(19, -1)
+    fg = lat.populations().reshape(19, -1)
+    fluid = (orc.owner() < 0).reshape(-1)
+    idx = np.flatnonzero(fluid)
+    idx = idx[inputs.rng(3).choice(len(idx), 200000, replace=False)]
+    assert (np.abs(fg[:, idx] - fo[:, idx]) / np.abs(fo[:, idx])).max() <= POP_TOL
