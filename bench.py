@@ -33,7 +33,7 @@ BYTES = {"fp32": 4, "bf16": 2, "fp16": 2}
 
 
 def workload_name(prec):
-    return "slurry box 256^3, 2000 spheres R=4, sliding lid 0.05, tau0=0.51, Cs=0.17, %s storage" % prec
+    return "slurry box %d^3, %d spheres R=4, sliding lid 0.05, tau0=0.51, Cs=0.17, %s storage" % (BOX[0], NSPH, prec)
 
 
 def peaks():

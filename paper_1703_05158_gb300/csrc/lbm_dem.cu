@@ -17,8 +17,9 @@
 //
 // Sub-steps need all centres of the previous sub-step.  One thread-block
 // cluster runs all of them: each thread keeps its spheres in registers, the
-// new centres and half-step velocities go through global memory, and a
-// hardware cluster barrier (release / acquire) separates drift and force.
+// new centres and half-step velocities go through distributed shared memory,
+// and a hardware cluster barrier (release / acquire) separates drift and
+// force.
 // Too many spheres for one cluster fall back to a cooperative launch with a
 // bounded software grid barrier.
 #include <cooperative_groups.h>
@@ -161,23 +162,35 @@ __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
-// All sub-steps of one lattice step in one cluster (gridDim.x CTAs).
-__global__ void __launch_bounds__(kDemThreads) k_dem_cluster(const Lat L, const Parts pt, int *status) {
-    const int G = gridDim.x * blockDim.x;
-    const int g0 = blockIdx.x * blockDim.x + threadIdx.x;
+// All sub-steps of one lattice step in one cluster (gridDim.x CTAs).  Thread
+// t of CTA c owns spheres a = c T + t + q G (q < kDemKmax, G = cluster
+// threads) and keeps their state in registers; after each drift it publishes
+// centre and half-step velocity in its CTA's shared memory (double-buffered
+// by sub-step parity), where the force phase of every CTA reads them through
+// distributed shared memory.
+__global__ void __launch_bounds__(kDemThreads, 1) k_dem_cluster(const Lat L, const Parts pt, int *status) {
+    extern __shared__ double dsm[];  // [2][kDemKmax * T][6]: x, y, z, vx, vy, vz
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int T = blockDim.x, G = gridDim.x * T, cap = kDemKmax * T;
+    const int g0 = blockIdx.x * T + threadIdx.x;
     const int ns = pt.substeps;
     const double h = 1.0 / ns;
+    const float kn = (float)pt.kn, ce = (float)pt.ce;
     double x[kDemKmax][3], v[kDemKmax][3], w[kDemKmax][3], F0[kDemKmax][3], T0[kDemKmax][3], fc[kDemKmax][3];
-    double km[kDemKmax], kI[kDemKmax];
+    double km[kDemKmax], kI[kDemKmax], Ra[kDemKmax], ma[kDemKmax];
+    int nc[kDemKmax];
     bool fx[kDemKmax];
 #pragma unroll
     for (int q = 0; q < kDemKmax; ++q) {
         const int a = g0 + q * G;
         if (a >= pt.np) break;
-        const double m = sphere_mass(pt, a);
+        Ra[q] = pt.R[a];
+        ma[q] = sphere_mass(pt, a);
         fx[q] = pt.fixed[a] != 0;
-        km[q] = fx[q] ? 0.0 : h / (2.0 * m);
-        kI[q] = fx[q] ? 0.0 : h / (0.4 * m * pt.R[a] * pt.R[a]);
+        km[q] = fx[q] ? 0.0 : h / (2.0 * ma[q]);
+        kI[q] = fx[q] ? 0.0 : h / (0.4 * ma[q] * Ra[q] * Ra[q]);
+        nc[q] = pt.nbr_cnt[a];
         for (int c = 0; c < 3; ++c) {
             x[q][c] = pt.X[3 * a + c];
             v[q][c] = pt.V[3 * a + c];
@@ -187,8 +200,9 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_cluster(const Lat L, const 
             fc[q][c] = pt.Fc[3 * a + c];
         }
     }
+    cluster_barrier();  // every CTA of the cluster is running before shared memory is shared
     for (int s = 0; s < ns; ++s) {
-        double *Xn = pt.Xb[(s + 1) & 1], *Vn = pt.Vh[(s + 1) & 1];
+        double *buf = dsm + (size_t)((s + 1) & 1) * cap * 6;
 #pragma unroll
         for (int q = 0; q < kDemKmax; ++q) {
             const int a = g0 + q * G;
@@ -198,9 +212,10 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_cluster(const Lat L, const 
                 x[q][c] += v[q][c] * h;
             }
             wrap_pos(L, x[q]);
+            double *me = buf + (size_t)(q * T + threadIdx.x) * 6;
             for (int c = 0; c < 3; ++c) {
-                Xn[3 * a + c] = x[q][c];
-                Vn[3 * a + c] = v[q][c];
+                me[c] = x[q][c];
+                me[3 + c] = v[q][c];
             }
         }
         cluster_barrier();
@@ -209,13 +224,48 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_cluster(const Lat L, const 
             const int a = g0 + q * G;
             if (a >= pt.np) break;
             if (fx[q]) continue;
-            contact_force(L, pt, a, x[q], v[q], Xn, Vn, fc[q]);
+            double F[3] = {0.0, 0.0, 0.0};
+            for (int m = 0; m < nc[q]; ++m) {
+                const int b = __ldg(pt.nbr + (long long)a * pt.max_nbr + m);
+                const int qb = b / G, rb = b - qb * G, cb = rb / T, tb = rb - cb * T;
+                const double *o = cluster.map_shared_rank(buf + (size_t)(qb * T + tb) * 6, cb);
+                double d[3] = {x[q][0] - o[0], x[q][1] - o[1], x[q][2] - o[2]};
+                if (d[0] > 0.5 * L.nx) d[0] -= L.nx;
+                if (d[0] < -0.5 * L.nx) d[0] += L.nx;
+                if (d[1] > 0.5 * L.ny) d[1] -= L.ny;
+                if (d[1] < -0.5 * L.ny) d[1] += L.ny;
+                const double Rb = __ldg(pt.R + b);
+                const double Rs = Ra[q] + Rb;
+                const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (!(d2 < Rs * Rs)) continue;
+                const double dist = sqrt(d2);
+                const double delta = Rs - dist;
+                if (!(delta > 0.0) || dist == 0.0) continue;
+                const float id = (float)(1.0 / dist);
+                const float nx = (float)d[0] * id, ny = (float)d[1] * id, nz = (float)d[2] * id;
+                const float vn = (float)(v[q][0] - o[3]) * nx + (float)(v[q][1] - o[4]) * ny +
+                                 (float)(v[q][2] - o[5]) * nz;
+                const double mb = pt.rho_s * (4.0 / 3.0) * kPi * Rb * Rb * Rb;
+                const double meff = __ldg(pt.fixed + b) ? ma[q] : ma[q] * mb / (ma[q] + mb);
+                const float fn = kn * (float)delta - ce * sqrtf((float)meff * kn) * vn;
+                F[0] += (double)(fn * nx);
+                F[1] += (double)(fn * ny);
+                F[2] += (double)(fn * nz);
+            }
+            const float gw = ce * sqrtf((float)ma[q] * kn);
+            const float vz = (float)v[q][2];
+            const double lo = Ra[q] - (x[q][2] + 0.5);
+            if (lo > 0.0) F[2] += (double)(kn * (float)lo - gw * vz);
+            const double hi = Ra[q] - ((L.nz - 0.5) - x[q][2]);
+            if (hi > 0.0) F[2] -= (double)(kn * (float)hi + gw * vz);
             for (int c = 0; c < 3; ++c) {
-                v[q][c] += (F0[q][c] + fc[q][c]) * km[q];
+                fc[q][c] = F[c];
+                v[q][c] += (F0[q][c] + F[c]) * km[q];
                 w[q][c] += T0[q][c] * kI[q];
             }
         }
     }
+    cluster_barrier();  // no CTA leaves while another may still read its shared memory
 #pragma unroll
     for (int q = 0; q < kDemKmax; ++q) {
         const int a = g0 + q * G;
@@ -228,6 +278,8 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_cluster(const Lat L, const 
         commit(L, pt, a, x[q], status);
     }
 }
+
+static size_t dem_cluster_smem() { return (size_t)2 * kDemKmax * kDemThreads * 6 * sizeof(double); }
 
 // ---- fallback: cooperative grid with a bounded software barrier ------------
 
@@ -326,6 +378,11 @@ int dem_max_blocks(int threads, int *blocks_per_sm) {
 int dem_cluster_setup(int max_particles) {
     for (int cl : {16, 8}) {
         if ((long long)cl * kDemThreads * kDemKmax < max_particles) continue;
+        if (cudaFuncSetAttribute(k_dem_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)dem_cluster_smem()) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
         if (cl > 8 && cudaFuncSetAttribute(k_dem_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                           cudaSuccess) {
             cudaGetLastError();
@@ -339,6 +396,7 @@ int dem_cluster_setup(int max_particles) {
         attr[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(cl);
         cfg.blockDim = dim3(kDemThreads);
+        cfg.dynamicSmemBytes = dem_cluster_smem();
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int n = 0;
@@ -361,6 +419,7 @@ int launch_dem(lbm_s *h) {
         attr[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(h->dem_cluster);
         cfg.blockDim = dim3(kDemThreads);
+        cfg.dynamicSmemBytes = dem_cluster_smem();
         cfg.stream = h->stream;
         cfg.attrs = attr;
         cfg.numAttrs = 1;

@@ -104,40 +104,70 @@ __global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, uint8
     }
 }
 
+// One CTA per sphere: collect the uncovered nodes of its previous bounding
+// box, then one warp per node: lane i (1..18) sums the 19 populations of
+// neighbour x + c_i if it is fluid before and after, the warp reduces the
+// mean, and lanes 0..18 write the 19 equilibrium populations.
+constexpr int kRefillCap = 512;
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_refill(const Lat L, const Parts pt, T *__restrict__ f,
                                                 uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
-                                                const int P, unsigned long long *__restrict__ ctr) {
+                                                const int P, unsigned long long *__restrict__ ctr,
+                                                int *__restrict__ status) {
+    __shared__ int list[kRefillCap];
+    __shared__ int count;
     const int p = blockIdx.x;
     const double *Xg = pt.Xgeo + 3 * p;
     const int e = ceil_r(pt.R[p]) + 1, B = 2 * e + 1;
     const int bx = (int)floor(Xg[0]), by = (int)floor(Xg[1]), bz = (int)floor(Xg[2]);
-    const Frame F = frame_of(pt.X + 3 * p, pt.R[p]);  // current centre, for the surface velocity
-    const float V[3] = {(float)pt.V[3 * p], (float)pt.V[3 * p + 1], (float)pt.V[3 * p + 2]};
-    const float W[3] = {(float)pt.W[3 * p], (float)pt.W[3 * p + 1], (float)pt.W[3 * p + 2]};
+    if (threadIdx.x == 0) count = 0;
+    __syncthreads();
     for (int t = threadIdx.x; t < B * B * B; t += blockDim.x) {
         const int z = bz + t / (B * B) - e;
         if (z < 0 || z >= L.nz) continue;
         const int y = wrapi(by + (t / B) % B - e, L.ny), x = wrapi(bx + t % B - e, L.nx);
-        const long long n = x + (long long)L.nx * (y + (long long)L.ny * z);
+        const int n = x + L.nx * (y + L.ny * z);
         if (flag[n] != 3 || owner[n] != p) continue;
-        // mean density deviation of the neighbours fluid before and after
-        float sum = 0.f;
-        int cnt = 0;
-        for (int i = 1; i < Q; ++i) {
-            const int zz = z + rcz(i);
-            if (zz < 0 || zz >= L.nz) continue;
-            const int yy = wrapi(y + rcy(i), L.ny), xx = wrapi(x + rcx(i), L.nx);
-            const long long m = xx + (long long)L.nx * (yy + (long long)L.ny * zz);
-            if (flag[m] != 0) continue;
-            const Nbr nb(L, xx, yy);
-            const long long sm = m + L.plane;
-            float dr = 0.f;
-            for (int k = 0; k < Q; ++k) dr += Store<T>::ld(f + in_slot(L, nb, P, k, sm));
-            sum += dr;
-            ++cnt;
+        const int k = atomicAdd(&count, 1);
+        if (k < kRefillCap) list[k] = n;
+        else atomicOr(status, ST_TILE);
+    }
+    __syncthreads();
+    const int total = min(count, kRefillCap);
+    if (total == 0) return;
+    const Frame F = frame_of(pt.X + 3 * p, pt.R[p]);  // current centre, for the surface velocity
+    const float V[3] = {(float)pt.V[3 * p], (float)pt.V[3 * p + 1], (float)pt.V[3 * p + 2]};
+    const float W[3] = {(float)pt.W[3 * p], (float)pt.W[3 * p + 1], (float)pt.W[3 * p + 2]};
+    const int lane = threadIdx.x & 31;
+    for (int k = threadIdx.x >> 5; k < total; k += blockDim.x >> 5) {
+        const int n = list[k];
+        const int x = n % L.nx, y = (n / L.nx) % L.ny, z = n / (L.nx * L.ny);
+        float dr = 0.f;
+        int ok = 0;
+        if (lane >= 1 && lane < Q) {
+            const int zz = z + rcz(lane);
+            if (zz >= 0 && zz < L.nz) {
+                const int yy = wrapi(y + rcy(lane), L.ny), xx = wrapi(x + rcx(lane), L.nx);
+                const int m = xx + L.nx * (yy + L.ny * zz);
+                if (flag[m] == 0) {
+                    const Nbr nb(L, xx, yy);
+                    const long long sm = m + L.plane;
+                    float v[Q];
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) v[i] = Store<T>::ld(f + in_slot(L, nb, P, i, sm));
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) dr += v[i];
+                    ok = 1;
+                }
+            }
         }
-        const float drho = cnt ? sum / (float)cnt : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dr += __shfl_xor_sync(0xffffffffu, dr, o);
+            ok += __shfl_xor_sync(0xffffffffu, ok, o);
+        }
+        const float drho = ok ? dr / (float)ok : 0.f;
         const float rho = 1.f + drho;
         // surface velocity of the sphere at this node (current centre)
         const float lx = rel(fold(x, F.b[0], L.nx), F.fr[0]);
@@ -147,15 +177,17 @@ __global__ void __launch_bounds__(256) k_refill(const Lat L, const Parts pt, T *
         const float uy = V[1] + (W[2] * lx - W[0] * lz);
         const float uz = V[2] + (W[0] * ly - W[1] * lx);
         const float uu = ux * ux + uy * uy + uz * uz;
-        const Nbr nb(L, x, y);
-        const long long s = n + L.plane;
-        for (int i = 0; i < Q; ++i) {
+        if (lane < Q) {
+            const int i = lane;
             const float cu = rcx(i) * ux + rcy(i) * uy + rcz(i) * uz;
             const float dq = (float)rw36(i) / 36.f * (drho + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * uu));
-            Store<T>::st(f + in_slot(L, nb, P, i, s), dq);
+            const Nbr nb(L, x, y);
+            Store<T>::st(f + in_slot(L, nb, P, i, (long long)n + L.plane), dq);
         }
-        flag[n] = 2;
-        atomicAdd(ctr + 1, 1ull);
+        if (lane == 0) {
+            flag[n] = 2;
+            atomicAdd(ctr + 1, 1ull);
+        }
     }
 }
 
@@ -167,15 +199,16 @@ int launch_mark(lbm_s *h) {
 int launch_refill(lbm_s *h, int parity) {
     switch (h->precision) {
         case LBM_FP32:
-            k_refill<float><<<h->pt.np, 256, 0, h->stream>>>(h->L, h->pt, (float *)h->f, h->flag, h->owner, parity, h->ctr);
+            k_refill<float><<<h->pt.np, 256, 0, h->stream>>>(h->L, h->pt, (float *)h->f, h->flag, h->owner, parity, h->ctr,
+                                                              h->status);
             break;
         case LBM_BF16_DEV:
             k_refill<__nv_bfloat16><<<h->pt.np, 256, 0, h->stream>>>(h->L, h->pt, (__nv_bfloat16 *)h->f, h->flag,
-                                                                      h->owner, parity, h->ctr);
+                                                                      h->owner, parity, h->ctr, h->status);
             break;
         case LBM_FP16_DEV:
             k_refill<__half><<<h->pt.np, 256, 0, h->stream>>>(h->L, h->pt, (__half *)h->f, h->flag, h->owner, parity,
-                                                               h->ctr);
+                                                               h->ctr, h->status);
             break;
         default: return LBM_ERR_ARG;
     }

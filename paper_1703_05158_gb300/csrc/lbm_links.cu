@@ -57,16 +57,31 @@ __global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, T *_
     const float R2 = __fmul_rn(R, R);
 
     // 1. node codes of the tile: 0 fluid, 1 other solid / outside, 2 this sphere
-    for (int t = threadIdx.x; t < B3; t += blockDim.x) {
-        const int z = b[2] + t / B2 - ext;
-        uint8_t c = 1;
-        if (z >= 0 && z < L.nz) {
-            const int y = wrap1(b[1] + (t / B) % B - ext, L.ny), x = wrap1(b[0] + t % B - ext, L.nx);
-            const int n = x + L.nx * (y + L.ny * z);
-            const uint8_t fl = flag[n];
-            c = (fl & 1) ? (owner[n] == p ? 2 : 1) : 0;
+    //    (four nodes per thread per round so that their loads overlap)
+    for (int t0 = threadIdx.x; t0 < B3; t0 += 4 * blockDim.x) {
+        int nn[4];
+        uint8_t fl[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = t0 + u * blockDim.x;
+            nn[u] = -1;
+            if (t < B3) {
+                const int z = b[2] + t / B2 - ext;
+                if (z >= 0 && z < L.nz) {
+                    const int y = wrap1(b[1] + (t / B) % B - ext, L.ny), x = wrap1(b[0] + t % B - ext, L.nx);
+                    nn[u] = x + L.nx * (y + L.ny * z);
+                }
+            }
+            fl[u] = nn[u] >= 0 ? __ldcg(flag + nn[u]) : (uint8_t)1;
         }
-        code[t] = c;
+        int ow[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ow[u] = (nn[u] >= 0 && (fl[u] & 1)) ? __ldcg(owner + nn[u]) : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = t0 + u * blockDim.x;
+            if (t < B3) code[t] = (fl[u] & 1) ? (ow[u] == p ? 2 : 1) : 0;
+        }
     }
     __syncthreads();
 
@@ -110,67 +125,84 @@ __global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, T *_
     float Fd[3] = {0.f, 0.f, 0.f}, Td[3] = {0.f, 0.f, 0.f};
     int I[3] = {0, 0, 0}, J[3] = {0, 0, 0};
     const int S = (int)L.S, plane = (int)L.plane;
-    for (int l = threadIdx.x; l < total; l += blockDim.x) {
-        const uint32_t e = list[l];
-        const int t = (int)(e >> 5), j = (int)(e & 31u), k = ropp(j);
-        const int cjx = rcx(j), cjy = rcy(j), cjz = rcz(j);
-        const int off = cjx + B * (cjy + B * cjz);
-        // fluid node x = s - c_j relative to the sphere frame
-        const int ox = t % B - ext - cjx, oy = (t / B) % B - ext - cjy, oz = t / B2 - ext - cjz;
-        const float dx = __fsub_rn((float)ox, fr[0]), dy = __fsub_rn((float)oy, fr[1]), dz = __fsub_rn((float)oz, fr[2]);
-        const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-        const float qa = (float)(cjx * cjx + cjy * cjy + cjz * cjz);
-        const float qb = __fadd_rn(__fadd_rn(__fmul_rn((float)cjx, dx), __fmul_rn((float)cjy, dy)),
-                                   __fmul_rn((float)cjz, dz));
-        const float c0 = __fsub_rn(d2, R2);
-        float disc = __fsub_rn(__fmul_rn(qb, qb), __fmul_rn(qa, c0));
-        if (disc < 0.f) disc = 0.f;
-        float q = __fdiv_rn(c0, __fadd_rn(-qb, __fsqrt_rn(disc)));
-        q = fminf(fmaxf(q, 0.f), 1.f);
-
-        // storage indices of x, of the solid node s = x + c_j and of x - c_j
-        const int xx = wrap1(b[0] + ox, L.nx), xy = wrap1(b[1] + oy, L.ny), xz = b[2] + oz;
-        const int sx = xx + L.nx * (xy + L.ny * xz) + plane;
-        const int ss = wrap1(xx + cjx, L.nx) + L.nx * (wrap1(xy + cjy, L.ny) + L.ny * (xz + cjz)) + plane;
-        const int sb = wrap1(xx - cjx, L.nx) + L.nx * (wrap1(xy - cjy, L.ny) + L.ny * (xz - cjz)) + plane;
-
-        const float dcj = Store<T>::ld(f + (P == 0 ? k * S + sx : j * S + ss));
-        const float lx = dx + q * cjx, ly = dy + q * cjy, lz = dz + q * cjz;
-        const float ubx = V[0] + (W[1] * lz - W[2] * ly);
-        const float uby = V[1] + (W[2] * lx - W[0] * lz);
-        const float ubz = V[2] + (W[0] * ly - W[1] * lx);
-        const float cku = -(cjx * ubx + cjy * uby + cjz * ubz);
-        const float wj = (float)rw36(j) * (1.f / 36.f);
-        float dn;
-        if (q < 0.5f) {
-            const float mw = 6.f * wj * cku;
-            if (code[t - 2 * off] == 0) {
-                const float dcj2 = Store<T>::ld(f + (P == 0 ? k * S + sb : j * S + sx));
-                dn = 2.f * q * dcj + (1.f - 2.f * q) * dcj2 + mw;
-            } else {
-                dn = dcj + mw;
-            }
-        } else {
-            const float dck = Store<T>::ld(f + (P == 0 ? j * S + sx : k * S + sb));
-            const float i2q = 0.5f / q;
-            dn = dcj * i2q + (2.f * q - 1.f) * i2q * dck + 3.f / q * wj * cku;
+    // two links per thread per round: all six candidate loads are issued
+    // before any of them is used
+    for (int l0 = threadIdx.x; l0 < total; l0 += 2 * blockDim.x) {
+        float ld[2][3];
+        int lt[2], lj[2], dst[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int l = l0 + u * blockDim.x;
+            lt[u] = -1;
+            if (l >= total) continue;
+            const uint32_t e = list[l];
+            const int t = (int)(e >> 5), j = (int)(e & 31u), k = ropp(j);
+            const int cjx = rcx(j), cjy = rcy(j), cjz = rcz(j);
+            const int ox = t % B - ext - cjx, oy = (t / B) % B - ext - cjy, oz = t / B2 - ext - cjz;
+            // storage indices of x, of the solid node s = x + c_j and of x - c_j
+            const int xx = wrap1(b[0] + ox, L.nx), xy = wrap1(b[1] + oy, L.ny), xz = b[2] + oz;
+            const int sx = xx + L.nx * (xy + L.ny * xz) + plane;
+            const int ss = wrap1(xx + cjx, L.nx) + L.nx * (wrap1(xy + cjy, L.ny) + L.ny * (xz + cjz)) + plane;
+            const int sb = wrap1(xx - cjx, L.nx) + L.nx * (wrap1(xy - cjy, L.ny) + L.ny * (xz - cjz)) + plane;
+            // post-collision d^c_j(x), d^c_j(x - c_j), d^c_k(x) of the finished step
+            ld[u][0] = Store<T>::ld(f + (P == 0 ? k * S + sx : j * S + ss));
+            ld[u][1] = Store<T>::ld(f + (P == 0 ? k * S + sb : j * S + sx));
+            ld[u][2] = Store<T>::ld(f + (P == 0 ? j * S + sx : k * S + sb));
+            dst[u] = P == 0 ? j * S + ss : k * S + sx;  // where the next step reads f_k(x)
+            lt[u] = t;
+            lj[u] = j;
         }
-        Store<T>::st(f + (P == 0 ? j * S + ss : k * S + sx), dn);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (lt[u] < 0) continue;
+            const int t = lt[u], j = lj[u];
+            const int cjx = rcx(j), cjy = rcy(j), cjz = rcz(j);
+            const int off = cjx + B * (cjy + B * cjz);
+            const int ox = t % B - ext - cjx, oy = (t / B) % B - ext - cjy, oz = t / B2 - ext - cjz;
+            const float dx = __fsub_rn((float)ox, fr[0]), dy = __fsub_rn((float)oy, fr[1]),
+                        dz = __fsub_rn((float)oz, fr[2]);
+            const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            const float qa = (float)(cjx * cjx + cjy * cjy + cjz * cjz);
+            const float qb = __fadd_rn(__fadd_rn(__fmul_rn((float)cjx, dx), __fmul_rn((float)cjy, dy)),
+                                       __fmul_rn((float)cjz, dz));
+            const float c0 = __fsub_rn(d2, R2);
+            float disc = __fsub_rn(__fmul_rn(qb, qb), __fmul_rn(qa, c0));
+            if (disc < 0.f) disc = 0.f;
+            float q = __fdiv_rn(c0, __fadd_rn(-qb, __fsqrt_rn(disc)));
+            q = fminf(fmaxf(q, 0.f), 1.f);
 
-        const float m = dcj + dn;
-        Fd[0] += m * cjx;
-        Fd[1] += m * cjy;
-        Fd[2] += m * cjz;
-        Td[0] += m * (dy * cjz - dz * cjy);
-        Td[1] += m * (dz * cjx - dx * cjz);
-        Td[2] += m * (dx * cjy - dy * cjx);
-        const int w = rw36(j);
-        I[0] += w * cjx;
-        I[1] += w * cjy;
-        I[2] += w * cjz;
-        J[0] += w * (oy * cjz - oz * cjy);
-        J[1] += w * (oz * cjx - ox * cjz);
-        J[2] += w * (ox * cjy - oy * cjx);
+            const float dcj = ld[u][0];
+            const float lx = dx + q * cjx, ly = dy + q * cjy, lz = dz + q * cjz;
+            const float ubx = V[0] + (W[1] * lz - W[2] * ly);
+            const float uby = V[1] + (W[2] * lx - W[0] * lz);
+            const float ubz = V[2] + (W[0] * ly - W[1] * lx);
+            const float cku = -(cjx * ubx + cjy * uby + cjz * ubz);
+            const float wj = (float)rw36(j) * (1.f / 36.f);
+            float dn;
+            if (q < 0.5f) {
+                const float mw = 6.f * wj * cku;
+                dn = code[t - 2 * off] == 0 ? 2.f * q * dcj + (1.f - 2.f * q) * ld[u][1] + mw : dcj + mw;
+            } else {
+                const float i2q = 0.5f / q;
+                dn = dcj * i2q + (2.f * q - 1.f) * i2q * ld[u][2] + 3.f / q * wj * cku;
+            }
+            Store<T>::st(f + dst[u], dn);
+
+            const float m = dcj + dn;
+            Fd[0] += m * cjx;
+            Fd[1] += m * cjy;
+            Fd[2] += m * cjz;
+            Td[0] += m * (dy * cjz - dz * cjy);
+            Td[1] += m * (dz * cjx - dx * cjz);
+            Td[2] += m * (dx * cjy - dy * cjx);
+            const int w = rw36(j);
+            I[0] += w * cjx;
+            I[1] += w * cjy;
+            I[2] += w * cjz;
+            J[0] += w * (oy * cjz - oz * cjy);
+            J[1] += w * (oz * cjx - ox * cjz);
+            J[2] += w * (ox * cjy - oy * cjx);
+        }
     }
 
     // 4. the nodes of this sphere become "owned at the previous geometry"

@@ -135,8 +135,12 @@ def test_many_spheres_moving_lid_contacts_periodic_edges():
     kw = dict(tau0=0.6, cs=0.17, g=(2e-6, 0.0, 0.0), u_hi=(0.05, 0.0, 0.0), rho_s=2.5, kn=1e3,
               restitution=0.8, dem_substeps=16)
     lat, orc = make_pair(shape, parts=p, max_radius=5.0, **kw)
-    lat.step(100)
-    orc.step(100)
+    touched = False
+    for _ in range(10):
+        lat.step(10)
+        orc.step(10)
+        touched |= bool(np.abs(orc.contact_forces()[-4:-2]).max() > 0.0)
+    assert touched  # the head-on pair was in contact during the run
     assert np.array_equal(lat.owner(), orc.owner())
     assert pop_error(lat, orc) <= POP_TOL
     ef, et, Fo, To = force_error(lat, orc)
@@ -146,8 +150,6 @@ def test_many_spheres_moving_lid_contacts_periodic_edges():
     xt, vt = motion_tolerance(orc, 100)
     assert np.abs(Xg - Xo).max() < xt
     assert np.abs(Vg - Vo).max() < vt
-    # the head-on pair did collide
-    assert Vo[-4, 0] < 0.0 < Vo[-3, 0]
     info = lat.info()
     node, _, _, _ = orc.links()
     assert info["links"] == len(node)
