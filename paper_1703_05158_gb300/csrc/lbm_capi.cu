@@ -12,8 +12,9 @@ using namespace lbm;
 namespace {
 
 constexpr int kMaxNbr = 48;
-constexpr int kDemThreads = 128;
-constexpr double kSkin = 1.0;
+constexpr int kDemThreads = 128;   // fallback cooperative DEM
+constexpr double kSkin = 1.5;      // neighbour-list skin (lattice units)
+constexpr double kMaxStep = 0.25;  // largest displacement of a sphere in one step
 
 int status_to_code(int st) {
     if (st & ST_TIMEOUT) return LBM_ERR_TIMEOUT;
@@ -51,8 +52,9 @@ int dalloc(lbm_s *h, T **p, size_t n) {
 
 void release(lbm_s *h) {
     void *ptrs[] = {h->f, h->flag, h->owner, h->status, h->bar, h->ctr, h->pt.X, h->pt.V, h->pt.W, h->pt.R,
-                    (void *)h->pt.fixed, h->pt.Fh, h->pt.Th, h->pt.Fc, h->pt.Fx, h->pt.Tx, h->pt.Xgeo, h->pt.Xf,
-                    h->pt.Xb[0], h->pt.Xb[1], h->pt.Vh[0], h->pt.Vh[1], h->pt.nbr, h->pt.nbr_cnt};
+                    (void *)h->pt.fixed, h->pt.Fh, h->pt.Th, h->pt.Fc, h->pt.Fx, h->pt.Tx, h->pt.Xf,
+                    h->pt.Xb[0], h->pt.Xb[1], h->pt.Vh[0], h->pt.Vh[1], h->pt.nbr, h->pt.nbr_cnt, h->pt.pairA,
+                    h->pt.pairB, h->pt.Xbuild, h->pt.rebuild, h->pt.frame[0], h->pt.frame[1]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->status_host) cudaFreeHost(h->status_host);
@@ -228,6 +230,7 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     pt.rho_s = p.rho_particle;
     pt.substeps = p.dem_substeps;
     pt.skin = kSkin;
+    pt.max_step = kMaxStep;
     h->tile_ext = (int)std::ceil(M > 0 ? p.max_radius : 1.0) + 3;
     h->link_cap = link_capacity(M > 0 ? p.max_radius : 1.0);
 
@@ -249,7 +252,12 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     if (!rc) rc = dalloc(h, &pt.Fc, 3 * (size_t)M);
     if (!rc) rc = dalloc(h, &pt.Fx, 3 * (size_t)M);
     if (!rc) rc = dalloc(h, &pt.Tx, 3 * (size_t)M);
-    if (!rc) rc = dalloc(h, &pt.Xgeo, 3 * (size_t)M);
+    if (!rc) rc = dalloc(h, &pt.Xbuild, 3 * (size_t)M);
+    if (!rc) rc = dalloc(h, &pt.rebuild, 1);
+    if (!rc) rc = dalloc(h, &pt.frame[0], (size_t)M);
+    if (!rc) rc = dalloc(h, &pt.frame[1], (size_t)M);
+    if (!rc) rc = dalloc(h, &pt.pairA, (size_t)M * kMaxNbr);
+    if (!rc) rc = dalloc(h, &pt.pairB, (size_t)M * kMaxNbr);
     if (!rc) rc = dalloc(h, &pt.Xf, (size_t)M);
     for (int b = 0; b < 2 && !rc; ++b) {
         rc = dalloc(h, &pt.Xb[b], 3 * (size_t)M);
@@ -320,12 +328,33 @@ int lbm_set_particles(lbm_handle h, int32_t n, const double *pos, const double *
     const size_t v3 = 3 * sizeof(double) * (size_t)n;
     int rc = LBM_OK;
     float4 *xf = n ? (float4 *)std::malloc(sizeof(float4) * (size_t)n) : nullptr;
-    if (n && !xf) return LBM_ERR_NOMEM;
-    for (int a = 0; a < n; ++a)
+    SFrame *fr = n ? (SFrame *)std::malloc(sizeof(SFrame) * (size_t)n) : nullptr;
+    if (n && (!xf || !fr)) {
+        std::free(xf);
+        std::free(fr);
+        return LBM_ERR_NOMEM;
+    }
+    for (int a = 0; a < n; ++a) {
         xf[a] = make_float4((float)pos[3 * a], (float)pos[3 * a + 1], (float)pos[3 * a + 2], (float)radius[a]);
+        // the same operations as the device frame of the DEM commit
+        SFrame &F = fr[a];
+        for (int c = 0; c < 3; ++c) {
+            const double b = std::floor(pos[3 * a + c]);
+            F.b[c] = (int)b;
+            F.fr[c] = (float)(pos[3 * a + c] - b);
+            F.V[c] = (float)vel[3 * a + c];
+            F.W[c] = (float)omega[3 * a + c];
+        }
+        F.R = (float)radius[a];
+        F.R2 = F.R * F.R;
+        F.pad[0] = F.pad[1] = 0.f;
+    }
     if (!rc) rc = copy_in(h, pt.X, pos, v3, LBM_HOST);
-    if (!rc) rc = copy_in(h, pt.Xgeo, pos, v3, LBM_HOST);
+    if (!rc) rc = copy_in(h, pt.Xbuild, pos, v3, LBM_HOST);
     if (!rc) rc = copy_in(h, pt.Xf, xf, sizeof(float4) * (size_t)n, LBM_HOST);
+    if (!rc) rc = copy_in(h, pt.frame[0], fr, sizeof(SFrame) * (size_t)n, LBM_HOST);
+    if (!rc) rc = copy_in(h, pt.frame[1], fr, sizeof(SFrame) * (size_t)n, LBM_HOST);
+    if (!rc && n && cudaMemsetAsync(pt.rebuild, 0, sizeof(int), h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
     if (!rc) rc = copy_in(h, pt.V, vel, v3, LBM_HOST);
     if (!rc) rc = copy_in(h, pt.W, omega, v3, LBM_HOST);
     if (!rc) rc = copy_in(h, pt.R, radius, sizeof(double) * (size_t)n, LBM_HOST);
@@ -343,13 +372,14 @@ int lbm_set_particles(lbm_handle h, int32_t n, const double *pos, const double *
     if (!rc && cudaMemsetAsync(h->owner, 0xff, (size_t)h->L.N * 4, h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
     if (!rc && cudaMemsetAsync(h->ctr, 0, 4 * sizeof(unsigned long long), h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
     pt.np = n;
-    if (!rc && n) rc = launch_neighbours(h);
-    if (!rc && n) rc = launch_mark(h);
-    if (!rc && n) rc = launch_contact(h);
     h->parity = 0;
     h->steps = 0;
+    if (!rc && n) rc = launch_neighbours(h, 1);
+    if (!rc && n) rc = launch_mark(h);
+    if (!rc && n) rc = launch_contact(h);
     if (!rc) rc = settle(h);
     std::free(xf);
+    std::free(fr);
     if (rc == LBM_ERR_CUDA && !h->sticky) h->sticky = rc;
     return rc;
 }
@@ -422,7 +452,7 @@ int lbm_step(lbm_handle h, int32_t nsteps) {
         if (!rc) rc = prof_mark(h, 2);
         if (!rc && parts) rc = launch_links(h, P);
         if (!rc) rc = prof_mark(h, 3);
-        if (!rc && parts) rc = launch_neighbours(h);
+        if (!rc && parts) rc = launch_neighbours(h, 0);
         if (!rc && parts) rc = launch_dem(h);
         if (!rc) rc = prof_mark(h, 4);
         if (!rc) {

@@ -7,21 +7,30 @@
 // gives a normal restitution of exactly e.  A fixed sphere moves with its
 // prescribed velocity and acts with infinite mass.
 //
-// Precision: centres, velocities and spins are integrated in FP64 (their
-// drift needs it); the contact decision and the overlap delta are FP64 (delta
-// is a small difference of O(R) numbers), the force law is FP32 and the
-// per-sphere sums FP64.  FP64 throughput is low on this GPU, so the O(P^2)
-// neighbour search runs in FP32 on a float copy of the centres with a skin of
-// one lattice unit; a sphere that moves half a skin in one step raises the
-// geometry error.
+// Precision.  Centres and velocities are FP64 and are updated once per
+// lattice step, x <- x0 + dx, v <- v0 + dv, so their drift is FP64.  Within
+// the step the sub-steps advance only the displacement dx and the velocity
+// change dv, which are small, in FP32 (FP64 throughput on this GPU is ~1/64
+// of FP32).  The overlap of a listed pair is evaluated without cancellation
+// from FP64 start-of-step data: with d0 = x0_a - x0_b and
+// c0 = (R_a + R_b)^2 - |d0|^2 (both FP64, once per step),
+//   c = c0 - 2 d0.D - D.D,  D = dx_a - dx_b,   delta = c / (R_a + R_b + |d0 + D|),
+// so delta keeps ~1e-8 absolute accuracy although |d0| ~ 2R.  Contact
+// forces are summed in FP32 per sub-step; the spin is advanced once per step
+// (the torque is constant over it).
 //
-// Sub-steps need all centres of the previous sub-step.  One thread-block
-// cluster runs all of them: each thread keeps its spheres in registers, the
-// new centres and half-step velocities go through distributed shared memory,
-// and a hardware cluster barrier (release / acquire) separates drift and
-// force.
-// Too many spheres for one cluster fall back to a cooperative launch with a
-// bounded software grid barrier.
+// Sub-steps need every sphere's displacement of the previous sub-step.  One
+// thread-block cluster runs all of them: each thread keeps its spheres in
+// registers, publishes (dx, dv) in its CTA's shared memory (double-buffered by
+// sub-step parity) and reads neighbours' through distributed shared memory;
+// a hardware cluster barrier (release / acquire) separates drift and force.
+// More spheres than one cluster holds fall back to a cooperative launch with
+// a bounded software grid barrier.
+//
+// Neighbour lists (pairs within R_a + R_b + skin, FP32 search) are rebuilt
+// only when a sphere has moved more than skin/2 - max_step since the last
+// build; every sphere moving less than max_step per step (else the geometry
+// error is raised) keeps every pair that can touch within a step in the list.
 #include <cooperative_groups.h>
 
 #include "lbm_internal.cuh"
@@ -37,56 +46,89 @@ __device__ __forceinline__ double sphere_mass(const Parts &pt, int a) {
     return pt.rho_s * (4.0 / 3.0) * kPi * r * r * r;
 }
 
-// Neighbour list of sphere a: every b != a with |X_a - X_b| < R_a + R_b + skin
-// (minimum image in x, y), in increasing b.  One warp per sphere; centres are
-// staged through shared memory in tiles.
+__device__ __forceinline__ void min_image(const Lat &L, double d[3]) {
+    if (d[0] > 0.5 * L.nx) d[0] -= L.nx;
+    if (d[0] < -0.5 * L.nx) d[0] += L.nx;
+    if (d[1] > 0.5 * L.ny) d[1] -= L.ny;
+    if (d[1] < -0.5 * L.ny) d[1] += L.ny;
+}
+
+// One warp per sphere.  If a rebuild is due (or forced), list every b != a
+// with |X_a - X_b| < R_a + R_b + skin in increasing b (centres staged through
+// shared memory); then compute the pair constants of every list entry for
+// the current centres and velocities:
+//   pairA = (d0, c0),  d0 = X_a - X_b (minimum image), c0 = (R_a+R_b)^2 - |d0|^2
+//   pairB = (V_a - V_b, gamma_n)
 constexpr int kNbrTile = 1024;
 
-__global__ void __launch_bounds__(256) k_neighbours(const Lat L, const Parts pt, int *__restrict__ status) {
+__global__ void __launch_bounds__(256) k_neighbours(const Lat L, const Parts pt, const int step, const int force,
+                                                    int *__restrict__ status) {
     __shared__ float4 tile[kNbrTile];
     const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const bool live = a < pt.np;
-    float4 me = live ? pt.Xf[a] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float ra = me.w + (float)pt.skin;
-    const float hx = 0.5f * L.nx, hy = 0.5f * L.ny;
-    int cnt = 0;
-    for (int t0 = 0; t0 < pt.np; t0 += kNbrTile) {
-        const int tn = min(kNbrTile, pt.np - t0);
-        __syncthreads();
-        for (int i = threadIdx.x; i < tn; i += blockDim.x) tile[i] = pt.Xf[t0 + i];
-        __syncthreads();
-        if (!live) continue;
-        for (int base = 0; base < tn; base += 32) {
-            const int i = base + lane, b = t0 + i;
-            bool ok = false;
-            if (i < tn && b != a) {
-                const float4 o = tile[i];
-                float dx = me.x - o.x, dy = me.y - o.y;
-                const float dz = me.z - o.z;
-                if (dx > hx) dx -= L.nx;
-                if (dx < -hx) dx += L.nx;
-                if (dy > hy) dy -= L.ny;
-                if (dy < -hy) dy += L.ny;
-                const float cut = ra + o.w;
-                ok = dx * dx + dy * dy + dz * dz < cut * cut;
+    const bool rebuild = force || *(volatile int *)pt.rebuild >= step;
+    if (rebuild) {
+        float4 me = live ? pt.Xf[a] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float ra = me.w + (float)pt.skin;
+        const float hx = 0.5f * L.nx, hy = 0.5f * L.ny;
+        int cnt = 0;
+        for (int t0 = 0; t0 < pt.np; t0 += kNbrTile) {
+            const int tn = min(kNbrTile, pt.np - t0);
+            __syncthreads();
+            for (int i = threadIdx.x; i < tn; i += blockDim.x) tile[i] = pt.Xf[t0 + i];
+            __syncthreads();
+            if (!live) continue;
+            for (int base = 0; base < tn; base += 32) {
+                const int i = base + lane, b = t0 + i;
+                bool ok = false;
+                if (i < tn && b != a) {
+                    const float4 o = tile[i];
+                    float dx = me.x - o.x, dy = me.y - o.y;
+                    const float dz = me.z - o.z;
+                    if (dx > hx) dx -= L.nx;
+                    if (dx < -hx) dx += L.nx;
+                    if (dy > hy) dy -= L.ny;
+                    if (dy < -hy) dy += L.ny;
+                    const float cut = ra + o.w;
+                    ok = dx * dx + dy * dy + dz * dz < cut * cut;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, ok);
+                if (ok) {
+                    const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+                    if (pos < pt.max_nbr) pt.nbr[(long long)a * pt.max_nbr + pos] = b;
+                }
+                cnt += __popc(m);
             }
-            const unsigned m = __ballot_sync(0xffffffffu, ok);
-            if (ok) {
-                const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-                if (pos < pt.max_nbr) pt.nbr[(long long)a * pt.max_nbr + pos] = b;
-            }
-            cnt += __popc(m);
         }
+        if (live && lane == 0) {
+            pt.nbr_cnt[a] = min(cnt, pt.max_nbr);
+            if (cnt > pt.max_nbr) atomicOr(status, ST_NBR_OVERFLOW);
+        }
+        if (live && lane < 3) pt.Xbuild[3 * a + lane] = pt.X[3 * a + lane];
+        __syncwarp();
     }
-    if (live && lane == 0) {
-        pt.nbr_cnt[a] = min(cnt, pt.max_nbr);
-        if (cnt > pt.max_nbr) atomicOr(status, ST_NBR_OVERFLOW);
+    if (!live) return;
+    const int cnt = pt.nbr_cnt[a];
+    for (int m = lane; m < cnt; m += 32) {
+        const int b = pt.nbr[(long long)a * pt.max_nbr + m];
+        double d[3] = {pt.X[3 * a] - pt.X[3 * b], pt.X[3 * a + 1] - pt.X[3 * b + 1], pt.X[3 * a + 2] - pt.X[3 * b + 2]};
+        min_image(L, d);
+        const double Rs = pt.R[a] + pt.R[b];
+        const double c0 = Rs * Rs - (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const double ma = sphere_mass(pt, a), mb = sphere_mass(pt, b);
+        const double meff = pt.fixed[b] ? ma : (pt.fixed[a] ? mb : ma * mb / (ma + mb));
+        const float gam = (float)pt.ce * sqrtf((float)(meff * pt.kn));
+        const long long e = (long long)a * pt.max_nbr + m;
+        pt.pairA[e] = make_float4((float)d[0], (float)d[1], (float)d[2], (float)c0);
+        pt.pairB[e] = make_float4((float)(pt.V[3 * a] - pt.V[3 * b]), (float)(pt.V[3 * a + 1] - pt.V[3 * b + 1]),
+                                  (float)(pt.V[3 * a + 2] - pt.V[3 * b + 2]), gam);
     }
 }
 
 // Contact force on sphere a at centre xa, velocity va, given the centres Xs
-// and velocities Vs of all spheres (FP64 arrays).
+// and velocities Vs of all spheres (FP64 throughout; used for the initial
+// contact force and by the cooperative fallback).
 __device__ void contact_force(const Lat &L, const Parts &pt, int a, const double xa[3], const double va[3],
                               const double *Xs, const double *Vs, double F[3]) {
     F[0] = F[1] = F[2] = 0.0;
@@ -97,10 +139,7 @@ __device__ void contact_force(const Lat &L, const Parts &pt, int a, const double
     for (int m = 0; m < cnt; ++m) {
         const int b = pt.nbr[(long long)a * pt.max_nbr + m];
         double d[3] = {xa[0] - Xs[3 * b], xa[1] - Xs[3 * b + 1], xa[2] - Xs[3 * b + 2]};
-        if (d[0] > 0.5 * L.nx) d[0] -= L.nx;
-        if (d[0] < -0.5 * L.nx) d[0] += L.nx;
-        if (d[1] > 0.5 * L.ny) d[1] -= L.ny;
-        if (d[1] < -0.5 * L.ny) d[1] += L.ny;
+        min_image(L, d);
         const double Rs = Ra + pt.R[b];
         const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
         if (!(d2 < Rs * Rs)) continue;
@@ -141,20 +180,45 @@ __device__ __forceinline__ void wrap_pos(const Lat &L, double *x) {
     if (x[1] < 0.0) x[1] += L.ny;
 }
 
-// After the last sub-step: commit the centres (and their FP32 copy) and flag
-// a sphere that moved half a skin in the step or left the box.
-__device__ __forceinline__ void commit(const Lat &L, const Parts &pt, int a, const double x[3], int *status) {
-    double m2 = 0.0;
+__device__ __forceinline__ SFrame make_frame(const double x[3], double R, const double v[3], const double w[3]) {
+    SFrame F;
     for (int c = 0; c < 3; ++c) {
-        double dd = x[c] - pt.Xgeo[3 * a + c];
-        const double n = c == 0 ? L.nx : (c == 1 ? L.ny : 1e300);
-        if (dd > 0.5 * n) dd -= n;
-        if (dd < -0.5 * n) dd += n;
-        m2 += dd * dd;
+        const double b = floor(x[c]);
+        F.b[c] = (int)b;
+        F.fr[c] = __double2float_rn(x[c] - b);
+        F.V[c] = (float)v[c];
+        F.W[c] = (float)w[c];
+    }
+    F.R = __double2float_rn(R);
+    F.R2 = __fmul_rn(F.R, F.R);
+    F.pad[0] = F.pad[1] = 0.f;
+    return F;
+}
+
+// End of a step for sphere a: store the new state and its frame, flag a sphere
+// that moved max_step in the step (or left the box), request a list rebuild
+// when it drifted skin/2 - max_step from where the lists were built.
+__device__ __forceinline__ void commit(const Lat &L, const Parts &pt, SFrame *fnext, int a, const double x[3],
+                                       const double v[3], const double w[3], const double fc[3], double moved2,
+                                       int step, int *status) {
+    double b2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        double dd = x[c] - pt.Xbuild[3 * a + c];
+        if (c == 0 && dd > 0.5 * L.nx) dd -= L.nx;
+        if (c == 0 && dd < -0.5 * L.nx) dd += L.nx;
+        if (c == 1 && dd > 0.5 * L.ny) dd -= L.ny;
+        if (c == 1 && dd < -0.5 * L.ny) dd += L.ny;
+        b2 += dd * dd;
         pt.X[3 * a + c] = x[c];
+        pt.V[3 * a + c] = v[c];
+        pt.W[3 * a + c] = w[c];
+        pt.Fc[3 * a + c] = fc[c];
     }
     pt.Xf[a] = make_float4((float)x[0], (float)x[1], (float)x[2], (float)pt.R[a]);
-    if (!(m2 < 0.25 * pt.skin * pt.skin) || !(x[2] > -0.5 && x[2] < L.nz - 0.5)) atomicOr(status, ST_FAST);
+    fnext[a] = make_frame(x, pt.R[a], v, w);
+    if (!(moved2 < pt.max_step * pt.max_step) || !(x[2] > -0.5 && x[2] < L.nz - 0.5)) atomicOr(status, ST_FAST);
+    const double lim = 0.5 * pt.skin - pt.max_step;
+    if (!(b2 < lim * lim)) atomicMax(pt.rebuild, step + 1);
 }
 
 __device__ __forceinline__ void cluster_barrier() {
@@ -162,61 +226,61 @@ __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
-// All sub-steps of one lattice step in one cluster (gridDim.x CTAs).  Thread
-// t of CTA c owns spheres a = c T + t + q G (q < kDemKmax, G = cluster
-// threads) and keeps their state in registers; after each drift it publishes
-// centre and half-step velocity in its CTA's shared memory (double-buffered
-// by sub-step parity), where the force phase of every CTA reads them through
-// distributed shared memory.
-__global__ void __launch_bounds__(kDemThreads, 1) k_dem_cluster(const Lat L, const Parts pt, int *status) {
-    extern __shared__ double dsm[];  // [2][kDemKmax * T][6]: x, y, z, vx, vy, vz
+// All sub-steps of lattice step `step` in one cluster (gridDim.x CTAs).
+// Thread t of CTA c owns spheres a = c T + t + q G (q < kDemKmax, G = cluster
+// threads).
+__global__ void __launch_bounds__(kDemThreads, 1) k_dem_cluster(const Lat L, const Parts pt, SFrame *fnext,
+                                                                const int step, int *status) {
+    extern __shared__ float4 dsm[];  // [2][kDemKmax * T][2]: (dx, -), (dv, -)
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const int T = blockDim.x, G = gridDim.x * T, cap = kDemKmax * T;
     const int g0 = blockIdx.x * T + threadIdx.x;
     const int ns = pt.substeps;
-    const double h = 1.0 / ns;
+    const float h = 1.f / ns, h2 = 0.5f * h;
     const float kn = (float)pt.kn, ce = (float)pt.ce;
-    double x[kDemKmax][3], v[kDemKmax][3], w[kDemKmax][3], F0[kDemKmax][3], T0[kDemKmax][3], fc[kDemKmax][3];
-    double km[kDemKmax], kI[kDemKmax], Ra[kDemKmax], ma[kDemKmax];
+    float3 dx[kDemKmax], dv[kDemKmax], v0[kDemKmax], fa[kDemKmax], fc[kDemKmax];
+    float im[kDemKmax], Rf[kDemKmax], Llo[kDemKmax], Lhi[kDemKmax], gw[kDemKmax];
     int nc[kDemKmax];
     bool fx[kDemKmax];
 #pragma unroll
     for (int q = 0; q < kDemKmax; ++q) {
         const int a = g0 + q * G;
         if (a >= pt.np) break;
-        Ra[q] = pt.R[a];
-        ma[q] = sphere_mass(pt, a);
+        const double m = sphere_mass(pt, a), R = pt.R[a], z0 = pt.X[3 * a + 2];
         fx[q] = pt.fixed[a] != 0;
-        km[q] = fx[q] ? 0.0 : h / (2.0 * ma[q]);
-        kI[q] = fx[q] ? 0.0 : h / (0.4 * ma[q] * Ra[q] * Ra[q]);
+        const double ia = 1.0 / m;
+        im[q] = (float)ia;
+        Rf[q] = (float)R;
+        fa[q] = make_float3((float)((pt.Fh[3 * a] + pt.Fx[3 * a]) * ia), (float)((pt.Fh[3 * a + 1] + pt.Fx[3 * a + 1]) * ia),
+                            (float)((pt.Fh[3 * a + 2] + pt.Fx[3 * a + 2]) * ia));
+        fc[q] = make_float3((float)pt.Fc[3 * a], (float)pt.Fc[3 * a + 1], (float)pt.Fc[3 * a + 2]);
+        v0[q] = make_float3((float)pt.V[3 * a], (float)pt.V[3 * a + 1], (float)pt.V[3 * a + 2]);
+        Llo[q] = (float)(R - (z0 + 0.5));
+        Lhi[q] = (float)(R - ((L.nz - 0.5) - z0));
+        gw[q] = ce * sqrtf((float)m * kn);
         nc[q] = pt.nbr_cnt[a];
-        for (int c = 0; c < 3; ++c) {
-            x[q][c] = pt.X[3 * a + c];
-            v[q][c] = pt.V[3 * a + c];
-            w[q][c] = pt.W[3 * a + c];
-            F0[q][c] = pt.Fh[3 * a + c] + pt.Fx[3 * a + c];
-            T0[q][c] = pt.Th[3 * a + c] + pt.Tx[3 * a + c];
-            fc[q][c] = pt.Fc[3 * a + c];
-        }
+        dx[q] = make_float3(0.f, 0.f, 0.f);
+        dv[q] = make_float3(0.f, 0.f, 0.f);
     }
     cluster_barrier();  // every CTA of the cluster is running before shared memory is shared
     for (int s = 0; s < ns; ++s) {
-        double *buf = dsm + (size_t)((s + 1) & 1) * cap * 6;
+        float4 *buf = dsm + (size_t)((s + 1) & 1) * cap * 2;
 #pragma unroll
         for (int q = 0; q < kDemKmax; ++q) {
             const int a = g0 + q * G;
             if (a >= pt.np) break;
-            for (int c = 0; c < 3; ++c) {
-                v[q][c] += (F0[q][c] + fc[q][c]) * km[q];  // half kick (fixed: km = 0)
-                x[q][c] += v[q][c] * h;
+            if (!fx[q]) {  // half kick
+                dv[q].x += (fa[q].x + fc[q].x * im[q]) * h2;
+                dv[q].y += (fa[q].y + fc[q].y * im[q]) * h2;
+                dv[q].z += (fa[q].z + fc[q].z * im[q]) * h2;
             }
-            wrap_pos(L, x[q]);
-            double *me = buf + (size_t)(q * T + threadIdx.x) * 6;
-            for (int c = 0; c < 3; ++c) {
-                me[c] = x[q][c];
-                me[3 + c] = v[q][c];
-            }
+            dx[q].x += (v0[q].x + dv[q].x) * h;
+            dx[q].y += (v0[q].y + dv[q].y) * h;
+            dx[q].z += (v0[q].z + dv[q].z) * h;
+            float4 *me = buf + (size_t)(q * T + threadIdx.x) * 2;
+            me[0] = make_float4(dx[q].x, dx[q].y, dx[q].z, 0.f);
+            me[1] = make_float4(dv[q].x, dv[q].y, dv[q].z, 0.f);
         }
         cluster_barrier();
 #pragma unroll
@@ -224,45 +288,38 @@ __global__ void __launch_bounds__(kDemThreads, 1) k_dem_cluster(const Lat L, con
             const int a = g0 + q * G;
             if (a >= pt.np) break;
             if (fx[q]) continue;
-            double F[3] = {0.0, 0.0, 0.0};
+            float3 F = make_float3(0.f, 0.f, 0.f);
             for (int m = 0; m < nc[q]; ++m) {
-                const int b = __ldg(pt.nbr + (long long)a * pt.max_nbr + m);
+                const long long e = (long long)a * pt.max_nbr + m;
+                const int b = __ldg(pt.nbr + e);
+                const float4 A = __ldg(pt.pairA + e), Bv = __ldg(pt.pairB + e);
                 const int qb = b / G, rb = b - qb * G, cb = rb / T, tb = rb - cb * T;
-                const double *o = cluster.map_shared_rank(buf + (size_t)(qb * T + tb) * 6, cb);
-                double d[3] = {x[q][0] - o[0], x[q][1] - o[1], x[q][2] - o[2]};
-                if (d[0] > 0.5 * L.nx) d[0] -= L.nx;
-                if (d[0] < -0.5 * L.nx) d[0] += L.nx;
-                if (d[1] > 0.5 * L.ny) d[1] -= L.ny;
-                if (d[1] < -0.5 * L.ny) d[1] += L.ny;
-                const double Rb = __ldg(pt.R + b);
-                const double Rs = Ra[q] + Rb;
-                const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                if (!(d2 < Rs * Rs)) continue;
-                const double dist = sqrt(d2);
-                const double delta = Rs - dist;
-                if (!(delta > 0.0) || dist == 0.0) continue;
-                const float id = (float)(1.0 / dist);
-                const float nx = (float)d[0] * id, ny = (float)d[1] * id, nz = (float)d[2] * id;
-                const float vn = (float)(v[q][0] - o[3]) * nx + (float)(v[q][1] - o[4]) * ny +
-                                 (float)(v[q][2] - o[5]) * nz;
-                const double mb = pt.rho_s * (4.0 / 3.0) * kPi * Rb * Rb * Rb;
-                const double meff = __ldg(pt.fixed + b) ? ma[q] : ma[q] * mb / (ma[q] + mb);
-                const float fn = kn * (float)delta - ce * sqrtf((float)meff * kn) * vn;
-                F[0] += (double)(fn * nx);
-                F[1] += (double)(fn * ny);
-                F[2] += (double)(fn * nz);
+                const float4 *o = cluster.map_shared_rank(buf + (size_t)(qb * T + tb) * 2, cb);
+                const float4 ox = o[0], ov = o[1];
+                const float Dx = dx[q].x - ox.x, Dy = dx[q].y - ox.y, Dz = dx[q].z - ox.z;
+                const float c = A.w - 2.f * (A.x * Dx + A.y * Dy + A.z * Dz) - (Dx * Dx + Dy * Dy + Dz * Dz);
+                if (!(c > 0.f)) continue;
+                const float ex = A.x + Dx, ey = A.y + Dy, ez = A.z + Dz;
+                const float dist = sqrtf(ex * ex + ey * ey + ez * ez);
+                const float Rs = Rf[q] + __ldg(&pt.Xf[b].w);
+                const float delta = c / (Rs + dist);
+                const float id = 1.f / dist;
+                const float nx = ex * id, ny = ey * id, nz = ez * id;
+                const float vn = (Bv.x + dv[q].x - ov.x) * nx + (Bv.y + dv[q].y - ov.y) * ny + (Bv.z + dv[q].z - ov.z) * nz;
+                const float fn = kn * delta - Bv.w * vn;
+                F.x += fn * nx;
+                F.y += fn * ny;
+                F.z += fn * nz;
             }
-            const float gw = ce * sqrtf((float)ma[q] * kn);
-            const float vz = (float)v[q][2];
-            const double lo = Ra[q] - (x[q][2] + 0.5);
-            if (lo > 0.0) F[2] += (double)(kn * (float)lo - gw * vz);
-            const double hi = Ra[q] - ((L.nz - 0.5) - x[q][2]);
-            if (hi > 0.0) F[2] -= (double)(kn * (float)hi + gw * vz);
-            for (int c = 0; c < 3; ++c) {
-                fc[q][c] = F[c];
-                v[q][c] += (F0[q][c] + F[c]) * km[q];
-                w[q][c] += T0[q][c] * kI[q];
-            }
+            const float vz = v0[q].z + dv[q].z;
+            const float lo = Llo[q] - dx[q].z;
+            if (lo > 0.f) F.z += kn * lo - gw[q] * vz;
+            const float hi = Lhi[q] + dx[q].z;
+            if (hi > 0.f) F.z -= kn * hi + gw[q] * vz;
+            fc[q] = F;
+            dv[q].x += (fa[q].x + F.x * im[q]) * h2;
+            dv[q].y += (fa[q].y + F.y * im[q]) * h2;
+            dv[q].z += (fa[q].z + F.z * im[q]) * h2;
         }
     }
     cluster_barrier();  // no CTA leaves while another may still read its shared memory
@@ -270,16 +327,25 @@ __global__ void __launch_bounds__(kDemThreads, 1) k_dem_cluster(const Lat L, con
     for (int q = 0; q < kDemKmax; ++q) {
         const int a = g0 + q * G;
         if (a >= pt.np) break;
-        for (int c = 0; c < 3; ++c) {
-            pt.V[3 * a + c] = v[q][c];
-            pt.W[3 * a + c] = w[q][c];
-            pt.Fc[3 * a + c] = fc[q][c];
+        double x[3] = {pt.X[3 * a] + (double)dx[q].x, pt.X[3 * a + 1] + (double)dx[q].y, pt.X[3 * a + 2] + (double)dx[q].z};
+        wrap_pos(L, x);
+        double v[3] = {pt.V[3 * a], pt.V[3 * a + 1], pt.V[3 * a + 2]};
+        double w[3] = {pt.W[3 * a], pt.W[3 * a + 1], pt.W[3 * a + 2]};
+        if (!fx[q]) {
+            const double m = sphere_mass(pt, a);
+            const double iI = 1.0 / (0.4 * m * pt.R[a] * pt.R[a]);
+            v[0] += (double)dv[q].x;
+            v[1] += (double)dv[q].y;
+            v[2] += (double)dv[q].z;
+            for (int c = 0; c < 3; ++c) w[c] += (pt.Th[3 * a + c] + pt.Tx[3 * a + c]) * iI;
         }
-        commit(L, pt, a, x[q], status);
+        const double f3[3] = {(double)fc[q].x, (double)fc[q].y, (double)fc[q].z};
+        const double moved2 = (double)(dx[q].x * dx[q].x + dx[q].y * dx[q].y + dx[q].z * dx[q].z);
+        commit(L, pt, fnext, a, x, v, w, f3, moved2, step, status);
     }
 }
 
-static size_t dem_cluster_smem() { return (size_t)2 * kDemKmax * kDemThreads * 6 * sizeof(double); }
+static size_t dem_cluster_smem() { return (size_t)2 * kDemKmax * kDemThreads * 2 * sizeof(float4); }
 
 // ---- fallback: cooperative grid with a bounded software barrier ------------
 
@@ -315,7 +381,12 @@ __device__ bool grid_barrier(unsigned *bar, unsigned target, int *status) {
     return ok != 0;
 }
 
-__global__ void __launch_bounds__(128) k_dem(const Lat L, const Parts pt, unsigned *bar, int *status) {
+// FP64 velocity Verlet with centres and half-step velocities exchanged
+// through global memory (any number of spheres).  pt.V holds the full-step
+// velocity between sub-steps; pt.X stays the start-of-step centre until the
+// commit.
+__global__ void __launch_bounds__(128) k_dem(const Lat L, const Parts pt, SFrame *fnext, const int step,
+                                             unsigned *bar, int *status) {
     const int G = gridDim.x * blockDim.x;
     const int g0 = blockIdx.x * blockDim.x + threadIdx.x;
     const int ns = pt.substeps;
@@ -341,25 +412,36 @@ __global__ void __launch_bounds__(128) k_dem(const Lat L, const Parts pt, unsign
             if (pt.fixed[a]) continue;
             double F[3];
             contact_force(L, pt, a, Xn + 3 * a, Vn + 3 * a, Xn, Vn, F);
-            const double m = sphere_mass(pt, a);
-            const double k = h / (2.0 * m), kI = h / (0.4 * m * pt.R[a] * pt.R[a]);
+            const double k = h / (2.0 * sphere_mass(pt, a));
             for (int c = 0; c < 3; ++c) {
-                pt.V[3 * a + c] = Vn[3 * a + c] + (pt.Fh[3 * a + c] + pt.Fx[3 * a + c] + F[c]) * k;
-                pt.W[3 * a + c] += (pt.Th[3 * a + c] + pt.Tx[3 * a + c]) * kI;
                 pt.Fc[3 * a + c] = F[c];
+                pt.V[3 * a + c] = Vn[3 * a + c] + (pt.Fh[3 * a + c] + pt.Fx[3 * a + c] + F[c]) * k;
             }
         }
     }
     const double *Xe = pt.Xb[ns & 1];
     for (int a = g0; a < pt.np; a += G) {
-        double x[3] = {Xe[3 * a], Xe[3 * a + 1], Xe[3 * a + 2]};
-        commit(L, pt, a, x, status);
+        double x[3], v[3], w[3], f3[3], moved2 = 0.0;
+        const double iI = pt.fixed[a] ? 0.0 : 1.0 / (0.4 * sphere_mass(pt, a) * pt.R[a] * pt.R[a]);
+        for (int c = 0; c < 3; ++c) {
+            x[c] = Xe[3 * a + c];
+            v[c] = pt.V[3 * a + c];
+            w[c] = pt.W[3 * a + c] + (pt.Th[3 * a + c] + pt.Tx[3 * a + c]) * iI;
+            f3[c] = pt.Fc[3 * a + c];
+            double dd = x[c] - pt.X[3 * a + c];
+            if (c == 0 && dd > 0.5 * L.nx) dd -= L.nx;
+            if (c == 0 && dd < -0.5 * L.nx) dd += L.nx;
+            if (c == 1 && dd > 0.5 * L.ny) dd -= L.ny;
+            if (c == 1 && dd < -0.5 * L.ny) dd += L.ny;
+            moved2 += dd * dd;
+        }
+        commit(L, pt, fnext, a, x, v, w, f3, moved2, step, status);
     }
 }
 
-int launch_neighbours(lbm_s *h) {
+int launch_neighbours(lbm_s *h, int force) {
     const int blocks = (h->pt.np * 32 + 255) / 256;
-    k_neighbours<<<blocks, 256, 0, h->stream>>>(h->L, h->pt, h->status);
+    k_neighbours<<<blocks, 256, 0, h->stream>>>(h->L, h->pt, (int)h->steps, force, h->status);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
@@ -376,13 +458,13 @@ int dem_max_blocks(int threads, int *blocks_per_sm) {
 // Largest cluster (16, else 8) that can run k_dem_cluster; 0 if none, or if
 // max_particles does not fit its registers.
 int dem_cluster_setup(int max_particles) {
+    if (cudaFuncSetAttribute(k_dem_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dem_cluster_smem()) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     for (int cl : {16, 8}) {
         if ((long long)cl * kDemThreads * kDemKmax < max_particles) continue;
-        if (cudaFuncSetAttribute(k_dem_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)dem_cluster_smem()) != cudaSuccess) {
-            cudaGetLastError();
-            return 0;
-        }
         if (cl > 8 && cudaFuncSetAttribute(k_dem_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                           cudaSuccess) {
             cudaGetLastError();
@@ -410,6 +492,8 @@ int launch_dem(lbm_s *h) {
     Lat L = h->L;
     Parts pt = h->pt;
     int *status = h->status;
+    SFrame *fnext = h->pt.frame[(h->steps + 1) & 1];
+    const int step = (int)h->steps;
     if (h->dem_cluster > 0) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
@@ -423,14 +507,15 @@ int launch_dem(lbm_s *h) {
         cfg.stream = h->stream;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, k_dem_cluster, L, pt, status) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+        return cudaLaunchKernelEx(&cfg, k_dem_cluster, L, pt, fnext, step, status) == cudaSuccess ? LBM_OK
+                                                                                                 : LBM_ERR_CUDA;
     }
     if (cudaMemsetAsync(h->bar, 0, sizeof(unsigned), h->stream) != cudaSuccess) return LBM_ERR_CUDA;
     int blocks = (h->pt.np + h->dem_threads - 1) / h->dem_threads;
     if (blocks > h->dem_blocks) blocks = h->dem_blocks;
     if (blocks < 1) blocks = 1;
     unsigned *bar = h->bar;
-    void *args[] = {&L, &pt, &bar, &status};
+    void *args[] = {&L, &pt, &fnext, (void *)&step, &bar, &status};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_dem, dim3(blocks), dim3(h->dem_threads), args, 0,
                                                 h->stream);
     return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;

@@ -17,33 +17,14 @@
 //           neighbours fluid before and after (flag 0), then become 2.
 //
 // Inside tests and keys are FP32 on relative coordinates
-// (float)(x - b) - (float)(X - b), b = floor(X), evaluated with
+// (float)(x - b) - (float)(X - b), b = floor(X) (the sphere frames written
+// by the DEM, see SFrame), evaluated with
 // round-to-nearest intrinsics so that no multiply-add is contracted: the
 // same operations, in the same order, as the FP64 oracle uses for its
 // geometric decisions, so both sides classify every node identically.
 #include "lbm_internal.cuh"
 
 namespace lbm {
-
-// Per-sphere FP32 frame: integer base b = floor(X) and fraction X - b.
-struct Frame {
-    int b[3];
-    float fr[3];
-    float R, R2;
-};
-
-__device__ __forceinline__ Frame frame_of(const double *X, double R) {
-    Frame F;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const double bb = floor(X[a]);
-        F.b[a] = (int)bb;
-        F.fr[a] = __double2float_rn(X[a] - bb);
-    }
-    F.R = __double2float_rn(R);
-    F.R2 = __fmul_rn(F.R, F.R);
-    return F;
-}
 
 __device__ __forceinline__ float rel(int o, float fr) { return __fsub_rn((float)o, fr); }
 
@@ -62,24 +43,25 @@ __device__ __forceinline__ int fold(int x, int b, int n) {
     return d;
 }
 
-__device__ __forceinline__ int ceil_r(double R) { return (int)ceil(R); }
+// Half width of the box holding every node inside a sphere of FP32 radius R.
+__device__ __forceinline__ int ext_of(float R) { return (int)ceilf(R) + 1; }
 
 constexpr int MAX_NBR_SMEM = 64;
 
-__global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, uint8_t *__restrict__ flag,
-                                              int32_t *__restrict__ owner) {
+__global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
+                                              uint8_t *__restrict__ flag, int32_t *__restrict__ owner) {
     const int p = blockIdx.x;
-    __shared__ Frame nf[MAX_NBR_SMEM];
+    __shared__ SFrame nf[MAX_NBR_SMEM];
     __shared__ int nid[MAX_NBR_SMEM];
     const int cnt = min(pt.nbr_cnt[p], MAX_NBR_SMEM);
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
         const int q = pt.nbr[(long long)p * pt.max_nbr + t];
         nid[t] = q;
-        nf[t] = frame_of(pt.X + 3 * q, pt.R[q]);
+        nf[t] = fcur[q];
     }
-    const Frame F = frame_of(pt.X + 3 * p, pt.R[p]);
+    const SFrame F = fcur[p];
     __syncthreads();
-    const int e = ceil_r(pt.R[p]) + 1, B = 2 * e + 1;
+    const int e = ext_of(F.R), B = 2 * e + 1;
     for (int t = threadIdx.x; t < B * B * B; t += blockDim.x) {
         const int oz = t / (B * B) - e, oy = (t / B) % B - e, ox = t % B - e;
         const int z = F.b[2] + oz;
@@ -90,7 +72,7 @@ __global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, uint8
         const int x = wrapi(F.b[0] + ox, L.nx), y = wrapi(F.b[1] + oy, L.ny);
         bool win = true;
         for (int m = 0; m < cnt && win; ++m) {
-            const Frame &G = nf[m];
+            const SFrame &G = nf[m];
             const float e2 = dist2(rel(fold(x, G.b[0], L.nx), G.fr[0]), rel(fold(y, G.b[1], L.ny), G.fr[1]),
                                    rel(z - G.b[2], G.fr[2]));
             if (!(e2 < G.R2)) continue;
@@ -98,7 +80,7 @@ __global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, uint8
             if (k2 < key || (k2 == key && nid[m] < p)) win = false;
         }
         if (!win) continue;
-        const long long n = x + (long long)L.nx * (y + (long long)L.ny * z);
+        const int n = x + L.nx * (y + L.ny * z);
         flag[n] = 1;
         owner[n] = p;
     }
@@ -111,16 +93,17 @@ __global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, uint8
 constexpr int kRefillCap = 512;
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_refill(const Lat L, const Parts pt, T *__restrict__ f,
+__global__ void __launch_bounds__(256) k_refill(const Lat L, const SFrame *__restrict__ fcur,
+                                                const SFrame *__restrict__ fprev, T *__restrict__ f,
                                                 uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
                                                 const int P, unsigned long long *__restrict__ ctr,
                                                 int *__restrict__ status) {
     __shared__ int list[kRefillCap];
     __shared__ int count;
     const int p = blockIdx.x;
-    const double *Xg = pt.Xgeo + 3 * p;
-    const int e = ceil_r(pt.R[p]) + 1, B = 2 * e + 1;
-    const int bx = (int)floor(Xg[0]), by = (int)floor(Xg[1]), bz = (int)floor(Xg[2]);
+    const SFrame Fp = fprev[p];  // the node geometry of the previous step was built from this centre
+    const int e = ext_of(Fp.R), B = 2 * e + 1;
+    const int bx = Fp.b[0], by = Fp.b[1], bz = Fp.b[2];
     if (threadIdx.x == 0) count = 0;
     __syncthreads();
     for (int t = threadIdx.x; t < B * B * B; t += blockDim.x) {
@@ -136,9 +119,8 @@ __global__ void __launch_bounds__(256) k_refill(const Lat L, const Parts pt, T *
     __syncthreads();
     const int total = min(count, kRefillCap);
     if (total == 0) return;
-    const Frame F = frame_of(pt.X + 3 * p, pt.R[p]);  // current centre, for the surface velocity
-    const float V[3] = {(float)pt.V[3 * p], (float)pt.V[3 * p + 1], (float)pt.V[3 * p + 2]};
-    const float W[3] = {(float)pt.W[3 * p], (float)pt.W[3 * p + 1], (float)pt.W[3 * p + 2]};
+    const SFrame F = fcur[p];  // current centre, velocity and spin, for the surface velocity
+    const float *V = F.V, *W = F.W;
     const int lane = threadIdx.x & 31;
     for (int k = threadIdx.x >> 5; k < total; k += blockDim.x >> 5) {
         const int n = list[k];
@@ -192,23 +174,25 @@ __global__ void __launch_bounds__(256) k_refill(const Lat L, const Parts pt, T *
 }
 
 int launch_mark(lbm_s *h) {
-    k_mark<<<h->pt.np, 256, 0, h->stream>>>(h->L, h->pt, h->flag, h->owner);
+    const SFrame *fcur = h->pt.frame[h->steps & 1];
+    k_mark<<<h->pt.np, 256, 0, h->stream>>>(h->L, h->pt, fcur, h->flag, h->owner);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
 int launch_refill(lbm_s *h, int parity) {
+    const SFrame *fcur = h->pt.frame[h->steps & 1], *fprev = h->pt.frame[(h->steps + 1) & 1];
     switch (h->precision) {
         case LBM_FP32:
-            k_refill<float><<<h->pt.np, 256, 0, h->stream>>>(h->L, h->pt, (float *)h->f, h->flag, h->owner, parity, h->ctr,
-                                                              h->status);
+            k_refill<float><<<h->pt.np, 256, 0, h->stream>>>(h->L, fcur, fprev, (float *)h->f, h->flag, h->owner,
+                                                              parity, h->ctr, h->status);
             break;
         case LBM_BF16_DEV:
-            k_refill<__nv_bfloat16><<<h->pt.np, 256, 0, h->stream>>>(h->L, h->pt, (__nv_bfloat16 *)h->f, h->flag,
-                                                                      h->owner, parity, h->ctr, h->status);
+            k_refill<__nv_bfloat16><<<h->pt.np, 256, 0, h->stream>>>(h->L, fcur, fprev, (__nv_bfloat16 *)h->f,
+                                                                      h->flag, h->owner, parity, h->ctr, h->status);
             break;
         case LBM_FP16_DEV:
-            k_refill<__half><<<h->pt.np, 256, 0, h->stream>>>(h->L, h->pt, (__half *)h->f, h->flag, h->owner, parity,
-                                                               h->ctr, h->status);
+            k_refill<__half><<<h->pt.np, 256, 0, h->stream>>>(h->L, fcur, fprev, (__half *)h->f, h->flag, h->owner,
+                                                               parity, h->ctr, h->status);
             break;
         default: return LBM_ERR_ARG;
     }

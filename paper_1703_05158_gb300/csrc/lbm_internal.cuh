@@ -134,6 +134,18 @@ struct Phys {
     float ulo[3], uhi[3];
 };
 
+// FP32 frame of a sphere for the lattice kernels, written once per step by
+// the DEM: integer base b = floor(X), fraction (float)(X - b), radius, and
+// velocity / angular velocity in FP32.  Relative coordinates of a lattice
+// point x are (float)(x - b) - fr.
+struct SFrame {
+    int b[3];
+    float fr[3];
+    float R, R2;
+    float V[3], W[3];
+    float pad[2];
+};
+
 // Sphere state on the device.
 struct Parts {
     int np;
@@ -142,14 +154,18 @@ struct Parts {
     double *Fh, *Th;               // hydrodynamic load of the last step
     double *Fc;                    // contact force at the current position
     double *Fx, *Tx;               // external load
-    double *Xgeo;                  // centres used by the current node geometry
     float4 *Xf;                    // FP32 copy of centre and radius (neighbour search)
     double *Xb[2], *Vh[2];         // DEM sub-step buffers
     int *nbr, *nbr_cnt;            // neighbour lists [np][max_nbr]
     int max_nbr;
+    float4 *pairA, *pairB;         // per list entry: (d0, c0) and (dv0, gamma), see lbm_dem.cu
+    double *Xbuild;                // centres when the lists were built
+    int *rebuild;                  // 1: rebuild the lists at the next neighbour pass
+    SFrame *frame[2];              // frames of the centres of even / odd steps
     double kn, ce, rho_s;          // ce = -2 ln e / sqrt(pi^2 + ln^2 e)
     int substeps;
-    double skin;
+    double skin;                   // list skin: pairs within R_a + R_b + skin are listed
+    double max_step;               // largest displacement allowed in one step
 };
 
 }  // namespace lbm
@@ -194,7 +210,7 @@ int launch_stream_collide(lbm_s *h, int parity);
 int launch_mark(lbm_s *h);
 int launch_refill(lbm_s *h, int parity);
 int launch_links(lbm_s *h, int parity);
-int launch_neighbours(lbm_s *h);
+int launch_neighbours(lbm_s *h, int force);
 int launch_contact(lbm_s *h);
 int launch_dem(lbm_s *h);
 int launch_set_populations(lbm_s *h, const double *f_dev, int parity);

@@ -32,29 +32,41 @@ namespace lbm {
 // Wrap a coordinate that is at most one box length outside [0, n).
 __device__ __forceinline__ int wrap1(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
+// Tile index t -> offsets (ox, oy, oz) in [-ext, ext]; the divisions by B and
+// B^2 use multiply-high with m = floor((2^32 - 1) / d) + 1, exact for the
+// tile sizes here (t < 2^17, d <= 2^12).
+__device__ __forceinline__ void tile_xyz(int t, int B, int B2, unsigned mB, unsigned mB2, int ext, int &ox, int &oy,
+                                         int &oz) {
+    const int z = (int)__umulhi((unsigned)t, mB2);
+    const int r = t - z * B2;
+    const int y = (int)__umulhi((unsigned)r, mB);
+    ox = r - y * B - ext;
+    oy = y - ext;
+    oz = z - ext;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, T *__restrict__ f,
+__global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
+                                               T *__restrict__ f,
                                                uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
-                                               const int P, const int ext, const int cap, int *__restrict__ status,
+                                               const int P, const int ext, const unsigned mB, const unsigned mB2,
+                                               const int cap, int *__restrict__ status,
                                                unsigned long long *__restrict__ ctr) {
     extern __shared__ unsigned char smem[];
     const int B = 2 * ext + 1, B2 = B * B, B3 = B2 * B;
     uint32_t *list = (uint32_t *)smem;            // cap entries: tile index << 5 | direction
     uint8_t *code = smem + 4 * (size_t)cap;       // B3 node codes
-    __shared__ double red[8][13];
+    uint16_t *nodes = (uint16_t *)(code + ((B3 + 15) & ~15));  // the sphere's own nodes, tile order
+    const int ncap = (B3 + 1) / 2;                // a ball fills at most 52% of its cube
+    __shared__ float redf[8][6];
+    __shared__ int redi[8][6];
+    __shared__ double sh[12];
     __shared__ int wsum[8];
     const int p = blockIdx.x;
-    const double *Xp = pt.X + 3 * p;
-    int b[3];
-    float fr[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const double bb = floor(Xp[a]);
-        b[a] = (int)bb;
-        fr[a] = __double2float_rn(Xp[a] - bb);
-    }
-    const float R = __double2float_rn(pt.R[p]);
-    const float R2 = __fmul_rn(R, R);
+    const SFrame Fr = fcur[p];
+    const int b[3] = {Fr.b[0], Fr.b[1], Fr.b[2]};
+    const float fr[3] = {Fr.fr[0], Fr.fr[1], Fr.fr[2]};
+    const float R2 = Fr.R2;
 
     // 1. node codes of the tile: 0 fluid, 1 other solid / outside, 2 this sphere
     //    (four nodes per thread per round so that their loads overlap)
@@ -66,9 +78,11 @@ __global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, T *_
             const int t = t0 + u * blockDim.x;
             nn[u] = -1;
             if (t < B3) {
-                const int z = b[2] + t / B2 - ext;
+                int ox, oy, oz;
+                tile_xyz(t, B, B2, mB, mB2, ext, ox, oy, oz);
+                const int z = b[2] + oz;
                 if (z >= 0 && z < L.nz) {
-                    const int y = wrap1(b[1] + (t / B) % B - ext, L.ny), x = wrap1(b[0] + t % B - ext, L.nx);
+                    const int y = wrap1(b[1] + oy, L.ny), x = wrap1(b[0] + ox, L.nx);
                     nn[u] = x + L.nx * (y + L.ny * z);
                 }
             }
@@ -85,14 +99,17 @@ __global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, T *_
     }
     __syncthreads();
 
-    // 2. cut links (s owned, x = s - c_j fluid) into a list, in tile order
-    //    (count, block scan, write: deterministic order)
-    int mine = 0;
-    for (int t = threadIdx.x; t < B3; t += blockDim.x) {
-        if (code[t] != 2) continue;
-        for (int j = 1; j < Q; ++j) mine += code[t - (rcx(j) + B * (rcy(j) + B * rcz(j)))] == 0;
-    }
+    // 2. cut links (s owned, x = s - c_j fluid) into a list in tile order,
+    //    direction minor.  (a) the sphere's own nodes are compacted in tile
+    //    order (threads own contiguous tile ranges, one block scan); (b) the
+    //    flattened (node, direction) pairs are tested in rounds of one pair per
+    //    thread and the links appended with warp ballots, so no warp walks
+    //    directions for nodes that are not its own.
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int chunk = (B3 + blockDim.x - 1) / blockDim.x;
+    const int t_lo = min(B3, (int)threadIdx.x * chunk), t_hi = min(B3, t_lo + chunk);
+    int mine = 0;
+    for (int t = t_lo; t < t_hi; ++t) mine += code[t] == 2;
     int incl = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -101,35 +118,61 @@ __global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, T *_
     }
     if (lane == 31) wsum[wid] = incl;
     __syncthreads();
-    int base = 0, total = 0;
+    int nbase = 0, nn = 0;
     for (int w = 0; w < nw; ++w) {
-        if (w < wid) base += wsum[w];
-        total += wsum[w];
+        if (w < wid) nbase += wsum[w];
+        nn += wsum[w];
     }
-    int pos = base + incl - mine;
-    for (int t = threadIdx.x; t < B3; t += blockDim.x) {
-        if (code[t] != 2) continue;
-        for (int j = 1; j < Q; ++j)
-            if (code[t - (rcx(j) + B * (rcy(j) + B * rcz(j)))] == 0) {
-                if (pos < cap) list[pos] = ((uint32_t)t << 5) | (uint32_t)j;
+    {
+        int pos = nbase + incl - mine;
+        for (int t = t_lo; t < t_hi; ++t)
+            if (code[t] == 2) {
+                if (pos < ncap) nodes[pos] = (uint16_t)t;
                 ++pos;
             }
+    }
+    if (nn > ncap && threadIdx.x == 0) atomicOr(status, ST_TILE);
+    nn = min(nn, ncap);
+    __syncthreads();
+    int total = 0;
+    for (int e0 = 0; e0 < nn * (Q - 1); e0 += blockDim.x) {
+        const int e = e0 + threadIdx.x;
+        bool is = false;
+        uint32_t entry = 0;
+        if (e < nn * (Q - 1)) {
+            const int t = nodes[e / (Q - 1)], j = e % (Q - 1) + 1;
+            is = code[t - (rcx(j) + B * (rcy(j) + B * rcz(j)))] == 0;
+            entry = ((uint32_t)t << 5) | (uint32_t)j;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, is);
+        if (lane == 0) wsum[wid] = __popc(m);
+        __syncthreads();
+        int off = total, round = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < wid) off += wsum[w];
+            round += wsum[w];
+        }
+        if (is) {
+            const int pos = off + __popc(m & ((1u << lane) - 1u));
+            if (pos < cap) list[pos] = entry;
+        }
+        total += round;
+        __syncthreads();
     }
     if (total > cap && threadIdx.x == 0) atomicOr(status, ST_TILE);
     total = min(total, cap);
     __syncthreads();
 
     // 3. bounce-back and momentum exchange, links spread over the threads
-    const float V[3] = {(float)pt.V[3 * p], (float)pt.V[3 * p + 1], (float)pt.V[3 * p + 2]};
-    const float W[3] = {(float)pt.W[3 * p], (float)pt.W[3 * p + 1], (float)pt.W[3 * p + 2]};
+    const float *V = Fr.V, *W = Fr.W;
     float Fd[3] = {0.f, 0.f, 0.f}, Td[3] = {0.f, 0.f, 0.f};
     int I[3] = {0, 0, 0}, J[3] = {0, 0, 0};
     const int S = (int)L.S, plane = (int)L.plane;
-    // two links per thread per round: all six candidate loads are issued
-    // before any of them is used
+    // two links per thread per round: the fractions q are computed first, then
+    // the two populations each link needs are loaded together
     for (int l0 = threadIdx.x; l0 < total; l0 += 2 * blockDim.x) {
-        float ld[2][3];
-        int lt[2], lj[2], dst[2];
+        float ld[2][2], lq[2], ldx[2][3];
+        int lt[2], lj[2], dst[2], lbr[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const int l = l0 + u * blockDim.x;
@@ -138,27 +181,13 @@ __global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, T *_
             const uint32_t e = list[l];
             const int t = (int)(e >> 5), j = (int)(e & 31u), k = ropp(j);
             const int cjx = rcx(j), cjy = rcy(j), cjz = rcz(j);
-            const int ox = t % B - ext - cjx, oy = (t / B) % B - ext - cjy, oz = t / B2 - ext - cjz;
-            // storage indices of x, of the solid node s = x + c_j and of x - c_j
-            const int xx = wrap1(b[0] + ox, L.nx), xy = wrap1(b[1] + oy, L.ny), xz = b[2] + oz;
-            const int sx = xx + L.nx * (xy + L.ny * xz) + plane;
-            const int ss = wrap1(xx + cjx, L.nx) + L.nx * (wrap1(xy + cjy, L.ny) + L.ny * (xz + cjz)) + plane;
-            const int sb = wrap1(xx - cjx, L.nx) + L.nx * (wrap1(xy - cjy, L.ny) + L.ny * (xz - cjz)) + plane;
-            // post-collision d^c_j(x), d^c_j(x - c_j), d^c_k(x) of the finished step
-            ld[u][0] = Store<T>::ld(f + (P == 0 ? k * S + sx : j * S + ss));
-            ld[u][1] = Store<T>::ld(f + (P == 0 ? k * S + sb : j * S + sx));
-            ld[u][2] = Store<T>::ld(f + (P == 0 ? j * S + sx : k * S + sb));
-            dst[u] = P == 0 ? j * S + ss : k * S + sx;  // where the next step reads f_k(x)
-            lt[u] = t;
-            lj[u] = j;
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            if (lt[u] < 0) continue;
-            const int t = lt[u], j = lj[u];
-            const int cjx = rcx(j), cjy = rcy(j), cjz = rcz(j);
             const int off = cjx + B * (cjy + B * cjz);
-            const int ox = t % B - ext - cjx, oy = (t / B) % B - ext - cjy, oz = t / B2 - ext - cjz;
+            int ox, oy, oz;
+            tile_xyz(t, B, B2, mB, mB2, ext, ox, oy, oz);
+            ox -= cjx;
+            oy -= cjy;
+            oz -= cjz;
+            // link fraction q of the fluid node x = s - c_j (FP32, the oracle's operations)
             const float dx = __fsub_rn((float)ox, fr[0]), dy = __fsub_rn((float)oy, fr[1]),
                         dz = __fsub_rn((float)oz, fr[2]);
             const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
@@ -170,7 +199,38 @@ __global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, T *_
             if (disc < 0.f) disc = 0.f;
             float q = __fdiv_rn(c0, __fadd_rn(-qb, __fsqrt_rn(disc)));
             q = fminf(fmaxf(q, 0.f), 1.f);
-
+            // branch of Eq. (19): 0 interpolate with x - c_j, 1 halfway fallback, 2 q >= 1/2
+            const int br = q < 0.5f ? (code[t - 2 * off] == 0 ? 0 : 1) : 2;
+            // storage indices of x, of the solid node s = x + c_j and of x - c_j
+            const int xx = wrap1(b[0] + ox, L.nx), xy = wrap1(b[1] + oy, L.ny), xz = b[2] + oz;
+            const int sx = xx + L.nx * (xy + L.ny * xz) + plane;
+            const int ss = wrap1(xx + cjx, L.nx) + L.nx * (wrap1(xy + cjy, L.ny) + L.ny * (xz + cjz)) + plane;
+            const int sb = wrap1(xx - cjx, L.nx) + L.nx * (wrap1(xy - cjy, L.ny) + L.ny * (xz - cjz)) + plane;
+            // post-collision d^c_j(x) and, by branch, d^c_j(x - c_j) or d^c_k(x)
+            ld[u][0] = Store<T>::ld(f + (P == 0 ? k * S + sx : j * S + ss));
+            ld[u][1] = br == 1 ? 0.f
+                               : Store<T>::ld(f + (br == 0 ? (P == 0 ? k * S + sb : j * S + sx)
+                                                           : (P == 0 ? j * S + sx : k * S + sb)));
+            dst[u] = P == 0 ? j * S + ss : k * S + sx;  // where the next step reads f_k(x)
+            lt[u] = t;
+            lj[u] = j;
+            lq[u] = q;
+            lbr[u] = br;
+            ldx[u][0] = dx;
+            ldx[u][1] = dy;
+            ldx[u][2] = dz;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (lt[u] < 0) continue;
+            const int t = lt[u], j = lj[u];
+            const int cjx = rcx(j), cjy = rcy(j), cjz = rcz(j);
+            int ox, oy, oz;
+            tile_xyz(t, B, B2, mB, mB2, ext, ox, oy, oz);
+            ox -= cjx;
+            oy -= cjy;
+            oz -= cjz;
+            const float dx = ldx[u][0], dy = ldx[u][1], dz = ldx[u][2], q = lq[u];
             const float dcj = ld[u][0];
             const float lx = dx + q * cjx, ly = dy + q * cjy, lz = dz + q * cjz;
             const float ubx = V[0] + (W[1] * lz - W[2] * ly);
@@ -179,12 +239,13 @@ __global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, T *_
             const float cku = -(cjx * ubx + cjy * uby + cjz * ubz);
             const float wj = (float)rw36(j) * (1.f / 36.f);
             float dn;
-            if (q < 0.5f) {
-                const float mw = 6.f * wj * cku;
-                dn = code[t - 2 * off] == 0 ? 2.f * q * dcj + (1.f - 2.f * q) * ld[u][1] + mw : dcj + mw;
+            if (lbr[u] == 0) {
+                dn = 2.f * q * dcj + (1.f - 2.f * q) * ld[u][1] + 6.f * wj * cku;
+            } else if (lbr[u] == 1) {
+                dn = dcj + 6.f * wj * cku;
             } else {
                 const float i2q = 0.5f / q;
-                dn = dcj * i2q + (2.f * q - 1.f) * i2q * ld[u][2] + 3.f / q * wj * cku;
+                dn = dcj * i2q + (2.f * q - 1.f) * i2q * ld[u][1] + 3.f / q * wj * cku;
             }
             Store<T>::st(f + dst[u], dn);
 
@@ -207,10 +268,10 @@ __global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, T *_
 
     // 4. the nodes of this sphere become "owned at the previous geometry"
     //    (3: still solid for every reader) for the next step's mark pass
-    for (int t = threadIdx.x; t < B3; t += blockDim.x) {
-        if (code[t] != 2) continue;
-        const int z = b[2] + t / B2 - ext;
-        const int y = wrap1(b[1] + (t / B) % B - ext, L.ny), x = wrap1(b[0] + t % B - ext, L.nx);
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+        int ox, oy, oz;
+        tile_xyz(nodes[i], B, B2, mB, mB2, ext, ox, oy, oz);
+        const int z = b[2] + oz, y = wrap1(b[1] + oy, L.ny), x = wrap1(b[0] + ox, L.nx);
         flag[x + L.nx * (y + L.ny * z)] = 3;
     }
 
@@ -227,27 +288,31 @@ __global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, T *_
     }
     if (lane == 0) {
         for (int a = 0; a < 6; ++a) {
-            red[wid][a] = (double)v[a];
-            red[wid][6 + a] = (double)iv[a];
+            redf[wid][a] = v[a];
+            redi[wid][a] = iv[a];
         }
     }
     __syncthreads();
+    // lanes 0..11 of warp 0 each sum one component over the warps in FP64
+    if (threadIdx.x < 12) {
+        const int a = threadIdx.x;
+        double sum = 0.0;
+        for (int w = 0; w < nw; ++w) sum += a < 6 ? (double)redf[w][a] : (double)redi[w][a - 6];
+        sh[a] = sum;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double sm[12] = {0};
-        for (int w = 0; w < nw; ++w)
-            for (int a = 0; a < 12; ++a) sm[a] += red[w][a];
         double frac[3];
-        for (int a = 0; a < 3; ++a) frac[a] = Xp[a] - floor(Xp[a]);
+        for (int a = 0; a < 3; ++a) frac[a] = pt.X[3 * p + a] - (double)b[a];  // exact: X - floor(X)
         // rest part 2 w_j c_j: F = I/18, T = (J - frac x I)/18
-        const double Ix = sm[6], Iy = sm[7], Iz = sm[8];
+        const double Ix = sh[6], Iy = sh[7], Iz = sh[8];
         double *F = pt.Fh + 3 * p, *Tq = pt.Th + 3 * p;
-        F[0] = sm[0] + Ix / 18.0;
-        F[1] = sm[1] + Iy / 18.0;
-        F[2] = sm[2] + Iz / 18.0;
-        Tq[0] = sm[3] + (sm[9] - (frac[1] * Iz - frac[2] * Iy)) / 18.0;
-        Tq[1] = sm[4] + (sm[10] - (frac[2] * Ix - frac[0] * Iz)) / 18.0;
-        Tq[2] = sm[5] + (sm[11] - (frac[0] * Iy - frac[1] * Ix)) / 18.0;
-        for (int a = 0; a < 3; ++a) pt.Xgeo[3 * p + a] = Xp[a];
+        F[0] = sh[0] + Ix / 18.0;
+        F[1] = sh[1] + Iy / 18.0;
+        F[2] = sh[2] + Iz / 18.0;
+        Tq[0] = sh[3] + (sh[9] - (frac[1] * Iz - frac[2] * Iy)) / 18.0;
+        Tq[1] = sh[4] + (sh[10] - (frac[2] * Ix - frac[0] * Iz)) / 18.0;
+        Tq[2] = sh[5] + (sh[11] - (frac[0] * Iy - frac[1] * Ix)) / 18.0;
         atomicAdd(ctr, (unsigned long long)total);
     }
 }
@@ -258,8 +323,8 @@ int link_capacity(double max_radius) {
 }
 
 size_t link_smem(int ext, int cap) {
-    const size_t B = 2 * (size_t)ext + 1;
-    return 4 * (size_t)cap + B * B * B;
+    const size_t B = 2 * (size_t)ext + 1, B3 = B * B * B;
+    return 4 * (size_t)cap + ((B3 + 15) & ~(size_t)15) + 2 * ((B3 + 1) / 2);
 }
 
 int links_setup(int ext, int cap) {
@@ -275,18 +340,21 @@ int links_setup(int ext, int cap) {
 int launch_links(lbm_s *h, int parity) {
     const int ext = h->tile_ext, cap = h->link_cap;
     const size_t smem = link_smem(ext, cap);
+    const SFrame *fcur = h->pt.frame[h->steps & 1];
+    const unsigned B = 2u * ext + 1u, mB = 0xFFFFFFFFu / B + 1u, mB2 = 0xFFFFFFFFu / (B * B) + 1u;
     switch (h->precision) {
         case LBM_FP32:
-            k_links<float><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, (float *)h->f, h->flag, h->owner, parity,
-                                                                ext, cap, h->status, h->ctr);
+            k_links<float><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, fcur, (float *)h->f, h->flag, h->owner,
+                                                                parity, ext, mB, mB2, cap, h->status, h->ctr);
             break;
         case LBM_BF16_DEV:
-            k_links<__nv_bfloat16><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, (__nv_bfloat16 *)h->f, h->flag,
-                                                                        h->owner, parity, ext, cap, h->status, h->ctr);
+            k_links<__nv_bfloat16><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, fcur, (__nv_bfloat16 *)h->f,
+                                                                        h->flag, h->owner, parity, ext, mB, mB2, cap,
+                                                                        h->status, h->ctr);
             break;
         case LBM_FP16_DEV:
-            k_links<__half><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, (__half *)h->f, h->flag, h->owner, parity,
-                                                                 ext, cap, h->status, h->ctr);
+            k_links<__half><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, fcur, (__half *)h->f, h->flag, h->owner,
+                                                                 parity, ext, mB, mB2, cap, h->status, h->ctr);
             break;
         default: return LBM_ERR_ARG;
     }
