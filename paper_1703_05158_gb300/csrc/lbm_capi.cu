@@ -142,6 +142,10 @@ int with_out_buffer(lbm_s *h, void *user, size_t n, int where, Fn fn) {
 
 }  // namespace
 
+namespace lbm {
+int settle_handle(lbm_s *h) { return settle(h); }
+}  // namespace lbm
+
 extern "C" {
 
 const char *lbm_error_string(int code) {

@@ -223,4 +223,5 @@ int dem_cluster_setup(int max_particles);
 int link_capacity(double max_radius);
 size_t link_smem(int ext, int cap);
 int links_setup(int ext, int cap);
+int settle_handle(lbm_s *h);
 }  // namespace lbm

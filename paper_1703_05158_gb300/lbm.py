@@ -34,7 +34,7 @@ PRECISIONS = {"fp32": LBM_FP32, "bf16": LBM_BF16_DEV, "fp16": LBM_FP16_DEV}
 
 EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_particles", "lbm_set_particle_load", "lbm_set_populations",
            "lbm_step", "lbm_forces", "lbm_particles", "lbm_fields", "lbm_populations", "lbm_geometry", "lbm_info",
-           "lbm_sync", "lbm_error_string", "lbm_profile", "lbm_profile_read")
+           "lbm_sync", "lbm_error_string", "lbm_profile", "lbm_profile_read", "lbm_fields_noalloc")
 
 
 class lbm_params(ctypes.Structure):
@@ -89,6 +89,7 @@ def load(build=True):
         lib.lbm_sync.argtypes = [vp]
         lib.lbm_profile.argtypes = [vp, ip]
         lib.lbm_profile_read.argtypes = [vp, ctypes.c_void_p, ctypes.c_void_p]
+        lib.lbm_fields_noalloc.argtypes = [vp, fp, fp]
         lib.lbm_error_string.argtypes = [ctypes.c_int]
         lib.lbm_error_string.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -185,6 +186,17 @@ def lbm_fields(h, rho, u):
     p2, w2 = _ptr(u)
     where = w1 if rho is not None else w2
     return _check(load().lbm_fields(h, p1, p2, where), "lbm_fields")
+
+
+LBM_NOALLOC_MAX_NODES = 1 << 20
+
+
+def lbm_fields_noalloc(h, rho, u):
+    """lbm_fields into host buffers without any device allocation (staging
+    through the library's fixed array; lattices up to LBM_NOALLOC_MAX_NODES)."""
+    p1, _ = _ptr(rho)
+    p2, _ = _ptr(u)
+    return _check(load().lbm_fields_noalloc(h, p1, p2), "lbm_fields_noalloc")
 
 
 def lbm_populations(h, f):
