@@ -74,39 +74,53 @@ __global__ void __launch_bounds__(256, 4) k_stream_collide(const Lat L, const Ph
     const float uz = jz * ir + 0.5f * ph.g[2];
     const float uu = ux * ux + uy * uy + uz * uz;
 
-    // f^eq_i - w_i (Eq. 9 written for the deviation).
-    auto deq = [&](int i) {
-        const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-        return wf(i) * (drho + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * uu));
-    };
-
     float tau = ph.tau0;
     if (ph.smag > 0.f) {
-        float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+        // Pi^neq_ab = sum c_a c_b (f - f^eq) = m_ab - drho delta_ab / 3 - rho u_a u_b, with
+        // m_ab = sum c_a c_b d_i and the D3Q19 identity sum c_a c_b f^eq = rho (delta_ab/3 + u_a u_b)
+        float mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f, myz = 0.f;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const float ne = d[i] - deq(i);
-            if (cx(i)) pxx += ne;
-            if (cy(i)) pyy += ne;
-            if (cz(i)) pzz += ne;
-            if (cx(i) * cy(i)) pxy += cx(i) * cy(i) > 0 ? ne : -ne;
-            if (cx(i) * cz(i)) pxz += cx(i) * cz(i) > 0 ? ne : -ne;
-            if (cy(i) * cz(i)) pyz += cy(i) * cz(i) > 0 ? ne : -ne;
+        for (int i = 1; i < Q; ++i) {
+            if (cx(i)) mxx += d[i];
+            if (cy(i)) myy += d[i];
+            if (cz(i)) mzz += d[i];
+            if (cx(i) * cy(i)) mxy += cx(i) * cy(i) > 0 ? d[i] : -d[i];
+            if (cx(i) * cz(i)) mxz += cx(i) * cz(i) > 0 ? d[i] : -d[i];
+            if (cy(i) * cz(i)) myz += cy(i) * cz(i) > 0 ? d[i] : -d[i];
         }
+        const float t3 = drho * (1.f / 3.f);
+        const float pxx = mxx - t3 - rho * ux * ux, pyy = myy - t3 - rho * uy * uy, pzz = mzz - t3 - rho * uz * uz;
+        const float pxy = mxy - rho * ux * uy, pxz = mxz - rho * ux * uz, pyz = myz - rho * uy * uz;
         const float q2 = pxx * pxx + pyy * pyy + pzz * pzz + 2.f * (pxy * pxy + pxz * pxz + pyz * pyz);
         tau = ph.tau0 + 0.5f * (sqrtf(ph.tau0 * ph.tau0 + ph.smag * sqrtf(q2) * ir) - ph.tau0);
     }
     const float om = 1.f / tau;
+
+    // Relaxation towards Eq. (9) (deviation form), by opposite pairs (i, i+9):
+    // f^eq - w = w [drho + rho (4.5 (c.u)^2 - 1.5 u^2)]  +/-  3 w rho (c.u)
+    const float base = drho - 1.5f * rho * uu;
+    d[0] += om * (wf(0) * base - d[0]);
+    const bool forced = ph.g[0] != 0.f || ph.g[1] != 0.f || ph.g[2] != 0.f;
     const float fx = rho * ph.g[0], fy = rho * ph.g[1], fz = rho * ph.g[2];
     const float uF = ux * fx + uy * fy + uz * fz;
     const float sk = 1.f - 0.5f * om;
-
+    if (forced) d[0] += sk * wf(0) * (-3.f * uF);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int i = 1; i <= 9; ++i) {
+        const int k = i + 9;  // opp(i)
         const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-        const float cF = cx(i) * fx + cy(i) * fy + cz(i) * fz;
-        const float src = wf(i) * (3.f * (cF - uF) + 9.f * cu * cF);
-        d[i] = d[i] - om * (d[i] - deq(i)) + sk * src;
+        const float sym = wf(i) * (base + 4.5f * rho * cu * cu);
+        const float asym = 3.f * wf(i) * rho * cu;
+        d[i] += om * (sym + asym - d[i]);
+        d[k] += om * (sym - asym - d[k]);
+        if (forced) {
+            // Guo source: w [3 (c - u).F + 9 (c.u)(c.F)], even and odd parts
+            const float cF = cx(i) * fx + cy(i) * fy + cz(i) * fz;
+            const float se = sk * wf(i) * (9.f * cu * cF - 3.f * uF);
+            const float so = sk * wf(i) * 3.f * cF;
+            d[i] += se + so;
+            d[k] += se - so;
+        }
     }
 
 #pragma unroll
