@@ -180,7 +180,7 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     if (p.max_particles > 0) {
         if (!(p.max_radius > 0.0 && p.max_radius <= 16.0)) return LBM_ERR_ARG;
         // a sphere's bounding box and link tile must not wrap onto itself
-        const int span = 2 * ((int)std::ceil(p.max_radius) + 4) + 1;
+        const int span = 2 * ((int)std::ceil(p.max_radius) + 3) + 1;
         if (p.nx < span || p.ny < span) return LBM_ERR_ARG;
     }
     const long long plane = (long long)p.nx * p.ny;
@@ -235,7 +235,9 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     pt.substeps = p.dem_substeps;
     pt.skin = kSkin;
     pt.max_step = kMaxStep;
-    h->tile_ext = (int)std::ceil(M > 0 ? p.max_radius : 1.0) + 3;
+    // a solid node lies within [-ceil(R) + 1, ceil(R)] of floor(X) per axis; the
+    // link tile also holds x = s - c_j and x - c_j, two more nodes out
+    h->tile_ext = (int)std::ceil(M > 0 ? p.max_radius : 1.0) + 2;
     h->link_cap = link_capacity(M > 0 ? p.max_radius : 1.0);
 
     unsigned char *fixed = nullptr;

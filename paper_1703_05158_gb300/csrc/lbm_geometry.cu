@@ -43,8 +43,9 @@ __device__ __forceinline__ int fold(int x, int b, int n) {
     return d;
 }
 
-// Half width of the box holding every node inside a sphere of FP32 radius R.
-__device__ __forceinline__ int ext_of(float R) { return (int)ceilf(R) + 1; }
+// Half width of the box (around floor(X)) holding every node inside a sphere
+// of FP32 radius R: offsets lie in [-ceil(R) + 1, ceil(R)].
+__device__ __forceinline__ int ext_of(float R) { return (int)ceilf(R); }
 
 constexpr int MAX_NBR_SMEM = 64;
 

@@ -46,7 +46,7 @@ __device__ __forceinline__ void tile_xyz(int t, int B, int B2, unsigned mB, unsi
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
+__global__ void __launch_bounds__(256, 3) k_links(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
                                                T *__restrict__ f,
                                                uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
                                                const int P, const int ext, const unsigned mB, const unsigned mB2,
@@ -134,30 +134,43 @@ __global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, cons
     if (nn > ncap && threadIdx.x == 0) atomicOr(status, ST_TILE);
     nn = min(nn, ncap);
     __syncthreads();
-    int total = 0;
-    for (int e0 = 0; e0 < nn * (Q - 1); e0 += blockDim.x) {
-        const int e = e0 + threadIdx.x;
+    // (b) each warp tests a contiguous segment of the (node, direction) pairs:
+    //     count, one block scan of the warp counts, then write in order
+    const int np_ = nn * (Q - 1);
+    const int seg = ((np_ + nw - 1) / nw + 31) & ~31;
+    const int p_lo = min(np_, wid * seg), p_hi = min(np_, p_lo + seg);
+    int wc = 0;
+    for (int e0 = p_lo; e0 < p_hi; e0 += 32) {
+        const int e = e0 + lane;
+        bool is = false;
+        if (e < p_hi) {
+            const int t = nodes[e / (Q - 1)], j = e % (Q - 1) + 1;
+            is = code[t - (rcx(j) + B * (rcy(j) + B * rcz(j)))] == 0;
+        }
+        wc += __popc(__ballot_sync(0xffffffffu, is));
+    }
+    if (lane == 0) wsum[wid] = wc;
+    __syncthreads();
+    int off = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+        if (w < wid) off += wsum[w];
+        total += wsum[w];
+    }
+    for (int e0 = p_lo; e0 < p_hi; e0 += 32) {
+        const int e = e0 + lane;
         bool is = false;
         uint32_t entry = 0;
-        if (e < nn * (Q - 1)) {
+        if (e < p_hi) {
             const int t = nodes[e / (Q - 1)], j = e % (Q - 1) + 1;
             is = code[t - (rcx(j) + B * (rcy(j) + B * rcz(j)))] == 0;
             entry = ((uint32_t)t << 5) | (uint32_t)j;
         }
         const unsigned m = __ballot_sync(0xffffffffu, is);
-        if (lane == 0) wsum[wid] = __popc(m);
-        __syncthreads();
-        int off = total, round = 0;
-        for (int w = 0; w < nw; ++w) {
-            if (w < wid) off += wsum[w];
-            round += wsum[w];
-        }
         if (is) {
             const int pos = off + __popc(m & ((1u << lane) - 1u));
             if (pos < cap) list[pos] = entry;
         }
-        total += round;
-        __syncthreads();
+        off += __popc(m);
     }
     if (total > cap && threadIdx.x == 0) atomicOr(status, ST_TILE);
     total = min(total, cap);
@@ -168,13 +181,14 @@ __global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, cons
     float Fd[3] = {0.f, 0.f, 0.f}, Td[3] = {0.f, 0.f, 0.f};
     int I[3] = {0, 0, 0}, J[3] = {0, 0, 0};
     const int S = (int)L.S, plane = (int)L.plane;
-    // two links per thread per round: the fractions q are computed first, then
-    // the two populations each link needs are loaded together
-    for (int l0 = threadIdx.x; l0 < total; l0 += 2 * blockDim.x) {
-        float ld[2][2], lq[2], ldx[2][3];
-        int lt[2], lj[2], dst[2], lbr[2];
+    // kLinkBatch links per thread per round: the fractions q are computed
+    // first, then the two populations each link needs are loaded together
+    constexpr int kLinkBatch = 4;
+    for (int l0 = threadIdx.x; l0 < total; l0 += kLinkBatch * blockDim.x) {
+        float ld[kLinkBatch][2], lq[kLinkBatch], ldx[kLinkBatch][3];
+        int lt[kLinkBatch], lj[kLinkBatch], dst[kLinkBatch], lbr[kLinkBatch];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kLinkBatch; ++u) {
             const int l = l0 + u * blockDim.x;
             lt[u] = -1;
             if (l >= total) continue;
@@ -221,7 +235,7 @@ __global__ void __launch_bounds__(256) k_links(const Lat L, const Parts pt, cons
             ldx[u][2] = dz;
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kLinkBatch; ++u) {
             if (lt[u] < 0) continue;
             const int t = lt[u], j = lj[u];
             const int cjx = rcx(j), cjy = rcy(j), cjz = rcz(j);
