@@ -69,12 +69,13 @@ __global__ void __launch_bounds__(256, 3) k_links(const Lat L, const Parts pt, c
     const float R2 = Fr.R2;
 
     // 1. node codes of the tile: 0 fluid, 1 other solid / outside, 2 this sphere
-    //    (four nodes per thread per round so that their loads overlap)
-    for (int t0 = threadIdx.x; t0 < B3; t0 += 4 * blockDim.x) {
-        int nn[4];
-        uint8_t fl[4];
+    //    (kTileBatch nodes per thread per round so that their loads overlap)
+    constexpr int kTileBatch = 12;
+    for (int t0 = threadIdx.x; t0 < B3; t0 += kTileBatch * blockDim.x) {
+        int nn[kTileBatch];
+        uint8_t fl[kTileBatch];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kTileBatch; ++u) {
             const int t = t0 + u * blockDim.x;
             nn[u] = -1;
             if (t < B3) {
@@ -88,11 +89,11 @@ __global__ void __launch_bounds__(256, 3) k_links(const Lat L, const Parts pt, c
             }
             fl[u] = nn[u] >= 0 ? __ldcg(flag + nn[u]) : (uint8_t)1;
         }
-        int ow[4];
+        int ow[kTileBatch];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) ow[u] = (nn[u] >= 0 && (fl[u] & 1)) ? __ldcg(owner + nn[u]) : -1;
+        for (int u = 0; u < kTileBatch; ++u) ow[u] = (nn[u] >= 0 && (fl[u] & 1)) ? __ldcg(owner + nn[u]) : -1;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kTileBatch; ++u) {
             const int t = t0 + u * blockDim.x;
             if (t < B3) code[t] = (fl[u] & 1) ? (ow[u] == p ? 2 : 1) : 0;
         }
@@ -134,44 +135,45 @@ __global__ void __launch_bounds__(256, 3) k_links(const Lat L, const Parts pt, c
     if (nn > ncap && threadIdx.x == 0) atomicOr(status, ST_TILE);
     nn = min(nn, ncap);
     __syncthreads();
-    // (b) each warp tests a contiguous segment of the (node, direction) pairs:
-    //     count, one block scan of the warp counts, then write in order
-    const int np_ = nn * (Q - 1);
-    const int seg = ((np_ + nw - 1) / nw + 31) & ~31;
-    const int p_lo = min(np_, wid * seg), p_hi = min(np_, p_lo + seg);
-    int wc = 0;
-    for (int e0 = p_lo; e0 < p_hi; e0 += 32) {
-        const int e = e0 + lane;
-        bool is = false;
-        if (e < p_hi) {
-            const int t = nodes[e / (Q - 1)], j = e % (Q - 1) + 1;
-            is = code[t - (rcx(j) + B * (rcy(j) + B * rcz(j)))] == 0;
+    // (b) thread i takes the owned nodes i, i + T, ... (tile order is kept
+    //     because node k's links precede node k+1's): an unrolled test of the
+    //     18 directions gives a mask, one block scan of the counts places them
+    int total = 0, pos0 = 0;
+    for (int k0 = 0; k0 < nn; k0 += blockDim.x) {
+        const int k = k0 + threadIdx.x;
+        unsigned mask = 0u;
+        int t = 0;
+        if (k < nn) {
+            t = nodes[k];
+#pragma unroll
+            for (int j = 1; j < Q; ++j)
+                if (code[t - (cx(j) + B * (cy(j) + B * cz(j)))] == 0) mask |= 1u << j;
         }
-        wc += __popc(__ballot_sync(0xffffffffu, is));
-    }
-    if (lane == 0) wsum[wid] = wc;
-    __syncthreads();
-    int off = 0, total = 0;
-    for (int w = 0; w < nw; ++w) {
-        if (w < wid) off += wsum[w];
-        total += wsum[w];
-    }
-    for (int e0 = p_lo; e0 < p_hi; e0 += 32) {
-        const int e = e0 + lane;
-        bool is = false;
-        uint32_t entry = 0;
-        if (e < p_hi) {
-            const int t = nodes[e / (Q - 1)], j = e % (Q - 1) + 1;
-            is = code[t - (rcx(j) + B * (rcy(j) + B * rcz(j)))] == 0;
-            entry = ((uint32_t)t << 5) | (uint32_t)j;
+        const int c = __popc(mask);
+        int inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
         }
-        const unsigned m = __ballot_sync(0xffffffffu, is);
-        if (is) {
-            const int pos = off + __popc(m & ((1u << lane) - 1u));
-            if (pos < cap) list[pos] = entry;
+        if (lane == 31) wsum[wid] = inc;
+        __syncthreads();
+        int off = total, round = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < wid) off += wsum[w];
+            round += wsum[w];
         }
-        off += __popc(m);
+        int pos = off + inc - c;
+        while (mask) {
+            const int j = __ffs(mask) - 1;
+            mask &= mask - 1u;
+            if (pos < cap) list[pos] = ((uint32_t)t << 5) | (uint32_t)j;
+            ++pos;
+        }
+        total += round;
+        __syncthreads();
     }
+    (void)pos0;
     if (total > cap && threadIdx.x == 0) atomicOr(status, ST_TILE);
     total = min(total, cap);
     __syncthreads();
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(256, 3) k_links(const Lat L, const Parts pt, c
     const int S = (int)L.S, plane = (int)L.plane;
     // kLinkBatch links per thread per round: the fractions q are computed
     // first, then the two populations each link needs are loaded together
-    constexpr int kLinkBatch = 4;
+    constexpr int kLinkBatch = 6;
     for (int l0 = threadIdx.x; l0 < total; l0 += kLinkBatch * blockDim.x) {
         float ld[kLinkBatch][2], lq[kLinkBatch], ldx[kLinkBatch][3];
         int lt[kLinkBatch], lj[kLinkBatch], dst[kLinkBatch], lbr[kLinkBatch];

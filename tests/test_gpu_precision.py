@@ -1,0 +1,72 @@
+"""Precision form: populations stored as deviations f - w in BF16 or FP16
+(arithmetic FP32), against the FP64 oracle on the same seeded inputs.
+
+The target is a relative velocity error <= 1e-3 (L2 over the fluid nodes,
+||u - u_64|| / ||u_64||) for BF16 storage; FP16 storage (11-bit significand)
+must be at least as accurate.  Geometry decisions do not depend on the
+storage precision, so node ownership stays identical.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1703_05158_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+VEL_TOL = {"bf16": 1e-3, "fp16": 1e-3}
+
+
+def _pair(shape, parts, precision, **kw):
+    from paper_1703_05158_gb300 import lbm
+
+    lbm.load()
+    lat = lbm.Lattice(*shape, precision=precision, max_particles=max(len(parts["R"]), 1), max_radius=6.0, **kw)
+    orc = oracle.Oracle(*shape, **kw)
+    for o in (lat, orc):
+        o.set_particles(parts["X"], V=parts["V"], R=parts["R"])
+    return lat, orc
+
+
+def _vel_error(lat, orc):
+    _, ug = lat.fields()
+    _, uo = orc.fields()
+    fluid = orc.owner() < 0
+    a, b = ug[:, fluid].astype(np.float64), uo[:, fluid]
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b)), float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_channel_with_polydisperse_spheres(precision):
+    """Body-force channel between walls with spheres of radius 3-6 (the
+    precision workload's sphere mix) on a 64^3 sub-box, 200 steps."""
+    shape = (64, 64, 64)
+    parts = inputs.polydisperse(shape, 24, (3.0, 6.0), seed=inputs.SEED_BASE + 3)
+    kw = dict(tau0=0.51, cs=0.17, g=(5e-6, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16)
+    lat, orc = _pair(shape, parts, precision, **kw)
+    lat.step(200)
+    orc.step(200)
+    assert np.array_equal(lat.owner(), orc.owner())
+    l2, mx = _vel_error(lat, orc)
+    print("%s: relative velocity error L2 %.2e, max %.2e" % (precision, l2, mx))
+    assert l2 <= VEL_TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_sheared_box_with_spheres(precision):
+    """Sliding lid, Smagorinsky, moving spheres (the production physics) on
+    a 64 x 48 x 40 box, 200 steps."""
+    shape = (64, 48, 40)
+    parts = inputs.slurry_box(box=shape, n=12, radius=4.0, seed=inputs.SEED_BASE + 4)
+    kw = dict(tau0=0.51, cs=0.17, u_hi=(0.05, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16)
+    lat, orc = _pair(shape, parts, precision, **kw)
+    lat.step(200)
+    orc.step(200)
+    l2, mx = _vel_error(lat, orc)
+    print("%s: relative velocity error L2 %.2e, max %.2e" % (precision, l2, mx))
+    assert l2 <= VEL_TOL[precision]
+    Fg, _ = lat.forces()
+    Fo, _ = orc.forces()
+    # forces follow the velocity field; report their error
+    print("%s: max relative force error %.2e" % (precision, float(
+        (np.linalg.norm(Fg - Fo, axis=1) / np.linalg.norm(Fo, axis=1)).max())))
