@@ -66,6 +66,18 @@ typedef struct lbm_s *lbm_handle;
 #define LBM_BF16_DEV 1   /* f_i - w_i stored as bfloat16 */
 #define LBM_FP16_DEV 2   /* f_i - w_i stored as binary16 */
 
+/* Order of the work inside lbm_step when spheres are present.  Both give
+ * bitwise the same results.  SERIAL (the default) runs every kernel on the
+ * handle's stream, one after the other.  OVERLAP collides the nodes of
+ * 32-byte groups far from every sphere on a second, low-priority stream
+ * while the link, DEM and geometry work of the neighbouring steps runs on a
+ * high-priority one; the near groups are collided from a compacted list.
+ * On a dense suspension (256^3, 2000 spheres of radius 4) OVERLAP is the
+ * slower of the two: a quarter of the groups are near, and splitting the
+ * collide costs more memory time than the overlap hides. */
+#define LBM_SCHEDULE_SERIAL 0
+#define LBM_SCHEDULE_OVERLAP 1
+
 /* Memory space of a caller buffer. */
 #define LBM_HOST 0
 #define LBM_DEVICE 1
@@ -87,6 +99,7 @@ typedef struct {
     double max_radius;         /* largest radius lbm_set_particles accepts, <= 16 */
     void *cuda_stream;         /* cudaStream_t to run on; NULL: the library makes one */
     int32_t device;            /* CUDA device ordinal */
+    int32_t schedule;          /* LBM_SCHEDULE_SERIAL (0) or LBM_SCHEDULE_OVERLAP */
 } lbm_params;
 
 typedef struct {
@@ -158,12 +171,19 @@ int lbm_geometry(lbm_handle h, int32_t *owner, int32_t where);
 /* Counters and sizes (synchronises the stream). */
 int lbm_info(lbm_handle h, lbm_info_t *info);
 
-/* Phases of a step timed by the profiler. */
-#define LBM_PHASE_GEOMETRY 0  /* node geometry and refill */
-#define LBM_PHASE_COLLIDE 1   /* fused collide-stream kernel */
-#define LBM_PHASE_LINKS 2     /* bounce-back on sphere links and momentum exchange */
-#define LBM_PHASE_DEM 3       /* neighbour lists and DEM sub-steps */
-#define LBM_PHASES 4
+/* Phases of a step timed by the profiler.  Under LBM_SCHEDULE_OVERLAP with
+ * spheres, the collisions of nodes far from every sphere run on a second
+ * stream (LBM_PHASE_COLLIDE_FAR), overlapped with the link / DEM / geometry
+ * work of the previous step and the near-node collisions of this one;
+ * LBM_PHASE_COLLIDE then times the near nodes only.  Otherwise
+ * LBM_PHASE_COLLIDE times the whole lattice and the two far phases are 0. */
+#define LBM_PHASE_GEOMETRY 0     /* node geometry and refill */
+#define LBM_PHASE_COLLIDE 1      /* fused collide-stream kernel (near nodes) */
+#define LBM_PHASE_LINKS 2        /* bounce-back on sphere links and momentum exchange */
+#define LBM_PHASE_DEM 3          /* neighbour lists and DEM sub-steps */
+#define LBM_PHASE_COLLIDE_FAR 4  /* fused collide-stream kernel, far nodes (second stream) */
+#define LBM_PHASE_WAIT_FAR 5     /* near tags of the next step, then the wait for the far collisions */
+#define LBM_PHASES 6
 
 /* enable != 0: from now on record CUDA events on the handle's stream around
  * each phase of every step and reset the totals; enable == 0: stop.  Adds no

@@ -16,6 +16,14 @@ constexpr int kDemThreads = 128;   // fallback cooperative DEM
 constexpr double kSkin = 1.5;      // neighbour-list skin (lattice units)
 constexpr double kMaxStep = 0.25;  // largest displacement of a sphere in one step
 
+// Profiler events of one step: on the main stream E0 before the geometry,
+// E1 after it, E2 after the (near) collide, E3 after waiting for the far
+// collide, E4 after the links, E5 after the DEM; on the second stream
+// E6 / E7 around the far collide.  Phase k is the time between two of them.
+enum { E0, E1, E2, E3, E4, E5, E6, E7, kProfEv };
+constexpr int kPhaseFrom[LBM_PHASES] = {E0, E1, E3, E4, E6, E2};
+constexpr int kPhaseTo[LBM_PHASES] = {E1, E2, E4, E5, E7, E3};
+
 int status_to_code(int st) {
     if (st & ST_TIMEOUT) return LBM_ERR_TIMEOUT;
     if (st & ST_DIVERGED) return LBM_ERR_DIVERGED;
@@ -59,10 +67,18 @@ void release(lbm_s *h) {
         if (p) cudaFree(p);
     if (h->status_host) cudaFreeHost(h->status_host);
     if (h->ev) {
-        for (int i = 0; i < 5 * h->ev_cap; ++i) cudaEventDestroy(h->ev[i]);
+        for (int i = 0; i < kProfEv * h->ev_cap; ++i) cudaEventDestroy(h->ev[i]);
         std::free(h->ev);
         h->ev = nullptr;
     }
+    void *ovl[] = {h->near[0], h->near[1], h->near_list[0], h->near_list[1], h->near_cnt};
+    for (void *p : ovl)
+        if (p) cudaFree(p);
+    cudaEvent_t evs[] = {h->ev_cf, h->ev_nm[0], h->ev_nm[1], h->ev_join};
+    for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
+    if (h->stream2) cudaStreamDestroy(h->stream2);
+    if (h->chain) cudaStreamDestroy(h->chain);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -72,10 +88,14 @@ constexpr int kProfSteps = 2048;
 int prof_flush(lbm_s *h) {
     if (!h->ev || h->ev_used == 0) return LBM_OK;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ERR_CUDA;
+    if (h->stream2 && cudaStreamSynchronize(h->stream2) != cudaSuccess) return LBM_ERR_CUDA;
+    if (h->chain && cudaStreamSynchronize(h->chain) != cudaSuccess) return LBM_ERR_CUDA;
     for (int s = 0; s < h->ev_used; ++s)
-        for (int ph = 0; ph < 4; ++ph) {
+        for (int ph = 0; ph < LBM_PHASES; ++ph) {
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, h->ev[5 * s + ph], h->ev[5 * s + ph + 1]) != cudaSuccess) return LBM_ERR_CUDA;
+            if (cudaEventElapsedTime(&ms, h->ev[kProfEv * s + kPhaseFrom[ph]], h->ev[kProfEv * s + kPhaseTo[ph]]) !=
+                cudaSuccess)
+                return LBM_ERR_CUDA;
             h->prof_ms[ph] += ms;
         }
     h->prof_steps += h->ev_used;
@@ -83,9 +103,9 @@ int prof_flush(lbm_s *h) {
     return LBM_OK;
 }
 
-inline int prof_mark(lbm_s *h, int k) {
+inline int prof_mark(lbm_s *h, int k, cudaStream_t st) {
     if (!h->prof) return LBM_OK;
-    return cudaEventRecord(h->ev[5 * h->ev_used + k], h->stream) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+    return cudaEventRecord(h->ev[kProfEv * h->ev_used + k], st) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
 // Sync the stream and fold the device status into the sticky error.
@@ -177,6 +197,7 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     if (p.dem_substeps < 1) return LBM_ERR_ARG;
     if (p.precision != LBM_FP32 && p.precision != LBM_BF16_DEV && p.precision != LBM_FP16_DEV) return LBM_ERR_ARG;
     if (p.max_particles < 0) return LBM_ERR_ARG;
+    if (p.schedule != LBM_SCHEDULE_OVERLAP && p.schedule != LBM_SCHEDULE_SERIAL) return LBM_ERR_ARG;
     if (p.max_particles > 0) {
         if (!(p.max_radius > 0.0 && p.max_radius <= 16.0)) return LBM_ERR_ARG;
         // a sphere's bounding box and link tile must not wrap onto itself
@@ -199,10 +220,17 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
         return LBM_ERR_CUDA;
     }
     int rc = LBM_OK;
+    // the link / DEM / geometry chain outranks the far-node collisions of
+    // the second stream when both have blocks waiting for an SM
+    int prio_low = 0, prio_high = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+        cudaGetLastError();
+        prio_low = prio_high = 0;
+    }
     if (p.cuda_stream) {
         h->stream = (cudaStream_t)p.cuda_stream;
     } else {
-        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        if (cudaStreamCreateWithPriority(&h->stream, cudaStreamNonBlocking, prio_high) != cudaSuccess) {
             cudaGetLastError();
             delete h;
             return LBM_ERR_CUDA;
@@ -276,6 +304,37 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
         rc = LBM_ERR_NOMEM;
     }
     if (!rc && M > 0 && links_setup(h->tile_ext, h->link_cap) != LBM_OK) rc = LBM_ERR_CUDA;
+    // overlapped schedule (spheres only): near tags, second stream, events
+    h->overlap = M > 0 && p.schedule == LBM_SCHEDULE_OVERLAP;
+    if (!rc && h->overlap) {
+        // groups of one 32-byte sector of a slot row
+        h->near_shift = h->esize == 4 ? 3 : 4;
+        h->near_ngx = (p.nx + (1 << h->near_shift) - 1) >> h->near_shift;
+        h->near_groups = (long long)h->near_ngx * p.ny * p.nz;
+        const long long NG = h->near_groups;
+        rc = dalloc(h, &h->near[0], (size_t)NG);
+        if (!rc) rc = dalloc(h, &h->near[1], (size_t)NG);
+        // a sphere tags at most (2 ceil(R + 0.05) + 7)^3 nodes, so as many groups
+        const long long e = 2 * (long long)std::ceil(p.max_radius + 0.05) + 7;
+        const long long cap = std::min(NG, (long long)M * e * e * e);
+        if (!rc) rc = dalloc(h, &h->near_list[0], (size_t)cap);
+        if (!rc) rc = dalloc(h, &h->near_list[1], (size_t)cap);
+        if (!rc) rc = dalloc(h, &h->near_cnt, 2);
+        bool ok = !rc && cudaStreamCreateWithPriority(&h->stream2, cudaStreamNonBlocking, prio_low) == cudaSuccess;
+        cudaEvent_t *evs[] = {&h->ev_cf, &h->ev_nm[0], &h->ev_nm[1], &h->ev_join};
+        for (cudaEvent_t *e : evs) ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+        int user_prio = prio_high;
+        if (ok && !h->own_stream) ok = cudaStreamGetPriority(h->stream, &user_prio) == cudaSuccess;
+        if (ok && user_prio != prio_high)
+            ok = cudaStreamCreateWithPriority(&h->chain, cudaStreamNonBlocking, prio_high) == cudaSuccess;
+        if (ok)
+            ok = cudaMemsetAsync(h->near[0], 0, (size_t)NG, h->stream) == cudaSuccess &&
+                 cudaMemsetAsync(h->near[1], 0, (size_t)NG, h->stream) == cudaSuccess;
+        if (!ok && !rc) {
+            cudaGetLastError();
+            rc = LBM_ERR_CUDA;
+        }
+    }
     if (!rc) {
         int per_sm = 0, sms = 0;
         if (dem_max_blocks(kDemThreads, &per_sm) != LBM_OK ||
@@ -283,6 +342,7 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
             rc = LBM_ERR_CUDA;
         h->dem_threads = kDemThreads;
         h->dem_blocks = per_sm * sms;
+        h->sms = sms;
         if (!rc && h->dem_blocks < 1) rc = LBM_ERR_CUDA;
         h->dem_cluster = M > 0 ? dem_cluster_setup(M) : 0;
     }
@@ -383,6 +443,18 @@ int lbm_set_particles(lbm_handle h, int32_t n, const double *pos, const double *
     if (!rc && n) rc = launch_neighbours(h, 1);
     if (!rc && n) rc = launch_mark(h);
     if (!rc && n) rc = launch_contact(h);
+    if (!rc && n && h->overlap) {
+        // near set of step 0 from the initial centres; events in a recorded state
+        if (cudaMemsetAsync(h->near[0], 0, (size_t)h->near_groups, h->stream) != cudaSuccess ||
+            cudaMemsetAsync(h->near[1], 0, (size_t)h->near_groups, h->stream) != cudaSuccess)
+            rc = LBM_ERR_CUDA;
+        if (!rc)
+            rc = launch_near_mark(h, h->near[0], near_tag(0), h->pt.frame[0], h->near_list[0], h->near_cnt,
+                                  h->stream);
+        cudaEvent_t evs[] = {h->ev_cf, h->ev_nm[0], h->ev_nm[1]};
+        for (cudaEvent_t e : evs)
+            if (!rc && cudaEventRecord(e, h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+    }
     if (!rc) rc = settle(h);
     std::free(xf);
     std::free(fr);
@@ -444,28 +516,76 @@ int lbm_step(lbm_handle h, int32_t nsteps) {
     DeviceScope ds(h->device);
     int rc = LBM_OK;
     const bool parts = h->pt.np > 0;
+    const bool ovl = parts && h->overlap;
+    auto ok = [](cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; };
+    // the main-stream work runs on the high-priority `chain` stream, after
+    // and before the caller's stream
+    cudaStream_t user = h->stream;
+    const bool handover = ovl && h->chain;
+    if (handover) {
+        rc = ok(cudaEventRecord(h->ev_join, user));
+        if (!rc) rc = ok(cudaStreamWaitEvent(h->chain, h->ev_join, 0));
+        if (!rc) h->stream = h->chain;
+    }
+    cudaStream_t A = h->stream, Bs = h->stream2;
+    // everything the caller enqueued since the last step (populations set,
+    // loads, ...) precedes this call's far collisions
+    if (ovl && !rc) rc = ok(cudaEventRecord(h->ev_nm[h->steps & 1], A));
     for (int it = 0; it < nsteps && !rc; ++it) {
         const int P = h->parity;
+        const long long s = h->steps;
+        const int cur = (int)(s & 1), nxt = (int)((s + 1) & 1);
         if (h->prof && h->ev_used == h->ev_cap) rc = prof_flush(h);
-        if (!rc && it == nsteps - 1 &&
-            cudaMemsetAsync(h->ctr, 0, 2 * sizeof(unsigned long long), h->stream) != cudaSuccess)
-            rc = LBM_ERR_CUDA;
-        if (!rc) rc = prof_mark(h, 0);
+        if (!rc && it == nsteps - 1) rc = ok(cudaMemsetAsync(h->ctr, 0, 2 * sizeof(unsigned long long), A));
+        if (ovl) {
+            // second stream: the far-node collisions of step s, once the
+            // near tags of step s exist (recorded after step s-1's near
+            // collisions); far nodes touch nothing the link / DEM / geometry
+            // work of steps s-1, s and the near collisions of step s touch
+            if (!rc) rc = ok(cudaStreamWaitEvent(Bs, h->ev_nm[cur], 0));
+            if (!rc) rc = prof_mark(h, E6, Bs);
+            if (!rc) rc = launch_stream_collide(h, P, 1, h->near[cur], near_tag(s), Bs);
+            if (!rc) rc = prof_mark(h, E7, Bs);
+            if (!rc) rc = ok(cudaEventRecord(h->ev_cf, Bs));
+        }
+        if (!rc) rc = prof_mark(h, E0, A);
         if (!rc && parts) rc = launch_mark(h);
         if (!rc && parts) rc = launch_refill(h, P);
-        if (!rc) rc = prof_mark(h, 1);
-        if (!rc) rc = launch_stream_collide(h, P);
-        if (!rc) rc = prof_mark(h, 2);
+        if (!rc) rc = prof_mark(h, E1, A);
+        if (ovl) {
+            if (!rc) rc = launch_collide_list(h, P, h->near_list[cur], h->near_cnt + cur, A);
+            if (!rc) rc = prof_mark(h, E2, A);
+            // near tags and list of step s+1 from the centres step s uses,
+            // while the far collisions of step s run
+            if (!rc && near_tag(s + 1) == 1) rc = ok(cudaMemsetAsync(h->near[nxt], 0, (size_t)h->near_groups, A));
+            if (!rc)
+                rc = launch_near_mark(h, h->near[nxt], near_tag(s + 1), h->pt.frame[cur], h->near_list[nxt],
+                                      h->near_cnt + nxt, A);
+            if (!rc) rc = ok(cudaEventRecord(h->ev_nm[nxt], A));
+            if (!rc) rc = ok(cudaStreamWaitEvent(A, h->ev_cf, 0));
+        } else {
+            if (!rc) rc = launch_stream_collide(h, P);
+            if (!rc) rc = prof_mark(h, E2, A);
+            if (!rc && h->prof) rc = prof_mark(h, E6, A);
+            if (!rc && h->prof) rc = prof_mark(h, E7, A);
+        }
+        if (!rc) rc = prof_mark(h, E3, A);
         if (!rc && parts) rc = launch_links(h, P);
-        if (!rc) rc = prof_mark(h, 3);
+        if (!rc) rc = prof_mark(h, E4, A);
         if (!rc && parts) rc = launch_neighbours(h, 0);
         if (!rc && parts) rc = launch_dem(h);
-        if (!rc) rc = prof_mark(h, 4);
+        if (!rc) rc = prof_mark(h, E5, A);
         if (!rc) {
             if (h->prof) ++h->ev_used;
             h->parity ^= 1;
             ++h->steps;
         }
+    }
+    if (handover && h->stream == h->chain) {
+        h->stream = user;
+        const int r2 = ok(cudaEventRecord(h->ev_join, h->chain));
+        const int r3 = r2 ? r2 : ok(cudaStreamWaitEvent(user, h->ev_join, 0));
+        if (!rc) rc = r3;
     }
     if (!rc && cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
         rc = LBM_ERR_CUDA;
@@ -561,9 +681,9 @@ int lbm_profile(lbm_handle h, int32_t enable) {
     if (!h) return LBM_ERR_ARG;
     DeviceScope ds(h->device);
     if (enable && !h->ev) {
-        h->ev = (cudaEvent_t *)std::calloc(5 * (size_t)kProfSteps, sizeof(cudaEvent_t));
+        h->ev = (cudaEvent_t *)std::calloc(kProfEv * (size_t)kProfSteps, sizeof(cudaEvent_t));
         if (!h->ev) return LBM_ERR_NOMEM;
-        for (int i = 0; i < 5 * kProfSteps; ++i)
+        for (int i = 0; i < kProfEv * kProfSteps; ++i)
             if (cudaEventCreate(&h->ev[i]) != cudaSuccess) {
                 cudaGetLastError();
                 for (int j = 0; j < i; ++j) cudaEventDestroy(h->ev[j]);
@@ -590,7 +710,7 @@ int lbm_profile_read(lbm_handle h, double *ms, int64_t *steps) {
     DeviceScope ds(h->device);
     const int rc = prof_flush(h);
     if (ms)
-        for (int i = 0; i < 4; ++i) ms[i] = h->prof_ms[i];
+        for (int i = 0; i < LBM_PHASES; ++i) ms[i] = h->prof_ms[i];
     if (steps) *steps = h->prof_steps;
     return rc;
 }

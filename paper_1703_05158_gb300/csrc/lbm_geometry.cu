@@ -174,6 +174,108 @@ __global__ void __launch_bounds__(256) k_refill(const Lat L, const SFrame *__res
     }
 }
 
+// Near set of step s+1, from the centres the geometry of step s uses.
+// The far-node collisions of step s+1 run while the link kernel of step s,
+// the geometry of step s+1 and the near-node collisions of step s+1 run.
+// Under the A-A layout a node's collision touches only its own 19 slot
+// locations, so the far collisions are safe if every node whose locations
+// those other kernels touch is near:
+//   links of step s: a fluid node x_f next to a solid node and x_f - c_j,
+//     both within Chebyshev distance 2 of a node inside a sphere of step s;
+//   refill of step s+1: nodes of step s's spheres and their neighbours
+//     (distance 1);
+//   marks of step s+1 (flags read by the collide kernels): nodes inside the
+//     spheres at the new centres, which moved < max_step < 2 since step s,
+//     hence inside the distance-2 dilation of step s's spheres.
+// A node within Chebyshev distance 2 of a point inside a sphere of radius R
+// centred at X has sum_a max(0, |x_a - X_a| - 2)^2 < R^2; the test below
+// adds `margin` to R for the FP32 rounding of the sphere test of k_mark.
+// A group (2^shift nodes along x) is tagged when any of its nodes passes.
+// Thread (0, 0) also clears the count of the list the same stream builds
+// next.
+__global__ void __launch_bounds__(256) k_near_mark(const Lat L, const SFrame *__restrict__ fr, const float margin,
+                                                   uint8_t *__restrict__ near, const uint8_t tag, const int ngx,
+                                                   const int shift, int *__restrict__ count) {
+    const int p = blockIdx.x;
+    if (p == 0 && threadIdx.x == 0) *count = 0;
+    const SFrame F = fr[p];
+    const float Rg = F.R + margin, R2 = Rg * Rg;
+    // |ox - fr| < Rg + 2 with fr in [0, 1): ox in [-(ceil(Rg) + 2), ceil(Rg) + 2]
+    const int e = (int)ceilf(Rg) + 3, B = 2 * e + 1;
+    for (int t = threadIdx.x; t < B * B * B; t += blockDim.x) {
+        const int oz = t / (B * B) - e, oy = (t / B) % B - e, ox = t % B - e;
+        const int z = F.b[2] + oz;
+        if (z < 0 || z >= L.nz) continue;
+        const float ax = fmaxf(0.f, fabsf((float)ox - F.fr[0]) - 2.f);
+        const float ay = fmaxf(0.f, fabsf((float)oy - F.fr[1]) - 2.f);
+        const float az = fmaxf(0.f, fabsf((float)oz - F.fr[2]) - 2.f);
+        if (!(ax * ax + ay * ay + az * az < R2)) continue;
+        const int x = wrapi(F.b[0] + ox, L.nx), y = wrapi(F.b[1] + oy, L.ny);
+        near[(y + L.ny * z) * ngx + (x >> shift)] = tag;
+    }
+}
+
+// Compaction of the entries tagged `tag` into list[0 .. *count), ascending
+// within each 4096-entry chunk (one chunk per block, one atomic per block;
+// the chunks land in any order).  *count must be 0 on entry.
+constexpr int kListPerThread = 16;
+__global__ void __launch_bounds__(256) k_near_list(const uint8_t *__restrict__ near, const uint8_t tag,
+                                                   const long long N, int *__restrict__ list,
+                                                   int *__restrict__ count) {
+    __shared__ int warp_sum[8];
+    __shared__ int base;
+    const long long n0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * kListPerThread;
+    unsigned bits = 0;
+    if (n0 + kListPerThread <= N) {
+        const uint4 v = *(const uint4 *)(near + n0);  // chunk starts are multiples of 16 bytes
+        const unsigned t4 = 0x01010101u * tag;
+        const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const unsigned m = __vcmpeq4(w[k], t4);  // 0xff in each matching byte
+            bits |= (((m >> 7) & 1u) | ((m >> 14) & 2u) | ((m >> 21) & 4u) | ((m >> 28) & 8u)) << (4 * k);
+        }
+    } else {
+        for (int k = 0; k < kListPerThread && n0 + k < N; ++k)
+            if (near[n0 + k] == tag) bits |= 1u << k;
+    }
+    const int c = __popc(bits);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int inc = c;  // inclusive scan over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) warp_sum[wid] = inc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            const int v = warp_sum[k];
+            warp_sum[k] = tot;
+            tot += v;
+        }
+        base = tot ? atomicAdd(count, tot) : 0;
+    }
+    __syncthreads();
+    int o = base + warp_sum[wid] + inc - c;
+    while (bits) {
+        const int k = __ffs(bits) - 1;
+        bits &= bits - 1;
+        list[o++] = (int)(n0 + k);
+    }
+}
+
+int launch_near_mark(lbm_s *h, uint8_t *near, uint8_t tag, const SFrame *frames, int *list, int *count,
+                     cudaStream_t stream) {
+    k_near_mark<<<h->pt.np, 256, 0, stream>>>(h->L, frames, 0.05f, near, tag, h->near_ngx, h->near_shift, count);
+    const long long per_block = 256ll * kListPerThread;
+    const long long blocks = (h->near_groups + per_block - 1) / per_block;
+    k_near_list<<<(unsigned)blocks, 256, 0, stream>>>(near, tag, h->near_groups, list, count);
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
 int launch_mark(lbm_s *h) {
     const SFrame *fcur = h->pt.frame[h->steps & 1];
     k_mark<<<h->pt.np, 256, 0, h->stream>>>(h->L, h->pt, fcur, h->flag, h->owner);

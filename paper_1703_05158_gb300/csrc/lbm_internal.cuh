@@ -78,16 +78,37 @@ template <>
 struct Store<float> {
     static __device__ __forceinline__ float ld(const float *p) { return *p; }
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+    static __device__ __forceinline__ float rt(float v) { return v; }  // v as stored and read back
 };
 template <>
 struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float rt(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 };
 template <>
 struct Store<__half> {
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ float rt(float v) { return __half2float(__float2half_rn(v)); }
+};
+
+// Exact unsigned division of n < 2^31 by a fixed d >= 1 (Granlund and
+// Montgomery 1994, Thm. 4.2): with l = ceil(log2 d) and
+// m = ceil(2^(31+l) / d) < 2^32, floor(n / d) = (n m) >> (31 + l), since
+// 0 <= m d - 2^(31+l) < d <= 2^l.
+struct FastDiv {
+    unsigned m;
+    int sh;
+    explicit FastDiv(unsigned d) {
+        int l = 0;
+        while ((1ull << l) < d) ++l;
+        m = (unsigned)(((1ull << (31 + l)) + d - 1) / d);
+        sh = 31 + l;
+    }
+    __device__ __forceinline__ unsigned div(unsigned n) const {
+        return (unsigned)(((unsigned long long)n * m) >> sh);
+    }
 };
 
 // Lattice extents.  Storage index of node (x, y, z) is x + nx*(y + ny*(z+1)):
@@ -168,6 +189,11 @@ struct Parts {
     double max_step;               // largest displacement allowed in one step
 };
 
+// Tag of the near set used by the collisions of step s (never 0).  Step s
+// uses buffer near[s & 1]; within one buffer the tags run 1..255 and the
+// buffer is cleared before its tag comes back to 1, so no stale tag matches.
+inline uint8_t near_tag(long long s) { return (uint8_t)(1 + (s >> 1) % 255); }
+
 }  // namespace lbm
 
 // Handle (opaque in the ABI).
@@ -196,17 +222,41 @@ struct lbm_s {
     int tile_ext;            // half width of the per-sphere link tile
     int link_cap;            // link-list capacity per sphere (shared memory)
     size_t bytes;
-    // phase profiler: 5 events per step (before geometry, after each phase)
+    // overlap of the next step's far-node collisions with the link / DEM /
+    // geometry chain (see lbm_capi.cu): near-node tags per step parity
+    uint8_t *near[2];
+    cudaStream_t stream2;    // far-node collisions, lowest priority
+    cudaStream_t chain;      // highest priority; runs lbm_step's main-stream work when the caller's stream
+                             // does not have that priority (null otherwise)
+    cudaEvent_t ev_join;     // hand-over between the caller's stream and `chain`
+    // Tags are kept per group of 2^near_shift consecutive nodes along x (one
+    // 32-byte sector of a slot row): group (x >> near_shift) of row
+    // y + ny z is tag entry row * near_ngx + (x >> near_shift).
+    int near_shift, near_ngx;
+    long long near_groups;   // rows * near_ngx
+    int *near_list[2];       // near groups of step parity 0 / 1, compacted
+    int *near_cnt;           // [2] their counts
+    int sms;                 // multiprocessors of the device
+    cudaEvent_t ev_cf;                 // after the far collisions
+    bool overlap;
+    cudaEvent_t ev_nm[2];              // after the near marks of step parity 0 / 1
+    // phase profiler: kProfEv events per step
     cudaEvent_t *ev;
     int ev_cap, ev_used;     // capacity and used count, in steps
     bool prof;
-    double prof_ms[4];
+    double prof_ms[LBM_PHASES];
     long long prof_steps;
 };
 
 // Launchers (one per translation unit).
 namespace lbm {
-int launch_stream_collide(lbm_s *h, int parity);
+// mode 0: every fluid node; 1: nodes whose group is not tagged near
+int launch_stream_collide(lbm_s *h, int parity, int mode = 0, const uint8_t *near = nullptr, uint8_t tag = 0,
+                          cudaStream_t stream = nullptr);
+// near tags of one step into `near`, the tagged groups compacted into list / *count
+int launch_near_mark(lbm_s *h, uint8_t *near, uint8_t tag, const SFrame *frames, int *list, int *count,
+                     cudaStream_t stream);
+int launch_collide_list(lbm_s *h, int parity, const int *list, const int *count, cudaStream_t stream);
 int launch_mark(lbm_s *h);
 int launch_refill(lbm_s *h, int parity);
 int launch_links(lbm_s *h, int parity);

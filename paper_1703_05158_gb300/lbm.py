@@ -37,6 +37,9 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_particles", "lbm_set_particle_l
            "lbm_sync", "lbm_error_string", "lbm_profile", "lbm_profile_read", "lbm_fields_noalloc")
 
 
+SCHEDULES = {"serial": 0, "overlap": 1}
+
+
 class lbm_params(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("periodic_z", ctypes.c_int32),
@@ -46,7 +49,7 @@ class lbm_params(ctypes.Structure):
         ("rho_particle", ctypes.c_double), ("kn", ctypes.c_double), ("restitution", ctypes.c_double),
         ("dem_substeps", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_particles", ctypes.c_int32),
         ("max_radius", ctypes.c_double),
-        ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int32),
+        ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int32), ("schedule", ctypes.c_int32),
     ]
 
 
@@ -219,7 +222,7 @@ def lbm_sync(h):
     return _check(load().lbm_sync(h), "lbm_sync")
 
 
-PHASES = ("geometry", "collide", "links", "dem")
+PHASES = ("geometry", "collide", "links", "dem", "collide_far", "wait_far")
 
 
 def lbm_profile(h, enable):
@@ -228,7 +231,7 @@ def lbm_profile(h, enable):
 
 def lbm_profile_read(h):
     """({phase: total ms}, steps) since profiling was enabled."""
-    ms = (ctypes.c_double * 4)()
+    ms = (ctypes.c_double * len(PHASES))()
     steps = ctypes.c_int64()
     _check(load().lbm_profile_read(h, ctypes.byref(ms), ctypes.byref(steps)), "lbm_profile_read")
     return dict(zip(PHASES, list(ms))), steps.value
@@ -245,7 +248,7 @@ class Lattice:
 
     def __init__(self, nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0), u_hi=(0.0, 0.0, 0.0),
                  rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16, precision="fp32", max_particles=0,
-                 max_radius=4.0, stream=None, device=0):
+                 max_radius=4.0, stream=None, device=0, schedule="serial"):
         p = lbm_params()
         p.nx, p.ny, p.nz, p.periodic_z = nx, ny, nz, 0
         p.tau0, p.cs_smag = tau0, cs
@@ -258,6 +261,7 @@ class Lattice:
         p.max_particles, p.max_radius = max_particles, max_radius
         p.cuda_stream = stream
         p.device = device
+        p.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
         self.params = p
         self.h = lbm_create(p)
         self.shape = (nz, ny, nx)

@@ -156,6 +156,56 @@ def test_many_spheres_moving_lid_contacts_periodic_edges():
     assert info["fluid_nodes"] == int((orc.owner() < 0).sum())
 
 
+def test_mostly_far_nodes_overlapped_schedule():
+    """A large box with a few spheres: most nodes are collided by the second
+    stream while the link / DEM / geometry work runs; 100 steps must still
+    match the oracle node for node.  (The centres differ from the oracle's
+    by rounding, ~1e-6 after 100 steps, so over much longer runs a node
+    right at a sphere surface can eventually fall on different sides.)"""
+    shape = (96, 80, 72)
+    p = inputs.polydisperse(shape, 5, (3.0, 4.5), seed=inputs.SEED_BASE + 21, vmax=0.03)
+    kw = dict(tau0=0.55, cs=0.17, g=(3e-6, 0.0, 0.0), u_hi=(0.04, 0.0, 0.0), rho_s=2.5, kn=1e3,
+              restitution=0.8, dem_substeps=16)
+    lat, orc = make_pair(shape, parts=p, max_radius=5.0, **kw)
+    for n in (1, 2, 47, 50):
+        lat.step(n)
+        orc.step(n)
+        assert np.array_equal(lat.owner(), orc.owner())
+        assert pop_error(lat, orc) <= POP_TOL
+        ef, _, Fo, _ = force_error(lat, orc)
+        assert ef <= FORCE_TOL, (ef, Fo)
+
+
+@pytest.mark.parametrize("case", ["few_spheres_large_box", "dense_slurry"])
+def test_overlapped_and_serial_schedules_are_bitwise_equal(case):
+    """The far-node collisions on the second stream touch no location the
+    link / refill / near-node work touches, so the overlapped schedule gives
+    bitwise the serial schedule's populations, forces and motion."""
+    if case == "few_spheres_large_box":
+        shape = (96, 80, 72)
+        p = inputs.polydisperse(shape, 5, (3.0, 4.5), seed=inputs.SEED_BASE + 21, vmax=0.03)
+    else:
+        shape = (64, 64, 48)
+        p = inputs.slurry_box(box=shape, n=30, radius=4.0, seed=inputs.SEED_BASE + 22)
+    kw = dict(tau0=0.55, cs=0.17, g=(3e-6, 0.0, 0.0), u_hi=(0.04, 0.0, 0.0), rho_s=2.5, kn=1e3,
+              restitution=0.8, dem_substeps=16)
+    L = lbm()
+    lats = []
+    for sched in ("overlap", "serial"):
+        lat = L.Lattice(*shape, max_particles=len(p["R"]), max_radius=5.0, schedule=sched, **kw)
+        lat.set_particles(p["X"], V=p["V"], R=p["R"])
+        lats.append(lat)
+    for n in (1, 2, 3, 60, 94):
+        for lat in lats:
+            lat.step(n)
+        a, b = lats
+        assert np.array_equal(a.owner(), b.owner())
+        assert np.array_equal(a.populations(), b.populations())
+        assert np.array_equal(a.forces()[0], b.forces()[0])
+        for u, v in zip(a.particles(), b.particles()):
+            assert np.array_equal(u, v)
+
+
 def test_no_particles_and_capacity_errors():
     L = lbm()
     lat = L.Lattice(40, 40, 12, tau0=0.7, max_particles=2, max_radius=4.0)
