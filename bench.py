@@ -283,6 +283,73 @@ def run_ours(args, rank, world, local_rank):
     lat.close()
 
 
+def run_batched(args, rank, world, local_rank):
+    """The batched form: 64 independent instances of a parameter sweep (box
+    edges from {48, 64, 96, 128, 160}, radii in [2, 6], solid fraction in
+    [0.05, 0.25], Cs in [0.1, 0.2], tau0 in [0.51, 0.8], body force in
+    [1e-6, 1e-5]), FP32, stepped together; MLUPS over all nodes of all
+    instances."""
+    import numpy as np
+    import torch
+
+    from paper_1703_05158_gb300 import inputs, lbm
+
+    torch.cuda.set_device(local_rank)
+    dev = local_rank
+    stream = torch.cuda.Stream(device=dev)
+    inst = inputs.batch_instances(count=args.batch)
+    cfgs = [dict(nx=i["box"][0], ny=i["box"][1], nz=i["box"][2], precision=args.precision, **i["params"])
+            for i in inst]
+    batch = lbm.Batch(cfgs, stream=ctypes_stream(stream), device=dev)
+    for m, i in zip(batch.members, inst):
+        if len(i["parts"]["R"]):
+            m.set_particles(i["parts"]["X"], V=i["parts"]["V"], R=i["parts"]["R"])
+    tpb, grid, tune_ms = batch.tune()
+    batch.step(args.warmup)
+    batch.sync()
+    infos = [m.info() for m in batch.members]
+    N = sum(int(np.prod(i["box"])) for i in inst)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with Clocks(dev) as clk:
+        start.record(stream)
+        batch.step(args.steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+    batch.sync()
+    ms = start.elapsed_time(end)
+    value = world * N * args.steps / (ms * 1e-3) / 1e6
+    if rank != 0:
+        batch.close()
+        return
+    s = BYTES[args.precision]
+    bytes_collide = sum(inf["fluid_nodes"] * 2 * 19 * s + inf["nodes"] + 2 * i["box"][0] * i["box"][1] * 5 * s
+                        for inf, i in zip(infos, inst))
+    achieved = bytes_collide / (tune_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    line = {
+        "metric": "MLUPS (all nodes of all instances) & % HBM roofline, batched parameter sweep", "value": value,
+        "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else args.precision, "data": "synthetic",
+        "config": {"workload": "batched sweep: %d instances, edges {48..160}, r in [2,6], phi in [0.05,0.25], "
+                               "%s storage" % (len(inst), args.precision),
+                   "instances": len(inst), "nodes": N, "spheres": int(sum(len(i["parts"]["R"]) for i in inst)),
+                   "mean_phi": round(float(np.mean([i["phi"] for i in inst])), 4),
+                   "collide_launch": {"threads": tpb, "blocks": grid},
+                   "l2": "inputs larger than L2 (populations %.2f GB)" % (19 * N * s / 1e9)},
+        "roofline": {"bound": "hbm", "kernel": "k_collide_batch", "achieved": achieved, "peak": peak,
+                     "peak_kind": "%s hbm_gbs" % peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "algorithmic_bytes_per_launch": bytes_collide, "avg_launch_ms": tune_ms},
+        "clocks": clk.summary(),
+        "e2e": None,
+        # per step: one graph of marks, refill, collide, links, neighbours, DEM
+        "gpu_launches": args.steps * 6,
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+
+
 def ctypes_stream(stream):
     return stream.cuda_stream
 
@@ -298,6 +365,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", choices=["serial", "overlap"], default="serial",
                     help="order of the kernels inside a step (same results)")
+    ap.add_argument("--workload", choices=["slurry", "batched"], default="slurry",
+                    help="slurry: the 256^3 box with 2000 spheres; batched: the parameter-sweep batch")
+    ap.add_argument("--batch", type=int, default=64, help="instances of the batched workload")
     ap.add_argument("--box", type=int, default=256,
                     help="cubic box edge for profiling runs; sphere count scaled to keep the solid fraction")
     args = ap.parse_args()
@@ -320,7 +390,10 @@ def main():
 
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    run_ours(args, rank, world, local_rank)
+    if args.workload == "batched":
+        run_batched(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
 

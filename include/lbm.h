@@ -221,6 +221,53 @@ int lbm_sync(lbm_handle h);
 /* Static description of a return code. */
 const char *lbm_error_string(int code);
 
+/* ---- Batched form: many independent simulations stepped together --------
+ *
+ * Not in the paper, which runs its parameter sweeps (particle size, packing
+ * fraction, polydispersity) as separate simulations.  A batch holds `count`
+ * members, each an lbm_handle created from params[i] (its own box, tau0,
+ * Cs, body force, capacities), all on one device, one precision and one
+ * stream (params[0].cuda_stream, or a stream the batch makes).  One batched
+ * step is six launches for all members together: marks, refill, one
+ * persistent collide launch over a table of 256-ish-node chunks of every
+ * member, links, neighbour lists, and the DEM with one thread-block cluster
+ * per member.  The six are captured once per step parity in a CUDA graph
+ * and replayed; the collide's block size and grid come from an autotuner
+ * that times the candidates on the members' own state (which it restores).
+ * Results are bitwise those of stepping each member alone with lbm_step. */
+typedef struct lbm_batch_s *lbm_batch;
+
+/* Create count >= 1 members.  LBM_ERR_ARG if the params differ in device,
+ * precision or stream or one is invalid (as lbm_create), LBM_ERR_UNSUPPORTED
+ * if the DEM cluster cannot hold the largest max_particles. */
+int lbm_batch_create(const lbm_params *params, int32_t count, lbm_batch *out);
+
+/* Destroy the batch and its members (synchronises the stream first). */
+int lbm_batch_destroy(lbm_batch b);
+
+/* Member i (0 <= i < count): use it with lbm_set_particles,
+ * lbm_set_particle_load, lbm_set_populations, lbm_forces, lbm_particles,
+ * lbm_fields, lbm_populations, lbm_geometry, lbm_info and lbm_sync.  The
+ * batch owns it: lbm_step and lbm_destroy on a member return LBM_ERR_ARG. */
+int lbm_batch_handle(lbm_batch b, int32_t i, lbm_handle *out);
+
+/* Run the collide autotuner now (lbm_batch_step runs it on first use):
+ * block sizes 128, 256, 512 x grids of half and all resident blocks and one
+ * block per chunk, three timed launches each on the members' state, which
+ * is copied aside and restored (needs that much free device memory, else
+ * LBM_ERR_NOMEM).  Outputs (each may be NULL): threads per block, blocks,
+ * mean ms per launch of the choice. */
+int lbm_batch_tune(lbm_batch b, int32_t *threads, int32_t *blocks, float *ms);
+
+/* Advance every member by nsteps (asynchronous on the batch stream).
+ * LBM_ERR_ARG if the members are not at the same step parity (a member's
+ * lbm_set_particles resets its step count); a member's sticky error is
+ * returned as is. */
+int lbm_batch_step(lbm_batch b, int32_t nsteps);
+
+/* Wait for the batch stream; the first member's sticky error, if any. */
+int lbm_batch_sync(lbm_batch b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,6 +5,9 @@
 #include <cstring>
 #include <new>
 
+#include <algorithm>
+#include <vector>
+
 #include "lbm_internal.cuh"
 
 using namespace lbm;
@@ -287,7 +290,7 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     if (!rc) rc = dalloc(h, &pt.Fx, 3 * (size_t)M);
     if (!rc) rc = dalloc(h, &pt.Tx, 3 * (size_t)M);
     if (!rc) rc = dalloc(h, &pt.Xbuild, 3 * (size_t)M);
-    if (!rc) rc = dalloc(h, &pt.rebuild, 1);
+    if (!rc) rc = dalloc(h, &pt.rebuild, 2);
     if (!rc) rc = dalloc(h, &pt.frame[0], (size_t)M);
     if (!rc) rc = dalloc(h, &pt.frame[1], (size_t)M);
     if (!rc) rc = dalloc(h, &pt.pairA, (size_t)M * kMaxNbr);
@@ -369,7 +372,7 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
 }
 
 int lbm_destroy(lbm_handle h) {
-    if (!h) return LBM_ERR_ARG;
+    if (!h || h->batch) return LBM_ERR_ARG;  // batch members go with their batch
     DeviceScope ds(h->device);
     cudaStreamSynchronize(h->stream);
     release(h);
@@ -420,7 +423,7 @@ int lbm_set_particles(lbm_handle h, int32_t n, const double *pos, const double *
     if (!rc) rc = copy_in(h, pt.Xf, xf, sizeof(float4) * (size_t)n, LBM_HOST);
     if (!rc) rc = copy_in(h, pt.frame[0], fr, sizeof(SFrame) * (size_t)n, LBM_HOST);
     if (!rc) rc = copy_in(h, pt.frame[1], fr, sizeof(SFrame) * (size_t)n, LBM_HOST);
-    if (!rc && n && cudaMemsetAsync(pt.rebuild, 0, sizeof(int), h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+    if (!rc && n && cudaMemsetAsync(pt.rebuild, 0, 2 * sizeof(int), h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
     if (!rc) rc = copy_in(h, pt.V, vel, v3, LBM_HOST);
     if (!rc) rc = copy_in(h, pt.W, omega, v3, LBM_HOST);
     if (!rc) rc = copy_in(h, pt.R, radius, sizeof(double) * (size_t)n, LBM_HOST);
@@ -456,6 +459,7 @@ int lbm_set_particles(lbm_handle h, int32_t n, const double *pos, const double *
             if (!rc && cudaEventRecord(e, h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
     }
     if (!rc) rc = settle(h);
+    if (h->batch) h->batch->dirty = true;  // sphere counts and grids change
     std::free(xf);
     std::free(fr);
     if (rc == LBM_ERR_CUDA && !h->sticky) h->sticky = rc;
@@ -506,7 +510,7 @@ int lbm_set_populations(lbm_handle h, const double *f, int32_t where) {
 }
 
 int lbm_step(lbm_handle h, int32_t nsteps) {
-    if (!h || nsteps < 0) return LBM_ERR_ARG;
+    if (!h || nsteps < 0 || h->batch) return LBM_ERR_ARG;  // batch members step through lbm_batch_step
     if (h->sticky) return h->sticky;
     const int polled = status_to_code(*h->status_host);  // mirror of an earlier call
     if (polled) {
@@ -719,6 +723,389 @@ int lbm_sync(lbm_handle h) {
     if (!h) return LBM_ERR_ARG;
     DeviceScope ds(h->device);
     return settle(h);
+}
+
+}  // extern "C"
+
+// ---- batched form -----------------------------------------------------------
+
+namespace {
+
+void batch_release(lbm_batch_s *b) {
+    for (cudaGraphExec_t &g : b->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    if (b->dinst) cudaFree(b->dinst);
+    if (b->chunks) cudaFree(b->chunks);
+    b->dinst = nullptr;
+    b->chunks = nullptr;
+    if (b->m) {
+        for (int i = 0; i < b->n; ++i)
+            if (b->m[i]) {
+                b->m[i]->batch = nullptr;
+                lbm_destroy(b->m[i]);
+            }
+        delete[] b->m;
+        b->m = nullptr;
+    }
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    b->stream = nullptr;
+}
+
+// Chunk table: TPB consecutive nodes of one instance per entry.
+int batch_chunks(const lbm_batch_s *b, int tpb, int2 **out, int *count) {
+    std::vector<int2> c;
+    for (int i = 0; i < b->n; ++i)
+        for (long long n0 = 0; n0 < b->m[i]->L.N; n0 += tpb) c.push_back(make_int2(i, (int)n0));
+    *out = nullptr;
+    *count = (int)c.size();
+    if (c.empty()) return LBM_OK;
+    if (cudaMalloc((void **)out, c.size() * sizeof(int2)) != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return LBM_ERR_NOMEM;
+    }
+    if (cudaMemcpy(*out, c.data(), c.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(*out);
+        *out = nullptr;
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}
+
+// Descriptors of the members' current state (sphere counts, pointers).
+int batch_descriptors(lbm_batch_s *b) {
+    std::vector<Inst> I((size_t)b->n);
+    b->max_np = 0;
+    for (int i = 0; i < b->n; ++i) {
+        const lbm_s *h = b->m[i];
+        Inst &a = I[i];
+        a.L = h->L;
+        a.ph = h->ph;
+        a.pt = h->pt;
+        a.f = h->f;
+        a.flag = h->flag;
+        a.owner = h->owner;
+        a.status = h->status;
+        a.ctr = h->ctr;
+        a.dnx = FastDiv((unsigned)h->L.nx);
+        a.dny = FastDiv((unsigned)h->L.ny);
+        b->max_np = std::max(b->max_np, h->pt.np);
+    }
+    if (cudaMemcpy(b->dinst, I.data(), I.size() * sizeof(Inst), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}
+
+// One lattice step of every member, parity P (= step parity).
+int batch_enqueue(const lbm_batch_s *b, int P) {
+    int rc = launch_mark_batch(b, P);
+    if (!rc) rc = launch_refill_batch(b, P);
+    if (!rc) rc = launch_collide_batch(b, P, b->tpb, b->grid, b->chunks, b->nchunks);
+    if (!rc) rc = launch_links_batch(b, P);
+    if (!rc) rc = launch_neighbours_batch(b, P);
+    if (!rc) rc = launch_dem_batch(b, P);
+    return rc;
+}
+
+int batch_capture(lbm_batch_s *b, int P, cudaGraphExec_t *out) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    const int rc = batch_enqueue(b, P);
+    const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (rc || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc ? rc : LBM_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}
+
+// Descriptors, chunk table of the tuned block size, and the two step graphs.
+int batch_prepare(lbm_batch_s *b) {
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    for (cudaGraphExec_t &g : b->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    int rc = batch_descriptors(b);
+    if (!rc && b->chunk_tpb != b->tpb) {
+        if (b->chunks) cudaFree(b->chunks);
+        b->chunks = nullptr;
+        rc = batch_chunks(b, b->tpb, &b->chunks, &b->nchunks);
+        b->chunk_tpb = rc ? 0 : b->tpb;
+    }
+    for (int P = 0; P < 2 && !rc; ++P) rc = batch_capture(b, P, &b->graph[P]);
+    if (!rc) b->dirty = false;
+    return rc;
+}
+
+// Members' common step parity, or -1 if they differ (or a member failed).
+int batch_parity(const lbm_batch_s *b, int *err) {
+    int P = -1;
+    *err = LBM_OK;
+    for (int i = 0; i < b->n; ++i) {
+        lbm_s *h = b->m[i];
+        if (h->sticky) {
+            *err = h->sticky;
+            return -1;
+        }
+        const int polled = status_to_code(*h->status_host);
+        if (polled) {
+            h->sticky = polled;
+            *err = polled;
+            return -1;
+        }
+        if (P < 0) P = h->parity;
+        if (h->parity != P) {
+            *err = LBM_ERR_ARG;
+            return -1;
+        }
+    }
+    return P;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(const lbm_params *params, int32_t count, lbm_batch *out) {
+    if (!params || !out || count < 1) return LBM_ERR_ARG;
+    *out = nullptr;
+    for (int i = 1; i < count; ++i)
+        if (params[i].device != params[0].device || params[i].precision != params[0].precision ||
+            params[i].cuda_stream != params[0].cuda_stream)
+            return LBM_ERR_ARG;
+    lbm_batch_s *b = new (std::nothrow) lbm_batch_s();
+    if (!b) return LBM_ERR_NOMEM;
+    b->device = params[0].device;
+    b->precision = params[0].precision;
+    DeviceScope ds(b->device);
+    if (cudaSetDevice(b->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return LBM_ERR_CUDA;
+    }
+    int rc = LBM_OK;
+    if (params[0].cuda_stream) {
+        b->stream = (cudaStream_t)params[0].cuda_stream;
+    } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess) {
+        b->own_stream = true;
+    } else {
+        cudaGetLastError();
+        rc = LBM_ERR_CUDA;
+    }
+    b->m = rc ? nullptr : new (std::nothrow) lbm_s *[count]();
+    if (!rc && !b->m) rc = LBM_ERR_NOMEM;
+    if (!rc) b->n = count;
+    int max_m = 0;
+    for (int i = 0; i < count && !rc; ++i) {
+        lbm_params p = params[i];
+        p.cuda_stream = b->stream;
+        p.schedule = LBM_SCHEDULE_SERIAL;
+        rc = lbm_create(&p, &b->m[i]);
+        if (rc) {
+            b->m[i] = nullptr;
+            break;
+        }
+        b->m[i]->batch = b;
+        if (p.max_particles > 0) {
+            b->ext = std::max(b->ext, b->m[i]->tile_ext);
+            b->cap = std::max(b->cap, b->m[i]->link_cap);
+            max_m = std::max(max_m, p.max_particles);
+        }
+    }
+    if (!rc && max_m > 0) {
+        b->dem_cluster = dem_cluster_setup(max_m);
+        if (b->dem_cluster == 0) rc = LBM_ERR_UNSUPPORTED;  // the batched DEM needs one cluster per instance
+        if (!rc) rc = dem_cluster_setup_batch(b->dem_cluster);
+        if (!rc) rc = links_setup_batch(b->ext, b->cap);
+    }
+    if (!rc && cudaMalloc((void **)&b->dinst, sizeof(Inst) * (size_t)count) != cudaSuccess) {
+        cudaGetLastError();
+        rc = LBM_ERR_NOMEM;
+    }
+    if (!rc && cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) {
+        cudaGetLastError();
+        rc = LBM_ERR_CUDA;
+    }
+    if (rc) {
+        batch_release(b);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch b) {
+    if (!b) return LBM_ERR_ARG;
+    DeviceScope ds(b->device);
+    cudaStreamSynchronize(b->stream);
+    batch_release(b);
+    delete b;
+    return LBM_OK;
+}
+
+int lbm_batch_handle(lbm_batch b, int32_t i, lbm_handle *out) {
+    if (!b || !out || i < 0 || i >= b->n) return LBM_ERR_ARG;
+    *out = b->m[i];
+    return LBM_OK;
+}
+
+int lbm_batch_tune(lbm_batch b, int32_t *threads, int32_t *blocks, float *ms) {
+    if (!b) return LBM_ERR_ARG;
+    DeviceScope ds(b->device);
+    int err = LBM_OK;
+    const int P = batch_parity(b, &err);
+    if (P < 0) return err;
+    // the trial launches collide the members' real state: keep a copy and put it back
+    size_t total = 0;
+    std::vector<size_t> off((size_t)b->n);
+    for (int i = 0; i < b->n; ++i) {
+        const lbm_s *h = b->m[i];
+        off[i] = total;
+        total += (size_t)Q * h->L.S * h->esize + (size_t)h->L.N + sizeof(int);
+        total = (total + 255) & ~(size_t)255;
+    }
+    unsigned char *save = nullptr;
+    if (cudaMalloc((void **)&save, total) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_NOMEM;
+    }
+    auto copy_state = [&](bool back) {
+        for (int i = 0; i < b->n; ++i) {
+            const lbm_s *h = b->m[i];
+            const size_t fb = (size_t)Q * h->L.S * h->esize;
+            unsigned char *s = save + off[i];
+            void *dev[3] = {h->f, h->flag, h->status};
+            const size_t sz[3] = {fb, (size_t)h->L.N, sizeof(int)};
+            unsigned char *sv[3] = {s, s + fb, s + fb + h->L.N};
+            for (int k = 0; k < 3; ++k) {
+                const cudaError_t e = back ? cudaMemcpyAsync(dev[k], sv[k], sz[k], cudaMemcpyDeviceToDevice, b->stream)
+                                           : cudaMemcpyAsync(sv[k], dev[k], sz[k], cudaMemcpyDeviceToDevice, b->stream);
+                if (e != cudaSuccess) return LBM_ERR_CUDA;
+            }
+        }
+        return LBM_OK;
+    };
+    int rc = batch_descriptors(b);
+    if (!rc) rc = copy_state(false);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = LBM_ERR_CUDA;
+    float best = 1e30f;
+    int best_tpb = 0, best_grid = 0;
+    for (int tpb : {128, 256, 512}) {
+        if (rc) break;
+        int2 *ch = nullptr;
+        int nch = 0, bps = 0;
+        rc = batch_chunks(b, tpb, &ch, &nch);
+        if (!rc) rc = collide_batch_occupancy(b->precision, P, tpb, &bps);
+        if (!rc && nch > 0 && bps > 0) {
+            // persistent grids of 1/2 and 1 times the resident blocks, and one block per chunk
+            const int cands[3] = {std::max(1, b->sms * bps / 2), b->sms * bps, nch};
+            for (int c = 0; c < 3 && !rc; ++c) {
+                const int grid = std::min(cands[c], nch);
+                rc = launch_collide_batch(b, P, tpb, grid, ch, nch);  // warm-up
+                if (!rc && cudaEventRecord(e0, b->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+                for (int r = 0; r < 3 && !rc; ++r) rc = launch_collide_batch(b, P, tpb, grid, ch, nch);
+                if (!rc && cudaEventRecord(e1, b->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+                float t = 0.f;
+                if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+                    rc = LBM_ERR_CUDA;
+                if (!rc && t / 3.f < best) {
+                    best = t / 3.f;
+                    best_tpb = tpb;
+                    best_grid = grid;
+                }
+            }
+        }
+        if (ch) cudaFree(ch);
+    }
+    const int rb = copy_state(true);
+    if (!rc) rc = rb;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess && !rc) rc = LBM_ERR_CUDA;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(save);
+    if (rc) {
+        cudaGetLastError();
+        return rc;
+    }
+    if (best_tpb == 0) {  // nothing to collide: any launch shape does
+        best_tpb = 256;
+        best_grid = 1;
+        best = 0.f;
+    }
+    b->tpb = best_tpb;
+    b->grid = best_grid;
+    b->dirty = true;
+    if (threads) *threads = best_tpb;
+    if (blocks) *blocks = best_grid;
+    if (ms) *ms = best;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch b, int32_t nsteps) {
+    if (!b || nsteps < 0) return LBM_ERR_ARG;
+    DeviceScope ds(b->device);
+    int err = LBM_OK;
+    int P = batch_parity(b, &err);
+    if (P < 0) return err;
+    int rc = LBM_OK;
+    if (!b->tpb) rc = lbm_batch_tune(b, nullptr, nullptr, nullptr);
+    if (!rc && b->dirty) rc = batch_prepare(b);
+    for (int it = 0; it < nsteps && !rc; ++it) {
+        if (cudaGraphLaunch(b->graph[P], b->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+        if (!rc) {
+            for (int i = 0; i < b->n; ++i) {
+                b->m[i]->parity ^= 1;
+                ++b->m[i]->steps;
+            }
+            P ^= 1;
+        }
+    }
+    for (int i = 0; i < b->n && !rc; ++i) {
+        lbm_s *h = b->m[i];
+        if (cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+            rc = LBM_ERR_CUDA;
+    }
+    if (rc) {
+        cudaGetLastError();
+        for (int i = 0; i < b->n; ++i)
+            if (!b->m[i]->sticky) b->m[i]->sticky = rc;
+    }
+    return rc;
+}
+
+int lbm_batch_sync(lbm_batch b) {
+    if (!b) return LBM_ERR_ARG;
+    DeviceScope ds(b->device);
+    int rc = LBM_OK;
+    for (int i = 0; i < b->n; ++i) {
+        const int r = settle(b->m[i]);
+        if (!rc) rc = r;
+    }
+    return rc;
 }
 
 }  // extern "C"

@@ -40,66 +40,89 @@ struct Off32 {
 // Collision of one node (deviations in d, in place): rho (Eq. 5), the
 // force-shifted velocity (Eq. 6), Pi^neq and the Smagorinsky relaxation
 // time (Eq. 18), BGK relaxation towards Eq. (9) by opposite pairs, and the
-// Guo source.  Every collide kernel calls this one function, so a node gets
-// bitwise the same result from any of them.
+// Guo source.  Every collide kernel calls this one function.  Each multiply
+// and add is an explicit round-to-nearest intrinsic (fused where written
+// __fmaf_rn), so the compiler cannot contract differently in different
+// kernels and a node gets bitwise the same result from any of them; the
+// products with lattice-vector components (0 or +-1) round the same either
+// way and are left to the compiler.
 __device__ __forceinline__ void collide_node(const Phys &ph, float (&d)[Q], int *status) {
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        drho += d[i];
-        if (cx(i)) jx += cx(i) > 0 ? d[i] : -d[i];
-        if (cy(i)) jy += cy(i) > 0 ? d[i] : -d[i];
-        if (cz(i)) jz += cz(i) > 0 ? d[i] : -d[i];
+        drho = __fadd_rn(drho, d[i]);
+        if (cx(i)) jx = cx(i) > 0 ? __fadd_rn(jx, d[i]) : __fsub_rn(jx, d[i]);
+        if (cy(i)) jy = cy(i) > 0 ? __fadd_rn(jy, d[i]) : __fsub_rn(jy, d[i]);
+        if (cz(i)) jz = cz(i) > 0 ? __fadd_rn(jz, d[i]) : __fsub_rn(jz, d[i]);
     }
-    const float rho = 1.f + drho;
+    const float rho = __fadd_rn(1.f, drho);
     if (!(rho > 0.f)) atomicOr(status, ST_DIVERGED);
-    const float ir = 1.f / rho;
-    const float ux = jx * ir + 0.5f * ph.g[0];
-    const float uy = jy * ir + 0.5f * ph.g[1];
-    const float uz = jz * ir + 0.5f * ph.g[2];
-    const float uu = ux * ux + uy * uy + uz * uz;
+    const float ir = __fdiv_rn(1.f, rho);
+    const float ux = __fmaf_rn(jx, ir, 0.5f * ph.g[0]);  // g/2 is exact
+    const float uy = __fmaf_rn(jy, ir, 0.5f * ph.g[1]);
+    const float uz = __fmaf_rn(jz, ir, 0.5f * ph.g[2]);
+    const float uu = __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmul_rn(ux, ux)));
     float tau = ph.tau0;
     if (ph.smag > 0.f) {
+        // Pi^neq_ab = sum c_a c_b (f - f^eq) = m_ab - drho delta_ab / 3 - rho u_a u_b, with
+        // m_ab = sum c_a c_b d_i and the D3Q19 identity sum c_a c_b f^eq = rho (delta_ab/3 + u_a u_b)
         float mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f, myz = 0.f;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            if (cx(i)) mxx += d[i];
-            if (cy(i)) myy += d[i];
-            if (cz(i)) mzz += d[i];
-            if (cx(i) * cy(i)) mxy += cx(i) * cy(i) > 0 ? d[i] : -d[i];
-            if (cx(i) * cz(i)) mxz += cx(i) * cz(i) > 0 ? d[i] : -d[i];
-            if (cy(i) * cz(i)) myz += cy(i) * cz(i) > 0 ? d[i] : -d[i];
+            if (cx(i)) mxx = __fadd_rn(mxx, d[i]);
+            if (cy(i)) myy = __fadd_rn(myy, d[i]);
+            if (cz(i)) mzz = __fadd_rn(mzz, d[i]);
+            if (cx(i) * cy(i)) mxy = cx(i) * cy(i) > 0 ? __fadd_rn(mxy, d[i]) : __fsub_rn(mxy, d[i]);
+            if (cx(i) * cz(i)) mxz = cx(i) * cz(i) > 0 ? __fadd_rn(mxz, d[i]) : __fsub_rn(mxz, d[i]);
+            if (cy(i) * cz(i)) myz = cy(i) * cz(i) > 0 ? __fadd_rn(myz, d[i]) : __fsub_rn(myz, d[i]);
         }
-        const float t3 = drho * (1.f / 3.f);
-        const float pxx = mxx - t3 - rho * ux * ux, pyy = myy - t3 - rho * uy * uy, pzz = mzz - t3 - rho * uz * uz;
-        const float pxy = mxy - rho * ux * uy, pxz = mxz - rho * ux * uz, pyz = myz - rho * uy * uz;
-        const float q2 = pxx * pxx + pyy * pyy + pzz * pzz + 2.f * (pxy * pxy + pxz * pxz + pyz * pyz);
-        tau = ph.tau0 + 0.5f * (sqrtf(ph.tau0 * ph.tau0 + ph.smag * sqrtf(q2) * ir) - ph.tau0);
+        const float t3 = __fmul_rn(drho, 1.f / 3.f);
+        const float rux = __fmul_rn(rho, ux), ruy = __fmul_rn(rho, uy), ruz = __fmul_rn(rho, uz);
+        const float pxx = __fmaf_rn(-rux, ux, __fsub_rn(mxx, t3));
+        const float pyy = __fmaf_rn(-ruy, uy, __fsub_rn(myy, t3));
+        const float pzz = __fmaf_rn(-ruz, uz, __fsub_rn(mzz, t3));
+        const float pxy = __fmaf_rn(-rux, uy, mxy), pxz = __fmaf_rn(-rux, uz, mxz), pyz = __fmaf_rn(-ruy, uz, myz);
+        const float off = __fmaf_rn(pyz, pyz, __fmaf_rn(pxz, pxz, __fmul_rn(pxy, pxy)));
+        const float q2 = __fmaf_rn(2.f, off, __fmaf_rn(pzz, pzz, __fmaf_rn(pyy, pyy, __fmul_rn(pxx, pxx))));
+        const float inner = __fmaf_rn(__fmul_rn(ph.smag, __fsqrt_rn(q2)), ir, __fmul_rn(ph.tau0, ph.tau0));
+        tau = __fmaf_rn(0.5f, __fsub_rn(__fsqrt_rn(inner), ph.tau0), ph.tau0);
     }
-    const float om = 1.f / tau;
-    const float base = drho - 1.5f * rho * uu;
-    d[0] += om * (wf(0) * base - d[0]);
+    const float om = __fdiv_rn(1.f, tau);
+
+    // Relaxation towards Eq. (9) (deviation form), by opposite pairs (i, i+9):
+    // f^eq - w = w [drho + rho (4.5 (c.u)^2 - 1.5 u^2)]  +/-  3 w rho (c.u)
+    const float base = __fmaf_rn(-__fmul_rn(1.5f, rho), uu, drho);
+    d[0] = __fmaf_rn(om, __fmaf_rn(wf(0), base, -d[0]), d[0]);
     const bool forced = ph.g[0] != 0.f || ph.g[1] != 0.f || ph.g[2] != 0.f;
-    const float fx = rho * ph.g[0], fy = rho * ph.g[1], fz = rho * ph.g[2];
-    const float uF = ux * fx + uy * fy + uz * fz;
-    const float sk = 1.f - 0.5f * om;
-    if (forced) d[0] += sk * wf(0) * (-3.f * uF);
+    const float fx = __fmul_rn(rho, ph.g[0]), fy = __fmul_rn(rho, ph.g[1]), fz = __fmul_rn(rho, ph.g[2]);
+    const float uF = __fmaf_rn(uz, fz, __fmaf_rn(uy, fy, __fmul_rn(ux, fx)));
+    const float sk = __fmaf_rn(-0.5f, om, 1.f);
+    const float r45 = __fmul_rn(4.5f, rho);
+    if (forced) d[0] = __fmaf_rn(__fmul_rn(sk, wf(0)), __fmul_rn(-3.f, uF), d[0]);
 #pragma unroll
     for (int i = 1; i <= 9; ++i) {
-        const int k = i + 9;
+        const int k = i + 9;  // opp(i)
         const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-        const float sym = wf(i) * (base + 4.5f * rho * cu * cu);
-        const float asym = 3.f * wf(i) * rho * cu;
-        d[i] += om * (sym + asym - d[i]);
-        d[k] += om * (sym - asym - d[k]);
+        const float sym = __fmul_rn(wf(i), __fmaf_rn(__fmul_rn(r45, cu), cu, base));
+        const float asym = __fmul_rn(__fmul_rn(3.f * wf(i), rho), cu);
+        d[i] = __fmaf_rn(om, __fsub_rn(__fadd_rn(sym, asym), d[i]), d[i]);
+        d[k] = __fmaf_rn(om, __fsub_rn(__fsub_rn(sym, asym), d[k]), d[k]);
         if (forced) {
+            // Guo source: w [3 (c - u).F + 9 (c.u)(c.F)], even and odd parts
             const float cF = cx(i) * fx + cy(i) * fy + cz(i) * fz;
-            const float se = sk * wf(i) * (9.f * cu * cF - 3.f * uF);
-            const float so = sk * wf(i) * 3.f * cF;
-            d[i] += se + so;
-            d[k] += se - so;
+            const float skw = __fmul_rn(sk, wf(i));
+            const float se = __fmul_rn(skw, __fmaf_rn(__fmul_rn(9.f, cu), cF, __fmul_rn(-3.f, uF)));
+            const float so = __fmul_rn(__fmul_rn(3.f, skw), cF);
+            d[i] = __fadd_rn(d[i], __fadd_rn(se, so));
+            d[k] = __fadd_rn(d[k], __fsub_rn(se, so));
         }
     }
+}
+
+// Halfway bounce-back value of Eqs. (19, 21) with q = 1/2 for the
+// population k arriving from a wall moving at u: d_stored + 6 w_k (c_k.u).
+__device__ __forceinline__ float wall_push(int k, float dstored, const float *u) {
+    return __fmaf_rn(6.f * wf(k), cx(k) * u[0] + cy(k) * u[1] + cz(k) * u[2], dstored);
 }
 
 // Stream-collide of node (x, y, z), index n, flag fl: load (A-A addressing
@@ -136,8 +159,7 @@ __device__ __forceinline__ void sc_node(const Lat &L, const Phys &ph, T *__restr
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
             if (cz(k) != 1) continue;
-            const float v =
-                Store<T>::rt(d[opp(k)]) + 6.f * wf(k) * (cx(k) * ph.ulo[0] + cy(k) * ph.ulo[1] + cz(k) * ph.ulo[2]);
+            const float v = wall_push(k, Store<T>::rt(d[opp(k)]), ph.ulo);
             const int a = ODD ? k * S + s : opp(k) * S + s + nb(-cx(k), -cy(k), -cz(k));
             Store<T>::st(f + a, v);
         }
@@ -146,8 +168,7 @@ __device__ __forceinline__ void sc_node(const Lat &L, const Phys &ph, T *__restr
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
             if (cz(k) != -1) continue;
-            const float v =
-                Store<T>::rt(d[opp(k)]) + 6.f * wf(k) * (cx(k) * ph.uhi[0] + cy(k) * ph.uhi[1] + cz(k) * ph.uhi[2]);
+            const float v = wall_push(k, Store<T>::rt(d[opp(k)]), ph.uhi);
             const int a = ODD ? k * S + s : opp(k) * S + s + nb(-cx(k), -cy(k), -cz(k));
             Store<T>::st(f + a, v);
         }
@@ -198,6 +219,38 @@ __global__ void __launch_bounds__(256, 4) k_collide_list(const Lat L, const Phys
         const int z = (int)dny.div((unsigned)row);
         const int n = x + L.nx * row;
         sc_node<ODD, T>(L, ph, f, flag, status, x, row - z * L.ny, z, n, flag[n]);
+    }
+}
+
+// Batched form: every node of every instance, one persistent launch.  Chunk
+// c = (instance, first node) covers TPB consecutive nodes of one instance
+// (a block's threads, coalesced); block b takes the contiguous chunk range
+// [b n / G, (b + 1) n / G).  The current instance's descriptor is staged in
+// shared memory (read on use, not held in registers).
+template <int ODD, typename T, int TPB>
+__global__ void __launch_bounds__(TPB, 1024 / TPB) k_collide_batch(const Inst *__restrict__ I,
+                                                                   const int2 *__restrict__ chunks, const int nchunks) {
+    __shared__ __align__(16) unsigned char si_raw[sizeof(Inst)];
+    Inst &si = *reinterpret_cast<Inst *>(si_raw);
+    const int c0 = (int)((long long)nchunks * blockIdx.x / gridDim.x);
+    const int c1 = (int)((long long)nchunks * (blockIdx.x + 1) / gridDim.x);
+    int cur = -1;
+    for (int c = c0; c < c1; ++c) {
+        const int2 ch = chunks[c];
+        if (ch.x != cur) {
+            __syncthreads();
+            const unsigned *src = (const unsigned *)(I + ch.x);
+            unsigned *dst = (unsigned *)&si;
+            for (int w = threadIdx.x; w < (int)(sizeof(Inst) / 4); w += TPB) dst[w] = src[w];
+            __syncthreads();
+            cur = ch.x;
+        }
+        const int n = ch.y + (int)threadIdx.x;
+        if (n >= (int)si.L.N) continue;
+        const int row = (int)si.dnx.div((unsigned)n);
+        const int z = (int)si.dny.div((unsigned)row);
+        sc_node<ODD, T>(si.L, si.ph, (T *)si.f, si.flag, si.status, n - row * si.L.nx, row - z * si.L.ny, z, n,
+                        si.flag[n]);
     }
 }
 
@@ -337,7 +390,7 @@ __global__ void __launch_bounds__(128, 8) k_stream_collide2(const Lat L, const P
                 for (int pass = 0; pass < 2; ++pass) {
                     if ((pass == 0 ? 1 : -1) != cz(k) || zw_in != cz(k)) continue;
                     const float dk = side == 0 ? Pack2<T>::lo(wv[opp(k)]) : Pack2<T>::hi(wv[opp(k)]);
-                    const float v = dk + 6.f * wf(k) * (cx(k) * u[0] + cy(k) * u[1] + cz(k) * u[2]);
+                    const float v = wall_push(k, dk, u);
                     int a;
                     if (ODD) {
                         a = k * S + ss;
@@ -419,6 +472,66 @@ int launch_collide_list(lbm_s *h, int parity, const int *list, const int *count,
         case LBM_FP16_DEV: return launch_list_type<__half>(h, parity, list, count, st);
     }
     return LBM_ERR_ARG;
+}
+
+template <int ODD, typename T, int TPB>
+static cudaError_t collide_batch_t(const lbm_batch_s *b, int grid, const int2 *chunks, int nchunks) {
+    k_collide_batch<ODD, T, TPB><<<grid, TPB, 0, b->stream>>>(b->dinst, chunks, nchunks);
+    return cudaGetLastError();
+}
+
+template <int ODD, typename T>
+static cudaError_t collide_batch_p(const lbm_batch_s *b, int tpb, int grid, const int2 *chunks, int nchunks) {
+    switch (tpb) {
+        case 128: return collide_batch_t<ODD, T, 128>(b, grid, chunks, nchunks);
+        case 256: return collide_batch_t<ODD, T, 256>(b, grid, chunks, nchunks);
+        case 512: return collide_batch_t<ODD, T, 512>(b, grid, chunks, nchunks);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static cudaError_t collide_batch_ty(const lbm_batch_s *b, int P, int tpb, int grid, const int2 *chunks,
+                                    int nchunks) {
+    return P ? collide_batch_p<1, T>(b, tpb, grid, chunks, nchunks) : collide_batch_p<0, T>(b, tpb, grid, chunks, nchunks);
+}
+
+int launch_collide_batch(const lbm_batch_s *b, int P, int tpb, int grid, const int2 *chunks, int nchunks) {
+    if (nchunks == 0) return LBM_OK;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (b->precision) {
+        case LBM_FP32: e = collide_batch_ty<float>(b, P, tpb, grid, chunks, nchunks); break;
+        case LBM_BF16_DEV: e = collide_batch_ty<__nv_bfloat16>(b, P, tpb, grid, chunks, nchunks); break;
+        case LBM_FP16_DEV: e = collide_batch_ty<__half>(b, P, tpb, grid, chunks, nchunks); break;
+    }
+    if (e != cudaSuccess) cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : (e == cudaErrorInvalidValue ? LBM_ERR_ARG : LBM_ERR_CUDA);
+}
+
+template <int ODD, typename T, int TPB>
+static cudaError_t occ_t(int *bps) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_collide_batch<ODD, T, TPB>, TPB, 0);
+}
+
+template <typename T>
+static cudaError_t occ_ty(int P, int tpb, int *bps) {
+    switch (tpb) {
+        case 128: return P ? occ_t<1, T, 128>(bps) : occ_t<0, T, 128>(bps);
+        case 256: return P ? occ_t<1, T, 256>(bps) : occ_t<0, T, 256>(bps);
+        case 512: return P ? occ_t<1, T, 512>(bps) : occ_t<0, T, 512>(bps);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int collide_batch_occupancy(int precision, int P, int tpb, int *blocks_per_sm) {
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (precision) {
+        case LBM_FP32: e = occ_ty<float>(P, tpb, blocks_per_sm); break;
+        case LBM_BF16_DEV: e = occ_ty<__nv_bfloat16>(P, tpb, blocks_per_sm); break;
+        case LBM_FP16_DEV: e = occ_ty<__half>(P, tpb, blocks_per_sm); break;
+    }
+    if (e != cudaSuccess) cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
 }  // namespace lbm

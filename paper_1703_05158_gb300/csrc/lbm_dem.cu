@@ -53,7 +53,8 @@ __device__ __forceinline__ void min_image(const Lat &L, double d[3]) {
     if (d[1] < -0.5 * L.ny) d[1] += L.ny;
 }
 
-// One warp per sphere.  If a rebuild is due (or forced), list every b != a
+// One warp per sphere, step parity sp.  If a rebuild is due (or forced),
+// list every b != a
 // with |X_a - X_b| < R_a + R_b + skin in increasing b (centres staged through
 // shared memory); then compute the pair constants of every list entry for
 // the current centres and velocities:
@@ -61,13 +62,13 @@ __device__ __forceinline__ void min_image(const Lat &L, double d[3]) {
 //   pairB = (V_a - V_b, gamma_n)
 constexpr int kNbrTile = 1024;
 
-__global__ void __launch_bounds__(256) k_neighbours(const Lat L, const Parts pt, const int step, const int force,
-                                                    int *__restrict__ status) {
+__device__ __forceinline__ void neighbours_body(const Lat &L, const Parts &pt, const int sp, const int force,
+                                                int *__restrict__ status) {
     __shared__ float4 tile[kNbrTile];
     const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const bool live = a < pt.np;
-    const bool rebuild = force || *(volatile int *)pt.rebuild >= step;
+    const bool rebuild = force || *(volatile int *)(pt.rebuild + sp) != 0;
     if (rebuild) {
         float4 me = live ? pt.Xf[a] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float ra = me.w + (float)pt.skin;
@@ -195,12 +196,13 @@ __device__ __forceinline__ SFrame make_frame(const double x[3], double R, const 
     return F;
 }
 
-// End of a step for sphere a: store the new state and its frame, flag a sphere
-// that moved max_step in the step (or left the box), request a list rebuild
-// when it drifted skin/2 - max_step from where the lists were built.
+// End of a step (parity sp) for sphere a: store the new state and its frame,
+// flag a sphere that moved max_step in the step (or left the box), and ask
+// the next step's neighbour pass for a list rebuild when it drifted
+// skin/2 - max_step from where the lists were built.
 __device__ __forceinline__ void commit(const Lat &L, const Parts &pt, SFrame *fnext, int a, const double x[3],
                                        const double v[3], const double w[3], const double fc[3], double moved2,
-                                       int step, int *status) {
+                                       int sp, int *status) {
     double b2 = 0.0;
     for (int c = 0; c < 3; ++c) {
         double dd = x[c] - pt.Xbuild[3 * a + c];
@@ -218,7 +220,7 @@ __device__ __forceinline__ void commit(const Lat &L, const Parts &pt, SFrame *fn
     fnext[a] = make_frame(x, pt.R[a], v, w);
     if (!(moved2 < pt.max_step * pt.max_step) || !(x[2] > -0.5 && x[2] < L.nz - 0.5)) atomicOr(status, ST_FAST);
     const double lim = 0.5 * pt.skin - pt.max_step;
-    if (!(b2 < lim * lim)) atomicMax(pt.rebuild, step + 1);
+    if (!(b2 < lim * lim)) pt.rebuild[sp ^ 1] = 1;
 }
 
 __device__ __forceinline__ void cluster_barrier() {
@@ -226,16 +228,18 @@ __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
-// All sub-steps of lattice step `step` in one cluster (gridDim.x CTAs).
-// Thread t of CTA c owns spheres a = c T + t + q G (q < kDemKmax, G = cluster
-// threads).
-__global__ void __launch_bounds__(kDemThreads, 1) k_dem_cluster(const Lat L, const Parts pt, SFrame *fnext,
-                                                                const int step, int *status) {
+// All sub-steps of the lattice step of parity sp in one cluster (gridDim.x
+// CTAs).  Thread t of CTA c owns spheres a = c T + t + q G (q < kDemKmax,
+// G = cluster threads).  The step's neighbour pass has read rebuild[sp], so
+// it is cleared here; the commits may set rebuild[sp ^ 1].
+__device__ __forceinline__ void dem_cluster_body(const Lat &L, const Parts &pt, SFrame *fnext, const int sp,
+                                                 int *status) {
     extern __shared__ float4 dsm[];  // [2][kDemKmax * T][2]: (dx, -), (dv, -)
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const int T = blockDim.x, G = gridDim.x * T, cap = kDemKmax * T;
     const int g0 = blockIdx.x * T + threadIdx.x;
+    if (g0 == 0) pt.rebuild[sp] = 0;
     const int ns = pt.substeps;
     const float h = 1.f / ns, h2 = 0.5f * h;
     const float kn = (float)pt.kn, ce = (float)pt.ce;
@@ -341,8 +345,31 @@ __global__ void __launch_bounds__(kDemThreads, 1) k_dem_cluster(const Lat L, con
         }
         const double f3[3] = {(double)fc[q].x, (double)fc[q].y, (double)fc[q].z};
         const double moved2 = (double)(dx[q].x * dx[q].x + dx[q].y * dx[q].y + dx[q].z * dx[q].z);
-        commit(L, pt, fnext, a, x, v, w, f3, moved2, step, status);
+        commit(L, pt, fnext, a, x, v, w, f3, moved2, sp, status);
     }
+}
+
+__global__ void __launch_bounds__(256) k_neighbours(const Lat L, const Parts pt, const int sp, const int force,
+                                                    int *__restrict__ status) {
+    neighbours_body(L, pt, sp, force, status);
+}
+
+__global__ void __launch_bounds__(kDemThreads, 1) k_dem_cluster(const Lat L, const Parts pt, SFrame *fnext,
+                                                                const int sp, int *status) {
+    dem_cluster_body(L, pt, fnext, sp, status);
+}
+
+// Batched forms: instance blockIdx.y.
+__global__ void __launch_bounds__(256) k_neighbours_b(const Inst *__restrict__ I, const int sp) {
+    const Inst &a = I[blockIdx.y];
+    if ((int)(blockIdx.x * (blockDim.x >> 5)) >= a.pt.np) return;
+    neighbours_body(a.L, a.pt, sp, 0, a.status);
+}
+
+__global__ void __launch_bounds__(kDemThreads, 1) k_dem_cluster_b(const Inst *__restrict__ I, const int sp) {
+    const Inst &a = I[blockIdx.y];
+    if (a.pt.np == 0) return;  // the whole cluster (one instance) leaves together
+    dem_cluster_body(a.L, a.pt, a.pt.frame[sp ^ 1], sp, a.status);
 }
 
 static size_t dem_cluster_smem() { return (size_t)2 * kDemKmax * kDemThreads * 2 * sizeof(float4); }
@@ -385,10 +412,11 @@ __device__ bool grid_barrier(unsigned *bar, unsigned target, int *status) {
 // through global memory (any number of spheres).  pt.V holds the full-step
 // velocity between sub-steps; pt.X stays the start-of-step centre until the
 // commit.
-__global__ void __launch_bounds__(128) k_dem(const Lat L, const Parts pt, SFrame *fnext, const int step,
+__global__ void __launch_bounds__(128) k_dem(const Lat L, const Parts pt, SFrame *fnext, const int sp,
                                              unsigned *bar, int *status) {
     const int G = gridDim.x * blockDim.x;
     const int g0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g0 == 0) pt.rebuild[sp] = 0;
     const int ns = pt.substeps;
     const double h = 1.0 / ns;
     unsigned target = 0;
@@ -435,13 +463,13 @@ __global__ void __launch_bounds__(128) k_dem(const Lat L, const Parts pt, SFrame
             if (c == 1 && dd < -0.5 * L.ny) dd += L.ny;
             moved2 += dd * dd;
         }
-        commit(L, pt, fnext, a, x, v, w, f3, moved2, step, status);
+        commit(L, pt, fnext, a, x, v, w, f3, moved2, sp, status);
     }
 }
 
 int launch_neighbours(lbm_s *h, int force) {
     const int blocks = (h->pt.np * 32 + 255) / 256;
-    k_neighbours<<<blocks, 256, 0, h->stream>>>(h->L, h->pt, (int)h->steps, force, h->status);
+    k_neighbours<<<blocks, 256, 0, h->stream>>>(h->L, h->pt, (int)(h->steps & 1), force, h->status);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
@@ -488,12 +516,49 @@ int dem_cluster_setup(int max_particles) {
     return 0;
 }
 
+int dem_cluster_setup_batch(int cl) {
+    if (cudaFuncSetAttribute(k_dem_cluster_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dem_cluster_smem()) !=
+            cudaSuccess ||
+        (cl > 8 && cudaFuncSetAttribute(k_dem_cluster_b, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                       cudaSuccess)) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}
+
+int launch_neighbours_batch(const lbm_batch_s *b, int sp) {
+    if (b->max_np == 0) return LBM_OK;
+    const int blocks = (b->max_np * 32 + 255) / 256;
+    k_neighbours_b<<<dim3(blocks, b->n), 256, 0, b->stream>>>(b->dinst, sp);
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+// One cluster of b->dem_cluster CTAs per instance.
+int launch_dem_batch(const lbm_batch_s *b, int sp) {
+    if (b->max_np == 0) return LBM_OK;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = b->dem_cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(b->dem_cluster, b->n);
+    cfg.blockDim = dim3(kDemThreads);
+    cfg.dynamicSmemBytes = dem_cluster_smem();
+    cfg.stream = b->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const Inst *I = b->dinst;
+    return cudaLaunchKernelEx(&cfg, k_dem_cluster_b, I, sp) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
 int launch_dem(lbm_s *h) {
     Lat L = h->L;
     Parts pt = h->pt;
     int *status = h->status;
     SFrame *fnext = h->pt.frame[(h->steps + 1) & 1];
-    const int step = (int)h->steps;
+    const int sp = (int)(h->steps & 1);
     if (h->dem_cluster > 0) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
@@ -507,7 +572,7 @@ int launch_dem(lbm_s *h) {
         cfg.stream = h->stream;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, k_dem_cluster, L, pt, fnext, step, status) == cudaSuccess ? LBM_OK
+        return cudaLaunchKernelEx(&cfg, k_dem_cluster, L, pt, fnext, sp, status) == cudaSuccess ? LBM_OK
                                                                                                  : LBM_ERR_CUDA;
     }
     if (cudaMemsetAsync(h->bar, 0, sizeof(unsigned), h->stream) != cudaSuccess) return LBM_ERR_CUDA;
@@ -515,7 +580,7 @@ int launch_dem(lbm_s *h) {
     if (blocks > h->dem_blocks) blocks = h->dem_blocks;
     if (blocks < 1) blocks = 1;
     unsigned *bar = h->bar;
-    void *args[] = {&L, &pt, &fnext, (void *)&step, &bar, &status};
+    void *args[] = {&L, &pt, &fnext, (void *)&sp, &bar, &status};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_dem, dim3(blocks), dim3(h->dem_threads), args, 0,
                                                 h->stream);
     return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;

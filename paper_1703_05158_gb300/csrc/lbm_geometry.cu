@@ -49,8 +49,8 @@ __device__ __forceinline__ int ext_of(float R) { return (int)ceilf(R); }
 
 constexpr int MAX_NBR_SMEM = 64;
 
-__global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
-                                              uint8_t *__restrict__ flag, int32_t *__restrict__ owner) {
+__device__ __forceinline__ void mark_body(const Lat &L, const Parts &pt, const SFrame *__restrict__ fcur,
+                                          uint8_t *__restrict__ flag, int32_t *__restrict__ owner) {
     const int p = blockIdx.x;
     __shared__ SFrame nf[MAX_NBR_SMEM];
     __shared__ int nid[MAX_NBR_SMEM];
@@ -87,6 +87,20 @@ __global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, const
     }
 }
 
+__global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
+                                              uint8_t *__restrict__ flag, int32_t *__restrict__ owner) {
+    mark_body(L, pt, fcur, flag, owner);
+}
+
+// Batched: instance blockIdx.y at step parity sp; block (0, i) also clears
+// the instance's link / refill counters of the step.
+__global__ void __launch_bounds__(256) k_mark_b(const Inst *__restrict__ I, const int sp) {
+    const Inst &a = I[blockIdx.y];
+    if (blockIdx.x == 0 && threadIdx.x < 2) a.ctr[threadIdx.x] = 0ull;
+    if ((int)blockIdx.x >= a.pt.np) return;
+    mark_body(a.L, a.pt, a.pt.frame[sp], a.flag, a.owner);
+}
+
 // One CTA per sphere: collect the uncovered nodes of its previous bounding
 // box, then one warp per node: lane i (1..18) sums the 19 populations of
 // neighbour x + c_i if it is fluid before and after, the warp reduces the
@@ -94,11 +108,11 @@ __global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, const
 constexpr int kRefillCap = 512;
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_refill(const Lat L, const SFrame *__restrict__ fcur,
-                                                const SFrame *__restrict__ fprev, T *__restrict__ f,
-                                                uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
-                                                const int P, unsigned long long *__restrict__ ctr,
-                                                int *__restrict__ status) {
+__device__ __forceinline__ void refill_body(const Lat &L, const SFrame *__restrict__ fcur,
+                                            const SFrame *__restrict__ fprev, T *__restrict__ f,
+                                            uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
+                                            const int P, unsigned long long *__restrict__ ctr,
+                                            int *__restrict__ status) {
     __shared__ int list[kRefillCap];
     __shared__ int count;
     const int p = blockIdx.x;
@@ -172,6 +186,23 @@ __global__ void __launch_bounds__(256) k_refill(const Lat L, const SFrame *__res
             atomicAdd(ctr + 1, 1ull);
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_refill(const Lat L, const SFrame *__restrict__ fcur,
+                                                const SFrame *__restrict__ fprev, T *__restrict__ f,
+                                                uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
+                                                const int P, unsigned long long *__restrict__ ctr,
+                                                int *__restrict__ status) {
+    refill_body<T>(L, fcur, fprev, f, flag, owner, P, ctr, status);
+}
+
+// Batched: instance blockIdx.y; parity P is also the step parity.
+template <typename T>
+__global__ void __launch_bounds__(256) k_refill_b(const Inst *__restrict__ I, const int P) {
+    const Inst &a = I[blockIdx.y];
+    if ((int)blockIdx.x >= a.pt.np) return;
+    refill_body<T>(a.L, a.pt.frame[P], a.pt.frame[P ^ 1], (T *)a.f, a.flag, a.owner, P, a.ctr, a.status);
 }
 
 // Near set of step s+1, from the centres the geometry of step s uses.
@@ -297,6 +328,24 @@ int launch_refill(lbm_s *h, int parity) {
             k_refill<__half><<<h->pt.np, 256, 0, h->stream>>>(h->L, fcur, fprev, (__half *)h->f, h->flag, h->owner,
                                                                parity, h->ctr, h->status);
             break;
+        default: return LBM_ERR_ARG;
+    }
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+int launch_mark_batch(const lbm_batch_s *b, int sp) {
+    if (b->max_np == 0) return LBM_OK;
+    k_mark_b<<<dim3(b->max_np, b->n), 256, 0, b->stream>>>(b->dinst, sp);
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+int launch_refill_batch(const lbm_batch_s *b, int P) {
+    if (b->max_np == 0) return LBM_OK;
+    const dim3 grid(b->max_np, b->n);
+    switch (b->precision) {
+        case LBM_FP32: k_refill_b<float><<<grid, 256, 0, b->stream>>>(b->dinst, P); break;
+        case LBM_BF16_DEV: k_refill_b<__nv_bfloat16><<<grid, 256, 0, b->stream>>>(b->dinst, P); break;
+        case LBM_FP16_DEV: k_refill_b<__half><<<grid, 256, 0, b->stream>>>(b->dinst, P); break;
         default: return LBM_ERR_ARG;
     }
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;

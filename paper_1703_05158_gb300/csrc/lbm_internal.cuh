@@ -100,6 +100,7 @@ struct Store<__half> {
 struct FastDiv {
     unsigned m;
     int sh;
+    FastDiv() : m(0u), sh(0) {}
     explicit FastDiv(unsigned d) {
         int l = 0;
         while ((1ull << l) < d) ++l;
@@ -181,7 +182,7 @@ struct Parts {
     int max_nbr;
     float4 *pairA, *pairB;         // per list entry: (d0, c0) and (dv0, gamma), see lbm_dem.cu
     double *Xbuild;                // centres when the lists were built
-    int *rebuild;                  // 1: rebuild the lists at the next neighbour pass
+    int *rebuild;                  // [2]: rebuild[s & 1] = 1 asks the neighbour pass of step s to rebuild
     SFrame *frame[2];              // frames of the centres of even / odd steps
     double kn, ce, rho_s;          // ce = -2 ln e / sqrt(pi^2 + ln^2 e)
     int substeps;
@@ -196,8 +197,11 @@ inline uint8_t near_tag(long long s) { return (uint8_t)(1 + (s >> 1) % 255); }
 
 }  // namespace lbm
 
+struct lbm_batch_s;
+
 // Handle (opaque in the ABI).
 struct lbm_s {
+    lbm_batch_s *batch;      // the batch this handle belongs to (steps only through it), or null
     lbm_params p;
     lbm::Lat L;
     lbm::Phys ph;
@@ -248,6 +252,43 @@ struct lbm_s {
     long long prof_steps;
 };
 
+namespace lbm {
+
+// What a kernel needs of one simulation; the batched kernels read one per
+// instance from a device array (instance = blockIdx.y, or from a chunk
+// table for the collide).
+struct Inst {
+    Lat L;
+    Phys ph;
+    Parts pt;
+    void *f;
+    uint8_t *flag;
+    int32_t *owner;
+    int *status;
+    unsigned long long *ctr;
+    FastDiv dnx, dny;
+};
+
+}  // namespace lbm
+
+// A batch of independent simulations stepped together (lbm_batch_*).
+struct lbm_batch_s {
+    int n = 0;
+    lbm_s **m = nullptr;          // members (their handles)
+    lbm::Inst *dinst = nullptr;   // device array [n]
+    int2 *chunks = nullptr;       // collide chunk table: (instance, first node), tpb nodes each
+    int nchunks = 0, chunk_tpb = 0;
+    int tpb = 0, grid = 0;        // collide launch picked by the autotuner (0: not tuned)
+    int max_np = 0;               // largest sphere count of a member
+    int ext = 0, cap = 0;         // link tile half width and list capacity (largest over members)
+    int dem_cluster = 0;          // CTAs per instance cluster of the DEM kernel
+    int precision = 0, device = 0, sms = 0;
+    bool dirty = true;            // descriptors / graphs to be rebuilt
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one step from parity 0 / 1
+};
+
 // Launchers (one per translation unit).
 namespace lbm {
 // mode 0: every fluid node; 1: nodes whose group is not tagged near
@@ -274,4 +315,14 @@ int link_capacity(double max_radius);
 size_t link_smem(int ext, int cap);
 int links_setup(int ext, int cap);
 int settle_handle(lbm_s *h);
+// batched forms (all members at step parity sp = P)
+int launch_mark_batch(const lbm_batch_s *b, int sp);
+int launch_refill_batch(const lbm_batch_s *b, int P);
+int launch_collide_batch(const lbm_batch_s *b, int P, int tpb, int grid, const int2 *chunks, int nchunks);
+int collide_batch_occupancy(int precision, int P, int tpb, int *blocks_per_sm);
+int launch_links_batch(const lbm_batch_s *b, int P);
+int links_setup_batch(int ext, int cap);
+int launch_neighbours_batch(const lbm_batch_s *b, int sp);
+int launch_dem_batch(const lbm_batch_s *b, int sp);
+int dem_cluster_setup_batch(int cl);
 }  // namespace lbm

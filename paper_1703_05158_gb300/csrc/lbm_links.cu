@@ -46,12 +46,11 @@ __device__ __forceinline__ void tile_xyz(int t, int B, int B2, unsigned mB, unsi
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, 3) k_links(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
-                                               T *__restrict__ f,
-                                               uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
-                                               const int P, const int ext, const unsigned mB, const unsigned mB2,
-                                               const int cap, int *__restrict__ status,
-                                               unsigned long long *__restrict__ ctr) {
+__device__ __forceinline__ void links_body(const Lat &L, const Parts &pt, const SFrame *__restrict__ fcur,
+                                           T *__restrict__ f, uint8_t *__restrict__ flag,
+                                           const int32_t *__restrict__ owner, const int P, const int ext,
+                                           const unsigned mB, const unsigned mB2, const int cap,
+                                           int *__restrict__ status, unsigned long long *__restrict__ ctr) {
     extern __shared__ unsigned char smem[];
     const int B = 2 * ext + 1, B2 = B * B, B3 = B2 * B;
     uint32_t *list = (uint32_t *)smem;            // cap entries: tile index << 5 | direction
@@ -333,6 +332,25 @@ __global__ void __launch_bounds__(256, 3) k_links(const Lat L, const Parts pt, c
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256, 3) k_links(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
+                                               T *__restrict__ f,
+                                               uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
+                                               const int P, const int ext, const unsigned mB, const unsigned mB2,
+                                               const int cap, int *__restrict__ status,
+                                               unsigned long long *__restrict__ ctr) {
+    links_body<T>(L, pt, fcur, f, flag, owner, P, ext, mB, mB2, cap, status, ctr);
+}
+
+// Batched: instance blockIdx.y; parity P is also the step parity.
+template <typename T>
+__global__ void __launch_bounds__(256, 3) k_links_b(const Inst *__restrict__ I, const int P, const int ext,
+                                                 const unsigned mB, const unsigned mB2, const int cap) {
+    const Inst &a = I[blockIdx.y];
+    if ((int)blockIdx.x >= a.pt.np) return;
+    links_body<T>(a.L, a.pt, a.pt.frame[P], (T *)a.f, a.flag, a.owner, P, ext, mB, mB2, cap, a.status, a.ctr);
+}
+
 int link_capacity(double max_radius) {
     const double r = max_radius < 1.0 ? 1.0 : max_radius;
     return (int)std::ceil(80.0 * r * r) + 64;
@@ -343,13 +361,23 @@ size_t link_smem(int ext, int cap) {
     return 4 * (size_t)cap + ((B3 + 15) & ~(size_t)15) + 2 * ((B3 + 1) / 2);
 }
 
+// Raise (never lower: other handles may need more) a kernel's dynamic
+// shared memory limit to smem bytes.
+template <typename K>
+static cudaError_t raise_smem(K kernel, size_t smem) {
+    cudaFuncAttributes at;
+    cudaError_t e = cudaFuncGetAttributes(&at, kernel);
+    if (e == cudaSuccess && at.maxDynamicSharedSizeBytes < (int)smem)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
+}
+
 int links_setup(int ext, int cap) {
-    const int smem = (int)link_smem(ext, cap);
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_links<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_links<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_links<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const size_t smem = link_smem(ext, cap);
+    cudaError_t e = raise_smem(k_links<float>, smem);
+    if (e == cudaSuccess) e = raise_smem(k_links<__nv_bfloat16>, smem);
+    if (e == cudaSuccess) e = raise_smem(k_links<__half>, smem);
+    if (e != cudaSuccess) cudaGetLastError();
     return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
@@ -372,6 +400,32 @@ int launch_links(lbm_s *h, int parity) {
             k_links<__half><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, fcur, (__half *)h->f, h->flag, h->owner,
                                                                  parity, ext, mB, mB2, cap, h->status, h->ctr);
             break;
+        default: return LBM_ERR_ARG;
+    }
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+int links_setup_batch(int ext, int cap) {
+    const size_t smem = link_smem(ext, cap);
+    cudaError_t e = raise_smem(k_links_b<float>, smem);
+    if (e == cudaSuccess) e = raise_smem(k_links_b<__nv_bfloat16>, smem);
+    if (e == cudaSuccess) e = raise_smem(k_links_b<__half>, smem);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+int launch_links_batch(const lbm_batch_s *b, int P) {
+    if (b->max_np == 0) return LBM_OK;
+    const int ext = b->ext, cap = b->cap;
+    const size_t smem = link_smem(ext, cap);
+    const unsigned B = 2u * ext + 1u, mB = 0xFFFFFFFFu / B + 1u, mB2 = 0xFFFFFFFFu / (B * B) + 1u;
+    const dim3 grid(b->max_np, b->n);
+    switch (b->precision) {
+        case LBM_FP32: k_links_b<float><<<grid, 256, smem, b->stream>>>(b->dinst, P, ext, mB, mB2, cap); break;
+        case LBM_BF16_DEV:
+            k_links_b<__nv_bfloat16><<<grid, 256, smem, b->stream>>>(b->dinst, P, ext, mB, mB2, cap);
+            break;
+        case LBM_FP16_DEV: k_links_b<__half><<<grid, 256, smem, b->stream>>>(b->dinst, P, ext, mB, mB2, cap); break;
         default: return LBM_ERR_ARG;
     }
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;

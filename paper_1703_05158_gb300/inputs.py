@@ -12,6 +12,11 @@ Workloads (all synthetic; the paper measures on no public dataset):
     production workload).
   * ``polydisperse``: radii uniform in [r_min, r_max], as in the paper's
     polydispersity sweep (Sect. 3, d_max/d_min).
+  * ``batch_instances``: a parameter sweep of independent boxes (edges from
+    {48, 64, 96, 128, 160}, radii in [2, 6], solid fraction in [0.05, 0.25],
+    Cs in [0.1, 0.2], tau0 in [0.51, 0.8], body force in [1e-6, 1e-5]) like
+    the paper's sweep over particle size, packing fraction and
+    polydispersity, all drawn from one master seed.
 """
 import numpy as np
 
@@ -22,7 +27,7 @@ def rng(seed):
     return np.random.default_rng(seed)
 
 
-def rsa_spheres(box, n, radius, seed, gap=1.0, wall_gap=1.0, periodic_z=False, max_tries=10 ** 7):
+def rsa_spheres(box, n, radius, seed, gap=1.0, wall_gap=1.0, periodic_z=False, max_tries=10 ** 7, partial=False):
     """Random sequential addition of ``n`` non-overlapping spheres.
 
     ``box`` = (nx, ny, nz); x and y are periodic, the z walls sit at -1/2 and
@@ -30,7 +35,8 @@ def rsa_spheres(box, n, radius, seed, gap=1.0, wall_gap=1.0, periodic_z=False, m
     Proposals are uniform in the box; a proposal is rejected when its surface
     is closer than ``gap`` to an accepted sphere (minimum image) or closer
     than ``wall_gap`` to a z wall.  Radii are drawn once, largest first.
-    Returns (X [n,3], R [n]).
+    Returns (X [n,3], R [n]).  With ``partial``, running out of proposals
+    returns the spheres placed so far (the largest radii) instead of raising.
     """
     nx, ny, nz = box
     g = rng(seed)
@@ -52,6 +58,8 @@ def rsa_spheres(box, n, radius, seed, gap=1.0, wall_gap=1.0, periodic_z=False, m
         while True:
             tries += 1
             if tries > max_tries:
+                if partial:
+                    return X[:a].copy(), R[:a].copy()
                 raise RuntimeError("random sequential addition failed after %d proposals" % max_tries)
             lo_z, hi_z = (0.0, nz) if periodic_z else (r - 0.5 + wall_gap, nz - 0.5 - r - wall_gap)
             if hi_z < lo_z:
@@ -113,3 +121,49 @@ def polydisperse(box, n, r_range, seed, vmax=0.01):
 
 def solid_fraction(box, R):
     return float(np.sum(4.0 / 3.0 * np.pi * np.asarray(R) ** 3) / (box[0] * box[1] * box[2]))
+
+
+def splitmix64(x):
+    """One step of SplitMix64 (Steele, Lea and Flood 2014): (next state, output)."""
+    m = (1 << 64) - 1
+    x = (x + 0x9E3779B97F4A7C15) & m
+    z = x
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return x, z ^ (z >> 31)
+
+
+def batch_instances(master_seed=SEED_BASE + 4, count=64, edges=(48, 64, 96, 128, 160), r_range=(2.0, 6.0),
+                    phi_range=(0.05, 0.25), cs_range=(0.1, 0.2), tau_range=(0.51, 0.8), g_range=(1e-6, 1e-5),
+                    max_spheres=500, vmax=0.01):
+    """Independent instances of a parameter sweep, one seed each from a
+    SplitMix64 stream on ``master_seed``.  Per instance: box edges drawn
+    from ``edges``, a target solid fraction phi, sphere count
+    min(max_spheres, round(phi V / v_mean)) with v_mean the mean sphere
+    volume of radii uniform in ``r_range``, RSA placement (gap 1; a dense
+    box keeps the spheres that fit), velocities uniform in [-vmax, vmax]^3,
+    Cs, tau0 and a body force along x.  Returns a list of dicts with
+    ``box``, ``params`` (Lattice keywords except the box), ``parts`` and the
+    target and realised solid fractions."""
+    r0, r1 = r_range
+    v_mean = 4.0 / 3.0 * np.pi * (r1 ** 4 - r0 ** 4) / (4.0 * (r1 - r0))  # E[4/3 pi r^3]
+    state = int(master_seed)
+    out = []
+    for _ in range(count):
+        state, seed = splitmix64(state)
+        g = rng(seed)
+        box = tuple(int(v) for v in g.choice(edges, size=3))
+        phi = float(g.uniform(*phi_range))
+        cs = float(g.uniform(*cs_range))
+        tau0 = float(g.uniform(*tau_range))
+        gx = float(g.uniform(*g_range))
+        V = box[0] * box[1] * box[2]
+        n = int(min(max_spheres, round(phi * V / v_mean)))
+        sub = int(g.integers(1 << 62))
+        X, R = rsa_spheres(box, n, r_range, sub, max_tries=50 * n + 20000, partial=True)
+        vel = uniform_vectors(len(R), -vmax, vmax, sub + 1)
+        params = dict(tau0=tau0, cs=cs, g=(gx, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16,
+                      max_particles=max(n, 1), max_radius=r1)
+        out.append(dict(box=box, params=params, parts=dict(X=X, V=vel, Om=np.zeros((len(R), 3)), R=R),
+                        phi_target=phi, phi=solid_fraction(box, R) if len(R) else 0.0))
+    return out

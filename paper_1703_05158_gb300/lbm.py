@@ -34,7 +34,9 @@ PRECISIONS = {"fp32": LBM_FP32, "bf16": LBM_BF16_DEV, "fp16": LBM_FP16_DEV}
 
 EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_particles", "lbm_set_particle_load", "lbm_set_populations",
            "lbm_step", "lbm_forces", "lbm_particles", "lbm_fields", "lbm_populations", "lbm_geometry", "lbm_info",
-           "lbm_sync", "lbm_error_string", "lbm_profile", "lbm_profile_read", "lbm_fields_noalloc")
+           "lbm_sync", "lbm_error_string", "lbm_profile", "lbm_profile_read", "lbm_fields_noalloc",
+           "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_handle", "lbm_batch_tune", "lbm_batch_step",
+           "lbm_batch_sync")
 
 
 SCHEDULES = {"serial": 0, "overlap": 1}
@@ -93,6 +95,13 @@ def load(build=True):
         lib.lbm_profile.argtypes = [vp, ip]
         lib.lbm_profile_read.argtypes = [vp, ctypes.c_void_p, ctypes.c_void_p]
         lib.lbm_fields_noalloc.argtypes = [vp, fp, fp]
+        lib.lbm_batch_create.argtypes = [ctypes.POINTER(lbm_params), ip, ctypes.POINTER(vp)]
+        lib.lbm_batch_destroy.argtypes = [vp]
+        lib.lbm_batch_handle.argtypes = [vp, ip, ctypes.POINTER(vp)]
+        lib.lbm_batch_tune.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_float)]
+        lib.lbm_batch_step.argtypes = [vp, ip]
+        lib.lbm_batch_sync.argtypes = [vp]
         lib.lbm_error_string.argtypes = [ctypes.c_int]
         lib.lbm_error_string.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -237,7 +246,59 @@ def lbm_profile_read(h):
     return dict(zip(PHASES, list(ms))), steps.value
 
 
-# ---- convenience wrapper ---------------------------------------------------
+def lbm_batch_create(params_list):
+    arr = (lbm_params * len(params_list))(*params_list)
+    b = ctypes.c_void_p()
+    _check(load().lbm_batch_create(arr, len(params_list), ctypes.byref(b)), "lbm_batch_create")
+    return b
+
+
+def lbm_batch_destroy(b):
+    return _check(load().lbm_batch_destroy(b), "lbm_batch_destroy")
+
+
+def lbm_batch_handle(b, i):
+    h = ctypes.c_void_p()
+    _check(load().lbm_batch_handle(b, int(i), ctypes.byref(h)), "lbm_batch_handle")
+    return h
+
+
+def lbm_batch_tune(b):
+    """(threads per block, blocks, ms per collide launch) picked by the autotuner."""
+    t, g, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(load().lbm_batch_tune(b, ctypes.byref(t), ctypes.byref(g), ctypes.byref(ms)), "lbm_batch_tune")
+    return t.value, g.value, ms.value
+
+
+def lbm_batch_step(b, nsteps=1):
+    return _check(load().lbm_batch_step(b, int(nsteps)), "lbm_batch_step")
+
+
+def lbm_batch_sync(b):
+    return _check(load().lbm_batch_sync(b), "lbm_batch_sync")
+
+
+def make_params(nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0), u_hi=(0.0, 0.0, 0.0),
+                rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16, precision="fp32", max_particles=0,
+                max_radius=4.0, stream=None, device=0, schedule="serial"):
+    """lbm_params from keyword arguments (the Lattice constructor's)."""
+    p = lbm_params()
+    p.nx, p.ny, p.nz, p.periodic_z = nx, ny, nz, 0
+    p.tau0, p.cs_smag = tau0, cs
+    p.body_accel[:] = list(g)
+    p.wall_vel_lo[:] = list(u_lo)
+    p.wall_vel_hi[:] = list(u_hi)
+    p.rho_particle, p.kn, p.restitution = rho_s, kn, restitution
+    p.dem_substeps = dem_substeps
+    p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    p.max_particles, p.max_radius = max_particles, max_radius
+    p.cuda_stream = stream
+    p.device = device
+    p.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
+    return p
+
+
+# ---- convenience wrappers ----------------------------------------------------
 
 class Lattice:
     """One simulation handle; x, y periodic, walls at z = -1/2 and nz - 1/2.
@@ -249,28 +310,31 @@ class Lattice:
     def __init__(self, nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0), u_hi=(0.0, 0.0, 0.0),
                  rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16, precision="fp32", max_particles=0,
                  max_radius=4.0, stream=None, device=0, schedule="serial"):
-        p = lbm_params()
-        p.nx, p.ny, p.nz, p.periodic_z = nx, ny, nz, 0
-        p.tau0, p.cs_smag = tau0, cs
-        p.body_accel[:] = list(g)
-        p.wall_vel_lo[:] = list(u_lo)
-        p.wall_vel_hi[:] = list(u_hi)
-        p.rho_particle, p.kn, p.restitution = rho_s, kn, restitution
-        p.dem_substeps = dem_substeps
-        p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        p.max_particles, p.max_radius = max_particles, max_radius
-        p.cuda_stream = stream
-        p.device = device
-        p.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
+        p = make_params(nx, ny, nz, tau0, cs, g, u_lo, u_hi, rho_s, kn, restitution, dem_substeps, precision,
+                        max_particles, max_radius, stream, device, schedule)
         self.params = p
         self.h = lbm_create(p)
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
         self.np = 0
+        self._owned = True
+
+    @classmethod
+    def member(cls, handle, params):
+        """Wrap a batch member's handle (the batch owns it)."""
+        self = cls.__new__(cls)
+        self.params = params
+        self.h = handle
+        self.shape = (params.nz, params.ny, params.nx)
+        self.N = params.nx * params.ny * params.nz
+        self.np = 0
+        self._owned = False
+        return self
 
     def close(self):
         if getattr(self, "h", None):
-            lbm_destroy(self.h)
+            if getattr(self, "_owned", True):
+                lbm_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -337,3 +401,50 @@ class Lattice:
 
     def profile_read(self):
         return lbm_profile_read(self.h)
+
+
+class Batch:
+    """Independent simulations stepped together (one graph replay per step).
+
+    ``configs`` is a list of keyword dicts for the Lattice constructor (each
+    with nx, ny, nz, tau0, ...); ``members`` are Lattice views of the members
+    (set particles, read forces / fields through them; step the batch)."""
+
+    def __init__(self, configs, stream=None, device=0):
+        plist = []
+        for c in configs:
+            c = dict(c)
+            c.setdefault("stream", stream)
+            c.setdefault("device", device)
+            plist.append(make_params(**c))
+        self.params = plist
+        self.b = lbm_batch_create(plist)
+        self.members = [Lattice.member(lbm_batch_handle(self.b, i), p) for i, p in enumerate(plist)]
+
+    def __len__(self):
+        return len(self.members)
+
+    def __getitem__(self, i):
+        return self.members[i]
+
+    def tune(self):
+        return lbm_batch_tune(self.b)
+
+    def step(self, n=1):
+        lbm_batch_step(self.b, n)
+
+    def sync(self):
+        lbm_batch_sync(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            for m in self.members:
+                m.h = None
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

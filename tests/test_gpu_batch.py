@@ -1,0 +1,116 @@
+"""Batched form: members of a batch, stepped together by graph replays of
+the batched kernels, against the same simulations stepped alone (bitwise:
+the batched kernels run the same per-node and per-sphere code) and one
+member against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1703_05158_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def lbm():
+    from paper_1703_05158_gb300 import lbm as mod
+
+    mod.load()
+    return mod
+
+
+def small_sweep():
+    """Four uneven boxes, one without spheres, different tau0 / Cs / g."""
+    cases = [
+        ((48, 40, 36), 6, (3.0, 4.0), dict(tau0=0.55, cs=0.15, g=(4e-6, 0.0, 0.0))),
+        ((64, 48, 40), 0, None, dict(tau0=0.7, cs=0.1, g=(1e-5, 0.0, 0.0), u_hi=(0.03, 0.0, 0.0))),
+        ((40, 56, 44), 10, (2.0, 5.0), dict(tau0=0.6, cs=0.2, g=(2e-6, 0.0, 0.0))),
+        ((56, 48, 48), 3, (4.0, 5.0), dict(tau0=0.51, cs=0.17, g=(6e-6, 0.0, 0.0), u_hi=(0.05, 0.0, 0.0))),
+    ]
+    out = []
+    for k, (box, n, rr, kw) in enumerate(cases):
+        parts = inputs.polydisperse(box, n, rr, seed=inputs.SEED_BASE + 40 + k, vmax=0.02) if n else None
+        kw = dict(kw, rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16, max_particles=max(n, 1), max_radius=5.0)
+        out.append((box, kw, parts))
+    return out
+
+
+def configs(sweep):
+    return [dict(nx=b[0], ny=b[1], nz=b[2], **kw) for b, kw, _ in sweep]
+
+
+def place(lat, parts):
+    if parts is not None:
+        lat.set_particles(parts["X"], V=parts["V"], R=parts["R"])
+
+
+def test_batch_is_bitwise_the_members_stepped_alone():
+    L = lbm()
+    sweep = small_sweep()
+    batch = L.Batch(configs(sweep))
+    alone = [L.Lattice(*box, **kw) for box, kw, _ in sweep]
+    for m, a, (_, _, parts) in zip(batch.members, alone, sweep):
+        place(m, parts)
+        place(a, parts)
+    tpb, grid, ms = batch.tune()
+    assert tpb in (128, 256, 512) and grid >= 1 and ms >= 0.0
+    for n in (1, 2, 27):  # both graph parities, odd counts
+        batch.step(n)
+        for a in alone:
+            a.step(n)
+        batch.sync()
+        for m, a in zip(batch.members, alone):
+            assert np.array_equal(m.owner(), a.owner())
+            assert np.array_equal(m.populations(), a.populations())
+            if m.np:
+                Fm, Tm = m.forces()
+                Fa, Ta = a.forces()
+                assert np.array_equal(Fm, Fa) and np.array_equal(Tm, Ta)
+                for u, v in zip(m.particles(), a.particles()):
+                    assert np.array_equal(u, v)
+    for m, a in zip(batch.members, alone):
+        assert m.info()["links"] == a.info()["links"]
+    batch.close()
+
+
+def test_batch_member_matches_oracle():
+    L = lbm()
+    sweep = small_sweep()
+    batch = L.Batch(configs(sweep))
+    box, kw, parts = sweep[0]
+    okw = {k: v for k, v in kw.items() if k not in ("max_particles", "max_radius")}
+    orc = oracle.Oracle(*box, **okw)
+    for m, (_, _, p) in zip(batch.members, sweep):
+        place(m, p)
+    orc.set_particles(parts["X"], V=parts["V"], R=parts["R"])
+    batch.step(60)
+    orc.step(60)
+    m = batch.members[0]
+    assert np.array_equal(m.owner(), orc.owner())
+    fo, fg = orc.populations(), m.populations()
+    fluid = orc.owner() < 0
+    assert float((np.abs(fg - fo)[:, fluid] / np.abs(fo[:, fluid])).max()) <= 1e-5
+    Fg, _ = m.forces()
+    Fo, _ = orc.forces()
+    assert float((np.linalg.norm(Fg - Fo, axis=1) / np.linalg.norm(Fo, axis=1)).max()) <= 1e-4
+    batch.close()
+
+
+def test_batch_rules():
+    L = lbm()
+    sweep = small_sweep()[:2]
+    batch = L.Batch(configs(sweep))
+    for m, (_, _, p) in zip(batch.members, sweep):
+        place(m, p)
+    with pytest.raises(L.LbmError):
+        L.lbm_step(batch.members[0].h, 1)  # members step only with their batch
+    with pytest.raises(L.LbmError):
+        L.lbm_destroy(batch.members[0].h)
+    batch.step(1)
+    place(batch.members[0], sweep[0][2])  # resets member 0 to step 0: parities differ
+    with pytest.raises(L.LbmError):
+        batch.step(1)
+    batch.members[1].set_particles(np.zeros((0, 3)), R=np.zeros(0))  # member 1 back to step 0 as well
+    batch.step(2)
+    batch.sync()
+    assert batch.members[0].info()["steps"] == 2
+    batch.close()

@@ -66,12 +66,15 @@ def force_error(lat, orc):
 
 
 def motion_tolerance(orc, steps, rho_s=2.5):
+    """Position and velocity bounds implied by the force tolerance: a relative
+    load error eps = FORCE_TOL held over t steps moves a sphere by at most
+    eps a t^2 / 2 and changes its velocity by at most eps a t (a = |F| / m)."""
     F, _ = orc.forces()
     _, _, _ = orc.particles()
     R = np.asarray(orc._keep[3])
     a = np.linalg.norm(F, axis=1) / (rho_s * 4.0 / 3.0 * np.pi * R ** 3)
     amax = float(a.max())
-    return 1e-5 * amax * steps ** 2 / 2 + 1e-12, 1e-5 * amax * steps + 1e-14
+    return FORCE_TOL * amax * steps ** 2 / 2 + 1e-12, FORCE_TOL * amax * steps + 1e-14
 
 
 def test_rest_state_is_exact():
