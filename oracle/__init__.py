@@ -35,6 +35,15 @@ class OrcParams(ctypes.Structure):
     ]
 
 
+class ChanParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("tau0", ctypes.c_double), ("cs", ctypes.c_double), ("gx", ctypes.c_double), ("u_peak", ctypes.c_double),
+        ("plate_lo", ctypes.c_int * 3), ("plate_hi", ctypes.c_int * 3),
+        ("steps", ctypes.c_int), ("avg_from", ctypes.c_int), ("periodic_x", ctypes.c_int),
+    ]
+
+
 _lib = None
 
 
@@ -68,6 +77,10 @@ def _load():
         lib.orc_feq.argtypes = [ctypes.c_double, dp, dp]
         lib.orc_refill_only.argtypes = [vp]
         lib.orc_set_load.argtypes = [vp, ctypes.c_void_p, ctypes.c_void_p]
+        lib.chan_run.restype = ctypes.c_int
+        lib.chan_run.argtypes = [ctypes.POINTER(ChanParams), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p]
         _lib = lib
     return _lib
 
@@ -214,4 +227,36 @@ def feq(rho, u):
     u = np.ascontiguousarray(u, dtype=np.float64).reshape(3)
     out = np.empty(NQ)
     lib.orc_feq(float(rho), _dp(u), _dp(out))
+    return out
+
+
+def channel(nx, ny, nz, tau0, cs, gx, u_peak, plate_lo, plate_hi, steps, avg_from, X=None, R=None,
+            dtheta=(0.0, 0.0, 0.0), periodic_x=False, populations=False):
+    """The differentiation-form channel (channel_oracle.c): returns a dict with
+    the mean plate drag ``J``, its derivative ``dJ`` along ``dtheta`` (a
+    direction in (u_peak, gx, cs)), the per-step drag ``drag``, the node
+    classes ``type`` [nz, ny, nx] (0 fluid, 1 sphere, 2 inlet, 3 outlet,
+    4 plate) and, if asked, the final populations ``f`` [19, nz, ny, nx]."""
+    lib = _load()
+    p = ChanParams()
+    p.nx, p.ny, p.nz = nx, ny, nz
+    p.tau0, p.cs, p.gx, p.u_peak = tau0, cs, gx, u_peak
+    p.plate_lo[:] = list(plate_lo)
+    p.plate_hi[:] = list(plate_hi)
+    p.steps, p.avg_from, p.periodic_x = steps, avg_from, int(bool(periodic_x))
+    X = np.ascontiguousarray(np.zeros((0, 3)) if X is None else X, dtype=np.float64).reshape(-1, 3)
+    R = np.ascontiguousarray(np.zeros(0) if R is None else R, dtype=np.float64).reshape(-1)
+    dt = np.ascontiguousarray(dtheta, dtype=np.float64)
+    J, dJ = ctypes.c_double(), ctypes.c_double()
+    drag = np.zeros(max(steps, 1))
+    N = nx * ny * nz
+    f = np.zeros(NQ * N) if populations else None
+    typ = np.zeros(N, dtype=np.uint8)
+    rc = lib.chan_run(ctypes.byref(p), len(R), X.ctypes.data, R.ctypes.data, dt.ctypes.data, ctypes.byref(J),
+                      ctypes.byref(dJ), drag.ctypes.data, None if f is None else f.ctypes.data, typ.ctypes.data)
+    if rc != 0:
+        raise ValueError("channel oracle rejected its input")
+    out = dict(J=J.value, dJ=dJ.value, drag=drag[:steps], type=typ.reshape(nz, ny, nx))
+    if f is not None:
+        out["f"] = f.reshape(NQ, nz, ny, nx)
     return out

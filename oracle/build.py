@@ -7,7 +7,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "lbm_oracle.c")
+SRCS = [os.path.join(HERE, "lbm_oracle.c"), os.path.join(HERE, "channel_oracle.c")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbm_oracle.so")
 
@@ -15,11 +15,11 @@ LIB = os.path.join(OUT_DIR, "liblbm_oracle.so")
 def build(force=False):
     """Build ``oracle/_build/liblbm_oracle.so`` if missing or stale; return its path."""
     os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+    if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(s) for s in SRCS):
         return LIB
     tmp = LIB + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-std=gnu11", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", SRC, "-o", tmp, "-lm"]
+           "-fPIC", "-shared"] + SRCS + ["-o", tmp, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB
