@@ -45,16 +45,26 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def collide_source_sha():
+    """First 16 hex digits of the SHA-256 of the collide kernel's sources."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in ("lbm_collide.cu", "lbm_collide_node.cuh"):
+        with open(os.path.join(ROOT, "paper_1703_05158_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(prec):
     """DRAM bytes per collide launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "stream_collide_256cubed_%s.md" % prec)
-    src = os.path.join(ROOT, "paper_1703_05158_gb300", "csrc", "lbm_collide.cu")
     try:
         text = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = collide_source_sha()
         vals = dict(l.split(":", 1) for l in text.splitlines() if l.startswith(("traffic_bytes_per_launch:",
                                                                                   "collide_source_sha256_16:")))
         if vals.get("collide_source_sha256_16:".rstrip(":"), "").strip() != sha:
@@ -350,6 +360,69 @@ def run_batched(args, rank, world, local_rank):
     batch.close()
 
 
+def run_adjoint(args, rank, world, local_rank):
+    """The differentiation form: a 128 x 64 x 64 channel (inlet peak 0.04,
+    pressure outlet, 4 x 40 x 40 plate at x = 80, 200 fixed spheres of radius
+    3, Cs = 0.15, tau0 = 0.6, g = 1e-6), 500 steps, checkpoints every 50, J =
+    plate drag averaged over steps 301..500; one timed "step" is a full
+    gradient evaluation (forward run plus adjoint sweep); MLUPS counts the
+    forward lattice updates of it (N x 500 per evaluation)."""
+    import numpy as np
+    import torch
+
+    from paper_1703_05158_gb300 import inputs, lbm
+
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.Stream(device=local_rank)
+    X, R = inputs.channel_spheres()
+    cfg = dict(nx=128, ny=64, nz=64, tau0=0.6, cs=0.15, gx=1e-6, u_peak=0.04, plate_lo=(80, 12, 12),
+               plate_hi=(83, 51, 51), steps=500, avg_from=301)
+    ch = lbm.Channel(**cfg, checkpoint_every=50, X=X, R=R, device=local_rank, stream=ctypes_stream(stream))
+    for _ in range(args.warmup):
+        ch.forward()
+        ch.backward()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tf = tb = 0.0
+    torch.cuda.synchronize()
+    with Clocks(local_rank) as clk:
+        for _ in range(args.steps):
+            ev[0].record(stream)
+            J = ch.forward()
+            ev[1].record(stream)
+            g = ch.backward()
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            tf += ev[0].elapsed_time(ev[1])
+            tb += ev[1].elapsed_time(ev[2])
+    if rank != 0:
+        return
+    N, S = 128 * 64 * 64, 500
+    ms = (tf + tb) / args.steps
+    # reverse sweep, per node and step: recompute (read G, write G and f, read the 19 link fractions)
+    # and adjoint step (read lambda^{s+1}, f^s and the link fractions, write lambda^s), FP32
+    bytes_bwd = N * S * (4 * 19 * 4 + 4 * 19 * 4)
+    achieved = bytes_bwd / (tb / args.steps * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    line = {
+        "metric": "gradient evaluations of the mean plate drag (forward + adjoint), MLUPS of the forward updates",
+        "value": N * S / (ms * 1e-3) / 1e6, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "differentiation form: 128x64x64 channel, plate 4x40x40 at x=80, 200 fixed spheres "
+                               "R=3, Cs=0.15, tau0=0.6, 500 steps, checkpoints every 50",
+                   "forward_ms": tf / args.steps, "backward_ms": tb / args.steps, "J": J, "grad": list(g),
+                   "l2": "inputs larger than L2 (checkpoint segment states %.2f GB)" % (50 * 19 * N * 4 / 1e9)},
+        "roofline": {"bound": "hbm", "kernel": "reverse sweep (k_chan_step recompute + k_chan_adj)",
+                     "achieved": achieved, "peak": peak, "peak_kind": "%s hbm_gbs" % peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "algorithmic_bytes_per_launch": bytes_bwd // S},
+        "clocks": clk.summary(),
+        "e2e": None,
+        "gpu_launches": args.steps * (S + 1 + (S // 50 + 1) + S + 2 * S),
+    }
+    print(json.dumps(line), flush=True)
+    ch.close()
+
+
 def ctypes_stream(stream):
     return stream.cuda_stream
 
@@ -365,8 +438,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", choices=["serial", "overlap"], default="serial",
                     help="order of the kernels inside a step (same results)")
-    ap.add_argument("--workload", choices=["slurry", "batched"], default="slurry",
-                    help="slurry: the 256^3 box with 2000 spheres; batched: the parameter-sweep batch")
+    ap.add_argument("--workload", choices=["slurry", "batched", "adjoint"], default="slurry",
+                    help="slurry: the 256^3 box with 2000 spheres; batched: the parameter-sweep batch; "
+                         "adjoint: gradient evaluations of the differentiation form")
     ap.add_argument("--batch", type=int, default=64, help="instances of the batched workload")
     ap.add_argument("--box", type=int, default=256,
                     help="cubic box edge for profiling runs; sphere count scaled to keep the solid fraction")
@@ -392,6 +466,8 @@ def main():
         dist.init_process_group("nccl")
     if args.workload == "batched":
         run_batched(args, rank, world, local_rank)
+    elif args.workload == "adjoint":
+        run_adjoint(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

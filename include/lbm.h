@@ -268,6 +268,61 @@ int lbm_batch_step(lbm_batch b, int32_t nsteps);
 /* Wait for the batch stream; the first member's sticky error, if any. */
 int lbm_batch_sync(lbm_batch b);
 
+/* ---- Differentiation form: plate drag of a channel flow and its gradient --
+ *
+ * Not in the paper.  A D3Q19 channel: an inlet plane x = 0 where the
+ * populations are the equilibrium (Eq. 9) at the density of plane x = 1 and
+ * the velocity u_peak 4 zh (1 - zh) x^, zh = (z + 1/2)/nz; an outlet plane
+ * x = nx - 1 at the equilibrium with density 1 and the velocity of plane
+ * nx - 2; y periodic; halfway walls at z = -1/2 and nz - 1/2; a fixed plate
+ * (node box, halfway bounce-back) and fixed spheres (interpolated
+ * bounce-back, Eq. 19).  The collision is the production one (Sect. 2.2:
+ * BGK, Smagorinsky tau of Eq. 18, body force g_x).  J is the plate drag
+ * (x component of the momentum exchange, Eq. 25) averaged over steps
+ * avg_from .. steps.  lbm_channel_backward returns dJ/dtheta,
+ * theta = (inlet_peak, body_accel_x, cs_smag), by a hand-written adjoint of
+ * the step, recomputing the states between checkpoints taken every
+ * checkpoint_every steps of the forward run. */
+typedef struct lbm_channel_s *lbm_channel;
+
+typedef struct {
+    int32_t nx, ny, nz;        /* nx >= 8, nz >= 2 */
+    double tau0;               /* > 1/2 */
+    double cs_smag;            /* theta[2], >= 0 */
+    double body_accel_x;       /* theta[1] */
+    double inlet_peak;         /* theta[0] */
+    int32_t plate_lo[3];       /* plate node box, inclusive (empty if lo > hi); 2 <= x <= nx - 3 */
+    int32_t plate_hi[3];
+    int32_t steps;             /* >= 1 */
+    int32_t avg_from;          /* first step of the drag average, 1 .. steps */
+    int32_t checkpoint_every;  /* K >= 1: device memory holds K + steps/K + 5 lattice states */
+    int32_t device;
+    void *cuda_stream;         /* NULL: the channel makes its own */
+} lbm_channel_params;
+
+/* Create; n fixed spheres (host arrays pos[n][3], radius[n]; x - R > 1 and
+ * x + R < nx - 2).  Decides the node classes and link fractions once. */
+int lbm_channel_create(const lbm_channel_params *params, int32_t n, const double *pos, const double *radius,
+                       lbm_channel *out);
+int lbm_channel_destroy(lbm_channel c);
+
+/* Replace theta = (inlet_peak, body_accel_x, cs_smag); drops the checkpoints. */
+int lbm_channel_set_theta(lbm_channel c, const double *theta);
+
+/* Run steps from rest, keep the checkpoints, *J = the mean plate drag. */
+int lbm_channel_forward(lbm_channel c, double *J);
+
+/* grad[3] = dJ/dtheta at the theta of the last lbm_channel_forward
+ * (LBM_ERR_ARG if there was none since the last set_theta). */
+int lbm_channel_backward(lbm_channel c, double *grad);
+
+/* After a forward: per-step plate drag drag[steps]; the final populations
+ * f[19][nx*ny*nz] (f = w + stored deviation); node classes type[nx*ny*nz]
+ * (0 fluid, 1 sphere, 2 inlet, 3 outlet, 4 plate; geometry needs no forward). */
+int lbm_channel_drag(lbm_channel c, double *drag);
+int lbm_channel_populations(lbm_channel c, double *f);
+int lbm_channel_geometry(lbm_channel c, uint8_t *type);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,18 +35,7 @@ int status_to_code(int st) {
     return LBM_OK;
 }
 
-struct DeviceScope {
-    int prev = -1;
-    explicit DeviceScope(int d) {
-        cudaGetDevice(&prev);
-        if (prev != d) cudaSetDevice(d);
-    }
-    ~DeviceScope() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
+
 
 template <class T>
 int dalloc(lbm_s *h, T **p, size_t n) {

@@ -1,0 +1,98 @@
+// The collision of one node (Sect. 2.2), shared by every kernel that
+// collides: the fused stream-collide kernels of lbm_collide.cu and the
+// channel kernels of the differentiation form (lbm_channel.cu).
+#pragma once
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+// Collision of one node (deviations in d, in place): rho (Eq. 5), the
+// force-shifted velocity (Eq. 6), Pi^neq and the Smagorinsky relaxation
+// time (Eq. 18), BGK relaxation towards Eq. (9) by opposite pairs, and the
+// Guo source.  Every collide kernel calls this one function.  Each multiply
+// and add is an explicit round-to-nearest intrinsic (fused where written
+// __fmaf_rn), so the compiler cannot contract differently in different
+// kernels and a node gets bitwise the same result from any of them; the
+// products with lattice-vector components (0 or +-1) round the same either
+// way and are left to the compiler.
+__device__ __forceinline__ void collide_node(const Phys &ph, float (&d)[Q], int *status) {
+    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        drho = __fadd_rn(drho, d[i]);
+        if (cx(i)) jx = cx(i) > 0 ? __fadd_rn(jx, d[i]) : __fsub_rn(jx, d[i]);
+        if (cy(i)) jy = cy(i) > 0 ? __fadd_rn(jy, d[i]) : __fsub_rn(jy, d[i]);
+        if (cz(i)) jz = cz(i) > 0 ? __fadd_rn(jz, d[i]) : __fsub_rn(jz, d[i]);
+    }
+    const float rho = __fadd_rn(1.f, drho);
+    if (!(rho > 0.f)) atomicOr(status, ST_DIVERGED);
+    const float ir = __fdiv_rn(1.f, rho);
+    const float ux = __fmaf_rn(jx, ir, 0.5f * ph.g[0]);  // g/2 is exact
+    const float uy = __fmaf_rn(jy, ir, 0.5f * ph.g[1]);
+    const float uz = __fmaf_rn(jz, ir, 0.5f * ph.g[2]);
+    const float uu = __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmul_rn(ux, ux)));
+    float tau = ph.tau0;
+    if (ph.smag > 0.f) {
+        // Pi^neq_ab = sum c_a c_b (f - f^eq) = m_ab - drho delta_ab / 3 - rho u_a u_b, with
+        // m_ab = sum c_a c_b d_i and the D3Q19 identity sum c_a c_b f^eq = rho (delta_ab/3 + u_a u_b)
+        float mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f, myz = 0.f;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            if (cx(i)) mxx = __fadd_rn(mxx, d[i]);
+            if (cy(i)) myy = __fadd_rn(myy, d[i]);
+            if (cz(i)) mzz = __fadd_rn(mzz, d[i]);
+            if (cx(i) * cy(i)) mxy = cx(i) * cy(i) > 0 ? __fadd_rn(mxy, d[i]) : __fsub_rn(mxy, d[i]);
+            if (cx(i) * cz(i)) mxz = cx(i) * cz(i) > 0 ? __fadd_rn(mxz, d[i]) : __fsub_rn(mxz, d[i]);
+            if (cy(i) * cz(i)) myz = cy(i) * cz(i) > 0 ? __fadd_rn(myz, d[i]) : __fsub_rn(myz, d[i]);
+        }
+        const float t3 = __fmul_rn(drho, 1.f / 3.f);
+        const float rux = __fmul_rn(rho, ux), ruy = __fmul_rn(rho, uy), ruz = __fmul_rn(rho, uz);
+        const float pxx = __fmaf_rn(-rux, ux, __fsub_rn(mxx, t3));
+        const float pyy = __fmaf_rn(-ruy, uy, __fsub_rn(myy, t3));
+        const float pzz = __fmaf_rn(-ruz, uz, __fsub_rn(mzz, t3));
+        const float pxy = __fmaf_rn(-rux, uy, mxy), pxz = __fmaf_rn(-rux, uz, mxz), pyz = __fmaf_rn(-ruy, uz, myz);
+        const float off = __fmaf_rn(pyz, pyz, __fmaf_rn(pxz, pxz, __fmul_rn(pxy, pxy)));
+        const float q2 = __fmaf_rn(2.f, off, __fmaf_rn(pzz, pzz, __fmaf_rn(pyy, pyy, __fmul_rn(pxx, pxx))));
+        const float inner = __fmaf_rn(__fmul_rn(ph.smag, __fsqrt_rn(q2)), ir, __fmul_rn(ph.tau0, ph.tau0));
+        tau = __fmaf_rn(0.5f, __fsub_rn(__fsqrt_rn(inner), ph.tau0), ph.tau0);
+    }
+    const float om = __fdiv_rn(1.f, tau);
+
+    // Relaxation towards Eq. (9) (deviation form), by opposite pairs (i, i+9):
+    // f^eq - w = w [drho + rho (4.5 (c.u)^2 - 1.5 u^2)]  +/-  3 w rho (c.u)
+    const float base = __fmaf_rn(-__fmul_rn(1.5f, rho), uu, drho);
+    d[0] = __fmaf_rn(om, __fmaf_rn(wf(0), base, -d[0]), d[0]);
+    const bool forced = ph.g[0] != 0.f || ph.g[1] != 0.f || ph.g[2] != 0.f;
+    const float fx = __fmul_rn(rho, ph.g[0]), fy = __fmul_rn(rho, ph.g[1]), fz = __fmul_rn(rho, ph.g[2]);
+    const float uF = __fmaf_rn(uz, fz, __fmaf_rn(uy, fy, __fmul_rn(ux, fx)));
+    const float sk = __fmaf_rn(-0.5f, om, 1.f);
+    const float r45 = __fmul_rn(4.5f, rho);
+    if (forced) d[0] = __fmaf_rn(__fmul_rn(sk, wf(0)), __fmul_rn(-3.f, uF), d[0]);
+#pragma unroll
+    for (int i = 1; i <= 9; ++i) {
+        const int k = i + 9;  // opp(i)
+        const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+        const float sym = __fmul_rn(wf(i), __fmaf_rn(__fmul_rn(r45, cu), cu, base));
+        const float asym = __fmul_rn(__fmul_rn(3.f * wf(i), rho), cu);
+        d[i] = __fmaf_rn(om, __fsub_rn(__fadd_rn(sym, asym), d[i]), d[i]);
+        d[k] = __fmaf_rn(om, __fsub_rn(__fsub_rn(sym, asym), d[k]), d[k]);
+        if (forced) {
+            // Guo source: w [3 (c - u).F + 9 (c.u)(c.F)], even and odd parts
+            const float cF = cx(i) * fx + cy(i) * fy + cz(i) * fz;
+            const float skw = __fmul_rn(sk, wf(i));
+            const float se = __fmul_rn(skw, __fmaf_rn(__fmul_rn(9.f, cu), cF, __fmul_rn(-3.f, uF)));
+            const float so = __fmul_rn(__fmul_rn(3.f, skw), cF);
+            d[i] = __fadd_rn(d[i], __fadd_rn(se, so));
+            d[k] = __fadd_rn(d[k], __fsub_rn(se, so));
+        }
+    }
+}
+
+// Halfway bounce-back value of Eqs. (19, 21) with q = 1/2 for the
+// population k arriving from a wall moving at u: d_stored + 6 w_k (c_k.u).
+__device__ __forceinline__ float wall_push(int k, float dstored, const float *u) {
+    return __fmaf_rn(6.f * wf(k), cx(k) * u[0] + cy(k) * u[1] + cz(k) * u[2], dstored);
+}
+
+}  // namespace lbm

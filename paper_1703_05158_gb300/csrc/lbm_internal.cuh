@@ -190,6 +190,21 @@ struct Parts {
     double max_step;               // largest displacement allowed in one step
 };
 
+// Makes device d current for the lifetime of the object, then restores the
+// caller's device.
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int d) {
+        cudaGetDevice(&prev);
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceScope() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 // Tag of the near set used by the collisions of step s (never 0).  Step s
 // uses buffer near[s & 1]; within one buffer the tags run 1..255 and the
 // buffer is cleared before its tag comes back to 1, so no stale tag matches.

@@ -167,3 +167,30 @@ def batch_instances(master_seed=SEED_BASE + 4, count=64, edges=(48, 64, 96, 128,
         out.append(dict(box=box, params=params, parts=dict(X=X, V=vel, Om=np.zeros((len(R), 3)), R=R),
                         phi_target=phi, phi=solid_fraction(box, R) if len(R) else 0.0))
     return out
+
+
+def channel_spheres(seed=SEED_BASE + 5, n=200, radius=3.0, box=(128, 64, 64), x_range=(4.0, 74.0), gap=1.0,
+                    max_tries=10 ** 6):
+    """Random sequential addition of n spheres of one radius upstream in a
+    channel: centres with x in [x_range[0] + R, x_range[1] - R] (x is not
+    periodic), y periodic, at least ``gap`` from each other's surfaces and
+    from the z walls (at -1/2 and nz - 1/2).  Returns (X [n, 3], R [n])."""
+    nx, ny, nz = box
+    g = rng(seed)
+    X = np.zeros((n, 3))
+    R = np.full(n, float(radius))
+    lo = np.array([x_range[0] + radius, 0.0, radius - 0.5 + gap])
+    hi = np.array([x_range[1] - radius, float(ny), nz - 0.5 - radius - gap])
+    tries = 0
+    for a in range(n):
+        while True:
+            tries += 1
+            if tries > max_tries:
+                raise RuntimeError("channel sphere placement failed")
+            p = g.uniform(lo, hi)
+            d = X[:a] - p
+            d[:, 1] -= ny * np.round(d[:, 1] / ny)
+            if a == 0 or np.min(np.einsum("ij,ij->i", d, d)) >= (2 * radius + gap) ** 2:
+                X[a] = p
+                break
+    return X, R

@@ -36,7 +36,9 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_particles", "lbm_set_particle_l
            "lbm_step", "lbm_forces", "lbm_particles", "lbm_fields", "lbm_populations", "lbm_geometry", "lbm_info",
            "lbm_sync", "lbm_error_string", "lbm_profile", "lbm_profile_read", "lbm_fields_noalloc",
            "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_handle", "lbm_batch_tune", "lbm_batch_step",
-           "lbm_batch_sync")
+           "lbm_batch_sync", "lbm_channel_create", "lbm_channel_destroy", "lbm_channel_set_theta",
+           "lbm_channel_forward", "lbm_channel_backward", "lbm_channel_drag", "lbm_channel_populations",
+           "lbm_channel_geometry")
 
 
 SCHEDULES = {"serial": 0, "overlap": 1}
@@ -52,6 +54,17 @@ class lbm_params(ctypes.Structure):
         ("dem_substeps", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_particles", ctypes.c_int32),
         ("max_radius", ctypes.c_double),
         ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int32), ("schedule", ctypes.c_int32),
+    ]
+
+
+class lbm_channel_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("tau0", ctypes.c_double), ("cs_smag", ctypes.c_double), ("body_accel_x", ctypes.c_double),
+        ("inlet_peak", ctypes.c_double),
+        ("plate_lo", ctypes.c_int32 * 3), ("plate_hi", ctypes.c_int32 * 3),
+        ("steps", ctypes.c_int32), ("avg_from", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
+        ("device", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
     ]
 
 
@@ -102,6 +115,14 @@ def load(build=True):
                                        ctypes.POINTER(ctypes.c_float)]
         lib.lbm_batch_step.argtypes = [vp, ip]
         lib.lbm_batch_sync.argtypes = [vp]
+        lib.lbm_channel_create.argtypes = [ctypes.POINTER(lbm_channel_params), ip, dp, dp, ctypes.POINTER(vp)]
+        lib.lbm_channel_destroy.argtypes = [vp]
+        lib.lbm_channel_set_theta.argtypes = [vp, dp]
+        lib.lbm_channel_forward.argtypes = [vp, dp]
+        lib.lbm_channel_backward.argtypes = [vp, dp]
+        lib.lbm_channel_drag.argtypes = [vp, dp]
+        lib.lbm_channel_populations.argtypes = [vp, dp]
+        lib.lbm_channel_geometry.argtypes = [vp, vp]
         lib.lbm_error_string.argtypes = [ctypes.c_int]
         lib.lbm_error_string.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -442,6 +463,105 @@ class Batch:
                 m.h = None
             lbm_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lbm_channel_create(params, X, R):
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+    R = np.ascontiguousarray(R, dtype=np.float64).reshape(-1)
+    c = ctypes.c_void_p()
+    _check(load().lbm_channel_create(ctypes.byref(params), len(R), X.ctypes.data, R.ctypes.data, ctypes.byref(c)),
+           "lbm_channel_create")
+    return c
+
+
+def lbm_channel_destroy(c):
+    return _check(load().lbm_channel_destroy(c), "lbm_channel_destroy")
+
+
+def lbm_channel_set_theta(c, theta):
+    t = np.ascontiguousarray(theta, dtype=np.float64).reshape(3)
+    return _check(load().lbm_channel_set_theta(c, t.ctypes.data), "lbm_channel_set_theta")
+
+
+def lbm_channel_forward(c):
+    J = ctypes.c_double()
+    _check(load().lbm_channel_forward(c, ctypes.byref(J)), "lbm_channel_forward")
+    return J.value
+
+
+def lbm_channel_backward(c):
+    g = np.zeros(3)
+    _check(load().lbm_channel_backward(c, g.ctypes.data), "lbm_channel_backward")
+    return g
+
+
+def lbm_channel_drag(c, steps):
+    d = np.zeros(steps)
+    _check(load().lbm_channel_drag(c, d.ctypes.data), "lbm_channel_drag")
+    return d
+
+
+def lbm_channel_populations(c, n):
+    f = np.zeros(19 * n)
+    _check(load().lbm_channel_populations(c, f.ctypes.data), "lbm_channel_populations")
+    return f
+
+
+def lbm_channel_geometry(c, n):
+    t = np.zeros(n, dtype=np.uint8)
+    _check(load().lbm_channel_geometry(c, t.ctypes.data), "lbm_channel_geometry")
+    return t
+
+
+class Channel:
+    """The differentiation form (lbm_channel_*): inlet / outlet channel with a
+    fixed plate and fixed spheres; ``forward()`` -> mean plate drag J,
+    ``backward()`` -> dJ/d(inlet_peak, body_accel_x, cs_smag)."""
+
+    def __init__(self, nx, ny, nz, tau0, cs, gx, u_peak, plate_lo, plate_hi, steps, avg_from, checkpoint_every=50,
+                 X=None, R=None, device=0, stream=None):
+        p = lbm_channel_params()
+        p.nx, p.ny, p.nz = nx, ny, nz
+        p.tau0, p.cs_smag, p.body_accel_x, p.inlet_peak = tau0, cs, gx, u_peak
+        p.plate_lo[:] = list(plate_lo)
+        p.plate_hi[:] = list(plate_hi)
+        p.steps, p.avg_from, p.checkpoint_every = steps, avg_from, checkpoint_every
+        p.device, p.cuda_stream = device, stream
+        self.c = lbm_channel_create(p, np.zeros((0, 3)) if X is None else X, np.zeros(0) if R is None else R)
+        self.params = p
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        self.theta = (u_peak, gx, cs)
+
+    def set_theta(self, theta):
+        lbm_channel_set_theta(self.c, theta)
+        self.theta = tuple(float(v) for v in np.asarray(theta, dtype=np.float64).reshape(3))
+
+    def forward(self):
+        return lbm_channel_forward(self.c)
+
+    def backward(self):
+        return lbm_channel_backward(self.c)
+
+    def drag(self):
+        return lbm_channel_drag(self.c, self.params.steps)
+
+    def populations(self):
+        return lbm_channel_populations(self.c, self.N).reshape((19,) + self.shape)
+
+    def geometry(self):
+        return lbm_channel_geometry(self.c, self.N).reshape(self.shape)
+
+    def close(self):
+        if getattr(self, "c", None):
+            lbm_channel_destroy(self.c)
+            self.c = None
 
     def __del__(self):
         try:

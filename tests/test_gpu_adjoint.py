@@ -1,0 +1,125 @@
+"""Differentiation form on the GPU (lbm_channel_*): geometry, forward run
+and the adjoint gradient of the mean plate drag against the FP64 channel
+oracle (its value, its tangent-linear pass and its central differences),
+independence of the checkpoint interval, the torch.autograd path, and the
+full-size workload against stored oracle values."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1703_05158_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GRAD_TOL = 1e-3
+
+MEDIUM = dict(nx=48, ny=20, nz=24, tau0=0.6, cs=0.15, gx=2e-6, u_peak=0.04, plate_lo=(30, 5, 6),
+              plate_hi=(31, 14, 17), steps=160, avg_from=81)
+
+
+def medium_spheres():
+    return inputs.channel_spheres(seed=inputs.SEED_BASE + 30, n=4, radius=2.5, box=(48, 20, 24), x_range=(6.0, 24.0))
+
+
+def lbm():
+    from paper_1703_05158_gb300 import lbm as mod
+
+    mod.load()
+    return mod
+
+
+def gpu_channel(cfg, X, R, K):
+    return lbm().Channel(**cfg, checkpoint_every=K, X=X, R=R)
+
+
+def test_geometry_is_the_oracle_geometry():
+    X, R = medium_spheres()
+    ch = gpu_channel(MEDIUM, X, R, 20)
+    ref = oracle.channel(**dict(MEDIUM, steps=1, avg_from=1), X=X, R=R)["type"]
+    assert np.array_equal(ch.geometry(), ref)
+    assert (ref == 1).sum() > 0 and (ref == 4).sum() == 2 * 10 * 12
+
+
+def test_forward_matches_the_oracle():
+    X, R = medium_spheres()
+    ch = gpu_channel(MEDIUM, X, R, 20)
+    J = ch.forward()
+    ref = oracle.channel(**MEDIUM, X=X, R=R, populations=True)
+    fluid = (ref["type"] != 1) & (ref["type"] != 4)
+    rel = np.abs(ch.populations() - ref["f"])[:, fluid] / np.abs(ref["f"][:, fluid])
+    assert rel.max() <= 1e-5
+    d = ch.drag()
+    assert np.abs(d - ref["drag"]).max() <= 1e-4 * np.abs(ref["drag"]).max()
+    assert abs(J - ref["J"]) <= 1e-4 * abs(ref["J"])
+
+
+def test_gradient_matches_tangent_linear_and_central_differences():
+    X, R = medium_spheres()
+    ch = gpu_channel(MEDIUM, X, R, 20)
+    ch.forward()
+    g = ch.backward()
+    names = ("u_peak", "gx", "cs")
+    for k, name in enumerate(names):
+        tl = oracle.channel(**MEDIUM, X=X, R=R, dtheta=np.eye(3)[k])["dJ"]
+        h = 1e-4 * MEDIUM[name]
+        jp = oracle.channel(**dict(MEDIUM, **{name: MEDIUM[name] + h}), X=X, R=R)["J"]
+        jm = oracle.channel(**dict(MEDIUM, **{name: MEDIUM[name] - h}), X=X, R=R)["J"]
+        fd = (jp - jm) / (2 * h)
+        print("%s: adjoint %.9g  tangent-linear %.9g  central difference %.9g" % (name, g[k], tl, fd))
+        assert abs(g[k] - tl) <= GRAD_TOL * abs(tl)
+        assert abs(g[k] - fd) <= GRAD_TOL * abs(fd)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    X, R = medium_spheres()
+    grads = []
+    for K in (7, 40, 160):
+        ch = gpu_channel(MEDIUM, X, R, K)
+        ch.forward()
+        grads.append(ch.backward())
+        ch.close()
+    for g in grads[1:]:
+        assert np.allclose(g, grads[0], rtol=1e-9, atol=0.0)
+
+
+def test_autograd_function_gives_the_adjoint_gradient():
+    torch = pytest.importorskip("torch")
+    from paper_1703_05158_gb300.adjoint import plate_drag
+
+    X, R = medium_spheres()
+    ch = gpu_channel(MEDIUM, X, R, 40)
+    theta = torch.tensor([MEDIUM["u_peak"], MEDIUM["gx"], MEDIUM["cs"]], dtype=torch.float64, requires_grad=True)
+    J = plate_drag(theta, ch)
+    (gt,) = torch.autograd.grad(J, theta)
+    ch.forward()
+    assert np.allclose(gt.numpy(), ch.backward(), rtol=1e-9, atol=0.0)
+    # a second objective evaluated in between does not corrupt the first's backward
+    J1 = plate_drag(theta, ch)
+    _ = plate_drag(theta.detach() * 1.01, ch)
+    (g1,) = torch.autograd.grad(J1, theta)
+    assert np.allclose(g1.numpy(), gt.numpy(), rtol=1e-9, atol=0.0)
+
+
+def test_full_differentiation_workload_against_stored_oracle_values():
+    """128 x 64 x 64, plate 4 x 40 x 40 at x = 80, 200 fixed spheres of
+    radius 3, 500 steps, checkpoints every 50, drag averaged over steps
+    301..500; the oracle values come from tests/golden/make_channel_golden.py."""
+    with open(os.path.join(HERE, "golden", "channel_config5.json")) as fh:
+        gold = json.load(fh)
+    c = gold["config"]
+    X, R = inputs.channel_spheres()
+    cfg = {k: c[k] for k in ("nx", "ny", "nz", "tau0", "cs", "gx", "u_peak", "steps", "avg_from")}
+    ch = gpu_channel(dict(cfg, plate_lo=tuple(c["plate_lo"]), plate_hi=tuple(c["plate_hi"])), X, R, 50)
+    J = ch.forward()
+    g = ch.backward()
+    print("J gpu %.9g oracle %.9g" % (J, gold["J"]))
+    print("grad gpu", g, "tangent-linear", gold["grad_tangent_linear"], "central difference",
+          gold["grad_central_difference"])
+    assert abs(J - gold["J"]) <= 1e-4 * abs(gold["J"])
+    for k in range(3):
+        assert abs(g[k] - gold["grad_tangent_linear"][k]) <= GRAD_TOL * abs(gold["grad_tangent_linear"][k])
+        assert abs(g[k] - gold["grad_central_difference"][k]) <= GRAD_TOL * abs(gold["grad_central_difference"][k])
