@@ -205,8 +205,8 @@ def run_ours(args, rank, world, local_rank):
     lat.sync()
     info = lat.info()
 
-    # timed region: events on the library's stream, phase profiler on
-    lat.profile(True)
+    # timed region: events on the library's stream (the steps replay the
+    # library's step graphs; the phase profiler is off here)
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
@@ -217,6 +217,11 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
     lat.sync()
     ms = start.elapsed_time(end)
+    # per-phase device times from a separate profiled run (events around each
+    # phase on the launching stream; these steps launch kernel by kernel)
+    lat.profile(True)
+    lat.step(min(args.steps, 400))
+    lat.sync()
     phases, psteps = lat.profile_read()
     lat.profile(False)
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")

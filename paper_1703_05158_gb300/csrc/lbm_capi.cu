@@ -69,6 +69,11 @@ void release(lbm_s *h) {
     cudaEvent_t evs[] = {h->ev_cf, h->ev_nm[0], h->ev_nm[1], h->ev_join};
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);
+    for (cudaGraphExec_t &g : h->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
     if (h->stream2) cudaStreamDestroy(h->stream2);
     if (h->chain) cudaStreamDestroy(h->chain);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -449,6 +454,7 @@ int lbm_set_particles(lbm_handle h, int32_t n, const double *pos, const double *
     }
     if (!rc) rc = settle(h);
     if (h->batch) h->batch->dirty = true;  // sphere counts and grids change
+    h->graph_stale = true;
     std::free(xf);
     std::free(fr);
     if (rc == LBM_ERR_CUDA && !h->sticky) h->sticky = rc;
@@ -498,6 +504,65 @@ int lbm_set_populations(lbm_handle h, const double *f, int32_t where) {
     return rc ? rc : s;
 }
 
+namespace {
+
+// One serial step with spheres at the handle's current parity (no profiler
+// marks): the launches a step graph holds.
+int serial_step_launches(lbm_s *h) {
+    const int P = h->parity;
+    int rc = launch_mark(h);
+    if (!rc) rc = launch_refill(h, P);
+    if (!rc) rc = launch_stream_collide(h, P);
+    if (!rc) rc = launch_links(h, P);
+    if (!rc) rc = launch_neighbours(h, 0);
+    if (!rc) rc = launch_dem(h);
+    return rc;
+}
+
+// Capture the serial step of each parity into a graph (the launchers read
+// the parity and the step parity from the handle, so both are set for the
+// capture and restored).
+int capture_step_graphs(lbm_s *h) {
+    for (cudaGraphExec_t &g : h->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    const int P0 = h->parity;
+    const long long s0 = h->steps;
+    int rc = LBM_OK;
+    for (int k = 0; k < 2 && !rc; ++k) {
+        const int P = P0 ^ k;
+        h->parity = P;
+        h->steps = s0 + k;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            rc = LBM_ERR_CUDA;
+            break;
+        }
+        const int r = serial_step_launches(h);
+        const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+        if (r || e != cudaSuccess) rc = r ? r : LBM_ERR_CUDA;
+        if (!rc && cudaGraphInstantiate(&h->graph[P], g, 0) != cudaSuccess) rc = LBM_ERR_CUDA;
+        if (g) cudaGraphDestroy(g);
+    }
+    h->parity = P0;
+    h->steps = s0;
+    if (rc) {
+        cudaGetLastError();
+        for (cudaGraphExec_t &g : h->graph)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+        return rc;
+    }
+    h->graph_stale = false;
+    return LBM_OK;
+}
+
+}  // namespace
+
 int lbm_step(lbm_handle h, int32_t nsteps) {
     if (!h || nsteps < 0 || h->batch) return LBM_ERR_ARG;  // batch members step through lbm_batch_step
     if (h->sticky) return h->sticky;
@@ -521,6 +586,21 @@ int lbm_step(lbm_handle h, int32_t nsteps) {
         if (!rc) h->stream = h->chain;
     }
     cudaStream_t A = h->stream, Bs = h->stream2;
+    // Serial steps with spheres, unprofiled: replay the captured step graphs
+    // (the captures need a stream other than the legacy default stream).
+    if (!rc && parts && !ovl && !h->prof && nsteps >= 2 && h->stream) {
+        if (h->graph_stale || !h->graph[0] || !h->graph[1]) rc = capture_step_graphs(h);
+        for (int it = 0; it < nsteps && !rc; ++it) {
+            // the link / refill counters report the last step of the call
+            if (it == nsteps - 1) rc = ok(cudaMemsetAsync(h->ctr, 0, 2 * sizeof(unsigned long long), A));
+            if (!rc) rc = ok(cudaGraphLaunch(h->graph[h->parity], A));
+            if (!rc) {
+                h->parity ^= 1;
+                ++h->steps;
+            }
+        }
+        nsteps = 0;  // done
+    }
     // everything the caller enqueued since the last step (populations set,
     // loads, ...) precedes this call's far collisions
     if (ovl && !rc) rc = ok(cudaEventRecord(h->ev_nm[h->steps & 1], A));

@@ -434,11 +434,10 @@ __device__ __forceinline__ void chan_collide_vjp(const Phys &ph, const float (&d
                   mb[4] * rcx(i) * rcz(i) + mb[5] * rcy(i) * rcz(i);
 }
 
-// Adjoint of the population pulled as k at fluid node t (interior), with
-// the inlet / outlet rows folded in.
+// Adjoint of the population pulled as k at interior fluid node t (at x = xt,
+// row yz = y + ny z), with the inlet / outlet rows folded in.
 __device__ __forceinline__ float eff(const ChanGeo &G, const float *__restrict__ lam1, const float *__restrict__ rho_bar,
-                                     const float *__restrict__ ext, int t, int k) {
-    const int xt = t % G.nx, yz = t / G.nx;
+                                     const float *__restrict__ ext, int t, int xt, int yz, int k) {
     float v = lam1[(size_t)k * G.N + t];
     if (xt == 1) v += rho_bar[yz];
     if (xt == G.nx - 2) v += ext[(size_t)k * (G.ny * G.nz) + yz];
@@ -462,14 +461,17 @@ __global__ void __launch_bounds__(256) k_chan_adj(const ChanGeo G, const Phys ph
         } else {
             float gb[Q];
             const uint32_t pm = G.plate[n];
+            const int yz0 = y + G.ny * z;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 float v = 0.f;
                 const int tn = nbr(G, x, y, z, rcx(i), rcy(i), rcz(i));
                 if (tn >= 0 && G.type[tn] == CH_FLUID) {
-                    v += eff(G, lam1, rho_bar, ext, tn, i);  // regular pull of x + c_i
+                    const int xt = x + rcx(i), yzt = wrapy(y + rcy(i), G.ny) + G.ny * (z + rcz(i));
+                    v += eff(G, lam1, rho_bar, ext, tn, xt, yzt, i);  // regular pull of x + c_i
                     const float qt = G.q[(size_t)i * G.N + tn];
-                    if (qt >= 0.f && qt < 0.5f) v += (1.f - 2.f * qt) * eff(G, lam1, rho_bar, ext, tn, ropp(i));
+                    if (qt >= 0.f && qt < 0.5f)
+                        v += (1.f - 2.f * qt) * eff(G, lam1, rho_bar, ext, tn, xt, yzt, ropp(i));
                 }
                 if (t == CH_FLUID) {
                     const float qi = G.q[(size_t)i * G.N + n];  // own link along c_i
@@ -481,10 +483,10 @@ __global__ void __launch_bounds__(256) k_chan_adj(const ChanGeo G, const Phys ph
                         } else {
                             a = 1.f / (2.f * qi);
                         }
-                        v += a * eff(G, lam1, rho_bar, ext, n, ropp(i));
+                        v += a * eff(G, lam1, rho_bar, ext, n, x, yz0, ropp(i));
                     }
                     const float qo = G.q[(size_t)ropp(i) * G.N + n];  // own link along -c_i
-                    if (qo >= 0.5f) v += (2.f * qo - 1.f) / (2.f * qo) * eff(G, lam1, rho_bar, ext, n, i);
+                    if (qo >= 0.5f) v += (2.f * qo - 1.f) / (2.f * qo) * eff(G, lam1, rho_bar, ext, n, x, yz0, i);
                 }
                 if (wd != 0.f && ((pm >> i) & 1u)) v += wd * 2.f * rcx(i);
                 gb[i] = v;

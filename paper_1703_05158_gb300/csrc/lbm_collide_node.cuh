@@ -17,13 +17,23 @@ namespace lbm {
 // products with lattice-vector components (0 or +-1) round the same either
 // way and are left to the compiler.
 __device__ __forceinline__ void collide_node(const Phys &ph, float (&d)[Q], int *status) {
-    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    // moments from the sums and differences of opposite pairs (i, i + 9):
+    // rho and the second moments take sp_i = d_i + d_i+9, the momentum
+    // takes dm_i = d_i - d_i+9 (c_i+9 = -c_i)
+    float sp[10], dm[10];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        drho = __fadd_rn(drho, d[i]);
-        if (cx(i)) jx = cx(i) > 0 ? __fadd_rn(jx, d[i]) : __fsub_rn(jx, d[i]);
-        if (cy(i)) jy = cy(i) > 0 ? __fadd_rn(jy, d[i]) : __fsub_rn(jy, d[i]);
-        if (cz(i)) jz = cz(i) > 0 ? __fadd_rn(jz, d[i]) : __fsub_rn(jz, d[i]);
+    for (int i = 1; i <= 9; ++i) {
+        static_assert(opp(1) == 10 && opp(9) == 18, "opposite pairs are (i, i + 9)");
+        sp[i] = __fadd_rn(d[i], d[i + 9]);
+        dm[i] = __fsub_rn(d[i], d[i + 9]);
+    }
+    float drho = d[0], jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 1; i <= 9; ++i) {
+        drho = __fadd_rn(drho, sp[i]);
+        if (cx(i)) jx = cx(i) > 0 ? __fadd_rn(jx, dm[i]) : __fsub_rn(jx, dm[i]);
+        if (cy(i)) jy = cy(i) > 0 ? __fadd_rn(jy, dm[i]) : __fsub_rn(jy, dm[i]);
+        if (cz(i)) jz = cz(i) > 0 ? __fadd_rn(jz, dm[i]) : __fsub_rn(jz, dm[i]);
     }
     const float rho = __fadd_rn(1.f, drho);
     if (!(rho > 0.f)) atomicOr(status, ST_DIVERGED);
@@ -38,13 +48,13 @@ __device__ __forceinline__ void collide_node(const Phys &ph, float (&d)[Q], int 
         // m_ab = sum c_a c_b d_i and the D3Q19 identity sum c_a c_b f^eq = rho (delta_ab/3 + u_a u_b)
         float mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f, myz = 0.f;
 #pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            if (cx(i)) mxx = __fadd_rn(mxx, d[i]);
-            if (cy(i)) myy = __fadd_rn(myy, d[i]);
-            if (cz(i)) mzz = __fadd_rn(mzz, d[i]);
-            if (cx(i) * cy(i)) mxy = cx(i) * cy(i) > 0 ? __fadd_rn(mxy, d[i]) : __fsub_rn(mxy, d[i]);
-            if (cx(i) * cz(i)) mxz = cx(i) * cz(i) > 0 ? __fadd_rn(mxz, d[i]) : __fsub_rn(mxz, d[i]);
-            if (cy(i) * cz(i)) myz = cy(i) * cz(i) > 0 ? __fadd_rn(myz, d[i]) : __fsub_rn(myz, d[i]);
+        for (int i = 1; i <= 9; ++i) {
+            if (cx(i)) mxx = __fadd_rn(mxx, sp[i]);
+            if (cy(i)) myy = __fadd_rn(myy, sp[i]);
+            if (cz(i)) mzz = __fadd_rn(mzz, sp[i]);
+            if (cx(i) * cy(i)) mxy = cx(i) * cy(i) > 0 ? __fadd_rn(mxy, sp[i]) : __fsub_rn(mxy, sp[i]);
+            if (cx(i) * cz(i)) mxz = cx(i) * cz(i) > 0 ? __fadd_rn(mxz, sp[i]) : __fsub_rn(mxz, sp[i]);
+            if (cy(i) * cz(i)) myz = cy(i) * cz(i) > 0 ? __fadd_rn(myz, sp[i]) : __fsub_rn(myz, sp[i]);
         }
         const float t3 = __fmul_rn(drho, 1.f / 3.f);
         const float rux = __fmul_rn(rho, ux), ruy = __fmul_rn(rho, uy), ruz = __fmul_rn(rho, uz);

@@ -217,6 +217,8 @@ struct lbm_batch_s;
 // Handle (opaque in the ABI).
 struct lbm_s {
     lbm_batch_s *batch;      // the batch this handle belongs to (steps only through it), or null
+    cudaGraphExec_t graph[2];  // one serial step from parity 0 / 1 (null: not captured)
+    bool graph_stale;          // sphere count changed since the capture
     lbm_params p;
     lbm::Lat L;
     lbm::Phys ph;
