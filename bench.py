@@ -150,6 +150,31 @@ def cpu_baseline(steps=2):
             "kind": "oracle", "sample": "%d steps of the full 256^3 + 2000-sphere workload, FP64, %.1f s" % (steps, dt)}
 
 
+def max_over_ranks(x, world):
+    """Maximum of a host float over the ranks of the job (every rank calls
+    it; NCCL on the GPU machine, gloo in the CPU tests)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def whole_job_mlups(updates_per_rank, world, seconds):
+    """Node updates of all ranks (replicas) over the slowest rank's time."""
+    return world * updates_per_rank / seconds / 1e6
+
+
 def run_reference(args, rank, world):
     """--impl reference: the FP64 oracle on the host, each step a bounded
     sample of the workload (a 48^3 box at the same solid fraction: 13 spheres
@@ -195,11 +220,6 @@ def run_ours(args, rank, world, local_rank):
     lat.set_particles(p["X"], V=p["V"], Om=p["Om"], R=p["R"])
     N = BOX[0] * BOX[1] * BOX[2]
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
     # warm-up
     lat.step(args.warmup)
     lat.sync()
@@ -208,7 +228,7 @@ def run_ours(args, rank, world, local_rank):
     # timed region: events on the library's stream (the steps replay the
     # library's step graphs; the phase profiler is off here)
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
+    barrier(world)
     torch.cuda.synchronize()
     with Clocks(dev) as clk:
         start.record(stream)
@@ -224,12 +244,8 @@ def run_ours(args, rank, world, local_rank):
     lat.sync()
     phases, psteps = lat.profile_read()
     lat.profile(False)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * N * args.steps / (ms_max * 1e-3) / 1e6
+    ms_max = max_over_ranks(ms, world)
+    value = whole_job_mlups(N * args.steps, world, ms_max * 1e-3)
 
     # end to end through the public API with host buffers: every step uploads
     # the external load (force, torque) from pinned host memory, steps, and
@@ -241,7 +257,7 @@ def run_ours(args, rank, world, local_rank):
     oT = torch.empty((n, 3), dtype=torch.float64).pin_memory()
     oX = torch.empty((n, 3), dtype=torch.float64).pin_memory()
     ke = args.e2e_steps
-    barrier()
+    barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(ke):
@@ -251,11 +267,7 @@ def run_ours(args, rank, world, local_rank):
         lbm.lbm_particles(lat.h, oX)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_val = world * N * ke / float(te.item()) / 1e6
+    e2e_val = whole_job_mlups(N * ke, world, max_over_ranks(e2e_s, world))
 
     if rank != 0:
         return
@@ -326,6 +338,7 @@ def run_batched(args, rank, world, local_rank):
     infos = [m.info() for m in batch.members]
     N = sum(int(np.prod(i["box"])) for i in inst)
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
     torch.cuda.synchronize()
     with Clocks(dev) as clk:
         start.record(stream)
@@ -333,8 +346,8 @@ def run_batched(args, rank, world, local_rank):
         end.record(stream)
         torch.cuda.synchronize()
     batch.sync()
-    ms = start.elapsed_time(end)
-    value = world * N * args.steps / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(start.elapsed_time(end), world)
+    value = whole_job_mlups(N * args.steps, world, ms * 1e-3)
     if rank != 0:
         batch.close()
         return
@@ -389,6 +402,7 @@ def run_adjoint(args, rank, world, local_rank):
         ch.backward()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     tf = tb = 0.0
+    barrier(world)
     torch.cuda.synchronize()
     with Clocks(local_rank) as clk:
         for _ in range(args.steps):
@@ -400,6 +414,7 @@ def run_adjoint(args, rank, world, local_rank):
             torch.cuda.synchronize()
             tf += ev[0].elapsed_time(ev[1])
             tb += ev[1].elapsed_time(ev[2])
+    tf, tb = max_over_ranks(tf, world), max_over_ranks(tb, world)
     if rank != 0:
         return
     N, S = 128 * 64 * 64, 500
@@ -411,7 +426,7 @@ def run_adjoint(args, rank, world, local_rank):
     peak, peak_kind = peaks()
     line = {
         "metric": "gradient evaluations of the mean plate drag (forward + adjoint), MLUPS of the forward updates",
-        "value": N * S / (ms * 1e-3) / 1e6, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "value": whole_job_mlups(N * S, world, ms * 1e-3), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "differentiation form: 128x64x64 channel, plate 4x40x40 at x=80, 200 fixed spheres "
