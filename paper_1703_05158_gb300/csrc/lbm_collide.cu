@@ -184,9 +184,15 @@ struct Pack2<__nv_bfloat16> {
 };
 template <>
 struct Pack2<__half> {
-    static __device__ __forceinline__ float lo(unsigned w) { return __half2float(__ushort_as_half((unsigned short)w)); }
+    static __device__ __forceinline__ float lo(unsigned w) {
+        __half2 h;
+        *reinterpret_cast<unsigned *>(&h) = w;
+        return __low2float(h);
+    }
     static __device__ __forceinline__ float hi(unsigned w) {
-        return __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+        __half2 h;
+        *reinterpret_cast<unsigned *>(&h) = w;
+        return __high2float(h);
     }
     static __device__ __forceinline__ unsigned short bits(float v) { return __half_as_ushort(__float2half_rn(v)); }
 };
@@ -246,14 +252,14 @@ __global__ void __launch_bounds__(128, 8) k_stream_collide2(const Lat L, const P
         for (int i = 0; i < Q; ++i) d[i] = Pack2<T>::lo(wv[i]);
         collide_node(ph, d, status);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) wv[i] = (wv[i] & 0xffff0000u) | (unsigned)Pack2<T>::bits(d[i]);
+        for (int i = 0; i < Q; ++i) wv[i] = __byte_perm(wv[i], (unsigned)Pack2<T>::bits(d[i]), 0x3254);
     }
     if (liveB) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) d[i] = Pack2<T>::hi(wv[i]);
         collide_node(ph, d, status);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) wv[i] = (wv[i] & 0x0000ffffu) | ((unsigned)Pack2<T>::bits(d[i]) << 16);
+        for (int i = 0; i < Q; ++i) wv[i] = __byte_perm(wv[i], (unsigned)Pack2<T>::bits(d[i]), 0x5410);
     }
     // write: even -> slot opp(i) of the pair; odd -> slot i at (x, x+1) + c_i
 #pragma unroll

@@ -66,6 +66,9 @@ __device__ __forceinline__ void links_body(const Lat &L, const Parts &pt, const 
     const int b[3] = {Fr.b[0], Fr.b[1], Fr.b[2]};
     const float fr[3] = {Fr.fr[0], Fr.fr[1], Fr.fr[2]};
     const float R2 = Fr.R2;
+    double Xp[3] = {0.0, 0.0, 0.0};
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 3; ++a) Xp[a] = pt.X[3 * p + a];  // used by the final sums
 
     // 1. node codes of the tile: 0 fluid, 1 other solid / outside, 2 this sphere
     //    (kTileBatch nodes per thread per round so that their loads overlap)
@@ -318,16 +321,17 @@ __device__ __forceinline__ void links_body(const Lat &L, const Parts &pt, const 
     __syncthreads();
     if (threadIdx.x == 0) {
         double frac[3];
-        for (int a = 0; a < 3; ++a) frac[a] = pt.X[3 * p + a] - (double)b[a];  // exact: X - floor(X)
+        for (int a = 0; a < 3; ++a) frac[a] = Xp[a] - (double)b[a];  // exact: X - floor(X)
         // rest part 2 w_j c_j: F = I/18, T = (J - frac x I)/18
         const double Ix = sh[6], Iy = sh[7], Iz = sh[8];
         double *F = pt.Fh + 3 * p, *Tq = pt.Th + 3 * p;
-        F[0] = sh[0] + Ix / 18.0;
-        F[1] = sh[1] + Iy / 18.0;
-        F[2] = sh[2] + Iz / 18.0;
-        Tq[0] = sh[3] + (sh[9] - (frac[1] * Iz - frac[2] * Iy)) / 18.0;
-        Tq[1] = sh[4] + (sh[10] - (frac[2] * Ix - frac[0] * Iz)) / 18.0;
-        Tq[2] = sh[5] + (sh[11] - (frac[0] * Iy - frac[1] * Ix)) / 18.0;
+        constexpr double i18 = 1.0 / 18.0;
+        F[0] = sh[0] + Ix * i18;
+        F[1] = sh[1] + Iy * i18;
+        F[2] = sh[2] + Iz * i18;
+        Tq[0] = sh[3] + (sh[9] - (frac[1] * Iz - frac[2] * Iy)) * i18;
+        Tq[1] = sh[4] + (sh[10] - (frac[2] * Ix - frac[0] * Iz)) * i18;
+        Tq[2] = sh[5] + (sh[11] - (frac[0] * Iy - frac[1] * Ix)) * i18;
         atomicAdd(ctr, (unsigned long long)total);
     }
 }
