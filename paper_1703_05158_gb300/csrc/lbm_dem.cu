@@ -293,27 +293,45 @@ __device__ __forceinline__ void dem_cluster_body(const Lat &L, const Parts &pt, 
             if (a >= pt.np) break;
             if (fx[q]) continue;
             float3 F = make_float3(0.f, 0.f, 0.f);
-            for (int m = 0; m < nc[q]; ++m) {
-                const long long e = (long long)a * pt.max_nbr + m;
-                const int b = __ldg(pt.nbr + e);
-                const float4 A = __ldg(pt.pairA + e), Bv = __ldg(pt.pairB + e);
-                const int qb = b / G, rb = b - qb * G, cb = rb / T, tb = rb - cb * T;
-                const float4 *o = cluster.map_shared_rank(buf + (size_t)(qb * T + tb) * 2, cb);
-                const float4 ox = o[0], ov = o[1];
-                const float Dx = dx[q].x - ox.x, Dy = dx[q].y - ox.y, Dz = dx[q].z - ox.z;
-                const float c = A.w - 2.f * (A.x * Dx + A.y * Dy + A.z * Dz) - (Dx * Dx + Dy * Dy + Dz * Dz);
-                if (!(c > 0.f)) continue;
-                const float ex = A.x + Dx, ey = A.y + Dy, ez = A.z + Dz;
-                const float dist = sqrtf(ex * ex + ey * ey + ez * ez);
-                const float Rs = Rf[q] + __ldg(&pt.Xf[b].w);
-                const float delta = c / (Rs + dist);
-                const float id = 1.f / dist;
-                const float nx = ex * id, ny = ey * id, nz = ez * id;
-                const float vn = (Bv.x + dv[q].x - ov.x) * nx + (Bv.y + dv[q].y - ov.y) * ny + (Bv.z + dv[q].z - ov.z) * nz;
-                const float fn = kn * delta - Bv.w * vn;
-                F.x += fn * nx;
-                F.y += fn * ny;
-                F.z += fn * nz;
+            // neighbours in groups of kNbrGroup: every load of a group is
+            // issued before any of its arithmetic; the sum keeps list order
+            constexpr int kNbrGroup = 4;
+            for (int m0 = 0; m0 < nc[q]; m0 += kNbrGroup) {
+                float4 A[kNbrGroup], Bv[kNbrGroup], ox[kNbrGroup], ov[kNbrGroup];
+                float Rb[kNbrGroup];
+#pragma unroll
+                for (int u = 0; u < kNbrGroup; ++u) {
+                    if (m0 + u >= nc[q]) break;
+                    const long long e = (long long)a * pt.max_nbr + m0 + u;
+                    const int b = __ldg(pt.nbr + e);
+                    A[u] = __ldg(pt.pairA + e);
+                    Bv[u] = __ldg(pt.pairB + e);
+                    Rb[u] = __ldg(&pt.Xf[b].w);
+                    const int qb = b / G, rb = b - qb * G, cb = rb / T, tb = rb - cb * T;
+                    const float4 *o = cluster.map_shared_rank(buf + (size_t)(qb * T + tb) * 2, cb);
+                    ox[u] = o[0];
+                    ov[u] = o[1];
+                }
+#pragma unroll
+                for (int u = 0; u < kNbrGroup; ++u) {
+                    if (m0 + u >= nc[q]) break;
+                    const float Dx = dx[q].x - ox[u].x, Dy = dx[q].y - ox[u].y, Dz = dx[q].z - ox[u].z;
+                    const float c =
+                        A[u].w - 2.f * (A[u].x * Dx + A[u].y * Dy + A[u].z * Dz) - (Dx * Dx + Dy * Dy + Dz * Dz);
+                    if (!(c > 0.f)) continue;
+                    const float ex = A[u].x + Dx, ey = A[u].y + Dy, ez = A[u].z + Dz;
+                    const float dist = sqrtf(ex * ex + ey * ey + ez * ez);
+                    const float Rs = Rf[q] + Rb[u];
+                    const float delta = c / (Rs + dist);
+                    const float id = 1.f / dist;
+                    const float nx = ex * id, ny = ey * id, nz = ez * id;
+                    const float vn = (Bv[u].x + dv[q].x - ov[u].x) * nx + (Bv[u].y + dv[q].y - ov[u].y) * ny +
+                                     (Bv[u].z + dv[q].z - ov[u].z) * nz;
+                    const float fn = kn * delta - Bv[u].w * vn;
+                    F.x += fn * nx;
+                    F.y += fn * ny;
+                    F.z += fn * nz;
+                }
             }
             const float vz = v0[q].z + dv[q].z;
             const float lo = Llo[q] - dx[q].z;
