@@ -76,6 +76,9 @@ void release(lbm_s *h) {
         }
     if (h->stream2) cudaStreamDestroy(h->stream2);
     if (h->chain) cudaStreamDestroy(h->chain);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_nbr) cudaEventDestroy(h->ev_nbr);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -507,14 +510,21 @@ int lbm_set_populations(lbm_handle h, const double *f, int32_t where) {
 namespace {
 
 // One serial step with spheres at the handle's current parity (no profiler
-// marks): the launches a step graph holds.
+// marks), as captured into a step graph: after the marks (which read the
+// neighbour lists) the lists are rebuilt on a side branch, concurrently with
+// refill, collide and links (which do not read them); the DEM waits for both.
 int serial_step_launches(lbm_s *h) {
     const int P = h->parity;
+    auto ok = [](cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; };
     int rc = launch_mark(h);
+    if (!rc) rc = ok(cudaEventRecord(h->ev_fork, h->stream));
+    if (!rc) rc = ok(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    if (!rc) rc = launch_neighbours(h, 0, h->side);
+    if (!rc) rc = ok(cudaEventRecord(h->ev_nbr, h->side));
     if (!rc) rc = launch_refill(h, P);
     if (!rc) rc = launch_stream_collide(h, P);
     if (!rc) rc = launch_links(h, P);
-    if (!rc) rc = launch_neighbours(h, 0);
+    if (!rc) rc = ok(cudaStreamWaitEvent(h->stream, h->ev_nbr, 0));
     if (!rc) rc = launch_dem(h);
     return rc;
 }
@@ -523,6 +533,14 @@ int serial_step_launches(lbm_s *h) {
 // the parity and the step parity from the handle, so both are set for the
 // capture and restored).
 int capture_step_graphs(lbm_s *h) {
+    if (!h->side) {
+        if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_nbr, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return LBM_ERR_CUDA;
+        }
+    }
     for (cudaGraphExec_t &g : h->graph)
         if (g) {
             cudaGraphExecDestroy(g);

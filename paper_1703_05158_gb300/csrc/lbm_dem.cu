@@ -485,9 +485,10 @@ __global__ void __launch_bounds__(128) k_dem(const Lat L, const Parts pt, SFrame
     }
 }
 
-int launch_neighbours(lbm_s *h, int force) {
+int launch_neighbours(lbm_s *h, int force, cudaStream_t stream) {
     const int blocks = (h->pt.np * 32 + 255) / 256;
-    k_neighbours<<<blocks, 256, 0, h->stream>>>(h->L, h->pt, (int)(h->steps & 1), force, h->status);
+    k_neighbours<<<blocks, 256, 0, stream ? stream : h->stream>>>(h->L, h->pt, (int)(h->steps & 1), force,
+                                                                 h->status);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 

@@ -219,6 +219,8 @@ struct lbm_s {
     lbm_batch_s *batch;      // the batch this handle belongs to (steps only through it), or null
     cudaGraphExec_t graph[2];  // one serial step from parity 0 / 1 (null: not captured)
     bool graph_stale;          // sphere count changed since the capture
+    cudaStream_t side;         // branch of the step graph that builds the neighbour lists
+    cudaEvent_t ev_fork, ev_nbr;
     lbm_params p;
     lbm::Lat L;
     lbm::Phys ph;
@@ -318,7 +320,7 @@ int launch_collide_list(lbm_s *h, int parity, const int *list, const int *count,
 int launch_mark(lbm_s *h);
 int launch_refill(lbm_s *h, int parity);
 int launch_links(lbm_s *h, int parity);
-int launch_neighbours(lbm_s *h, int force);
+int launch_neighbours(lbm_s *h, int force, cudaStream_t stream = nullptr);
 int launch_contact(lbm_s *h);
 int launch_dem(lbm_s *h);
 int launch_set_populations(lbm_s *h, const double *f_dev, int parity);

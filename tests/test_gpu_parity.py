@@ -224,6 +224,42 @@ def test_no_particles_and_capacity_errors():
     assert lat.info()["steps"] == 3
 
 
+def test_largest_lattice_and_the_index_limit():
+    """Populations are addressed with 32-bit element offsets: a box whose
+    19 slot arrays (with the two wall planes and padding) reach 2^31
+    elements is refused with LBM_ERR_UNSUPPORTED; the largest cube below the
+    limit (480^3, 110.6 M nodes, 8.4 GB of FP32 populations) steps, and a
+    rest state stays exactly at rest (its deviations are exactly zero)."""
+    L = lbm()
+    with pytest.raises(L.LbmError) as e:
+        L.Lattice(512, 512, 512, tau0=0.7)
+    assert e.value.code == L.LBM_ERR_UNSUPPORTED
+    lat = L.Lattice(480, 480, 480, tau0=0.7, cs=0.17)
+    lat.step(3)
+    lat.sync()
+    rho, u = lat.fields()
+    assert np.all(rho == 1.0) and np.all(u == 0.0)
+    lat.close()
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_odd_nx_takes_the_single_node_16_bit_kernel(precision):
+    """nx odd: the 16-bit storage runs one node per thread (the pair kernel
+    needs even rows); same tolerance as FP32 storage against the oracle on
+    the rounding of one store, checked on velocities after 60 steps."""
+    shape = (37, 29, 23)
+    kw = dict(tau0=0.6, cs=0.17, g=(1e-5, 0.0, 0.0), u_hi=(0.04, 0.0, 0.0))
+    lat = lbm().Lattice(*shape, precision=precision, **kw)
+    orc = oracle.Oracle(*shape, **kw)
+    lat.step(60)
+    orc.step(60)
+    ug = lat.fields()[1].astype(np.float64)
+    uo = orc.fields()[1]
+    err = float(np.linalg.norm(ug - uo) / np.linalg.norm(uo))
+    print("%s, nx = 37: relative velocity error %.2e" % (precision, err))
+    assert err <= (1e-3 if precision == "fp16" else 1e-2)
+
+
 def test_mass_conservation_gpu():
     shape = (96, 64, 48)
     kw = dict(tau0=0.6, cs=0.17, u_hi=(0.05, 0.0, 0.0))
