@@ -1022,7 +1022,7 @@ int lbm_batch_create(const lbm_params *params, int32_t count, lbm_batch *out) {
         }
     }
     if (!rc && max_m > 0) {
-        b->dem_cluster = dem_cluster_setup(max_m);
+        b->dem_cluster = dem_cluster_setup(max_m, true);
         if (b->dem_cluster == 0) rc = LBM_ERR_UNSUPPORTED;  // the batched DEM needs one cluster per instance
         if (!rc) rc = dem_cluster_setup_batch(b->dem_cluster);
         if (!rc) rc = links_setup_batch(b->ext, b->cap);

@@ -33,6 +33,8 @@
 // error is raised) keeps every pair that can touch within a step in the list.
 #include <cooperative_groups.h>
 
+#include <vector>
+
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -504,14 +506,20 @@ int dem_max_blocks(int threads, int *blocks_per_sm) {
 
 // Largest cluster (16, else 8) that can run k_dem_cluster; 0 if none, or if
 // max_particles does not fit its registers.
-int dem_cluster_setup(int max_particles) {
+int dem_cluster_setup(int max_particles, bool small) {
     if (cudaFuncSetAttribute(k_dem_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dem_cluster_smem()) !=
         cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    for (int cl : {16, 8}) {
+    // one simulation: the widest cluster (16 or 8 CTAs: measured equal at
+    // 2000 spheres, narrower ones slower); a batch: the narrowest cluster
+    // that gives every sphere its own thread, so that the members' clusters
+    // run side by side
+    const std::vector<int> sizes = small ? std::vector<int>{1, 2, 4, 8, 16} : std::vector<int>{16, 8};
+    for (int cl : sizes) {
         if ((long long)cl * kDemThreads * kDemKmax < max_particles) continue;
+        if (small && (long long)cl * kDemThreads < max_particles && cl < 16) continue;
         if (cl > 8 && cudaFuncSetAttribute(k_dem_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                           cudaSuccess) {
             cudaGetLastError();

@@ -329,7 +329,7 @@ int launch_fields(lbm_s *h, float *rho, float *u, int parity);
 int launch_owner(lbm_s *h, int32_t *owner);
 int launch_count_fluid(lbm_s *h);
 int dem_max_blocks(int threads, int *blocks_per_sm);
-int dem_cluster_setup(int max_particles);
+int dem_cluster_setup(int max_particles, bool small = false);
 int link_capacity(double max_radius);
 size_t link_smem(int ext, int cap);
 int links_setup(int ext, int cap);
