@@ -252,8 +252,9 @@ int lbm_batch_destroy(lbm_batch b);
 int lbm_batch_handle(lbm_batch b, int32_t i, lbm_handle *out);
 
 /* Run the collide autotuner now (lbm_batch_step runs it on first use):
- * block sizes 128, 256, 512 x grids of half and all resident blocks and one
- * block per chunk, three timed launches each on the members' state, which
+ * block sizes 128, 256, 512, each with a register budget of 64 or 85 per
+ * thread, x grids of half and all resident blocks and one block per chunk,
+ * three timed launches each on the members' state, which
  * is copied aside and restored (needs that much free device memory, else
  * LBM_ERR_NOMEM).  Outputs (each may be NULL): threads per block, blocks,
  * mean ms per launch of the choice. */

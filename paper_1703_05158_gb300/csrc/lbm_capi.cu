@@ -893,7 +893,7 @@ int batch_descriptors(lbm_batch_s *b) {
 int batch_enqueue(const lbm_batch_s *b, int P) {
     int rc = launch_mark_batch(b, P);
     if (!rc) rc = launch_refill_batch(b, P);
-    if (!rc) rc = launch_collide_batch(b, P, b->tpb, b->grid, b->chunks, b->nchunks);
+    if (!rc) rc = launch_collide_batch(b, P, b->tpb, b->minb, b->grid, b->chunks, b->nchunks);
     if (!rc) rc = launch_links_batch(b, P);
     if (!rc) rc = launch_neighbours_batch(b, P);
     if (!rc) rc = launch_dem_batch(b, P);
@@ -1100,21 +1100,23 @@ int lbm_batch_tune(lbm_batch b, int32_t *threads, int32_t *blocks, float *ms) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = LBM_ERR_CUDA;
     float best = 1e30f;
-    int best_tpb = 0, best_grid = 0;
-    for (int tpb : {128, 256, 512}) {
+    int best_tpb = 0, best_minb = 0, best_grid = 0;
+    const int shapes[6][2] = {{128, 8}, {128, 6}, {256, 4}, {256, 3}, {512, 2}, {512, 1}};
+    for (const auto &sh : shapes) {
         if (rc) break;
+        const int tpb = sh[0], minb = sh[1];
         int2 *ch = nullptr;
         int nch = 0, bps = 0;
         rc = batch_chunks(b, tpb, &ch, &nch);
-        if (!rc) rc = collide_batch_occupancy(b->precision, P, tpb, &bps);
+        if (!rc) rc = collide_batch_occupancy(b->precision, P, tpb, minb, &bps);
         if (!rc && nch > 0 && bps > 0) {
             // persistent grids of 1/2 and 1 times the resident blocks, and one block per chunk
             const int cands[3] = {std::max(1, b->sms * bps / 2), b->sms * bps, nch};
             for (int c = 0; c < 3 && !rc; ++c) {
                 const int grid = std::min(cands[c], nch);
-                rc = launch_collide_batch(b, P, tpb, grid, ch, nch);  // warm-up
+                rc = launch_collide_batch(b, P, tpb, minb, grid, ch, nch);  // warm-up
                 if (!rc && cudaEventRecord(e0, b->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
-                for (int r = 0; r < 3 && !rc; ++r) rc = launch_collide_batch(b, P, tpb, grid, ch, nch);
+                for (int r = 0; r < 3 && !rc; ++r) rc = launch_collide_batch(b, P, tpb, minb, grid, ch, nch);
                 if (!rc && cudaEventRecord(e1, b->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
                 float t = 0.f;
                 if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
@@ -1122,6 +1124,7 @@ int lbm_batch_tune(lbm_batch b, int32_t *threads, int32_t *blocks, float *ms) {
                 if (!rc && t / 3.f < best) {
                     best = t / 3.f;
                     best_tpb = tpb;
+                    best_minb = minb;
                     best_grid = grid;
                 }
             }
@@ -1140,10 +1143,12 @@ int lbm_batch_tune(lbm_batch b, int32_t *threads, int32_t *blocks, float *ms) {
     }
     if (best_tpb == 0) {  // nothing to collide: any launch shape does
         best_tpb = 256;
+        best_minb = 4;
         best_grid = 1;
         best = 0.f;
     }
     b->tpb = best_tpb;
+    b->minb = best_minb;
     b->grid = best_grid;
     b->dirty = true;
     if (threads) *threads = best_tpb;

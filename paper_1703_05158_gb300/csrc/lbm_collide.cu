@@ -138,9 +138,11 @@ __global__ void __launch_bounds__(256, 4) k_collide_list(const Lat L, const Phys
 // c = (instance, first node) covers TPB consecutive nodes of one instance
 // (a block's threads, coalesced); block b takes the contiguous chunk range
 // [b n / G, (b + 1) n / G).  The current instance's descriptor is staged in
-// shared memory (read on use, not held in registers).
-template <int ODD, typename T, int TPB>
-__global__ void __launch_bounds__(TPB, 1024 / TPB) k_collide_batch(const Inst *__restrict__ I,
+// shared memory (read on use, not held in registers).  MINB resident blocks
+// per SM bound the registers (64 per thread at TPB * MINB = 1024, 85 at
+// 768); the autotuner picks both.
+template <int ODD, typename T, int TPB, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) k_collide_batch(const Inst *__restrict__ I,
                                                                    const int2 *__restrict__ chunks, const int nchunks) {
     __shared__ __align__(16) unsigned char si_raw[sizeof(Inst)];
     Inst &si = *reinterpret_cast<Inst *>(si_raw);
@@ -392,61 +394,65 @@ int launch_collide_list(lbm_s *h, int parity, const int *list, const int *count,
     return LBM_ERR_ARG;
 }
 
-template <int ODD, typename T, int TPB>
+template <int ODD, typename T, int TPB, int MINB>
 static cudaError_t collide_batch_t(const lbm_batch_s *b, int grid, const int2 *chunks, int nchunks) {
-    k_collide_batch<ODD, T, TPB><<<grid, TPB, 0, b->stream>>>(b->dinst, chunks, nchunks);
+    k_collide_batch<ODD, T, TPB, MINB><<<grid, TPB, 0, b->stream>>>(b->dinst, chunks, nchunks);
     return cudaGetLastError();
 }
 
+// Launch shapes of the batched collide: (threads per block, minimum resident
+// blocks per SM), i.e. 64 or 85 registers per thread.
+#define LBM_BATCH_SHAPES(X) X(128, 8) X(128, 6) X(256, 4) X(256, 3) X(512, 2) X(512, 1)
+
 template <int ODD, typename T>
-static cudaError_t collide_batch_p(const lbm_batch_s *b, int tpb, int grid, const int2 *chunks, int nchunks) {
-    switch (tpb) {
-        case 128: return collide_batch_t<ODD, T, 128>(b, grid, chunks, nchunks);
-        case 256: return collide_batch_t<ODD, T, 256>(b, grid, chunks, nchunks);
-        case 512: return collide_batch_t<ODD, T, 512>(b, grid, chunks, nchunks);
-    }
+static cudaError_t collide_batch_p(const lbm_batch_s *b, int tpb, int minb, int grid, const int2 *chunks,
+                                   int nchunks) {
+#define LBM_CASE(t, m) \
+    if (tpb == t && minb == m) return collide_batch_t<ODD, T, t, m>(b, grid, chunks, nchunks);
+    LBM_BATCH_SHAPES(LBM_CASE)
+#undef LBM_CASE
     return cudaErrorInvalidValue;
 }
 
 template <typename T>
-static cudaError_t collide_batch_ty(const lbm_batch_s *b, int P, int tpb, int grid, const int2 *chunks,
+static cudaError_t collide_batch_ty(const lbm_batch_s *b, int P, int tpb, int minb, int grid, const int2 *chunks,
                                     int nchunks) {
-    return P ? collide_batch_p<1, T>(b, tpb, grid, chunks, nchunks) : collide_batch_p<0, T>(b, tpb, grid, chunks, nchunks);
+    return P ? collide_batch_p<1, T>(b, tpb, minb, grid, chunks, nchunks)
+             : collide_batch_p<0, T>(b, tpb, minb, grid, chunks, nchunks);
 }
 
-int launch_collide_batch(const lbm_batch_s *b, int P, int tpb, int grid, const int2 *chunks, int nchunks) {
+int launch_collide_batch(const lbm_batch_s *b, int P, int tpb, int minb, int grid, const int2 *chunks, int nchunks) {
     if (nchunks == 0) return LBM_OK;
     cudaError_t e = cudaErrorInvalidValue;
     switch (b->precision) {
-        case LBM_FP32: e = collide_batch_ty<float>(b, P, tpb, grid, chunks, nchunks); break;
-        case LBM_BF16_DEV: e = collide_batch_ty<__nv_bfloat16>(b, P, tpb, grid, chunks, nchunks); break;
-        case LBM_FP16_DEV: e = collide_batch_ty<__half>(b, P, tpb, grid, chunks, nchunks); break;
+        case LBM_FP32: e = collide_batch_ty<float>(b, P, tpb, minb, grid, chunks, nchunks); break;
+        case LBM_BF16_DEV: e = collide_batch_ty<__nv_bfloat16>(b, P, tpb, minb, grid, chunks, nchunks); break;
+        case LBM_FP16_DEV: e = collide_batch_ty<__half>(b, P, tpb, minb, grid, chunks, nchunks); break;
     }
     if (e != cudaSuccess) cudaGetLastError();
     return e == cudaSuccess ? LBM_OK : (e == cudaErrorInvalidValue ? LBM_ERR_ARG : LBM_ERR_CUDA);
 }
 
-template <int ODD, typename T, int TPB>
+template <int ODD, typename T, int TPB, int MINB>
 static cudaError_t occ_t(int *bps) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_collide_batch<ODD, T, TPB>, TPB, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_collide_batch<ODD, T, TPB, MINB>, TPB, 0);
 }
 
 template <typename T>
-static cudaError_t occ_ty(int P, int tpb, int *bps) {
-    switch (tpb) {
-        case 128: return P ? occ_t<1, T, 128>(bps) : occ_t<0, T, 128>(bps);
-        case 256: return P ? occ_t<1, T, 256>(bps) : occ_t<0, T, 256>(bps);
-        case 512: return P ? occ_t<1, T, 512>(bps) : occ_t<0, T, 512>(bps);
-    }
+static cudaError_t occ_ty(int P, int tpb, int minb, int *bps) {
+#define LBM_CASE(t, m) \
+    if (tpb == t && minb == m) return P ? occ_t<1, T, t, m>(bps) : occ_t<0, T, t, m>(bps);
+    LBM_BATCH_SHAPES(LBM_CASE)
+#undef LBM_CASE
     return cudaErrorInvalidValue;
 }
 
-int collide_batch_occupancy(int precision, int P, int tpb, int *blocks_per_sm) {
+int collide_batch_occupancy(int precision, int P, int tpb, int minb, int *blocks_per_sm) {
     cudaError_t e = cudaErrorInvalidValue;
     switch (precision) {
-        case LBM_FP32: e = occ_ty<float>(P, tpb, blocks_per_sm); break;
-        case LBM_BF16_DEV: e = occ_ty<__nv_bfloat16>(P, tpb, blocks_per_sm); break;
-        case LBM_FP16_DEV: e = occ_ty<__half>(P, tpb, blocks_per_sm); break;
+        case LBM_FP32: e = occ_ty<float>(P, tpb, minb, blocks_per_sm); break;
+        case LBM_BF16_DEV: e = occ_ty<__nv_bfloat16>(P, tpb, minb, blocks_per_sm); break;
+        case LBM_FP16_DEV: e = occ_ty<__half>(P, tpb, minb, blocks_per_sm); break;
     }
     if (e != cudaSuccess) cudaGetLastError();
     return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;

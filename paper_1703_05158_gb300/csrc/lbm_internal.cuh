@@ -297,7 +297,7 @@ struct lbm_batch_s {
     lbm::Inst *dinst = nullptr;   // device array [n]
     int2 *chunks = nullptr;       // collide chunk table: (instance, first node), tpb nodes each
     int nchunks = 0, chunk_tpb = 0;
-    int tpb = 0, grid = 0;        // collide launch picked by the autotuner (0: not tuned)
+    int tpb = 0, minb = 0, grid = 0;  // collide launch picked by the autotuner (0: not tuned)
     int max_np = 0;               // largest sphere count of a member
     int ext = 0, cap = 0;         // link tile half width and list capacity (largest over members)
     int dem_cluster = 0;          // CTAs per instance cluster of the DEM kernel
@@ -337,8 +337,8 @@ int settle_handle(lbm_s *h);
 // batched forms (all members at step parity sp = P)
 int launch_mark_batch(const lbm_batch_s *b, int sp);
 int launch_refill_batch(const lbm_batch_s *b, int P);
-int launch_collide_batch(const lbm_batch_s *b, int P, int tpb, int grid, const int2 *chunks, int nchunks);
-int collide_batch_occupancy(int precision, int P, int tpb, int *blocks_per_sm);
+int launch_collide_batch(const lbm_batch_s *b, int P, int tpb, int minb, int grid, const int2 *chunks, int nchunks);
+int collide_batch_occupancy(int precision, int P, int tpb, int minb, int *blocks_per_sm);
 int launch_links_batch(const lbm_batch_s *b, int P);
 int links_setup_batch(int ext, int cap);
 int launch_neighbours_batch(const lbm_batch_s *b, int sp);
