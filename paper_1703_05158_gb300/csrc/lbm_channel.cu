@@ -52,6 +52,7 @@ enum : uint8_t { CH_FLUID = 0, CH_SOLID = 1, CH_INLET = 2, CH_OUTLET = 3, CH_PLA
 struct ChanGeo {
     int nx, ny, nz, N;
     const uint8_t *type;    // [N]
+    const uint8_t *cut;     // [N]: 1 if some link x -> x + c_j is cut (then q is read)
     const float *q;         // [Q][N]: fraction of the cut link x -> x + c_j, -1 if not cut
     const uint32_t *plate;  // [N]: bit j set if x -> x + c_j ends in the plate
 };
@@ -115,12 +116,13 @@ __global__ void k_chan_types(const int nx, const int ny, const int nz, const Pla
 // kept when q is rounded to FP32).
 __global__ void k_chan_links(const int nx, const int ny, const int nz, const int np, const double *__restrict__ X,
                              const double *__restrict__ R, const uint8_t *__restrict__ type, float *__restrict__ qout,
-                             uint32_t *__restrict__ plate) {
+                             uint32_t *__restrict__ plate, uint8_t *__restrict__ cut) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = nx * ny * nz;
     if (n >= N) return;
     const int x = n % nx, y = (n / nx) % ny, z = n / (nx * ny);
     uint32_t pm = 0;
+    bool any = false;
     qout[n] = -1.f;  // j = 0
     for (int j = 1; j < Q; ++j) {
         float qf = -1.f;
@@ -157,17 +159,20 @@ __global__ void k_chan_links(const int nx, const int ny, const int nz, const int
             }
         }
         qout[(size_t)j * N + n] = qf;
+        any |= qf >= 0.f;
     }
     plate[n] = pm;
+    cut[n] = any ? 1 : 0;
 }
 
 // ---- forward -----------------------------------------------------------------
 
-// Incoming population i at interior fluid node (x, y, z), index n, from G.
+// Incoming population i at interior fluid node (x, y, z), index n, from G
+// (cut: whether any link of the node is cut).
 __device__ __forceinline__ float pull(const ChanGeo &G, const float *__restrict__ Gin, int x, int y, int z, int n,
-                                      int i) {
+                                      int i, bool cut) {
     const int j = ropp(i);
-    const float q = G.q[(size_t)j * G.N + n];
+    const float q = cut ? G.q[(size_t)j * G.N + n] : -1.f;
     if (q < 0.f) return Gin[(size_t)i * G.N + nbr(G, x, y, z, -rcx(i), -rcy(i), -rcz(i))];
     const float gj = Gin[(size_t)j * G.N + n];
     if (q < 0.5f) {
@@ -212,48 +217,38 @@ __device__ __forceinline__ void block_add(double v, double *dst) {
     }
 }
 
-// One step: f^s from G^{s-1} (PULL) or from fin (the stored f^s), record
-// f^s in frec (may be null), G^s = C(f^s) into Gout, plate drag of G^s
-// added to *drag (may be null).
+// Warp sum of a plate-drag contribution, one FP64 atomic per warp that has
+// any (most warps have none).
+__device__ __forceinline__ void warp_add(double v, double *dst) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(dst, v);
+}
+
+// One step at the interior fluid nodes (PULL: f^s pulled from G^{s-1}) or at
+// every fluid node (!PULL: f^s = fin, the stored state): record f^s in frec
+// (may be null), G^s = C(f^s) into Gout (G = f at inlet and outlet nodes),
+// plate drag of G^s added to *drag (may be null).  With PULL the inlet and
+// outlet planes are k_chan_bc_step's.
 template <bool PULL>
-__global__ void __launch_bounds__(256) k_chan_step(const ChanGeo G, const Phys ph, const float u_peak,
-                                                   const float *__restrict__ Gin, const float *__restrict__ fin,
-                                                   float *__restrict__ frec, float *__restrict__ Gout,
-                                                   double *__restrict__ drag, int *__restrict__ status) {
+__global__ void __launch_bounds__(256) k_chan_step(const ChanGeo G, const Phys ph, const float *__restrict__ Gin,
+                                                   const float *__restrict__ fin, float *__restrict__ frec,
+                                                   float *__restrict__ Gout, double *__restrict__ drag,
+                                                   int *__restrict__ status) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     double D = 0.0;
     if (n < G.N) {
-        const int x = n % G.nx, y = (n / G.nx) % G.ny, z = n / (G.nx * G.ny);
         const uint8_t t = G.type[n];
-        float d[Q];
-        bool live = is_fluid_type(t);
-        if (live) {
+        if (PULL ? t == CH_FLUID : is_fluid_type(t)) {
+            float d[Q];
             if (!PULL) {
 #pragma unroll
                 for (int i = 0; i < Q; ++i) d[i] = fin[(size_t)i * G.N + n];
-            } else if (t == CH_FLUID) {
-#pragma unroll
-                for (int i = 0; i < Q; ++i) d[i] = pull(G, Gin, x, y, z, n, i);
             } else {
-                // inlet / outlet: from the pulled populations of the neighbour plane
-                const int xs = t == CH_INLET ? 1 : G.nx - 2;
-                const int ns = xs + G.nx * (y + G.ny * z);
-                float e[Q];
+                const int x = n % G.nx, y = (n / G.nx) % G.ny, z = n / (G.nx * G.ny);
+                const bool cut = G.cut[n] != 0;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) e[i] = pull(G, Gin, xs, y, z, ns, i);
-                float rho, jx, jy, jz;
-                moments(e, rho, jx, jy, jz);
-                if (t == CH_INLET) {
-                    const float zh = (z + 0.5f) / G.nz;
-                    const float ux = u_peak * 4.f * zh * (1.f - zh);
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) d[i] = feq_dev(i, rho, ux, 0.f, 0.f);
-                } else {
-                    const float ux = jx / rho + 0.5f * ph.g[0], uy = jy / rho + 0.5f * ph.g[1],
-                                uz = jz / rho + 0.5f * ph.g[2];
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) d[i] = feq_dev(i, 1.f, ux, uy, uz);
-                }
+                for (int i = 0; i < Q; ++i) d[i] = pull(G, Gin, x, y, z, n, i, cut);
             }
             if (frec)
 #pragma unroll
@@ -269,7 +264,42 @@ __global__ void __launch_bounds__(256) k_chan_step(const ChanGeo G, const Phys p
                         D += 2.0 * rcx(j) * ((double)d[j] + (double)rw36(j) / 36.0);
         }
     }
-    if (drag) block_add(D, drag);
+    if (drag) warp_add(D, drag);
+}
+
+// Inlet (x = 0) and outlet (x = nx - 1) planes of a pulled step, one thread
+// per (y, z, side): the equilibrium of Eq. (9) from the populations pulled at
+// the neighbour plane; G = f there (not collided).
+__global__ void __launch_bounds__(128) k_chan_bc_step(const ChanGeo G, const Phys ph, const float u_peak,
+                                                      const float *__restrict__ Gin, float *__restrict__ frec,
+                                                      float *__restrict__ Gout) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int P = G.ny * G.nz;
+    if (k >= 2 * P) return;
+    const bool inlet = k < P;
+    const int yz = inlet ? k : k - P, y = yz % G.ny, z = yz / G.ny;
+    const int xs = inlet ? 1 : G.nx - 2, ns = xs + G.nx * yz, n = (inlet ? 0 : G.nx - 1) + G.nx * yz;
+    float e[Q], d[Q];
+    const bool cut = G.cut[ns] != 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) e[i] = pull(G, Gin, xs, y, z, ns, i, cut);
+    float rho, jx, jy, jz;
+    moments(e, rho, jx, jy, jz);
+    if (inlet) {
+        const float zh = (z + 0.5f) / G.nz;
+        const float ux = u_peak * 4.f * zh * (1.f - zh);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = feq_dev(i, rho, ux, 0.f, 0.f);
+    } else {
+        const float ux = jx / rho + 0.5f * ph.g[0], uy = jy / rho + 0.5f * ph.g[1], uz = jz / rho + 0.5f * ph.g[2];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = feq_dev(i, 1.f, ux, uy, uz);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (frec) frec[(size_t)i * G.N + n] = d[i];
+        Gout[(size_t)i * G.N + n] = d[i];
+    }
 }
 
 // ---- reverse -----------------------------------------------------------------
@@ -461,6 +491,7 @@ __global__ void __launch_bounds__(256) k_chan_adj(const ChanGeo G, const Phys ph
         } else {
             float gb[Q];
             const uint32_t pm = G.plate[n];
+            const bool cut = G.cut[n] != 0;
             const int yz0 = y + G.ny * z;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -469,11 +500,11 @@ __global__ void __launch_bounds__(256) k_chan_adj(const ChanGeo G, const Phys ph
                 if (tn >= 0 && G.type[tn] == CH_FLUID) {
                     const int xt = x + rcx(i), yzt = wrapy(y + rcy(i), G.ny) + G.ny * (z + rcz(i));
                     v += eff(G, lam1, rho_bar, ext, tn, xt, yzt, i);  // regular pull of x + c_i
-                    const float qt = G.q[(size_t)i * G.N + tn];
+                    const float qt = G.cut[tn] ? G.q[(size_t)i * G.N + tn] : -1.f;
                     if (qt >= 0.f && qt < 0.5f)
                         v += (1.f - 2.f * qt) * eff(G, lam1, rho_bar, ext, tn, xt, yzt, ropp(i));
                 }
-                if (t == CH_FLUID) {
+                if (t == CH_FLUID && cut) {
                     const float qi = G.q[(size_t)i * G.N + n];  // own link along c_i
                     if (qi >= 0.f) {
                         float a;
@@ -518,7 +549,7 @@ using namespace lbm;
 struct lbm_channel_s {
     lbm_channel_params p;
     int N = 0, np = 0, K = 0, nck = 0;
-    uint8_t *type = nullptr;
+    uint8_t *type = nullptr, *cut = nullptr;
     float *q = nullptr;
     uint32_t *plate = nullptr;
     double *X = nullptr, *R = nullptr;
@@ -546,6 +577,7 @@ ChanGeo geo_of(const lbm_channel_s *c) {
     g.nz = c->p.nz;
     g.N = c->N;
     g.type = c->type;
+    g.cut = c->cut;
     g.q = c->q;
     g.plate = c->plate;
     return g;
@@ -572,7 +604,7 @@ int calloc_dev(lbm_channel_s *c, T **p, size_t n) {
 }
 
 void chan_release(lbm_channel_s *c) {
-    void *ptrs[] = {c->type, c->q, c->plate, c->X, c->R, c->G[0], c->G[1], c->lam[0], c->lam[1], c->seg, c->ckpt,
+    void *ptrs[] = {c->type, c->cut, c->q, c->plate, c->X, c->R, c->G[0], c->G[1], c->lam[0], c->lam[1], c->seg, c->ckpt,
                     c->fend, c->rho_bar, c->ext, c->drag, c->grad, c->status};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -604,15 +636,18 @@ int launch_ok() { return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CU
 template <typename Rec>
 int chan_run(lbm_channel_s *c, const float *fin, int s0, int s1, Rec rec, bool with_drag) {
     const ChanGeo g = geo_of(c);
-    const int blocks = (c->N + 255) / 256;
+    const int blocks = (c->N + 255) / 256, bblocks = (2 * c->p.ny * c->p.nz + 127) / 128;
     const float up = (float)c->theta[0];
-    k_chan_step<false><<<blocks, 256, 0, c->stream>>>(g, c->ph, up, nullptr, fin, nullptr, c->G[s0 & 1],
+    k_chan_step<false><<<blocks, 256, 0, c->stream>>>(g, c->ph, nullptr, fin, nullptr, c->G[s0 & 1],
                                                       with_drag && s0 >= 1 ? c->drag + (s0 - 1) : nullptr, c->status);
     int rc = launch_ok();
     for (int s = s0 + 1; s <= s1 && !rc; ++s) {
-        k_chan_step<true><<<blocks, 256, 0, c->stream>>>(g, c->ph, up, c->G[(s - 1) & 1], nullptr, rec(s), c->G[s & 1],
+        float *fr = rec(s);
+        k_chan_step<true><<<blocks, 256, 0, c->stream>>>(g, c->ph, c->G[(s - 1) & 1], nullptr, fr, c->G[s & 1],
                                                          with_drag ? c->drag + (s - 1) : nullptr, c->status);
         rc = launch_ok();
+        if (!rc) k_chan_bc_step<<<bblocks, 128, 0, c->stream>>>(g, c->ph, up, c->G[(s - 1) & 1], fr, c->G[s & 1]);
+        if (!rc) rc = launch_ok();
     }
     return rc;
 }
@@ -662,6 +697,7 @@ int lbm_channel_create(const lbm_channel_params *prm, int32_t n, const double *p
     }
     const size_t NQs = (size_t)c->N * Q, P = (size_t)p.ny * p.nz;
     if (!rc) rc = calloc_dev(c, &c->type, (size_t)c->N);
+    if (!rc) rc = calloc_dev(c, &c->cut, (size_t)c->N);
     if (!rc) rc = calloc_dev(c, &c->q, NQs);
     if (!rc) rc = calloc_dev(c, &c->plate, (size_t)c->N);
     if (!rc) rc = calloc_dev(c, &c->X, 3 * (size_t)n);
@@ -691,7 +727,9 @@ int lbm_channel_create(const lbm_channel_params *prm, int32_t n, const double *p
         const int blocks = (c->N + 255) / 256;
         k_chan_types<<<blocks, 256, 0, c->stream>>>(p.nx, p.ny, p.nz, pb, n, c->X, c->R, c->type);
         rc = launch_ok();
-        if (!rc) k_chan_links<<<blocks, 256, 0, c->stream>>>(p.nx, p.ny, p.nz, n, c->X, c->R, c->type, c->q, c->plate);
+        if (!rc)
+            k_chan_links<<<blocks, 256, 0, c->stream>>>(p.nx, p.ny, p.nz, n, c->X, c->R, c->type, c->q, c->plate,
+                                                        c->cut);
         if (!rc) rc = launch_ok();
     }
     rc = chan_check(c, rc);
