@@ -31,7 +31,7 @@ class OrcParams(ctypes.Structure):
         ("u_lo", ctypes.c_double * 3), ("u_hi", ctypes.c_double * 3),
         ("rho_s", ctypes.c_double), ("kn", ctypes.c_double), ("restitution", ctypes.c_double),
         ("dem_substeps", ctypes.c_int), ("les", ctypes.c_int), ("fluid", ctypes.c_int),
-        ("periodic_z", ctypes.c_int),
+        ("periodic_z", ctypes.c_int), ("momentum_correction", ctypes.c_int),
     ]
 
 
@@ -97,7 +97,7 @@ class Oracle:
 
     def __init__(self, nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0),
                  u_hi=(0.0, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16,
-                 les=True, fluid=True, periodic_z=False, threads=None):
+                 les=True, fluid=True, periodic_z=False, momentum_correction=False, threads=None):
         if threads is not None:
             os.environ["OMP_NUM_THREADS"] = str(threads)
         lib = _load()
@@ -110,6 +110,7 @@ class Oracle:
         p.rho_s, p.kn, p.restitution = rho_s, kn, restitution
         p.dem_substeps, p.les, p.fluid = dem_substeps, int(bool(les)), int(bool(fluid))
         p.periodic_z = int(bool(periodic_z))
+        p.momentum_correction = int(bool(momentum_correction))
         self._h = lib.orc_create(ctypes.byref(p))
         if not self._h:
             raise MemoryError("oracle allocation failed")

@@ -76,6 +76,7 @@ typedef struct {
     int les;                /* 1: Smagorinsky tau (Eq. 18); 0: plain BGK path */
     int fluid;              /* 0: DEM only, no lattice (hydrodynamic load 0) */
     int periodic_z;         /* 1: z periodic too (no walls) */
+    int momentum_correction; /* 1: covered / uncovered nodes exchange their momentum with the sphere */
 } orc_params;
 
 typedef struct {
@@ -94,6 +95,7 @@ typedef struct {
     double *Fh, *Th;        /* hydrodynamic force and torque of the last step */
     double *Fc;             /* contact force at the current position (carried) */
     double *Fx, *Tx;        /* external force and torque held over every step */
+    double *Fcorr, *Tcorr;  /* momentum of the nodes covered / uncovered this step (correction) */
     unsigned char *fixed;   /* 1: prescribed motion, X += V dt; V, Om constant */
     long step;
     long refilled;          /* nodes refilled in the last step */
@@ -403,6 +405,57 @@ static void momentum_exchange(orc_state *s) {
             }
 }
 
+/* Momentum correction (optional; the paper uses none), after Aidun, Lu &
+ * Ding (1998): the populations of a node that becomes solid are dropped and
+ * their momentum sum_i c_i f_i is handed to the sphere that covers it; the
+ * equilibrium given to a node that becomes fluid (the refill below) is paid
+ * by its previous sphere.  Torques with the arm x - X_p (minimum image).
+ * The corrections join the momentum exchange of the same step, so the total
+ * momentum of fluid and spheres changes only by the body force, contacts
+ * and walls.  This part: the nodes covered at step n. */
+static void arm_of(const orc_state *s, int p, int x, int y, int z, double l[3]) {
+    const double *X = s->X + 3 * p;
+    l[0] = (double)image(x, X[0], s->p.nx, 1) - X[0];
+    l[1] = (double)image(y, X[1], s->p.ny, 1) - X[1];
+    l[2] = (double)image(z, X[2], s->p.nz, s->p.periodic_z) - X[2];
+}
+
+static void add_momentum(orc_state *s, int p, const double l[3], const double m[3], double sign) {
+    double *F = s->Fcorr + 3 * p, *T = s->Tcorr + 3 * p;
+    for (int a = 0; a < 3; ++a) F[a] += sign * m[a];
+    T[0] += sign * (l[1] * m[2] - l[2] * m[1]);
+    T[1] += sign * (l[2] * m[0] - l[0] * m[2]);
+    T[2] += sign * (l[0] * m[1] - l[1] * m[0]);
+}
+
+static void node_momentum(const orc_state *s, long n, double m[3]) {
+    m[0] = m[1] = m[2] = 0.0;
+    for (int i = 0; i < NQ; ++i) {
+        double fi = s->f[(long)i * s->N + n];
+        m[0] += CX[i] * fi;
+        m[1] += CY[i] * fi;
+        m[2] += CZ[i] * fi;
+    }
+}
+
+static void covered_correction(orc_state *s) {
+    const orc_params *P = &s->p;
+    memset(s->Fcorr, 0, sizeof(double) * 3 * s->np);
+    memset(s->Tcorr, 0, sizeof(double) * 3 * s->np);
+    if (!P->momentum_correction) return;
+    for (int z = 0; z < P->nz; ++z)
+        for (int y = 0; y < P->ny; ++y)
+            for (int x = 0; x < P->nx; ++x) {
+                long n = node_of(s, x, y, z);
+                int p = s->owner[n];
+                if (p < 0 || s->owner_prev[n] >= 0) continue;
+                double m[3], l[3];
+                node_momentum(s, n, m);
+                arm_of(s, p, x, y, z, l);
+                add_momentum(s, p, l, m, 1.0);
+            }
+}
+
 /* Step 2.  reading (the paper does not describe it): a node solid at n-1
  * and fluid at n takes the equilibrium (Eq. 9) at the velocity of the
  * surface of its previous owner, u_s = V_p + Om_p x (x - X_p), and at the
@@ -438,6 +491,11 @@ static void refill(orc_state *s) {
                                 V[2] + (W[0] * l[1] - W[1] * l[0])};
                 for (int i = 0; i < NQ; ++i) s->f[(long)i * s->N + n] = feq(s, i, rho, us);
                 ++s->refilled;
+                if (P->momentum_correction) {
+                    double m[3];
+                    node_momentum(s, n, m);
+                    add_momentum(s, p, l, m, -1.0);
+                }
             }
 }
 
@@ -580,7 +638,7 @@ void orc_destroy(orc_state *s) {
     if (!s) return;
     free(s->f); free(s->fc); free(s->fn); free(s->owner); free(s->owner_prev); free(s->key);
     free(s->X); free(s->V); free(s->Om); free(s->R); free(s->Fh); free(s->Th); free(s->Fc); free(s->fixed);
-    free(s->Fx); free(s->Tx);
+    free(s->Fx); free(s->Tx); free(s->Fcorr); free(s->Tcorr);
     free(s);
 }
 
@@ -588,8 +646,10 @@ void orc_destroy(orc_state *s) {
 int orc_set_particles(orc_state *s, int n, const double *X, const double *V, const double *Om,
                       const double *R, const unsigned char *fixed) {
     free(s->X); free(s->V); free(s->Om); free(s->R); free(s->Fh); free(s->Th); free(s->Fc); free(s->fixed);
-    free(s->Fx); free(s->Tx);
+    free(s->Fx); free(s->Tx); free(s->Fcorr); free(s->Tcorr);
     s->np = n;
+    s->Fcorr = (double *)xcalloc(3 * (size_t)n, sizeof(double));
+    s->Tcorr = (double *)xcalloc(3 * (size_t)n, sizeof(double));
     s->Fx = (double *)xcalloc(3 * (size_t)n, sizeof(double));
     s->Tx = (double *)xcalloc(3 * (size_t)n, sizeof(double));
     s->X = (double *)xcalloc(3 * (size_t)n, sizeof(double));
@@ -642,12 +702,17 @@ void orc_step(orc_state *s, int nsteps) {
         if (s->N) {
             memcpy(s->owner_prev, s->owner, sizeof(int) * s->N);
             geometry(s);
+            covered_correction(s);
             refill(s);
 #pragma omp parallel for schedule(static)
             for (long n = 0; n < s->N; ++n)
                 if (s->owner[n] < 0) collide_node(s, n);
             stream(s);
             momentum_exchange(s);
+            for (long k = 0; k < 3 * (long)s->np; ++k) {
+                s->Fh[k] += s->Fcorr[k];
+                s->Th[k] += s->Tcorr[k];
+            }
             double *t = s->f;
             s->f = s->fn;
             s->fn = t;

@@ -8,7 +8,10 @@
   a fixed point for every branch of Eq. (19), and the momentum-exchange force
   and torque on the sphere vanish (symmetry of the cut-link set);
 * with a body force the post-collision momentum of a uniform node grows by
-  exactly rho g per step (the Guo source carries the whole force).
+  exactly rho g per step (the Guo source carries the whole force);
+* with the covered / uncovered momentum correction, the total momentum of
+  fluid and free spheres in a fully periodic box is constant (and it is not
+  without the correction).
 """
 import numpy as np
 
@@ -81,3 +84,40 @@ def test_body_force_momentum_per_step():
     for z in range(2, 6):
         assert np.allclose(u[:, z], (1.5 * g)[:, None, None], rtol=1e-9, atol=0)
         assert np.allclose(rho[z], 1.0, atol=1e-15)
+
+
+def _total_momentum(o, R, rho_s):
+    """Fluid momentum sum_i c_i f_i over fluid nodes plus sum_p m_p V_p."""
+    c, _, _ = oracle.tables()
+    f = o.populations()
+    fluid = o.owner() < 0
+    P = np.tensordot(c.T.astype(np.float64), f, axes=(1, 0))[:, fluid].sum(axis=1)
+    _, V, _ = o.particles()
+    m = rho_s * 4.0 / 3.0 * np.pi * np.asarray(R) ** 3
+    return P + (m[:, None] * V).sum(axis=0)
+
+
+def test_momentum_correction_conserves_total_momentum():
+    """Fully periodic box (no walls, no body force) with free spheres that
+    cover and uncover nodes every few steps: with the covered / uncovered
+    momentum correction the total momentum of fluid and spheres is constant
+    to rounding; without it the dropped and refilled nodes change it."""
+    shape = (24, 20, 18)
+    X = np.array([[6.3, 5.2, 5.9], [16.8, 13.1, 11.4], [7.7, 14.6, 13.2]])
+    V = np.array([[0.06, 0.02, -0.01], [-0.03, 0.05, 0.02], [0.01, -0.04, 0.05]])
+    R = np.array([3.1, 2.6, 2.2])
+    drift = {}
+    for corr in (True, False):
+        o = oracle.Oracle(*shape, tau0=0.7, cs=0.17, rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=8,
+                          periodic_z=True, momentum_correction=corr)
+        o.set_particles(X, V=V, R=R)
+        P0 = _total_momentum(o, R, 2.5)
+        worst, refills = 0.0, 0
+        for _ in range(40):
+            o.step(1)
+            refills += o.refilled
+            worst = max(worst, float(np.abs(_total_momentum(o, R, 2.5) - P0).max()))
+        assert refills > 20  # nodes were uncovered (and covered) along the way
+        drift[corr] = worst / float(np.abs(P0).max())
+    assert drift[True] <= 1e-12, drift
+    assert drift[False] >= 1e-6, drift
