@@ -185,7 +185,8 @@ def run_reference(args, rank, world):
 
     box, nsph = (48, 48, 48), 13
     p = oracle_sample(box, nsph, seed_offset=100)
-    o = oracle.Oracle(*box, **PHYS)
+    corr = bool(getattr(args, "momentum_correction", False))
+    o = oracle.Oracle(*box, momentum_correction=corr, **PHYS)
     o.set_particles(p["X"], V=p["V"], Om=p["Om"], R=p["R"])
     o.step(args.warmup)
     t0 = time.perf_counter()
@@ -197,7 +198,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args.precision), "sample": "48^3 box, 13 spheres R=4 per step"},
+            "config": {"workload": workload_name(args.precision), "sample": "48^3 box, 13 spheres R=4 per step",
+                       "momentum_correction": corr},
             "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                              "sample": "48^3 box with 13 spheres (solid fraction of the workload), %d steps" %
                                        args.steps},
@@ -216,7 +218,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     p = oracle_sample(BOX, NSPH)
     lat = lbm.Lattice(*BOX, precision=args.precision, max_particles=NSPH, max_radius=4.0,
-                      stream=ctypes_stream(stream), device=dev, schedule=args.schedule, **PHYS)
+                      stream=ctypes_stream(stream), device=dev, schedule=args.schedule,
+                      momentum_correction=args.momentum_correction, **PHYS)
     lat.set_particles(p["X"], V=p["V"], Om=p["Om"], R=p["R"])
     N = BOX[0] * BOX[1] * BOX[2]
 
@@ -288,6 +291,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": workload_name(args.precision), "box": list(BOX), "spheres": NSPH,
                    "radius": 4.0, "solid_fraction": round(float(np.sum(4 / 3 * np.pi * p["R"] ** 3)) / N, 4),
                    "storage": args.precision, "schedule": args.schedule, "fluid_nodes": nf, "links": info["links"],
+                   "momentum_correction": args.momentum_correction,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (populations %.2f GB)" % (19 * N * s / 1e9)},
         "roofline": {"bound": "hbm", "kernel": "k_stream_collide" + (" (near + far launches)" if args.schedule == "overlap" else ""),
@@ -459,6 +463,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", choices=["serial", "overlap"], default="serial",
                     help="order of the kernels inside a step (same results)")
+    ap.add_argument("--momentum-correction", action="store_true",
+                    help="covered / uncovered nodes exchange their momentum with the spheres (slurry workload)")
     ap.add_argument("--workload", choices=["slurry", "batched", "adjoint"], default="slurry",
                     help="slurry: the 256^3 box with 2000 spheres; batched: the parameter-sweep batch; "
                          "adjoint: gradient evaluations of the differentiation form")

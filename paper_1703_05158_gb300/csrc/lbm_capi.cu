@@ -54,7 +54,8 @@ void release(lbm_s *h) {
     void *ptrs[] = {h->f, h->flag, h->owner, h->status, h->bar, h->ctr, h->pt.X, h->pt.V, h->pt.W, h->pt.R,
                     (void *)h->pt.fixed, h->pt.Fh, h->pt.Th, h->pt.Fc, h->pt.Fx, h->pt.Tx, h->pt.Xf,
                     h->pt.Xb[0], h->pt.Xb[1], h->pt.Vh[0], h->pt.Vh[1], h->pt.nbr, h->pt.nbr_cnt, h->pt.pairA,
-                    h->pt.pairB, h->pt.Xbuild, h->pt.rebuild, h->pt.frame[0], h->pt.frame[1]};
+                    h->pt.pairB, h->pt.Xbuild, h->pt.rebuild, h->pt.frame[0], h->pt.frame[1], h->pt.Fcorr,
+                    h->pt.Tcorr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->status_host) cudaFreeHost(h->status_host);
@@ -198,6 +199,7 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     if (p.precision != LBM_FP32 && p.precision != LBM_BF16_DEV && p.precision != LBM_FP16_DEV) return LBM_ERR_ARG;
     if (p.max_particles < 0) return LBM_ERR_ARG;
     if (p.schedule != LBM_SCHEDULE_OVERLAP && p.schedule != LBM_SCHEDULE_SERIAL) return LBM_ERR_ARG;
+    if (p.momentum_correction != 0 && p.momentum_correction != 1) return LBM_ERR_ARG;
     if (p.max_particles > 0) {
         if (!(p.max_radius > 0.0 && p.max_radius <= 16.0)) return LBM_ERR_ARG;
         // a sphere's bounding box and link tile must not wrap onto itself
@@ -288,6 +290,9 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     if (!rc) rc = dalloc(h, &pt.Tx, 3 * (size_t)M);
     if (!rc) rc = dalloc(h, &pt.Xbuild, 3 * (size_t)M);
     if (!rc) rc = dalloc(h, &pt.rebuild, 2);
+    if (!rc) rc = dalloc(h, &pt.Fcorr, 3 * (size_t)M);
+    if (!rc) rc = dalloc(h, &pt.Tcorr, 3 * (size_t)M);
+    pt.corr = p.momentum_correction;
     if (!rc) rc = dalloc(h, &pt.frame[0], (size_t)M);
     if (!rc) rc = dalloc(h, &pt.frame[1], (size_t)M);
     if (!rc) rc = dalloc(h, &pt.pairA, (size_t)M * kMaxNbr);
@@ -430,7 +435,7 @@ int lbm_set_particles(lbm_handle h, int32_t n, const double *pos, const double *
         else if (cudaMemsetAsync((void *)pt.fixed, 0, (size_t)n, h->stream) != cudaSuccess)
             rc = LBM_ERR_CUDA;
     }
-    double *zero[] = {pt.Fh, pt.Th, pt.Fc, pt.Fx, pt.Tx};
+    double *zero[] = {pt.Fh, pt.Th, pt.Fc, pt.Fx, pt.Tx, pt.Fcorr, pt.Tcorr};
     for (double *z : zero)
         if (!rc && n && cudaMemsetAsync(z, 0, v3, h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
     if (!rc && cudaMemsetAsync(h->f, 0, (size_t)Q * h->L.S * h->esize, h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
@@ -441,7 +446,7 @@ int lbm_set_particles(lbm_handle h, int32_t n, const double *pos, const double *
     h->parity = 0;
     h->steps = 0;
     if (!rc && n) rc = launch_neighbours(h, 1);
-    if (!rc && n) rc = launch_mark(h);
+    if (!rc && n) rc = launch_mark(h, h->parity, 0);
     if (!rc && n) rc = launch_contact(h);
     if (!rc && n && h->overlap) {
         // near set of step 0 from the initial centres; events in a recorded state
@@ -516,7 +521,7 @@ namespace {
 int serial_step_launches(lbm_s *h) {
     const int P = h->parity;
     auto ok = [](cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; };
-    int rc = launch_mark(h);
+    int rc = launch_mark(h, P, h->pt.corr);
     if (!rc) rc = ok(cudaEventRecord(h->ev_fork, h->stream));
     if (!rc) rc = ok(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
     if (!rc) rc = launch_neighbours(h, 0, h->side);
@@ -640,7 +645,7 @@ int lbm_step(lbm_handle h, int32_t nsteps) {
             if (!rc) rc = ok(cudaEventRecord(h->ev_cf, Bs));
         }
         if (!rc) rc = prof_mark(h, E0, A);
-        if (!rc && parts) rc = launch_mark(h);
+        if (!rc && parts) rc = launch_mark(h, P, h->pt.corr);
         if (!rc && parts) rc = launch_refill(h, P);
         if (!rc) rc = prof_mark(h, E1, A);
         if (ovl) {

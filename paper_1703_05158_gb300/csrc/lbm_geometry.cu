@@ -49,6 +49,43 @@ __device__ __forceinline__ int ext_of(float R) { return (int)ceilf(R); }
 
 constexpr int MAX_NBR_SMEM = 64;
 
+// Momentum m of a node and its moment l x m, accumulated into acc[0..5]
+// (sign +1 or -1); round-to-nearest intrinsics keep the compiler from
+// contracting the cross products, so every kernel that inlines this rounds
+// alike.
+__device__ __forceinline__ double cross_rn(double a, double b, double c, double d) {
+    return __dsub_rn(__dmul_rn(a, b), __dmul_rn(c, d));
+}
+__device__ __forceinline__ void add_moment(double *acc, double sign, float lx, float ly, float lz, double mx,
+                                           double my, double mz) {
+    const double m[6] = {mx, my, mz, cross_rn(ly, mz, lz, my), cross_rn(lz, mx, lx, mz), cross_rn(lx, my, ly, mx)};
+#pragma unroll
+    for (int a = 0; a < 6; ++a) acc[a] = sign > 0.0 ? __dadd_rn(acc[a], m[a]) : __dsub_rn(acc[a], m[a]);
+}
+
+// Node of box offset t (of the (2e+1)^3 box around floor(X_p)) if sphere p
+// wins it, else -1.
+__device__ __forceinline__ int mark_node(const Lat &L, const SFrame &F, const SFrame *nf, const int *nid,
+                                         const int cnt, const int p, const int e, const int B, const int t) {
+    const int oz = t / (B * B) - e, oy = (t / B) % B - e, ox = t % B - e;
+    const int z = F.b[2] + oz;
+    if (z < 0 || z >= L.nz) return -1;
+    const float d2 = dist2(rel(ox, F.fr[0]), rel(oy, F.fr[1]), rel(oz, F.fr[2]));
+    if (!(d2 < F.R2)) return -1;
+    const float key = __fsub_rn(__fsqrt_rn(d2), F.R);
+    const int x = wrapi(F.b[0] + ox, L.nx), y = wrapi(F.b[1] + oy, L.ny);
+    for (int m = 0; m < cnt; ++m) {
+        const SFrame &G = nf[m];
+        const float e2 = dist2(rel(fold(x, G.b[0], L.nx), G.fr[0]), rel(fold(y, G.b[1], L.ny), G.fr[1]),
+                               rel(z - G.b[2], G.fr[2]));
+        if (!(e2 < G.R2)) continue;
+        const float k2 = __fsub_rn(__fsqrt_rn(e2), G.R);
+        if (k2 < key || (k2 == key && nid[m] < p)) return -1;
+    }
+    return x + L.nx * (y + L.ny * z);
+}
+
+// The plain marks: flag 1 and owner p on every node sphere p wins.
 __device__ __forceinline__ void mark_body(const Lat &L, const Parts &pt, const SFrame *__restrict__ fcur,
                                           uint8_t *__restrict__ flag, int32_t *__restrict__ owner) {
     const int p = blockIdx.x;
@@ -62,43 +99,136 @@ __device__ __forceinline__ void mark_body(const Lat &L, const Parts &pt, const S
     }
     const SFrame F = fcur[p];
     __syncthreads();
-    const int e = ext_of(F.R), B = 2 * e + 1;
-    for (int t = threadIdx.x; t < B * B * B; t += blockDim.x) {
-        const int oz = t / (B * B) - e, oy = (t / B) % B - e, ox = t % B - e;
-        const int z = F.b[2] + oz;
-        if (z < 0 || z >= L.nz) continue;
-        const float d2 = dist2(rel(ox, F.fr[0]), rel(oy, F.fr[1]), rel(oz, F.fr[2]));
-        if (!(d2 < F.R2)) continue;
-        const float key = __fsub_rn(__fsqrt_rn(d2), F.R);
-        const int x = wrapi(F.b[0] + ox, L.nx), y = wrapi(F.b[1] + oy, L.ny);
-        bool win = true;
-        for (int m = 0; m < cnt && win; ++m) {
-            const SFrame &G = nf[m];
-            const float e2 = dist2(rel(fold(x, G.b[0], L.nx), G.fr[0]), rel(fold(y, G.b[1], L.ny), G.fr[1]),
-                                   rel(z - G.b[2], G.fr[2]));
-            if (!(e2 < G.R2)) continue;
-            const float k2 = __fsub_rn(__fsqrt_rn(e2), G.R);
-            if (k2 < key || (k2 == key && nid[m] < p)) win = false;
-        }
-        if (!win) continue;
-        const int n = x + L.nx * (y + L.ny * z);
+    const int e = ext_of(F.R), B = 2 * e + 1, B3 = B * B * B;
+    for (int t = threadIdx.x; t < B3; t += blockDim.x) {
+        const int n = mark_node(L, F, nf, nid, cnt, p, e, B, t);
+        if (n < 0) continue;
         flag[n] = 1;
         owner[n] = p;
     }
 }
 
-__global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
-                                              uint8_t *__restrict__ flag, int32_t *__restrict__ owner) {
-    mark_body(L, pt, fcur, flag, owner);
+// Marks with the optional momentum correction (Aidun, Lu & Ding 1998; not
+// part of the paper): a node that was fluid (flag 0) and is now won by
+// sphere p hands its momentum sum_i c_i f_i (read from the pre-collision
+// slots of parity P) and the moment about X_p to the sphere.  Per round of
+// kCovRound box offsets: the previous flags of the round's nodes are
+// fetched into shared memory first (only p writes a node p wins, so these
+// are the values before this step's marks), the marks compact the covered
+// nodes, which are then put in ascending node order and summed one warp per
+// node (lane i loads f_i); the CTA writes the total to Fcorr / Tcorr (zero
+// when it covers nothing).  blockDim.x = 256.
+template <typename T>
+__device__ __forceinline__ void mark_corr_body(const Lat &L, const Parts &pt, const SFrame *__restrict__ fcur,
+                                               uint8_t *__restrict__ flag, int32_t *__restrict__ owner,
+                                               const T *__restrict__ f, const int P) {
+    constexpr int kCovRound = 1024;
+    const int p = blockIdx.x;
+    __shared__ SFrame nf[MAX_NBR_SMEM];
+    __shared__ int nid[MAX_NBR_SMEM];
+    __shared__ uint8_t prev[kCovRound];
+    __shared__ int clist[kCovRound];
+    __shared__ int ccount;
+    __shared__ double wacc[8][6];  // per warp: its nodes' momentum and moment, in node order
+    const int cnt = min(pt.nbr_cnt[p], MAX_NBR_SMEM);
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int q = pt.nbr[(long long)p * pt.max_nbr + t];
+        nid[t] = q;
+        nf[t] = fcur[q];
+    }
+    const SFrame F = fcur[p];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x < 8 * 6) wacc[threadIdx.x / 6][threadIdx.x % 6] = 0.0;
+    if (threadIdx.x == 0) ccount = 0;
+    const int e = ext_of(F.R), B = 2 * e + 1, B3 = B * B * B;
+    for (int t0 = 0; t0 < B3; t0 += kCovRound) {
+        const int t1 = min(B3, t0 + kCovRound);
+        for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+            const int z = F.b[2] + t / (B * B) - e;
+            const int y = wrapi(F.b[1] + (t / B) % B - e, L.ny), x = wrapi(F.b[0] + t % B - e, L.nx);
+            prev[t - t0] = z >= 0 && z < L.nz ? flag[x + L.nx * (y + L.ny * z)] : 1;
+        }
+        __syncthreads();
+        for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+            const int n = mark_node(L, F, nf, nid, cnt, p, e, B, t);
+            if (n < 0) continue;
+            if (prev[t - t0] == 0) clist[atomicAdd(&ccount, 1)] = n;
+            flag[n] = 1;
+            owner[n] = p;
+        }
+        __syncthreads();
+        const int total = ccount;
+        __syncthreads();  // every thread has read ccount (and prev) before they are rewritten
+        if (threadIdx.x == 0) ccount = 0;
+        if (total == 0) continue;
+        // ascending node order (the entries are distinct): rank, then scatter
+        int v[kCovRound / 256], r[kCovRound / 256];
+#pragma unroll
+        for (int j = 0; j < kCovRound / 256; ++j) {
+            const int k = threadIdx.x + 256 * j;
+            r[j] = -1;
+            if (k < total) {
+                v[j] = clist[k];
+                int rank = 0;
+                for (int i = 0; i < total; ++i) rank += clist[i] < v[j];
+                r[j] = rank;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kCovRound / 256; ++j)
+            if (r[j] >= 0) clist[r[j]] = v[j];
+        __syncthreads();
+        for (int k = wid; k < total; k += nw) {
+            const int m = clist[k];
+            const int x = m % L.nx, y = (m / L.nx) % L.ny, z = m / (L.nx * L.ny);
+            float d = 0.f;
+            if (lane >= 1 && lane < Q) {
+                const Nbr nb(L, x, y);
+                d = Store<T>::ld(f + in_slot(L, nb, P, lane, (long long)m + L.plane));
+            }
+            float mx = lane < Q ? rcx(lane) * d : 0.f, my = lane < Q ? rcy(lane) * d : 0.f,
+                  mz = lane < Q ? rcz(lane) * d : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mx += __shfl_xor_sync(0xffffffffu, mx, o);
+                my += __shfl_xor_sync(0xffffffffu, my, o);
+                mz += __shfl_xor_sync(0xffffffffu, mz, o);
+            }
+            if (lane == 0)
+                add_moment(wacc[wid], 1.0, rel(fold(x, F.b[0], L.nx), F.fr[0]), rel(fold(y, F.b[1], L.ny), F.fr[1]),
+                           rel(z - F.b[2], F.fr[2]), mx, my, mz);
+        }
+        __syncthreads();  // clist is rewritten by the next round
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int a = threadIdx.x;
+        double sum = 0.0;
+        for (int w = 0; w < nw; ++w) sum = __dadd_rn(sum, wacc[w][a]);
+        (a < 3 ? pt.Fcorr : pt.Tcorr)[3 * p + a % 3] = sum;
+    }
 }
 
-// Batched: instance blockIdx.y at step parity sp; block (0, i) also clears
-// the instance's link / refill counters of the step.
+// CORR = false: the plain marks (no population reads); true: with the
+// momentum correction where the argument corr (per instance) asks for it.
+template <typename T, bool CORR>
+__global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
+                                              uint8_t *__restrict__ flag, int32_t *__restrict__ owner,
+                                              const T *__restrict__ f, const int P, const int corr) {
+    if (CORR && corr) mark_corr_body<T>(L, pt, fcur, flag, owner, f, P);
+    else mark_body(L, pt, fcur, flag, owner);
+}
+
+// Batched: instance blockIdx.y at step parity sp (also the population
+// parity); block (0, i) also clears the instance's link / refill counters.
+template <typename T, bool CORR>
 __global__ void __launch_bounds__(256) k_mark_b(const Inst *__restrict__ I, const int sp) {
     const Inst &a = I[blockIdx.y];
     if (blockIdx.x == 0 && threadIdx.x < 2) a.ctr[threadIdx.x] = 0ull;
     if ((int)blockIdx.x >= a.pt.np) return;
-    mark_body(a.L, a.pt, a.pt.frame[sp], a.flag, a.owner);
+    if (CORR && a.pt.corr) mark_corr_body<T>(a.L, a.pt, a.pt.frame[sp], a.flag, a.owner, (const T *)a.f, sp);
+    else mark_body(a.L, a.pt, a.pt.frame[sp], a.flag, a.owner);
 }
 
 // One CTA per sphere: collect the uncovered nodes of its previous bounding
@@ -107,12 +237,12 @@ __global__ void __launch_bounds__(256) k_mark_b(const Inst *__restrict__ I, cons
 // mean, and lanes 0..18 write the 19 equilibrium populations.
 constexpr int kRefillCap = 512;
 
-template <typename T>
+template <typename T, bool CORR>
 __device__ __forceinline__ void refill_body(const Lat &L, const SFrame *__restrict__ fcur,
                                             const SFrame *__restrict__ fprev, T *__restrict__ f,
                                             uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
                                             const int P, unsigned long long *__restrict__ ctr,
-                                            int *__restrict__ status) {
+                                            int *__restrict__ status, const Parts &pt) {
     __shared__ int list[kRefillCap];
     __shared__ int count;
     const int p = blockIdx.x;
@@ -132,11 +262,36 @@ __device__ __forceinline__ void refill_body(const Lat &L, const SFrame *__restri
         else atomicOr(status, ST_TILE);
     }
     __syncthreads();
+    if constexpr (CORR) {
+        // with the correction, ascending node order (the entries are
+        // distinct), so that the per-sphere sums below do not depend on timing
+        const int cnt = min(count, kRefillCap);
+        int v[kRefillCap / 256], r[kRefillCap / 256];
+#pragma unroll
+        for (int j = 0; j < kRefillCap / 256; ++j) {
+            const int k = threadIdx.x + 256 * j;
+            r[j] = -1;
+            if (k < cnt && threadIdx.x < 256) {
+                v[j] = list[k];
+                int rank = 0;
+                for (int i = 0; i < cnt; ++i) rank += list[i] < v[j];
+                r[j] = rank;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kRefillCap / 256; ++j)
+            if (r[j] >= 0) list[r[j]] = v[j];
+        __syncthreads();
+    }
     const int total = min(count, kRefillCap);
     if (total == 0) return;
     const SFrame F = fcur[p];  // current centre, velocity and spin, for the surface velocity
     const float *V = F.V, *W = F.W;
     const int lane = threadIdx.x & 31;
+    __shared__ double wacc[8][6];  // with CORR, per warp: the momentum its refilled nodes take, in node order
+    if (CORR && threadIdx.x < 8 * 6) wacc[threadIdx.x / 6][threadIdx.x % 6] = 0.0;
+    if (CORR) __syncthreads();
     for (int k = threadIdx.x >> 5; k < total; k += blockDim.x >> 5) {
         const int n = list[k];
         const int x = n % L.nx, y = (n / L.nx) % L.ny, z = n / (L.nx * L.ny);
@@ -184,25 +339,41 @@ __device__ __forceinline__ void refill_body(const Lat &L, const SFrame *__restri
         if (lane == 0) {
             flag[n] = 2;
             atomicAdd(ctr + 1, 1ull);
+            // momentum correction: the sphere pays the momentum rho u_s of
+            // the equilibrium it leaves behind
+            if (CORR && pt.corr)
+                add_moment(wacc[threadIdx.x >> 5], -1.0, lx, ly, lz, __dmul_rn(rho, ux), __dmul_rn(rho, uy),
+                           __dmul_rn(rho, uz));
+        }
+    }
+    if (CORR && pt.corr) {
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            const int a = threadIdx.x;
+            double sum = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum = __dadd_rn(sum, wacc[w][a]);
+            double *dst = (a < 3 ? pt.Fcorr : pt.Tcorr) + 3 * p + a % 3;
+            *dst = __dadd_rn(*dst, sum);
         }
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_refill(const Lat L, const SFrame *__restrict__ fcur,
+template <typename T, bool CORR>
+__global__ void __launch_bounds__(256, 4) k_refill(const Lat L, const SFrame *__restrict__ fcur,
                                                 const SFrame *__restrict__ fprev, T *__restrict__ f,
                                                 uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
                                                 const int P, unsigned long long *__restrict__ ctr,
-                                                int *__restrict__ status) {
-    refill_body<T>(L, fcur, fprev, f, flag, owner, P, ctr, status);
+                                                int *__restrict__ status, const Parts pt) {
+    refill_body<T, CORR>(L, fcur, fprev, f, flag, owner, P, ctr, status, pt);
 }
 
 // Batched: instance blockIdx.y; parity P is also the step parity.
-template <typename T>
-__global__ void __launch_bounds__(256) k_refill_b(const Inst *__restrict__ I, const int P) {
+template <typename T, bool CORR>
+__global__ void __launch_bounds__(256, 4) k_refill_b(const Inst *__restrict__ I, const int P) {
     const Inst &a = I[blockIdx.y];
     if ((int)blockIdx.x >= a.pt.np) return;
-    refill_body<T>(a.L, a.pt.frame[P], a.pt.frame[P ^ 1], (T *)a.f, a.flag, a.owner, P, a.ctr, a.status);
+    refill_body<T, CORR>(a.L, a.pt.frame[P], a.pt.frame[P ^ 1], (T *)a.f, a.flag, a.owner, P, a.ctr, a.status,
+                         a.pt);
 }
 
 // Near set of step s+1, from the centres the geometry of step s uses.
@@ -307,48 +478,88 @@ int launch_near_mark(lbm_s *h, uint8_t *near, uint8_t tag, const SFrame *frames,
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
-int launch_mark(lbm_s *h) {
+template <bool CORR>
+int mark_launch(lbm_s *h, int P, int corr) {
     const SFrame *fcur = h->pt.frame[h->steps & 1];
-    k_mark<<<h->pt.np, 256, 0, h->stream>>>(h->L, h->pt, fcur, h->flag, h->owner);
+    const dim3 g(h->pt.np);
+    switch (h->precision) {
+        case LBM_FP32:
+            k_mark<float, CORR><<<g, 256, 0, h->stream>>>(h->L, h->pt, fcur, h->flag, h->owner,
+                                                           (const float *)h->f, P, corr);
+            break;
+        case LBM_BF16_DEV:
+            k_mark<__nv_bfloat16, CORR><<<g, 256, 0, h->stream>>>(h->L, h->pt, fcur, h->flag, h->owner,
+                                                                   (const __nv_bfloat16 *)h->f, P, corr);
+            break;
+        case LBM_FP16_DEV:
+            k_mark<__half, CORR><<<g, 256, 0, h->stream>>>(h->L, h->pt, fcur, h->flag, h->owner,
+                                                            (const __half *)h->f, P, corr);
+            break;
+        default: return LBM_ERR_ARG;
+    }
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+int launch_mark(lbm_s *h, int P, int corr) {
+    return corr ? mark_launch<true>(h, P, corr) : mark_launch<false>(h, P, 0);
+}
+
+template <typename T, bool CORR>
+void refill_launch(lbm_s *h, int parity) {
+    const SFrame *fcur = h->pt.frame[h->steps & 1], *fprev = h->pt.frame[(h->steps + 1) & 1];
+    k_refill<T, CORR><<<h->pt.np, 256, 0, h->stream>>>(h->L, fcur, fprev, (T *)h->f, h->flag, h->owner, parity,
+                                                         h->ctr, h->status, h->pt);
 }
 
 int launch_refill(lbm_s *h, int parity) {
-    const SFrame *fcur = h->pt.frame[h->steps & 1], *fprev = h->pt.frame[(h->steps + 1) & 1];
+    const bool c = h->pt.corr != 0;
     switch (h->precision) {
-        case LBM_FP32:
-            k_refill<float><<<h->pt.np, 256, 0, h->stream>>>(h->L, fcur, fprev, (float *)h->f, h->flag, h->owner,
-                                                              parity, h->ctr, h->status);
-            break;
+        case LBM_FP32: c ? refill_launch<float, true>(h, parity) : refill_launch<float, false>(h, parity); break;
         case LBM_BF16_DEV:
-            k_refill<__nv_bfloat16><<<h->pt.np, 256, 0, h->stream>>>(h->L, fcur, fprev, (__nv_bfloat16 *)h->f,
-                                                                      h->flag, h->owner, parity, h->ctr, h->status);
+            c ? refill_launch<__nv_bfloat16, true>(h, parity) : refill_launch<__nv_bfloat16, false>(h, parity);
             break;
         case LBM_FP16_DEV:
-            k_refill<__half><<<h->pt.np, 256, 0, h->stream>>>(h->L, fcur, fprev, (__half *)h->f, h->flag, h->owner,
-                                                               parity, h->ctr, h->status);
+            c ? refill_launch<__half, true>(h, parity) : refill_launch<__half, false>(h, parity);
             break;
         default: return LBM_ERR_ARG;
     }
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
-int launch_mark_batch(const lbm_batch_s *b, int sp) {
-    if (b->max_np == 0) return LBM_OK;
-    k_mark_b<<<dim3(b->max_np, b->n), 256, 0, b->stream>>>(b->dinst, sp);
-    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+// Any member with the momentum correction selects the CORR kernels (each
+// instance still follows its own flag).
+static bool batch_corr(const lbm_batch_s *b) {
+    for (int i = 0; i < b->n; ++i)
+        if (b->m[i]->pt.corr) return true;
+    return false;
 }
 
-int launch_refill_batch(const lbm_batch_s *b, int P) {
-    if (b->max_np == 0) return LBM_OK;
+template <typename T>
+void geometry_batch(const lbm_batch_s *b, bool refill, bool corr, int P) {
     const dim3 grid(b->max_np, b->n);
+    if (refill) {
+        if (corr) k_refill_b<T, true><<<grid, 256, 0, b->stream>>>(b->dinst, P);
+        else k_refill_b<T, false><<<grid, 256, 0, b->stream>>>(b->dinst, P);
+    } else {
+        if (corr) k_mark_b<T, true><<<grid, 256, 0, b->stream>>>(b->dinst, P);
+        else k_mark_b<T, false><<<grid, 256, 0, b->stream>>>(b->dinst, P);
+    }
+}
+
+static int geometry_batch_launch(const lbm_batch_s *b, bool refill, int P) {
+    if (b->max_np == 0) return LBM_OK;
+    const bool c = batch_corr(b);
     switch (b->precision) {
-        case LBM_FP32: k_refill_b<float><<<grid, 256, 0, b->stream>>>(b->dinst, P); break;
-        case LBM_BF16_DEV: k_refill_b<__nv_bfloat16><<<grid, 256, 0, b->stream>>>(b->dinst, P); break;
-        case LBM_FP16_DEV: k_refill_b<__half><<<grid, 256, 0, b->stream>>>(b->dinst, P); break;
+        case LBM_FP32: geometry_batch<float>(b, refill, c, P); break;
+        case LBM_BF16_DEV: geometry_batch<__nv_bfloat16>(b, refill, c, P); break;
+        case LBM_FP16_DEV: geometry_batch<__half>(b, refill, c, P); break;
         default: return LBM_ERR_ARG;
     }
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
+
+int launch_mark_batch(const lbm_batch_s *b, int sp) { return geometry_batch_launch(b, false, sp); }
+
+int launch_refill_batch(const lbm_batch_s *b, int P) { return geometry_batch_launch(b, true, P); }
 
 }  // namespace lbm

@@ -188,6 +188,8 @@ struct Parts {
     int substeps;
     double skin;                   // list skin: pairs within R_a + R_b + skin are listed
     double max_step;               // largest displacement allowed in one step
+    int corr;                      // 1: covered / uncovered nodes exchange momentum with the sphere
+    double *Fcorr, *Tcorr;         // that exchange in the current step (marks write, refill adds)
 };
 
 // Makes device d current for the lifetime of the object, then restores the
@@ -317,7 +319,7 @@ int launch_stream_collide(lbm_s *h, int parity, int mode = 0, const uint8_t *nea
 int launch_near_mark(lbm_s *h, uint8_t *near, uint8_t tag, const SFrame *frames, int *list, int *count,
                      cudaStream_t stream);
 int launch_collide_list(lbm_s *h, int parity, const int *list, const int *count, cudaStream_t stream);
-int launch_mark(lbm_s *h);
+int launch_mark(lbm_s *h, int P, int corr);  // corr: momentum correction of the covered nodes
 int launch_refill(lbm_s *h, int parity);
 int launch_links(lbm_s *h, int parity);
 int launch_neighbours(lbm_s *h, int force, cudaStream_t stream = nullptr);

@@ -332,6 +332,11 @@ __device__ __forceinline__ void links_body(const Lat &L, const Parts &pt, const 
         Tq[0] = sh[3] + (sh[9] - (frac[1] * Iz - frac[2] * Iy)) * i18;
         Tq[1] = sh[4] + (sh[10] - (frac[2] * Ix - frac[0] * Iz)) * i18;
         Tq[2] = sh[5] + (sh[11] - (frac[0] * Iy - frac[1] * Ix)) * i18;
+        if (pt.corr)  // momentum of the nodes covered / uncovered this step
+            for (int a = 0; a < 3; ++a) {
+                F[a] += pt.Fcorr[3 * p + a];
+                Tq[a] += pt.Tcorr[3 * p + a];
+            }
         atomicAdd(ctr, (unsigned long long)total);
     }
 }

@@ -54,6 +54,7 @@ class lbm_params(ctypes.Structure):
         ("dem_substeps", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_particles", ctypes.c_int32),
         ("max_radius", ctypes.c_double),
         ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int32), ("schedule", ctypes.c_int32),
+        ("momentum_correction", ctypes.c_int32),
     ]
 
 
@@ -301,7 +302,7 @@ def lbm_batch_sync(b):
 
 def make_params(nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0), u_hi=(0.0, 0.0, 0.0),
                 rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16, precision="fp32", max_particles=0,
-                max_radius=4.0, stream=None, device=0, schedule="serial"):
+                max_radius=4.0, stream=None, device=0, schedule="serial", momentum_correction=False):
     """lbm_params from keyword arguments (the Lattice constructor's)."""
     p = lbm_params()
     p.nx, p.ny, p.nz, p.periodic_z = nx, ny, nz, 0
@@ -316,6 +317,7 @@ def make_params(nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0
     p.cuda_stream = stream
     p.device = device
     p.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
+    p.momentum_correction = int(bool(momentum_correction))
     return p
 
 
@@ -330,9 +332,9 @@ class Lattice:
 
     def __init__(self, nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0), u_hi=(0.0, 0.0, 0.0),
                  rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16, precision="fp32", max_particles=0,
-                 max_radius=4.0, stream=None, device=0, schedule="serial"):
+                 max_radius=4.0, stream=None, device=0, schedule="serial", momentum_correction=False):
         p = make_params(nx, ny, nz, tau0, cs, g, u_lo, u_hi, rho_s, kn, restitution, dem_substeps, precision,
-                        max_particles, max_radius, stream, device, schedule)
+                        max_particles, max_radius, stream, device, schedule, momentum_correction)
         self.params = p
         self.h = lbm_create(p)
         self.shape = (nz, ny, nx)
