@@ -102,7 +102,8 @@ typedef struct {
     int32_t schedule;          /* LBM_SCHEDULE_SERIAL (0) or LBM_SCHEDULE_OVERLAP */
     int32_t momentum_correction; /* 1: a node a sphere covers hands its fluid momentum (and torque)
                                     to the sphere, a refilled node takes its momentum from it
-                                    (Aidun, Lu & Ding 1998; not in the paper); 0: off */
+                                    (Aidun, Lu & Ding 1998; not in the paper); 0: off;
+                                    other values: LBM_ERR_ARG */
 } lbm_params;
 
 typedef struct {

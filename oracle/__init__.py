@@ -32,6 +32,7 @@ class OrcParams(ctypes.Structure):
         ("rho_s", ctypes.c_double), ("kn", ctypes.c_double), ("restitution", ctypes.c_double),
         ("dem_substeps", ctypes.c_int), ("les", ctypes.c_int), ("fluid", ctypes.c_int),
         ("periodic_z", ctypes.c_int), ("momentum_correction", ctypes.c_int),
+        ("kt", ctypes.c_double), ("mu", ctypes.c_double), ("restitution_t", ctypes.c_double),
     ]
 
 
@@ -62,6 +63,7 @@ def _load():
         lib.orc_step.argtypes = [vp, ctypes.c_int]
         lib.orc_forces.argtypes = [vp, dp, dp]
         lib.orc_contact_forces.argtypes = [vp, dp]
+        lib.orc_contact_torques.argtypes = [vp, dp]
         lib.orc_particles.argtypes = [vp, dp, dp, dp]
         lib.orc_fields.argtypes = [vp, dp, dp]
         lib.orc_tau_eff.argtypes = [vp, dp]
@@ -97,7 +99,8 @@ class Oracle:
 
     def __init__(self, nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0),
                  u_hi=(0.0, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16,
-                 les=True, fluid=True, periodic_z=False, momentum_correction=False, threads=None):
+                 les=True, fluid=True, periodic_z=False, momentum_correction=False, kt=0.0, mu=0.0,
+                 restitution_t=1.0, threads=None):
         if threads is not None:
             os.environ["OMP_NUM_THREADS"] = str(threads)
         lib = _load()
@@ -111,6 +114,7 @@ class Oracle:
         p.dem_substeps, p.les, p.fluid = dem_substeps, int(bool(les)), int(bool(fluid))
         p.periodic_z = int(bool(periodic_z))
         p.momentum_correction = int(bool(momentum_correction))
+        p.kt, p.mu, p.restitution_t = kt, mu, restitution_t
         self._h = lib.orc_create(ctypes.byref(p))
         if not self._h:
             raise MemoryError("oracle allocation failed")
@@ -133,8 +137,10 @@ class Oracle:
         R = np.ascontiguousarray(R, dtype=np.float64).reshape(n)
         fx = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8).reshape(n)
         self._keep = (X, V, Om, R, fx)
-        self.lib.orc_set_particles(self._h, n, _dp(X), _dp(V), _dp(Om), _dp(R),
-                                   None if fx is None else fx.ctypes.data)
+        rc = self.lib.orc_set_particles(self._h, n, _dp(X), _dp(V), _dp(Om), _dp(R),
+                                        None if fx is None else fx.ctypes.data)
+        if rc != 0:
+            raise MemoryError("oracle allocation failed")
         self.np = n
 
     def set_load(self, F=None, T=None):
@@ -167,6 +173,12 @@ class Oracle:
         if self.np:
             self.lib.orc_contact_forces(self._h, _dp(F))
         return F
+
+    def contact_torques(self):
+        T = np.empty((self.np, 3))
+        if self.np:
+            self.lib.orc_contact_torques(self._h, _dp(T))
+        return T
 
     def particles(self):
         X, V, Om = np.empty((self.np, 3)), np.empty((self.np, 3)), np.empty((self.np, 3))

@@ -77,6 +77,9 @@ typedef struct {
     int fluid;              /* 0: DEM only, no lattice (hydrodynamic load 0) */
     int periodic_z;         /* 1: z periodic too (no walls) */
     int momentum_correction; /* 1: covered / uncovered nodes exchange their momentum with the sphere */
+    double kt;              /* tangential contact stiffness (Eq. 2); friction is on when kt > 0 and mu > 0 */
+    double mu;              /* Coulomb friction coefficient mu_s (Eq. 2) */
+    double restitution_t;   /* tangential restitution, sets gamma_t (Eq. 2); 1: no tangential damping */
 } orc_params;
 
 typedef struct {
@@ -94,6 +97,9 @@ typedef struct {
     double *X, *V, *Om, *R; /* sphere centre, velocity, angular velocity, radius */
     double *Fh, *Th;        /* hydrodynamic force and torque of the last step */
     double *Fc;             /* contact force at the current position (carried) */
+    double *Tc;             /* contact (friction) torque at the current position (carried) */
+    double *dt_pair;        /* [np][np][3] tangential displacement delta_t of contact a-b, seen from a */
+    double *dt_wall;        /* [np][2][3] the same against the lower and the upper wall */
     double *Fx, *Tx;        /* external force and torque held over every step */
     double *Fcorr, *Tcorr;  /* momentum of the nodes covered / uncovered this step (correction) */
     unsigned char *fixed;   /* 1: prescribed motion, X += V dt; V, Om constant */
@@ -517,19 +523,82 @@ static double gamma_n(const orc_state *s, double meff) {
     return -2.0 * le * sqrt(meff * s->p.kn) / sqrt(M_PI * M_PI + le * le);
 }
 
-/* Contact force on every sphere at positions X and velocities v (Eq. 1,
- * reading: f^n = k_n delta - gamma_n v_n with delta > 0 the overlap,
- * unclipped).  Sphere-sphere with the minimum image in x and y; sphere-wall
- * against the planes z = -1/2 and z = nz - 1/2 with m_eff = m.  A fixed
- * sphere acts with infinite mass. */
-static void contact_forces(orc_state *s, const double *X, const double *v, double *Fc) {
+static int friction_on(const orc_state *s) { return s->p.kt > 0.0 && s->p.mu > 0.0; }
+
+/* Damping coefficient of the tangential law (Eq. 2).  reading: the paper says
+ * only that it depends on the tangential restitution; the same
+ * spring-dashpot relation as gamma_n with k_t in place of k_n (and the same
+ * m_eff), 0 for restitution_t >= 1. */
+static double gamma_t(const orc_state *s, double meff) {
+    if (!(s->p.restitution_t < 1.0)) return 0.0;
+    double le = log(s->p.restitution_t);
+    return -2.0 * le * sqrt(meff * s->p.kt) / sqrt(M_PI * M_PI + le * le);
+}
+
+static void cross(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Tangential force of one contact (Eqs. 2, 3).  readings: the force on the
+ * sphere opposes its tangential displacement and its tangential relative
+ * velocity, f_t = -k_t delta_t - gamma_t v_t (the paper's sliding branch,
+ * -mu f^n v_t/|v_t|, fixes this sign convention); delta_t is first turned
+ * into the current tangent plane (its normal part removed), then advanced by
+ * v_t h; when |f_t| exceeds mu max(f^n, 0) the contact slides,
+ * f_t = -mu f^n v_t/|v_t| (along the trial force if v_t = 0), and delta_t is
+ * reset to -f_t / k_t.  h = 0 evaluates the force without advancing or
+ * storing delta_t. */
+static void tangential(const orc_state *s, double *state, const double n[3], const double vt[3], double fn,
+                       double gt, double h, double ft[3]) {
+    double d[3] = {state[0], state[1], state[2]};
+    double dn = d[0] * n[0] + d[1] * n[1] + d[2] * n[2];
+    for (int c = 0; c < 3; ++c) d[c] -= dn * n[c];
+    if (h > 0.0)
+        for (int c = 0; c < 3; ++c) d[c] += vt[c] * h;
+    double tr[3], t2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        tr[c] = -s->p.kt * d[c] - gt * vt[c];
+        t2 += tr[c] * tr[c];
+    }
+    double cap = s->p.mu * (fn > 0.0 ? fn : 0.0);
+    if (t2 > cap * cap) {
+        double v = sqrt(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
+        double tl = sqrt(t2);
+        for (int c = 0; c < 3; ++c) ft[c] = v > 0.0 ? -cap * vt[c] / v : cap * tr[c] / tl;
+        for (int c = 0; c < 3; ++c) d[c] = -ft[c] / s->p.kt;
+    } else {
+        for (int c = 0; c < 3; ++c) ft[c] = tr[c];
+    }
+    if (h > 0.0)
+        for (int c = 0; c < 3; ++c) state[c] = d[c];
+}
+
+/* Contact force (and, with friction, torque) on every sphere at positions X,
+ * velocities v and spins Om (Eq. 1, reading: f^n = k_n delta - gamma_n v_n
+ * with delta > 0 the overlap, unclipped).  Sphere-sphere with the minimum
+ * image in x and y; sphere-wall against the planes z = -1/2 and z = nz - 1/2
+ * with m_eff = m.  A fixed sphere acts with infinite mass.  With friction
+ * (Eqs. 2, 3): reading, the contact point is the middle of the overlap, at
+ * R - delta/2 from each centre along the line of centres; the relative
+ * velocity there is v^r = v_a - v_b - ((R_a - delta/2) Om_a + (R_b -
+ * delta/2) Om_b) x n (n from b to a; a wall moves with its lattice velocity
+ * and does not spin), and the torque on a is (-(R_a - delta/2) n) x f_t, so
+ * that a pair conserves linear and angular momentum exactly.  The
+ * tangential displacement of a contact that opened is reset to 0.  h > 0
+ * advances the tangential displacements by one sub-step of length h. */
+static void contact_forces(orc_state *s, const double *X, const double *v, const double *Om, double *Fc, double *Tc,
+                           double h) {
     const orc_params *P = &s->p;
+    const int fric = friction_on(s);
 #pragma omp parallel for schedule(static)
     for (int a = 0; a < s->np; ++a) {
-        double F[3] = {0, 0, 0};
+        double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
         double ma = sphere_mass(s, a);
         for (int b = 0; b < s->np; ++b) {
             if (b == a) continue;
+            double *st = fric ? s->dt_pair + 3 * ((long)a * s->np + b) : NULL;
             double d[3] = {X[3 * a] - X[3 * b], X[3 * a + 1] - X[3 * b + 1], X[3 * a + 2] - X[3 * b + 2]};
             if (d[0] > 0.5 * P->nx) d[0] -= P->nx;
             if (d[0] < -0.5 * P->nx) d[0] += P->nx;
@@ -539,7 +608,10 @@ static void contact_forces(orc_state *s, const double *X, const double *v, doubl
             if (P->periodic_z && d[2] < -0.5 * P->nz) d[2] += P->nz;
             double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
             double delta = s->R[a] + s->R[b] - dist;
-            if (!(delta > 0.0) || dist == 0.0) continue;
+            if (!(delta > 0.0) || dist == 0.0) {
+                if (fric && h > 0.0) st[0] = st[1] = st[2] = 0.0;
+                continue;
+            }
             double nv[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
             double vn = (v[3 * a] - v[3 * b]) * nv[0] + (v[3 * a + 1] - v[3 * b + 1]) * nv[1] +
                         (v[3 * a + 2] - v[3 * b + 2]) * nv[2];
@@ -549,14 +621,62 @@ static void contact_forces(orc_state *s, const double *X, const double *v, doubl
             F[0] += fn * nv[0];
             F[1] += fn * nv[1];
             F[2] += fn * nv[2];
+            if (fric) {
+                double la = s->R[a] - 0.5 * delta, lb = s->R[b] - 0.5 * delta;
+                double S[3], Sn[3], vt[3], ft[3], r[3], tq[3];
+                for (int c = 0; c < 3; ++c) S[c] = la * Om[3 * a + c] + lb * Om[3 * b + c];
+                cross(S, nv, Sn);
+                double vr[3], vrn = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    vr[c] = v[3 * a + c] - v[3 * b + c] - Sn[c];
+                    vrn += vr[c] * nv[c];
+                }
+                for (int c = 0; c < 3; ++c) vt[c] = vr[c] - vrn * nv[c];
+                tangential(s, st, nv, vt, fn, gamma_t(s, meff), h, ft);
+                for (int c = 0; c < 3; ++c) {
+                    F[c] += ft[c];
+                    r[c] = -la * nv[c];
+                }
+                cross(r, ft, tq);
+                for (int c = 0; c < 3; ++c) T[c] += tq[c];
+            }
         }
-        double lo = s->R[a] - (X[3 * a + 2] + 0.5);
-        if (!P->periodic_z && lo > 0.0) F[2] += P->kn * lo - gamma_n(s, ma) * v[3 * a + 2];
-        double hi = s->R[a] - ((P->nz - 0.5) - X[3 * a + 2]);
-        if (!P->periodic_z && hi > 0.0) F[2] -= P->kn * hi - gamma_n(s, ma) * (-v[3 * a + 2]);
-        Fc[3 * a] = F[0];
-        Fc[3 * a + 1] = F[1];
-        Fc[3 * a + 2] = F[2];
+        for (int side = 0; side < 2 && !P->periodic_z; ++side) {
+            /* side 0: wall z = -1/2, normal +z into the sphere; side 1: z = nz - 1/2, normal -z */
+            double pen = side == 0 ? s->R[a] - (X[3 * a + 2] + 0.5) : s->R[a] - ((P->nz - 0.5) - X[3 * a + 2]);
+            double *st = fric ? s->dt_wall + 3 * (2L * a + side) : NULL;
+            if (!(pen > 0.0)) {
+                if (fric && h > 0.0) st[0] = st[1] = st[2] = 0.0;
+                continue;
+            }
+            if (side == 0) F[2] += P->kn * pen - gamma_n(s, ma) * v[3 * a + 2];
+            else F[2] -= P->kn * pen - gamma_n(s, ma) * (-v[3 * a + 2]);
+            if (fric) {
+                double nv[3] = {0.0, 0.0, side == 0 ? 1.0 : -1.0};
+                const double *uw = side == 0 ? P->u_lo : P->u_hi;
+                double fn = P->kn * pen - gamma_n(s, ma) * (v[3 * a + 2] * nv[2]);
+                double la = s->R[a] - 0.5 * pen;
+                double S[3], Sn[3], vt[3], ft[3], r[3], tq[3], vr[3], vrn = 0.0;
+                for (int c = 0; c < 3; ++c) S[c] = la * Om[3 * a + c];
+                cross(S, nv, Sn);
+                for (int c = 0; c < 3; ++c) {
+                    vr[c] = v[3 * a + c] - uw[c] - Sn[c];
+                    vrn += vr[c] * nv[c];
+                }
+                for (int c = 0; c < 3; ++c) vt[c] = vr[c] - vrn * nv[c];
+                tangential(s, st, nv, vt, fn, gamma_t(s, ma), h, ft);
+                for (int c = 0; c < 3; ++c) {
+                    F[c] += ft[c];
+                    r[c] = -la * nv[c];
+                }
+                cross(r, ft, tq);
+                for (int c = 0; c < 3; ++c) T[c] += tq[c];
+            }
+        }
+        for (int c = 0; c < 3; ++c) {
+            Fc[3 * a + c] = F[c];
+            Tc[3 * a + c] = T[c];
+        }
     }
 }
 
@@ -565,18 +685,25 @@ static void contact_forces(orc_state *s, const double *X, const double *v, doubl
  * lattice step, and no body force on spheres:
  *   v += (F_h + F_x + F_c) h/(2m);  X += v h;  F_c = contact(X, v);
  *   v += (F_h + F_x + F_c) h/(2m);  Om += (T_h + T_x) h / I,  I = 2/5 m R^2.
+ * With friction the spin takes the same two half kicks as v, with the
+ * contact torque T_c of the last contact evaluation added:
+ *   Om += (T_h + T_x + T_c) h/(2I) before the drift and after the contacts.
  * A fixed sphere moves with its prescribed velocity: X += V h only.  Centres
  * are wrapped into [0, n) on periodic axes after every drift. */
 static void dem(orc_state *s) {
     const orc_params *P = &s->p;
+    const int fric = friction_on(s);
     int ns = P->dem_substeps > 0 ? P->dem_substeps : 1;
     double h = 1.0 / ns;
     for (int it = 0; it < ns; ++it) {
         for (int a = 0; a < s->np; ++a) {
             double m = sphere_mass(s, a);
+            double I = 0.4 * m * s->R[a] * s->R[a];
             for (int c = 0; c < 3; ++c) {
-                if (!s->fixed[a])
+                if (!s->fixed[a]) {
                     s->V[3 * a + c] += (s->Fh[3 * a + c] + s->Fx[3 * a + c] + s->Fc[3 * a + c]) * h / (2.0 * m);
+                    if (fric) s->Om[3 * a + c] += (s->Th[3 * a + c] + s->Tx[3 * a + c] + s->Tc[3 * a + c]) * h / (2.0 * I);
+                }
                 s->X[3 * a + c] += s->V[3 * a + c] * h;
             }
             if (s->X[3 * a] >= P->nx) s->X[3 * a] -= P->nx;
@@ -586,14 +713,15 @@ static void dem(orc_state *s) {
             if (P->periodic_z && s->X[3 * a + 2] >= P->nz) s->X[3 * a + 2] -= P->nz;
             if (P->periodic_z && s->X[3 * a + 2] < 0.0) s->X[3 * a + 2] += P->nz;
         }
-        contact_forces(s, s->X, s->V, s->Fc);
+        contact_forces(s, s->X, s->V, s->Om, s->Fc, s->Tc, h);
         for (int a = 0; a < s->np; ++a) {
             if (s->fixed[a]) continue;
             double m = sphere_mass(s, a);
             double I = 0.4 * m * s->R[a] * s->R[a];
             for (int c = 0; c < 3; ++c) {
                 s->V[3 * a + c] += (s->Fh[3 * a + c] + s->Fx[3 * a + c] + s->Fc[3 * a + c]) * h / (2.0 * m);
-                s->Om[3 * a + c] += (s->Th[3 * a + c] + s->Tx[3 * a + c]) * h / I;
+                if (fric) s->Om[3 * a + c] += (s->Th[3 * a + c] + s->Tx[3 * a + c] + s->Tc[3 * a + c]) * h / (2.0 * I);
+                else s->Om[3 * a + c] += (s->Th[3 * a + c] + s->Tx[3 * a + c]) * h / I;
             }
         }
     }
@@ -638,7 +766,7 @@ void orc_destroy(orc_state *s) {
     if (!s) return;
     free(s->f); free(s->fc); free(s->fn); free(s->owner); free(s->owner_prev); free(s->key);
     free(s->X); free(s->V); free(s->Om); free(s->R); free(s->Fh); free(s->Th); free(s->Fc); free(s->fixed);
-    free(s->Fx); free(s->Tx); free(s->Fcorr); free(s->Tcorr);
+    free(s->Fx); free(s->Tx); free(s->Fcorr); free(s->Tcorr); free(s->Tc); free(s->dt_pair); free(s->dt_wall);
     free(s);
 }
 
@@ -646,8 +774,15 @@ void orc_destroy(orc_state *s) {
 int orc_set_particles(orc_state *s, int n, const double *X, const double *V, const double *Om,
                       const double *R, const unsigned char *fixed) {
     free(s->X); free(s->V); free(s->Om); free(s->R); free(s->Fh); free(s->Th); free(s->Fc); free(s->fixed);
-    free(s->Fx); free(s->Tx); free(s->Fcorr); free(s->Tcorr);
+    free(s->Fx); free(s->Tx); free(s->Fcorr); free(s->Tcorr); free(s->Tc); free(s->dt_pair); free(s->dt_wall);
+    s->dt_pair = s->dt_wall = NULL;
     s->np = n;
+    s->Tc = (double *)xcalloc(3 * (size_t)n, sizeof(double));
+    if (friction_on(s)) {
+        s->dt_pair = (double *)xcalloc(3 * (size_t)n * n, sizeof(double));
+        s->dt_wall = (double *)xcalloc(6 * (size_t)n, sizeof(double));
+        if (n && (!s->dt_pair || !s->dt_wall)) return -1;
+    }
     s->Fcorr = (double *)xcalloc(3 * (size_t)n, sizeof(double));
     s->Tcorr = (double *)xcalloc(3 * (size_t)n, sizeof(double));
     s->Fx = (double *)xcalloc(3 * (size_t)n, sizeof(double));
@@ -673,7 +808,7 @@ int orc_set_particles(orc_state *s, int n, const double *X, const double *V, con
         geometry(s);
         memcpy(s->owner_prev, s->owner, sizeof(int) * s->N);
     }
-    contact_forces(s, s->X, s->V, s->Fc);
+    contact_forces(s, s->X, s->V, s->Om, s->Fc, s->Tc, 0.0);
     s->step = 0;
     s->refilled = 0;
     return 0;
@@ -728,6 +863,8 @@ void orc_forces(const orc_state *s, double *F, double *T) {
 }
 
 void orc_contact_forces(const orc_state *s, double *Fc) { memcpy(Fc, s->Fc, sizeof(double) * 3 * s->np); }
+
+void orc_contact_torques(const orc_state *s, double *Tc) { memcpy(Tc, s->Tc, sizeof(double) * 3 * s->np); }
 
 void orc_particles(const orc_state *s, double *X, double *V, double *Om) {
     memcpy(X, s->X, sizeof(double) * 3 * s->np);
