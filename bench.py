@@ -175,6 +175,13 @@ def whole_job_mlups(updates_per_rank, world, seconds):
     return world * updates_per_rank / seconds / 1e6
 
 
+def friction_params(args):
+    """Tangential contact law of the --friction runs (none by default)."""
+    if not getattr(args, "friction", False):
+        return {}
+    return dict(kt=0.5 * PHYS["kn"], mu=0.3, restitution_t=0.6)
+
+
 def run_reference(args, rank, world):
     """--impl reference: the FP64 oracle on the host, each step a bounded
     sample of the workload (a 48^3 box at the same solid fraction: 13 spheres
@@ -186,7 +193,7 @@ def run_reference(args, rank, world):
     box, nsph = (48, 48, 48), 13
     p = oracle_sample(box, nsph, seed_offset=100)
     corr = bool(getattr(args, "momentum_correction", False))
-    o = oracle.Oracle(*box, momentum_correction=corr, **PHYS)
+    o = oracle.Oracle(*box, momentum_correction=corr, **PHYS, **friction_params(args))
     o.set_particles(p["X"], V=p["V"], Om=p["Om"], R=p["R"])
     o.step(args.warmup)
     t0 = time.perf_counter()
@@ -199,7 +206,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args.precision), "sample": "48^3 box, 13 spheres R=4 per step",
-                       "momentum_correction": corr},
+                       "momentum_correction": corr, "friction": friction_params(args) or None},
             "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                              "sample": "48^3 box with 13 spheres (solid fraction of the workload), %d steps" %
                                        args.steps},
@@ -219,7 +226,7 @@ def run_ours(args, rank, world, local_rank):
     p = oracle_sample(BOX, NSPH)
     lat = lbm.Lattice(*BOX, precision=args.precision, max_particles=NSPH, max_radius=4.0,
                       stream=ctypes_stream(stream), device=dev, schedule=args.schedule,
-                      momentum_correction=args.momentum_correction, **PHYS)
+                      momentum_correction=args.momentum_correction, **PHYS, **friction_params(args))
     lat.set_particles(p["X"], V=p["V"], Om=p["Om"], R=p["R"])
     N = BOX[0] * BOX[1] * BOX[2]
 
@@ -291,7 +298,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": workload_name(args.precision), "box": list(BOX), "spheres": NSPH,
                    "radius": 4.0, "solid_fraction": round(float(np.sum(4 / 3 * np.pi * p["R"] ** 3)) / N, 4),
                    "storage": args.precision, "schedule": args.schedule, "fluid_nodes": nf, "links": info["links"],
-                   "momentum_correction": args.momentum_correction,
+                   "momentum_correction": args.momentum_correction, "friction": friction_params(args) or None,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (populations %.2f GB)" % (19 * N * s / 1e9)},
         "roofline": {"bound": "hbm", "kernel": "k_stream_collide" + (" (near + far launches)" if args.schedule == "overlap" else ""),
@@ -463,6 +470,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", choices=["serial", "overlap"], default="serial",
                     help="order of the kernels inside a step (same results)")
+    ap.add_argument("--friction", action="store_true",
+                    help="tangential contact law (Eqs. 2, 3) with k_t = k_n / 2, mu = 0.3, e_t = 0.6 (slurry workload)")
     ap.add_argument("--momentum-correction", action="store_true",
                     help="covered / uncovered nodes exchange their momentum with the spheres (slurry workload)")
     ap.add_argument("--workload", choices=["slurry", "batched", "adjoint"], default="slurry",

@@ -104,6 +104,13 @@ typedef struct {
                                     to the sphere, a refilled node takes its momentum from it
                                     (Aidun, Lu & Ding 1998; not in the paper); 0: off;
                                     other values: LBM_ERR_ARG */
+    double kt;                 /* tangential contact stiffness (Eq. 2), >= 0 */
+    double mu;                 /* Coulomb friction coefficient mu_s (Eq. 2), >= 0; friction acts
+                                  between spheres and against the walls when kt > 0 and mu > 0
+                                  (then LBM_ERR_UNSUPPORTED if max_particles exceeds what one
+                                  thread-block cluster of the DEM holds) */
+    double restitution_t;      /* tangential restitution in (0, 1], sets the dashpot gamma_t of
+                                  Eq. 2 like restitution sets gamma_n; 1: no tangential damping */
 } lbm_params;
 
 typedef struct {

@@ -14,7 +14,8 @@ using namespace lbm;
 
 namespace {
 
-constexpr int kMaxNbr = 48;
+constexpr int kMaxNbr = 48;  // at most 64: the DEM keeps one contact bit per list entry
+static_assert(kMaxNbr <= 64, "contact mask");
 constexpr int kDemThreads = 128;   // fallback cooperative DEM
 constexpr double kSkin = 1.5;      // neighbour-list skin (lattice units)
 constexpr double kMaxStep = 0.25;  // largest displacement of a sphere in one step
@@ -55,7 +56,7 @@ void release(lbm_s *h) {
                     (void *)h->pt.fixed, h->pt.Fh, h->pt.Th, h->pt.Fc, h->pt.Fx, h->pt.Tx, h->pt.Xf,
                     h->pt.Xb[0], h->pt.Xb[1], h->pt.Vh[0], h->pt.Vh[1], h->pt.nbr, h->pt.nbr_cnt, h->pt.pairA,
                     h->pt.pairB, h->pt.Xbuild, h->pt.rebuild, h->pt.frame[0], h->pt.frame[1], h->pt.Fcorr,
-                    h->pt.Tcorr};
+                    h->pt.Tcorr, h->pt.Tc, h->pt.pairC, h->pt.tdisp, h->pt.tmask, h->pt.twall};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->status_host) cudaFreeHost(h->status_host);
@@ -200,6 +201,9 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     if (p.max_particles < 0) return LBM_ERR_ARG;
     if (p.schedule != LBM_SCHEDULE_OVERLAP && p.schedule != LBM_SCHEDULE_SERIAL) return LBM_ERR_ARG;
     if (p.momentum_correction != 0 && p.momentum_correction != 1) return LBM_ERR_ARG;
+    if (!(p.kt >= 0.0) || !(p.mu >= 0.0) || !(p.restitution_t > 0.0 && p.restitution_t <= 1.0) ||
+        !std::isfinite(p.kt) || !std::isfinite(p.mu))
+        return LBM_ERR_ARG;
     if (p.max_particles > 0) {
         if (!(p.max_radius > 0.0 && p.max_radius <= 16.0)) return LBM_ERR_ARG;
         // a sphere's bounding box and link tile must not wrap onto itself
@@ -265,6 +269,17 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     pt.substeps = p.dem_substeps;
     pt.skin = kSkin;
     pt.max_step = kMaxStep;
+    pt.fric = p.kt > 0.0 && p.mu > 0.0;
+    pt.kt = p.kt;
+    pt.mu = p.mu;
+    {
+        const double lt = std::log(p.restitution_t);
+        pt.ct = p.restitution_t < 1.0 ? -2.0 * lt / std::sqrt(M_PI * M_PI + lt * lt) : 0.0;
+    }
+    for (int a = 0; a < 3; ++a) {
+        pt.ulo[a] = (float)p.wall_vel_lo[a];
+        pt.uhi[a] = (float)p.wall_vel_hi[a];
+    }
     // a solid node lies within [-ceil(R) + 1, ceil(R)] of floor(X) per axis; the
     // link tile also holds x = s - c_j and x - c_j, two more nodes out
     h->tile_ext = (int)std::ceil(M > 0 ? p.max_radius : 1.0) + 2;
@@ -292,6 +307,13 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     if (!rc) rc = dalloc(h, &pt.rebuild, 2);
     if (!rc) rc = dalloc(h, &pt.Fcorr, 3 * (size_t)M);
     if (!rc) rc = dalloc(h, &pt.Tcorr, 3 * (size_t)M);
+    if (!rc) rc = dalloc(h, &pt.Tc, 3 * (size_t)M);
+    if (!rc && pt.fric) {
+        rc = dalloc(h, &pt.pairC, (size_t)M * kMaxNbr);
+        if (!rc) rc = dalloc(h, &pt.tdisp, (size_t)M * kMaxNbr);
+        if (!rc) rc = dalloc(h, &pt.tmask, (size_t)M);
+        if (!rc) rc = dalloc(h, &pt.twall, 2 * (size_t)M);
+    }
     pt.corr = p.momentum_correction;
     if (!rc) rc = dalloc(h, &pt.frame[0], (size_t)M);
     if (!rc) rc = dalloc(h, &pt.frame[1], (size_t)M);
@@ -349,7 +371,9 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
         h->dem_blocks = per_sm * sms;
         h->sms = sms;
         if (!rc && h->dem_blocks < 1) rc = LBM_ERR_CUDA;
-        h->dem_cluster = M > 0 ? dem_cluster_setup(M) : 0;
+        h->dem_cluster = M > 0 ? dem_cluster_setup(M, false, h->pt.fric != 0) : 0;
+        // the tangential contact state lives in the cluster kernel only
+        if (!rc && M > 0 && h->pt.fric && h->dem_cluster == 0) rc = LBM_ERR_UNSUPPORTED;
     }
     if (!rc) {
         *h->status_host = 0;
@@ -435,9 +459,14 @@ int lbm_set_particles(lbm_handle h, int32_t n, const double *pos, const double *
         else if (cudaMemsetAsync((void *)pt.fixed, 0, (size_t)n, h->stream) != cudaSuccess)
             rc = LBM_ERR_CUDA;
     }
-    double *zero[] = {pt.Fh, pt.Th, pt.Fc, pt.Fx, pt.Tx, pt.Fcorr, pt.Tcorr};
+    double *zero[] = {pt.Fh, pt.Th, pt.Fc, pt.Fx, pt.Tx, pt.Fcorr, pt.Tcorr, pt.Tc};
     for (double *z : zero)
         if (!rc && n && cudaMemsetAsync(z, 0, v3, h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+    if (!rc && n && pt.fric &&
+        (cudaMemsetAsync(pt.tmask, 0, sizeof(unsigned long long) * (size_t)n, h->stream) != cudaSuccess ||
+         cudaMemsetAsync(pt.tdisp, 0, sizeof(float4) * (size_t)n * kMaxNbr, h->stream) != cudaSuccess ||
+         cudaMemsetAsync(pt.twall, 0, sizeof(float4) * 2 * (size_t)n, h->stream) != cudaSuccess))
+        rc = LBM_ERR_CUDA;
     if (!rc && cudaMemsetAsync(h->f, 0, (size_t)Q * h->L.S * h->esize, h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
     if (!rc && cudaMemsetAsync(h->flag, 0, (size_t)h->L.N, h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
     if (!rc && cudaMemsetAsync(h->owner, 0xff, (size_t)h->L.N * 4, h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
@@ -1027,9 +1056,10 @@ int lbm_batch_create(const lbm_params *params, int32_t count, lbm_batch *out) {
         }
     }
     if (!rc && max_m > 0) {
-        b->dem_cluster = dem_cluster_setup(max_m, true);
+        for (int i = 0; i < count; ++i) b->fric = b->fric || b->m[i]->pt.fric != 0;
+        b->dem_cluster = dem_cluster_setup(max_m, true, b->fric);
         if (b->dem_cluster == 0) rc = LBM_ERR_UNSUPPORTED;  // the batched DEM needs one cluster per instance
-        if (!rc) rc = dem_cluster_setup_batch(b->dem_cluster);
+        if (!rc) rc = dem_cluster_setup_batch(b->dem_cluster, b->fric);
         if (!rc) rc = links_setup_batch(b->ext, b->cap);
     }
     if (!rc && cudaMalloc((void **)&b->dinst, sizeof(Inst) * (size_t)count) != cudaSuccess) {

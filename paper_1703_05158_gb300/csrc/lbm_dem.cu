@@ -27,6 +27,19 @@
 // More spheres than one cluster holds fall back to a cooperative launch with
 // a bounded software grid barrier.
 //
+// Tangential contact law (Eqs. 2, 3; on when k_t > 0 and mu > 0, the
+// template argument FRIC of the cluster kernel): the readings of the oracle
+// (contact point at the middle of the overlap, v^r = v_a - v_b - ((R_a -
+// delta/2) Om_a + (R_b - delta/2) Om_b) x n, f_t = -k_t delta_t - gamma_t v_t
+// capped at mu max(f^n, 0) along -v_t with delta_t reset to -f_t / k_t,
+// delta_t turned into the tangent plane and advanced by v_t h every
+// sub-step, reset when the contact opens; walls move with their lattice
+// velocity).  Each list entry keeps its delta_t (FP32) in tdisp, valid when
+// its bit of the sphere's tmask is set; a list rebuild carries the state of
+// the pairs that stay listed.  The spin then takes half kicks with the
+// contact torque like the velocity (dOm in FP32 per sub-step, published with
+// dx and dv).
+//
 // Neighbour lists (pairs within R_a + R_b + skin, FP32 search) are rebuilt
 // only when a sphere has moved more than skin/2 - max_step since the last
 // build; every sphere moving less than max_step per step (else the geometry
@@ -41,6 +54,8 @@ namespace lbm {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kDemKmax = 4;       // spheres per thread held in registers
+// with friction each sphere holds more state: fewer spheres per thread
+__host__ __device__ constexpr int dem_kmax(bool fric) { return fric ? 2 : kDemKmax; }
 constexpr int kDemThreads = 256;  // threads per CTA of the cluster kernel
 
 __device__ __forceinline__ double sphere_mass(const Parts &pt, int a) {
@@ -64,14 +79,30 @@ __device__ __forceinline__ void min_image(const Lat &L, double d[3]) {
 //   pairB = (V_a - V_b, gamma_n)
 constexpr int kNbrTile = 1024;
 
+constexpr int kMaxNbrFric = 64;  // list length the 64-bit contact mask covers
+
 __device__ __forceinline__ void neighbours_body(const Lat &L, const Parts &pt, const int sp, const int force,
                                                 int *__restrict__ status) {
     __shared__ float4 tile[kNbrTile];
+    __shared__ int oid[8][kMaxNbrFric];     // with friction: the old list of each warp's sphere
+    __shared__ float4 odisp[8][kMaxNbrFric];  // and the tangential displacement of its open contacts
     const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wid = (threadIdx.x >> 5) & 7;
     const bool live = a < pt.np;
     const bool rebuild = force || *(volatile int *)(pt.rebuild + sp) != 0;
     if (rebuild) {
+        int ocnt = 0;
+        unsigned long long omask = 0ull;
+        if (pt.fric && !force && live) {  // a forced rebuild starts every contact afresh
+            ocnt = min(pt.nbr_cnt[a], min(pt.max_nbr, kMaxNbrFric));
+            omask = pt.tmask[a];
+            for (int m = lane; m < ocnt; m += 32) {
+                const long long e = (long long)a * pt.max_nbr + m;
+                oid[wid][m] = pt.nbr[e];
+                odisp[wid][m] = (omask >> m) & 1ull ? pt.tdisp[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncwarp();
+        }
         float4 me = live ? pt.Xf[a] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float ra = me.w + (float)pt.skin;
         const float hx = 0.5f * L.nx, hy = 0.5f * L.ny;
@@ -110,6 +141,27 @@ __device__ __forceinline__ void neighbours_body(const Lat &L, const Parts &pt, c
         }
         if (live && lane < 3) pt.Xbuild[3 * a + lane] = pt.X[3 * a + lane];
         __syncwarp();
+        if (pt.fric && live) {  // the open contacts of pairs still listed keep their state
+            const int ncnt = min(cnt, min(pt.max_nbr, kMaxNbrFric));
+            unsigned long long nmask = 0ull;
+            for (int r = 0; r * 32 < ncnt; ++r) {
+                const int pos = r * 32 + lane;
+                bool hit = false;
+                if (pos < ncnt) {
+                    const long long e = (long long)a * pt.max_nbr + pos;
+                    const int b = pt.nbr[e];
+                    for (int m = 0; m < ocnt; ++m)
+                        if (oid[wid][m] == b) {
+                            hit = (omask >> m) & 1ull;
+                            if (hit) pt.tdisp[e] = odisp[wid][m];
+                            break;
+                        }
+                }
+                nmask |= (unsigned long long)__ballot_sync(0xffffffffu, hit) << (32 * r);
+            }
+            if (lane == 0) pt.tmask[a] = nmask;
+            __syncwarp();
+        }
     }
     if (!live) return;
     const int cnt = pt.nbr_cnt[a];
@@ -126,15 +178,45 @@ __device__ __forceinline__ void neighbours_body(const Lat &L, const Parts &pt, c
         pt.pairA[e] = make_float4((float)d[0], (float)d[1], (float)d[2], (float)c0);
         pt.pairB[e] = make_float4((float)(pt.V[3 * a] - pt.V[3 * b]), (float)(pt.V[3 * a + 1] - pt.V[3 * b + 1]),
                                   (float)(pt.V[3 * a + 2] - pt.V[3 * b + 2]), gam);
+        if (pt.fric)
+            pt.pairC[e] = make_float4((float)pt.W[3 * b], (float)pt.W[3 * b + 1], (float)pt.W[3 * b + 2],
+                                      (float)pt.ct * sqrtf((float)(meff * pt.kt)));
     }
 }
 
-// Contact force on sphere a at centre xa, velocity va, given the centres Xs
-// and velocities Vs of all spheres (FP64 throughout; used for the initial
-// contact force and by the cooperative fallback).
+// Tangential force of one contact (Eqs. 2, 3), FP64, delta_t = 0 (a contact
+// as it opens): the trial force -gamma_t v_t, capped at mu max(f^n, 0) along
+// -v_t.  Adds it to F and its moment (-l n) x f_t to T.
+__device__ void open_contact_friction(const Parts &pt, const double n[3], const double vr[3], double fn, double gt,
+                                      double l, double F[3], double T[3]) {
+    const double vrn = vr[0] * n[0] + vr[1] * n[1] + vr[2] * n[2];
+    double vt[3], ft[3], t2 = 0.0, v2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        vt[c] = vr[c] - vrn * n[c];
+        ft[c] = -gt * vt[c];
+        t2 += ft[c] * ft[c];
+        v2 += vt[c] * vt[c];
+    }
+    const double cap = pt.mu * (fn > 0.0 ? fn : 0.0);
+    if (t2 > cap * cap)  // t2 > 0 implies v_t != 0
+        for (int c = 0; c < 3; ++c) ft[c] = -cap * vt[c] / sqrt(v2);
+    for (int c = 0; c < 3; ++c) F[c] += ft[c];
+    T[0] += -l * (n[1] * ft[2] - n[2] * ft[1]);
+    T[1] += -l * (n[2] * ft[0] - n[0] * ft[2]);
+    T[2] += -l * (n[0] * ft[1] - n[1] * ft[0]);
+}
+
+// Contact force (and, with friction, torque) on sphere a at centre xa,
+// velocity va, spin wa, given the centres Xs, velocities Vs and spins Ws of
+// all spheres (FP64 throughout; used for the initial contact force, where
+// every contact is new, and by the cooperative fallback, which runs without
+// friction).
 __device__ void contact_force(const Lat &L, const Parts &pt, int a, const double xa[3], const double va[3],
-                              const double *Xs, const double *Vs, double F[3]) {
+                              const double *Xs, const double *Vs, double F[3], const double *wa = nullptr,
+                              const double *Ws = nullptr, double *T = nullptr) {
     F[0] = F[1] = F[2] = 0.0;
+    const bool fric = pt.fric && T;
+    if (fric) T[0] = T[1] = T[2] = 0.0;
     const double ma = sphere_mass(pt, a);
     const double Ra = pt.R[a];
     const float kn = (float)pt.kn, ce = (float)pt.ce;
@@ -159,6 +241,16 @@ __device__ void contact_force(const Lat &L, const Parts &pt, int a, const double
         F[0] += (double)(fn * nx);
         F[1] += (double)(fn * ny);
         F[2] += (double)(fn * nz);
+        if (fric) {
+            const double n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+            const double la = Ra - 0.5 * delta, lb = pt.R[b] - 0.5 * delta;
+            double S[3], vr[3];
+            for (int c = 0; c < 3; ++c) S[c] = la * wa[c] + lb * Ws[3 * b + c];
+            vr[0] = va[0] - Vs[3 * b] - (S[1] * n[2] - S[2] * n[1]);
+            vr[1] = va[1] - Vs[3 * b + 1] - (S[2] * n[0] - S[0] * n[2]);
+            vr[2] = va[2] - Vs[3 * b + 2] - (S[0] * n[1] - S[1] * n[0]);
+            open_contact_friction(pt, n, vr, (double)fn, pt.ct * sqrt(meff * pt.kt), la, F, T);
+        }
     }
     const float gw = ce * sqrtf((float)ma * kn);
     const float vz = (float)va[2];
@@ -166,14 +258,30 @@ __device__ void contact_force(const Lat &L, const Parts &pt, int a, const double
     if (lo > 0.0) F[2] += (double)(kn * (float)lo - gw * vz);
     const double hi = Ra - ((L.nz - 0.5) - xa[2]);
     if (hi > 0.0) F[2] -= (double)(kn * (float)hi + gw * vz);
+    for (int side = 0; side < 2 && fric; ++side) {
+        const double pen = side == 0 ? lo : hi;
+        if (!(pen > 0.0)) continue;
+        const double n[3] = {0.0, 0.0, side == 0 ? 1.0 : -1.0};
+        const float *uw = side == 0 ? pt.ulo : pt.uhi;
+        const double l = Ra - 0.5 * pen;
+        const double fn = side == 0 ? (double)(kn * (float)lo - gw * vz) : (double)(kn * (float)hi + gw * vz);
+        double vr[3];
+        vr[0] = va[0] - uw[0] - (l * wa[1] * n[2] - l * wa[2] * n[1]);
+        vr[1] = va[1] - uw[1] - (l * wa[2] * n[0] - l * wa[0] * n[2]);
+        vr[2] = va[2] - uw[2] - (l * wa[0] * n[1] - l * wa[1] * n[0]);
+        open_contact_friction(pt, n, vr, fn, pt.ct * sqrt(ma * pt.kt), l, F, T);
+    }
 }
 
 __global__ void k_contact(const Lat L, const Parts pt) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= pt.np) return;
-    double F[3];
-    contact_force(L, pt, a, pt.X + 3 * a, pt.V + 3 * a, pt.X, pt.V, F);
-    for (int c = 0; c < 3; ++c) pt.Fc[3 * a + c] = F[c];
+    double F[3], T[3] = {0.0, 0.0, 0.0};
+    contact_force(L, pt, a, pt.X + 3 * a, pt.V + 3 * a, pt.X, pt.V, F, pt.W + 3 * a, pt.W, T);
+    for (int c = 0; c < 3; ++c) {
+        pt.Fc[3 * a + c] = F[c];
+        pt.Tc[3 * a + c] = T[c];
+    }
 }
 
 __device__ __forceinline__ void wrap_pos(const Lat &L, double *x) {
@@ -230,27 +338,82 @@ __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
+// FP32 tangential force of a contact (Eqs. 2, 3) with displacement d (in /
+// out): d turned into the plane normal to n and advanced by v_t h; the trial
+// force -k_t d - gamma_t v_t, capped at mu max(f^n, 0) along -v_t (along the
+// trial force if v_t = 0) with d reset to -f_t / k_t.
+__device__ __forceinline__ float3 tangential_force(float3 &d, const float3 n, const float3 vt, const float fn,
+                                                   const float gt, const float kt, const float mu, const float h) {
+    const float dn = d.x * n.x + d.y * n.y + d.z * n.z;
+    d.x += vt.x * h - dn * n.x;
+    d.y += vt.y * h - dn * n.y;
+    d.z += vt.z * h - dn * n.z;
+    float3 f = make_float3(-kt * d.x - gt * vt.x, -kt * d.y - gt * vt.y, -kt * d.z - gt * vt.z);
+    const float t2 = f.x * f.x + f.y * f.y + f.z * f.z;
+    const float cap = mu * fmaxf(fn, 0.f);
+    if (t2 > cap * cap) {
+        const float v2 = vt.x * vt.x + vt.y * vt.y + vt.z * vt.z;
+        const float s = v2 > 0.f ? -cap * rsqrtf(v2) : cap * rsqrtf(t2);
+        const float3 u = v2 > 0.f ? vt : f;
+        f = make_float3(s * u.x, s * u.y, s * u.z);
+        const float ik = -1.f / kt;
+        d = make_float3(f.x * ik, f.y * ik, f.z * ik);
+    }
+    return f;
+}
+
+// Tangential force and its moment on a sphere at contact normal n (pointing
+// into the sphere), lever l, relative velocity vr of the contact point.
+__device__ __forceinline__ void friction_add(float3 &F, float3 &T, float3 &d, const float3 n, const float3 vr,
+                                             const float l, const float fn, const float gt, const float kt,
+                                             const float mu, const float h) {
+    const float vrn = vr.x * n.x + vr.y * n.y + vr.z * n.z;
+    const float3 vt = make_float3(vr.x - vrn * n.x, vr.y - vrn * n.y, vr.z - vrn * n.z);
+    const float3 f = tangential_force(d, n, vt, fn, gt, kt, mu, h);
+    F.x += f.x;
+    F.y += f.y;
+    F.z += f.z;
+    T.x -= l * (n.y * f.z - n.z * f.y);
+    T.y -= l * (n.z * f.x - n.x * f.z);
+    T.z -= l * (n.x * f.y - n.y * f.x);
+}
+
+__device__ __forceinline__ float3 cross3(const float3 a, const float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
 // All sub-steps of the lattice step of parity sp in one cluster (gridDim.x
-// CTAs).  Thread t of CTA c owns spheres a = c T + t + q G (q < kDemKmax,
+// CTAs).  Thread t of CTA c owns spheres a = c T + t + q G (q < K,
 // G = cluster threads).  The step's neighbour pass has read rebuild[sp], so
-// it is cleared here; the commits may set rebuild[sp ^ 1].
+// it is cleared here; the commits may set rebuild[sp ^ 1].  FRIC: with the
+// tangential contact law (each sphere also publishes its spin change).
+template <bool FRIC>
 __device__ __forceinline__ void dem_cluster_body(const Lat &L, const Parts &pt, SFrame *fnext, const int sp,
                                                  int *status) {
-    extern __shared__ float4 dsm[];  // [2][kDemKmax * T][2]: (dx, -), (dv, -)
+    constexpr int S = FRIC ? 3 : 2;  // float4 per sphere in the exchange buffer: dx, dv (, dOm)
+    constexpr int K = dem_kmax(FRIC);
+    extern __shared__ float4 dsm[];  // [2][K * T][S]
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
-    const int T = blockDim.x, G = gridDim.x * T, cap = kDemKmax * T;
+    const int T = blockDim.x, G = gridDim.x * T, cap = K * T;
     const int g0 = blockIdx.x * T + threadIdx.x;
     if (g0 == 0) pt.rebuild[sp] = 0;
     const int ns = pt.substeps;
     const float h = 1.f / ns, h2 = 0.5f * h;
     const float kn = (float)pt.kn, ce = (float)pt.ce;
-    float3 dx[kDemKmax], dv[kDemKmax], v0[kDemKmax], fa[kDemKmax], fc[kDemKmax];
-    float im[kDemKmax], Rf[kDemKmax], Llo[kDemKmax], Lhi[kDemKmax], gw[kDemKmax];
-    int nc[kDemKmax];
-    bool fx[kDemKmax];
+    const float kt = (float)pt.kt, mu = (float)pt.mu;
+    float3 dx[K], dv[K], v0[K], fa[K], fc[K];
+    float im[K], Rf[K], Llo[K], Lhi[K], gw[K];
+    int nc[K];
+    bool fx[K];
+    // with friction: spin change, start spin, torque / I, contact torque, 1 / I,
+    // open-contact mask, wall displacements (w = 1: in contact), wall gamma_t
+    float3 dw[FRIC ? K : 1], w0[FRIC ? K : 1], ta[FRIC ? K : 1], tc[FRIC ? K : 1];
+    float iI[FRIC ? K : 1], gwt[FRIC ? K : 1];
+    unsigned long long msk[FRIC ? K : 1];
+    float4 wl[FRIC ? K : 1][2];
 #pragma unroll
-    for (int q = 0; q < kDemKmax; ++q) {
+    for (int q = 0; q < K; ++q) {
         const int a = g0 + q * G;
         if (a >= pt.np) break;
         const double m = sphere_mass(pt, a), R = pt.R[a], z0 = pt.X[3 * a + 2];
@@ -268,38 +431,60 @@ __device__ __forceinline__ void dem_cluster_body(const Lat &L, const Parts &pt, 
         nc[q] = pt.nbr_cnt[a];
         dx[q] = make_float3(0.f, 0.f, 0.f);
         dv[q] = make_float3(0.f, 0.f, 0.f);
+        if constexpr (FRIC) {
+            const double ii = 1.0 / (0.4 * m * R * R);
+            iI[q] = (float)ii;
+            w0[q] = make_float3((float)pt.W[3 * a], (float)pt.W[3 * a + 1], (float)pt.W[3 * a + 2]);
+            ta[q] = make_float3((float)((pt.Th[3 * a] + pt.Tx[3 * a]) * ii),
+                                (float)((pt.Th[3 * a + 1] + pt.Tx[3 * a + 1]) * ii),
+                                (float)((pt.Th[3 * a + 2] + pt.Tx[3 * a + 2]) * ii));
+            tc[q] = make_float3((float)pt.Tc[3 * a], (float)pt.Tc[3 * a + 1], (float)pt.Tc[3 * a + 2]);
+            dw[q] = make_float3(0.f, 0.f, 0.f);
+            msk[q] = pt.tmask[a];
+            wl[q][0] = pt.twall[2 * a];
+            wl[q][1] = pt.twall[2 * a + 1];
+            gwt[q] = (float)pt.ct * sqrtf((float)m * kt);
+        }
     }
     cluster_barrier();  // every CTA of the cluster is running before shared memory is shared
     for (int s = 0; s < ns; ++s) {
-        float4 *buf = dsm + (size_t)((s + 1) & 1) * cap * 2;
+        float4 *buf = dsm + (size_t)((s + 1) & 1) * cap * S;
 #pragma unroll
-        for (int q = 0; q < kDemKmax; ++q) {
+        for (int q = 0; q < K; ++q) {
             const int a = g0 + q * G;
             if (a >= pt.np) break;
             if (!fx[q]) {  // half kick
                 dv[q].x += (fa[q].x + fc[q].x * im[q]) * h2;
                 dv[q].y += (fa[q].y + fc[q].y * im[q]) * h2;
                 dv[q].z += (fa[q].z + fc[q].z * im[q]) * h2;
+                if constexpr (FRIC) {
+                    dw[q].x += (ta[q].x + tc[q].x * iI[q]) * h2;
+                    dw[q].y += (ta[q].y + tc[q].y * iI[q]) * h2;
+                    dw[q].z += (ta[q].z + tc[q].z * iI[q]) * h2;
+                }
             }
             dx[q].x += (v0[q].x + dv[q].x) * h;
             dx[q].y += (v0[q].y + dv[q].y) * h;
             dx[q].z += (v0[q].z + dv[q].z) * h;
-            float4 *me = buf + (size_t)(q * T + threadIdx.x) * 2;
+            float4 *me = buf + (size_t)(q * T + threadIdx.x) * S;
             me[0] = make_float4(dx[q].x, dx[q].y, dx[q].z, 0.f);
             me[1] = make_float4(dv[q].x, dv[q].y, dv[q].z, 0.f);
+            if constexpr (FRIC) me[2] = make_float4(dw[q].x, dw[q].y, dw[q].z, 0.f);
         }
         cluster_barrier();
 #pragma unroll
-        for (int q = 0; q < kDemKmax; ++q) {
+        for (int q = 0; q < K; ++q) {
             const int a = g0 + q * G;
             if (a >= pt.np) break;
             if (fx[q]) continue;
             float3 F = make_float3(0.f, 0.f, 0.f);
+            float3 Tq = make_float3(0.f, 0.f, 0.f);
             // neighbours in groups of kNbrGroup: every load of a group is
             // issued before any of its arithmetic; the sum keeps list order
             constexpr int kNbrGroup = 4;
             for (int m0 = 0; m0 < nc[q]; m0 += kNbrGroup) {
                 float4 A[kNbrGroup], Bv[kNbrGroup], ox[kNbrGroup], ov[kNbrGroup];
+                float4 C[FRIC ? kNbrGroup : 1], ow[FRIC ? kNbrGroup : 1];
                 float Rb[kNbrGroup];
 #pragma unroll
                 for (int u = 0; u < kNbrGroup; ++u) {
@@ -310,9 +495,13 @@ __device__ __forceinline__ void dem_cluster_body(const Lat &L, const Parts &pt, 
                     Bv[u] = __ldg(pt.pairB + e);
                     Rb[u] = __ldg(&pt.Xf[b].w);
                     const int qb = b / G, rb = b - qb * G, cb = rb / T, tb = rb - cb * T;
-                    const float4 *o = cluster.map_shared_rank(buf + (size_t)(qb * T + tb) * 2, cb);
+                    const float4 *o = cluster.map_shared_rank(buf + (size_t)(qb * T + tb) * S, cb);
                     ox[u] = o[0];
                     ov[u] = o[1];
+                    if constexpr (FRIC) {
+                        C[u] = __ldg(pt.pairC + e);
+                        ow[u] = o[2];
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < kNbrGroup; ++u) {
@@ -320,7 +509,10 @@ __device__ __forceinline__ void dem_cluster_body(const Lat &L, const Parts &pt, 
                     const float Dx = dx[q].x - ox[u].x, Dy = dx[q].y - ox[u].y, Dz = dx[q].z - ox[u].z;
                     const float c =
                         A[u].w - 2.f * (A[u].x * Dx + A[u].y * Dy + A[u].z * Dz) - (Dx * Dx + Dy * Dy + Dz * Dz);
-                    if (!(c > 0.f)) continue;
+                    if (!(c > 0.f)) {
+                        if constexpr (FRIC) msk[q] &= ~(1ull << (m0 + u));  // the contact opened
+                        continue;
+                    }
                     const float ex = A[u].x + Dx, ey = A[u].y + Dy, ez = A[u].z + Dz;
                     const float dist = sqrtf(ex * ex + ey * ey + ez * ez);
                     const float Rs = Rf[q] + Rb[u];
@@ -333,6 +525,27 @@ __device__ __forceinline__ void dem_cluster_body(const Lat &L, const Parts &pt, 
                     F.x += fn * nx;
                     F.y += fn * ny;
                     F.z += fn * nz;
+                    if constexpr (FRIC) {
+                        const int m = m0 + u;
+                        const long long e = (long long)a * pt.max_nbr + m;
+                        const float la = Rf[q] - 0.5f * delta, lb = Rb[u] - 0.5f * delta;
+                        const float3 n = make_float3(nx, ny, nz);
+                        const float3 Sw = make_float3(la * (w0[q].x + dw[q].x) + lb * (C[u].x + ow[u].x),
+                                                      la * (w0[q].y + dw[q].y) + lb * (C[u].y + ow[u].y),
+                                                      la * (w0[q].z + dw[q].z) + lb * (C[u].z + ow[u].z));
+                        const float3 Sn = cross3(Sw, n);
+                        const float3 vr = make_float3(Bv[u].x + dv[q].x - ov[u].x - Sn.x,
+                                                      Bv[u].y + dv[q].y - ov[u].y - Sn.y,
+                                                      Bv[u].z + dv[q].z - ov[u].z - Sn.z);
+                        float3 d = make_float3(0.f, 0.f, 0.f);
+                        if ((msk[q] >> m) & 1ull) {
+                            const float4 t = pt.tdisp[e];
+                            d = make_float3(t.x, t.y, t.z);
+                        }
+                        friction_add(F, Tq, d, n, vr, la, fn, C[u].w, kt, mu, h);
+                        pt.tdisp[e] = make_float4(d.x, d.y, d.z, 0.f);
+                        msk[q] |= 1ull << m;
+                    }
                 }
             }
             const float vz = v0[q].z + dv[q].z;
@@ -340,6 +553,33 @@ __device__ __forceinline__ void dem_cluster_body(const Lat &L, const Parts &pt, 
             if (lo > 0.f) F.z += kn * lo - gw[q] * vz;
             const float hi = Lhi[q] + dx[q].z;
             if (hi > 0.f) F.z -= kn * hi + gw[q] * vz;
+            if constexpr (FRIC) {
+                const float3 w = make_float3(w0[q].x + dw[q].x, w0[q].y + dw[q].y, w0[q].z + dw[q].z);
+                const float3 v = make_float3(v0[q].x + dv[q].x, v0[q].y + dv[q].y, vz);
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const float pen = side == 0 ? lo : hi;
+                    if (!(pen > 0.f)) {
+                        wl[q][side] = make_float4(0.f, 0.f, 0.f, 0.f);  // the contact opened
+                        continue;
+                    }
+                    const float sg = side == 0 ? 1.f : -1.f;
+                    const float3 n = make_float3(0.f, 0.f, sg);
+                    const float *uw = side == 0 ? pt.ulo : pt.uhi;
+                    const float l = Rf[q] - 0.5f * pen;
+                    const float3 Sn = cross3(make_float3(l * w.x, l * w.y, l * w.z), n);
+                    const float3 vr = make_float3(v.x - uw[0] - Sn.x, v.y - uw[1] - Sn.y, v.z - uw[2] - Sn.z);
+                    const float fn = side == 0 ? kn * lo - gw[q] * vz : kn * hi + gw[q] * vz;
+                    float3 d = wl[q][side].w != 0.f ? make_float3(wl[q][side].x, wl[q][side].y, wl[q][side].z)
+                                                    : make_float3(0.f, 0.f, 0.f);
+                    friction_add(F, Tq, d, n, vr, l, fn, gwt[q], kt, mu, h);
+                    wl[q][side] = make_float4(d.x, d.y, d.z, 1.f);
+                }
+                tc[q] = Tq;
+                dw[q].x += (ta[q].x + Tq.x * iI[q]) * h2;
+                dw[q].y += (ta[q].y + Tq.y * iI[q]) * h2;
+                dw[q].z += (ta[q].z + Tq.z * iI[q]) * h2;
+            }
             fc[q] = F;
             dv[q].x += (fa[q].x + F.x * im[q]) * h2;
             dv[q].y += (fa[q].y + F.y * im[q]) * h2;
@@ -348,7 +588,7 @@ __device__ __forceinline__ void dem_cluster_body(const Lat &L, const Parts &pt, 
     }
     cluster_barrier();  // no CTA leaves while another may still read its shared memory
 #pragma unroll
-    for (int q = 0; q < kDemKmax; ++q) {
+    for (int q = 0; q < K; ++q) {
         const int a = g0 + q * G;
         if (a >= pt.np) break;
         double x[3] = {pt.X[3 * a] + (double)dx[q].x, pt.X[3 * a + 1] + (double)dx[q].y, pt.X[3 * a + 2] + (double)dx[q].z};
@@ -361,7 +601,21 @@ __device__ __forceinline__ void dem_cluster_body(const Lat &L, const Parts &pt, 
             v[0] += (double)dv[q].x;
             v[1] += (double)dv[q].y;
             v[2] += (double)dv[q].z;
-            for (int c = 0; c < 3; ++c) w[c] += (pt.Th[3 * a + c] + pt.Tx[3 * a + c]) * iI;
+            if constexpr (FRIC) {
+                w[0] += (double)dw[q].x;
+                w[1] += (double)dw[q].y;
+                w[2] += (double)dw[q].z;
+            } else {
+                for (int c = 0; c < 3; ++c) w[c] += (pt.Th[3 * a + c] + pt.Tx[3 * a + c]) * iI;
+            }
+        }
+        if constexpr (FRIC) {
+            pt.Tc[3 * a] = (double)tc[q].x;
+            pt.Tc[3 * a + 1] = (double)tc[q].y;
+            pt.Tc[3 * a + 2] = (double)tc[q].z;
+            pt.tmask[a] = msk[q];
+            pt.twall[2 * a] = wl[q][0];
+            pt.twall[2 * a + 1] = wl[q][1];
         }
         const double f3[3] = {(double)fc[q].x, (double)fc[q].y, (double)fc[q].z};
         const double moved2 = (double)(dx[q].x * dx[q].x + dx[q].y * dx[q].y + dx[q].z * dx[q].z);
@@ -374,9 +628,10 @@ __global__ void __launch_bounds__(256) k_neighbours(const Lat L, const Parts pt,
     neighbours_body(L, pt, sp, force, status);
 }
 
+template <bool FRIC>
 __global__ void __launch_bounds__(kDemThreads, 1) k_dem_cluster(const Lat L, const Parts pt, SFrame *fnext,
                                                                 const int sp, int *status) {
-    dem_cluster_body(L, pt, fnext, sp, status);
+    dem_cluster_body<FRIC>(L, pt, fnext, sp, status);
 }
 
 // Batched forms: instance blockIdx.y.
@@ -386,13 +641,19 @@ __global__ void __launch_bounds__(256) k_neighbours_b(const Inst *__restrict__ I
     neighbours_body(a.L, a.pt, sp, 0, a.status);
 }
 
+// FRIC = true when a member has friction; the clusters of members without
+// it run the frictionless body.
+template <bool FRIC>
 __global__ void __launch_bounds__(kDemThreads, 1) k_dem_cluster_b(const Inst *__restrict__ I, const int sp) {
     const Inst &a = I[blockIdx.y];
     if (a.pt.np == 0) return;  // the whole cluster (one instance) leaves together
-    dem_cluster_body(a.L, a.pt, a.pt.frame[sp ^ 1], sp, a.status);
+    if (FRIC && !a.pt.fric) dem_cluster_body<false>(a.L, a.pt, a.pt.frame[sp ^ 1], sp, a.status);
+    else dem_cluster_body<FRIC>(a.L, a.pt, a.pt.frame[sp ^ 1], sp, a.status);
 }
 
-static size_t dem_cluster_smem() { return (size_t)2 * kDemKmax * kDemThreads * 2 * sizeof(float4); }
+static size_t dem_cluster_smem(bool fric) {
+    return (size_t)2 * dem_kmax(fric) * kDemThreads * (fric ? 3 : 2) * sizeof(float4);
+}
 
 // ---- fallback: cooperative grid with a bounded software barrier ------------
 
@@ -504,27 +765,30 @@ int dem_max_blocks(int threads, int *blocks_per_sm) {
                                                                                                          : LBM_ERR_CUDA;
 }
 
+template <typename K>
+static bool cluster_attrs(K kernel, bool fric, int cl) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dem_cluster_smem(fric)) !=
+            cudaSuccess ||
+        (cl > 8 && cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 // Largest cluster (16, else 8) that can run k_dem_cluster; 0 if none, or if
 // max_particles does not fit its registers.
-int dem_cluster_setup(int max_particles, bool small) {
-    if (cudaFuncSetAttribute(k_dem_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dem_cluster_smem()) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
+int dem_cluster_setup(int max_particles, bool small, bool fric) {
     // one simulation: the widest cluster (16 or 8 CTAs: measured equal at
     // 2000 spheres, narrower ones slower); a batch: the narrowest cluster
     // that gives every sphere its own thread, so that the members' clusters
     // run side by side
     const std::vector<int> sizes = small ? std::vector<int>{1, 2, 4, 8, 16} : std::vector<int>{16, 8};
     for (int cl : sizes) {
-        if ((long long)cl * kDemThreads * kDemKmax < max_particles) continue;
+        if ((long long)cl * kDemThreads * dem_kmax(fric) < max_particles) continue;
         if (small && (long long)cl * kDemThreads < max_particles && cl < 16) continue;
-        if (cl > 8 && cudaFuncSetAttribute(k_dem_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                          cudaSuccess) {
-            cudaGetLastError();
+        if (!(fric ? cluster_attrs(k_dem_cluster<true>, true, cl) : cluster_attrs(k_dem_cluster<false>, false, cl)))
             continue;
-        }
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -533,25 +797,21 @@ int dem_cluster_setup(int max_particles, bool small) {
         attr[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(cl);
         cfg.blockDim = dim3(kDemThreads);
-        cfg.dynamicSmemBytes = dem_cluster_smem();
+        cfg.dynamicSmemBytes = dem_cluster_smem(fric);
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, k_dem_cluster, &cfg) == cudaSuccess && n >= 1) return cl;
+        const cudaError_t e = fric ? cudaOccupancyMaxActiveClusters(&n, k_dem_cluster<true>, &cfg)
+                                   : cudaOccupancyMaxActiveClusters(&n, k_dem_cluster<false>, &cfg);
+        if (e == cudaSuccess && n >= 1) return cl;
         cudaGetLastError();
     }
     return 0;
 }
 
-int dem_cluster_setup_batch(int cl) {
-    if (cudaFuncSetAttribute(k_dem_cluster_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dem_cluster_smem()) !=
-            cudaSuccess ||
-        (cl > 8 && cudaFuncSetAttribute(k_dem_cluster_b, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                       cudaSuccess)) {
-        cudaGetLastError();
-        return LBM_ERR_CUDA;
-    }
-    return LBM_OK;
+int dem_cluster_setup_batch(int cl, bool fric) {
+    const bool ok = fric ? cluster_attrs(k_dem_cluster_b<true>, true, cl) : cluster_attrs(k_dem_cluster_b<false>, false, cl);
+    return ok ? LBM_OK : LBM_ERR_CUDA;
 }
 
 int launch_neighbours_batch(const lbm_batch_s *b, int sp) {
@@ -572,12 +832,14 @@ int launch_dem_batch(const lbm_batch_s *b, int sp) {
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(b->dem_cluster, b->n);
     cfg.blockDim = dim3(kDemThreads);
-    cfg.dynamicSmemBytes = dem_cluster_smem();
+    cfg.dynamicSmemBytes = dem_cluster_smem(b->fric);
     cfg.stream = b->stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const Inst *I = b->dinst;
-    return cudaLaunchKernelEx(&cfg, k_dem_cluster_b, I, sp) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+    const cudaError_t e = b->fric ? cudaLaunchKernelEx(&cfg, k_dem_cluster_b<true>, I, sp)
+                                  : cudaLaunchKernelEx(&cfg, k_dem_cluster_b<false>, I, sp);
+    return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
 int launch_dem(lbm_s *h) {
@@ -595,13 +857,16 @@ int launch_dem(lbm_s *h) {
         attr[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(h->dem_cluster);
         cfg.blockDim = dim3(kDemThreads);
-        cfg.dynamicSmemBytes = dem_cluster_smem();
+        const bool fric = pt.fric != 0;
+        cfg.dynamicSmemBytes = dem_cluster_smem(fric);
         cfg.stream = h->stream;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, k_dem_cluster, L, pt, fnext, sp, status) == cudaSuccess ? LBM_OK
-                                                                                                 : LBM_ERR_CUDA;
+        const cudaError_t e = fric ? cudaLaunchKernelEx(&cfg, k_dem_cluster<true>, L, pt, fnext, sp, status)
+                                   : cudaLaunchKernelEx(&cfg, k_dem_cluster<false>, L, pt, fnext, sp, status);
+        return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
     }
+    if (pt.fric) return LBM_ERR_UNSUPPORTED;  // the tangential state lives in the cluster kernel only
     if (cudaMemsetAsync(h->bar, 0, sizeof(unsigned), h->stream) != cudaSuccess) return LBM_ERR_CUDA;
     int blocks = (h->pt.np + h->dem_threads - 1) / h->dem_threads;
     if (blocks > h->dem_blocks) blocks = h->dem_blocks;

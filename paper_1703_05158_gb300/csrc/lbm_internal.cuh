@@ -190,6 +190,15 @@ struct Parts {
     double max_step;               // largest displacement allowed in one step
     int corr;                      // 1: covered / uncovered nodes exchange momentum with the sphere
     double *Fcorr, *Tcorr;         // that exchange in the current step (marks write, refill adds)
+    // tangential contact law (Eqs. 2, 3), on when fric != 0
+    int fric;
+    double kt, mu, ct;             // ct = -2 ln e_t / sqrt(pi^2 + ln^2 e_t) (0 for e_t = 1)
+    double *Tc;                    // contact torque at the current position [np][3]
+    float4 *pairC;                 // per list entry: (spin of b at the start of the step, gamma_t)
+    float4 *tdisp;                 // per list entry: tangential displacement of the contact (xyz)
+    unsigned long long *tmask;     // per sphere: bit m set = list entry m was in contact
+    float4 *twall;                 // [np][2]: tangential displacement against the lower / upper wall
+    float ulo[3], uhi[3];          // wall velocities
 };
 
 // Makes device d current for the lifetime of the object, then restores the
@@ -303,6 +312,7 @@ struct lbm_batch_s {
     int max_np = 0;               // largest sphere count of a member
     int ext = 0, cap = 0;         // link tile half width and list capacity (largest over members)
     int dem_cluster = 0;          // CTAs per instance cluster of the DEM kernel
+    bool fric = false;            // a member has tangential friction: the DEM kernel that keeps its state
     int precision = 0, device = 0, sms = 0;
     bool dirty = true;            // descriptors / graphs to be rebuilt
     cudaStream_t stream = nullptr;
@@ -331,7 +341,7 @@ int launch_fields(lbm_s *h, float *rho, float *u, int parity);
 int launch_owner(lbm_s *h, int32_t *owner);
 int launch_count_fluid(lbm_s *h);
 int dem_max_blocks(int threads, int *blocks_per_sm);
-int dem_cluster_setup(int max_particles, bool small = false);
+int dem_cluster_setup(int max_particles, bool small = false, bool fric = false);
 int link_capacity(double max_radius);
 size_t link_smem(int ext, int cap);
 int links_setup(int ext, int cap);
@@ -345,5 +355,5 @@ int launch_links_batch(const lbm_batch_s *b, int P);
 int links_setup_batch(int ext, int cap);
 int launch_neighbours_batch(const lbm_batch_s *b, int sp);
 int launch_dem_batch(const lbm_batch_s *b, int sp);
-int dem_cluster_setup_batch(int cl);
+int dem_cluster_setup_batch(int cl, bool fric);
 }  // namespace lbm

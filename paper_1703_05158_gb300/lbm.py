@@ -55,6 +55,7 @@ class lbm_params(ctypes.Structure):
         ("max_radius", ctypes.c_double),
         ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int32), ("schedule", ctypes.c_int32),
         ("momentum_correction", ctypes.c_int32),
+        ("kt", ctypes.c_double), ("mu", ctypes.c_double), ("restitution_t", ctypes.c_double),
     ]
 
 
@@ -302,7 +303,8 @@ def lbm_batch_sync(b):
 
 def make_params(nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0), u_hi=(0.0, 0.0, 0.0),
                 rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16, precision="fp32", max_particles=0,
-                max_radius=4.0, stream=None, device=0, schedule="serial", momentum_correction=False):
+                max_radius=4.0, stream=None, device=0, schedule="serial", momentum_correction=False, kt=0.0,
+                mu=0.0, restitution_t=1.0):
     """lbm_params from keyword arguments (the Lattice constructor's)."""
     p = lbm_params()
     p.nx, p.ny, p.nz, p.periodic_z = nx, ny, nz, 0
@@ -318,6 +320,7 @@ def make_params(nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0
     p.device = device
     p.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
     p.momentum_correction = int(bool(momentum_correction))
+    p.kt, p.mu, p.restitution_t = kt, mu, restitution_t
     return p
 
 
@@ -332,9 +335,11 @@ class Lattice:
 
     def __init__(self, nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0), u_hi=(0.0, 0.0, 0.0),
                  rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16, precision="fp32", max_particles=0,
-                 max_radius=4.0, stream=None, device=0, schedule="serial", momentum_correction=False):
+                 max_radius=4.0, stream=None, device=0, schedule="serial", momentum_correction=False, kt=0.0,
+                 mu=0.0, restitution_t=1.0):
         p = make_params(nx, ny, nz, tau0, cs, g, u_lo, u_hi, rho_s, kn, restitution, dem_substeps, precision,
-                        max_particles, max_radius, stream, device, schedule, momentum_correction)
+                        max_particles, max_radius, stream, device, schedule, momentum_correction, kt, mu,
+                        restitution_t)
         self.params = p
         self.h = lbm_create(p)
         self.shape = (nz, ny, nx)
