@@ -26,14 +26,27 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS & % HBM roofline at 256^3 + 2000 spheres; FP32 vs BF16-storage vs FP64 err"
 BOX = (256, 256, 256)
 NSPH = 2000
-NSPH_RUN = [NSPH]
 PHYS = dict(tau0=0.51, cs=0.17, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0), u_hi=(0.05, 0.0, 0.0), rho_s=2.5,
             kn=1e3, restitution=0.8, dem_substeps=16)
 BYTES = {"fp32": 4, "bf16": 2, "fp16": 2}
 
 
-def workload_name(prec):
-    return "slurry box %d^3, %d spheres R=4, sliding lid 0.05, tau0=0.51, Cs=0.17, %s storage" % (BOX[0], NSPH, prec)
+def workload_name(prec, nsph=None, dense=False):
+    name = "slurry box %d^3, %d spheres R=4, sliding lid 0.05, tau0=0.51, Cs=0.17, %s storage" % (
+        BOX[0], NSPH if nsph is None else nsph, prec)
+    if dense:
+        name += ", solid fraction 0.13 (phi-matched count), tangential friction"
+    return name
+
+
+def workload_spheres(args):
+    """Spheres of the timed workload: the 2000-sphere box, or with
+    --workload dense the same box at the solid fraction 0.13 it names."""
+    from paper_1703_05158_gb300 import inputs
+
+    if getattr(args, "workload", "slurry") == "dense":
+        return inputs.phi_matched_slurry(box=BOX)
+    return oracle_sample(BOX, NSPH)
 
 
 def peaks():
@@ -176,8 +189,9 @@ def whole_job_mlups(updates_per_rank, world, seconds):
 
 
 def friction_params(args):
-    """Tangential contact law of the --friction runs (none by default)."""
-    if not getattr(args, "friction", False):
+    """Tangential contact law of the --friction and --workload dense runs
+    (none by default)."""
+    if not (getattr(args, "friction", False) or getattr(args, "workload", "slurry") == "dense"):
         return {}
     return dict(kt=0.5 * PHYS["kn"], mu=0.3, restitution_t=0.6)
 
@@ -223,8 +237,10 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = local_rank
     stream = torch.cuda.Stream(device=dev)
-    p = oracle_sample(BOX, NSPH)
-    lat = lbm.Lattice(*BOX, precision=args.precision, max_particles=NSPH, max_radius=4.0,
+    p = workload_spheres(args)
+    nsph = len(p["R"])
+    dense = args.workload == "dense"
+    lat = lbm.Lattice(*BOX, precision=args.precision, max_particles=nsph, max_radius=4.0,
                       stream=ctypes_stream(stream), device=dev, schedule=args.schedule,
                       momentum_correction=args.momentum_correction, **PHYS, **friction_params(args))
     lat.set_particles(p["X"], V=p["V"], Om=p["Om"], R=p["R"])
@@ -260,7 +276,7 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the public API with host buffers: every step uploads
     # the external load (force, torque) from pinned host memory, steps, and
     # reads the hydrodynamic force, torque and the centres back
-    n = NSPH
+    n = nsph
     hF = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
     hT = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
     oF = torch.empty((n, 3), dtype=torch.float64).pin_memory()
@@ -295,7 +311,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(args.precision), "box": list(BOX), "spheres": NSPH,
+        "config": {"workload": workload_name(args.precision, nsph, dense), "box": list(BOX), "spheres": nsph,
                    "radius": 4.0, "solid_fraction": round(float(np.sum(4 / 3 * np.pi * p["R"] ** 3)) / N, 4),
                    "storage": args.precision, "schedule": args.schedule, "fluid_nodes": nf, "links": info["links"],
                    "momentum_correction": args.momentum_correction, "friction": friction_params(args) or None,
@@ -314,9 +330,9 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": int((oF.numel() + oT.numel() + oX.numel()) * 8)},
         # per step with spheres: overlapped = far collide, near marks, near list, marks, refill,
         # near collide, links, neighbours, DEM; serial = marks, refill, collide, links, neighbours, DEM
-        "gpu_launches": args.steps * ((9 if args.schedule == "overlap" else 6) if NSPH_RUN[0] else 1),
+        "gpu_launches": args.steps * ((9 if args.schedule == "overlap" else 6) if nsph else 1),
     }
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and not dense:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
     lat.close()
@@ -474,8 +490,9 @@ def main():
                     help="tangential contact law (Eqs. 2, 3) with k_t = k_n / 2, mu = 0.3, e_t = 0.6 (slurry workload)")
     ap.add_argument("--momentum-correction", action="store_true",
                     help="covered / uncovered nodes exchange their momentum with the spheres (slurry workload)")
-    ap.add_argument("--workload", choices=["slurry", "batched", "adjoint"], default="slurry",
-                    help="slurry: the 256^3 box with 2000 spheres; batched: the parameter-sweep batch; "
+    ap.add_argument("--workload", choices=["slurry", "dense", "batched", "adjoint"], default="slurry",
+                    help="slurry: the 256^3 box with 2000 spheres; dense: the same box at solid fraction 0.13 "
+                         "(8136 spheres) with tangential friction; batched: the parameter-sweep batch; "
                          "adjoint: gradient evaluations of the differentiation form")
     ap.add_argument("--batch", type=int, default=64, help="instances of the batched workload")
     ap.add_argument("--box", type=int, default=256,
@@ -485,7 +502,6 @@ def main():
         global BOX, NSPH
         BOX = (args.box,) * 3
         NSPH = int(round(2000 * (args.box / 256.0) ** 3))
-        NSPH_RUN[0] = NSPH
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank = int(os.environ.get("RANK", "0"))

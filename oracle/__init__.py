@@ -64,6 +64,8 @@ def _load():
         lib.orc_forces.argtypes = [vp, dp, dp]
         lib.orc_contact_forces.argtypes = [vp, dp]
         lib.orc_contact_torques.argtypes = [vp, dp]
+        lib.orc_contact_overflow.restype = ctypes.c_int
+        lib.orc_contact_overflow.argtypes = [vp]
         lib.orc_particles.argtypes = [vp, dp, dp, dp]
         lib.orc_fields.argtypes = [vp, dp, dp]
         lib.orc_tau_eff.argtypes = [vp, dp]
@@ -161,6 +163,8 @@ class Oracle:
 
     def step(self, n=1):
         self.lib.orc_step(self._h, int(n))
+        if self.lib.orc_contact_overflow(self._h):
+            raise RuntimeError("a sphere had more open contacts than the oracle keeps (64)")
 
     def forces(self):
         F, T = np.empty((self.np, 3)), np.empty((self.np, 3))

@@ -82,6 +82,12 @@ typedef struct {
     double restitution_t;   /* tangential restitution, sets gamma_t (Eq. 2); 1: no tangential damping */
 } orc_params;
 
+#define CT_MAX 64
+struct orc_contact {
+    int id;
+    double d[3];
+};
+
 typedef struct {
     orc_params p;
     long N;                 /* nx*ny*nz */
@@ -98,8 +104,10 @@ typedef struct {
     double *Fh, *Th;        /* hydrodynamic force and torque of the last step */
     double *Fc;             /* contact force at the current position (carried) */
     double *Tc;             /* contact (friction) torque at the current position (carried) */
-    double *dt_pair;        /* [np][np][3] tangential displacement delta_t of contact a-b, seen from a */
-    double *dt_wall;        /* [np][2][3] the same against the lower and the upper wall */
+    struct orc_contact *ct; /* [np][CT_MAX] open sphere contacts of a: partner and delta_t seen from a */
+    int *ct_n;              /* [np] number of open contacts */
+    int ct_overflow;        /* a sphere had more than CT_MAX contacts (its extra ones lose their state) */
+    double *dt_wall;        /* [np][2][3] delta_t against the lower and the upper wall */
     double *Fx, *Tx;        /* external force and torque held over every step */
     double *Fcorr, *Tcorr;  /* momentum of the nodes covered / uncovered this step (correction) */
     unsigned char *fixed;   /* 1: prescribed motion, X += V dt; V, Om constant */
@@ -596,9 +604,11 @@ static void contact_forces(orc_state *s, const double *X, const double *v, const
     for (int a = 0; a < s->np; ++a) {
         double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
         double ma = sphere_mass(s, a);
+        struct orc_contact next[CT_MAX]; /* the contacts of a still open after this evaluation */
+        int nnext = 0;
         for (int b = 0; b < s->np; ++b) {
             if (b == a) continue;
-            double *st = fric ? s->dt_pair + 3 * ((long)a * s->np + b) : NULL;
+            double stv[3] = {0.0, 0.0, 0.0}, *st = stv;
             double d[3] = {X[3 * a] - X[3 * b], X[3 * a + 1] - X[3 * b + 1], X[3 * a + 2] - X[3 * b + 2]};
             if (d[0] > 0.5 * P->nx) d[0] -= P->nx;
             if (d[0] < -0.5 * P->nx) d[0] += P->nx;
@@ -608,10 +618,7 @@ static void contact_forces(orc_state *s, const double *X, const double *v, const
             if (P->periodic_z && d[2] < -0.5 * P->nz) d[2] += P->nz;
             double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
             double delta = s->R[a] + s->R[b] - dist;
-            if (!(delta > 0.0) || dist == 0.0) {
-                if (fric && h > 0.0) st[0] = st[1] = st[2] = 0.0;
-                continue;
-            }
+            if (!(delta > 0.0) || dist == 0.0) continue; /* an opened contact is not carried over */
             double nv[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
             double vn = (v[3 * a] - v[3 * b]) * nv[0] + (v[3 * a + 1] - v[3 * b + 1]) * nv[1] +
                         (v[3 * a + 2] - v[3 * b + 2]) * nv[2];
@@ -622,6 +629,12 @@ static void contact_forces(orc_state *s, const double *X, const double *v, const
             F[1] += fn * nv[1];
             F[2] += fn * nv[2];
             if (fric) {
+                const struct orc_contact *old = s->ct + (long)a * CT_MAX;
+                for (int k = 0; k < s->ct_n[a]; ++k)
+                    if (old[k].id == b) {
+                        for (int c = 0; c < 3; ++c) stv[c] = old[k].d[c];
+                        break;
+                    }
                 double la = s->R[a] - 0.5 * delta, lb = s->R[b] - 0.5 * delta;
                 double S[3], Sn[3], vt[3], ft[3], r[3], tq[3];
                 for (int c = 0; c < 3; ++c) S[c] = la * Om[3 * a + c] + lb * Om[3 * b + c];
@@ -639,7 +652,20 @@ static void contact_forces(orc_state *s, const double *X, const double *v, const
                 }
                 cross(r, ft, tq);
                 for (int c = 0; c < 3; ++c) T[c] += tq[c];
+                if (h > 0.0) {
+                    if (nnext < CT_MAX) {
+                        next[nnext].id = b;
+                        for (int c = 0; c < 3; ++c) next[nnext].d[c] = stv[c];
+                        ++nnext;
+                    } else {
+                        s->ct_overflow = 1;
+                    }
+                }
             }
+        }
+        if (fric && h > 0.0) {
+            memcpy(s->ct + (long)a * CT_MAX, next, sizeof(struct orc_contact) * (size_t)nnext);
+            s->ct_n[a] = nnext;
         }
         for (int side = 0; side < 2 && !P->periodic_z; ++side) {
             /* side 0: wall z = -1/2, normal +z into the sphere; side 1: z = nz - 1/2, normal -z */
@@ -766,7 +792,7 @@ void orc_destroy(orc_state *s) {
     if (!s) return;
     free(s->f); free(s->fc); free(s->fn); free(s->owner); free(s->owner_prev); free(s->key);
     free(s->X); free(s->V); free(s->Om); free(s->R); free(s->Fh); free(s->Th); free(s->Fc); free(s->fixed);
-    free(s->Fx); free(s->Tx); free(s->Fcorr); free(s->Tcorr); free(s->Tc); free(s->dt_pair); free(s->dt_wall);
+    free(s->Fx); free(s->Tx); free(s->Fcorr); free(s->Tcorr); free(s->Tc); free(s->ct); free(s->ct_n); free(s->dt_wall);
     free(s);
 }
 
@@ -774,14 +800,19 @@ void orc_destroy(orc_state *s) {
 int orc_set_particles(orc_state *s, int n, const double *X, const double *V, const double *Om,
                       const double *R, const unsigned char *fixed) {
     free(s->X); free(s->V); free(s->Om); free(s->R); free(s->Fh); free(s->Th); free(s->Fc); free(s->fixed);
-    free(s->Fx); free(s->Tx); free(s->Fcorr); free(s->Tcorr); free(s->Tc); free(s->dt_pair); free(s->dt_wall);
-    s->dt_pair = s->dt_wall = NULL;
+    free(s->Fx); free(s->Tx); free(s->Fcorr); free(s->Tcorr); free(s->Tc); free(s->ct); free(s->ct_n);
+    free(s->dt_wall);
+    s->ct = NULL;
+    s->ct_n = NULL;
+    s->dt_wall = NULL;
+    s->ct_overflow = 0;
     s->np = n;
     s->Tc = (double *)xcalloc(3 * (size_t)n, sizeof(double));
     if (friction_on(s)) {
-        s->dt_pair = (double *)xcalloc(3 * (size_t)n * n, sizeof(double));
+        s->ct = (struct orc_contact *)xcalloc((size_t)n * CT_MAX, sizeof(struct orc_contact));
+        s->ct_n = (int *)xcalloc((size_t)n, sizeof(int));
         s->dt_wall = (double *)xcalloc(6 * (size_t)n, sizeof(double));
-        if (n && (!s->dt_pair || !s->dt_wall)) return -1;
+        if (n && (!s->ct || !s->ct_n || !s->dt_wall)) return -1;
     }
     s->Fcorr = (double *)xcalloc(3 * (size_t)n, sizeof(double));
     s->Tcorr = (double *)xcalloc(3 * (size_t)n, sizeof(double));
@@ -865,6 +896,8 @@ void orc_forces(const orc_state *s, double *F, double *T) {
 void orc_contact_forces(const orc_state *s, double *Fc) { memcpy(Fc, s->Fc, sizeof(double) * 3 * s->np); }
 
 void orc_contact_torques(const orc_state *s, double *Tc) { memcpy(Tc, s->Tc, sizeof(double) * 3 * s->np); }
+
+int orc_contact_overflow(const orc_state *s) { return s->ct_overflow; }
 
 void orc_particles(const orc_state *s, double *X, double *V, double *Om) {
     memcpy(X, s->X, sizeof(double) * 3 * s->np);

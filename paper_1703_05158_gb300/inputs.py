@@ -113,6 +113,26 @@ def slurry_box(box=(256, 256, 256), n=2000, radius=4.0, seed=SEED_BASE + 2, vmax
     return dict(X=X, V=V, Om=np.zeros((n, 3)), R=R)
 
 
+def phi_matched_count(box, phi, radius):
+    """Sphere count that gives solid fraction phi in the box: round(phi V / v),
+    v the mean sphere volume (radius a scalar or a uniform (r_min, r_max))."""
+    if np.isscalar(radius):
+        r3 = float(radius) ** 3
+    else:
+        a, b = radius
+        r3 = (b ** 4 - a ** 4) / (4.0 * (b - a))
+    return int(round(phi * box[0] * box[1] * box[2] / (4.0 / 3.0 * np.pi * r3)))
+
+
+def phi_matched_slurry(box=(256, 256, 256), phi=0.13, radius=4.0, seed=SEED_BASE + 6, vmax=0.01):
+    """The production slurry box at the solid fraction it names (0.13: 8136
+    spheres of radius 4 instead of 2000), RSA placement, uniform velocities."""
+    n = phi_matched_count(box, phi, radius)
+    X, R = rsa_spheres(box, n, radius, seed)
+    V = uniform_vectors(n, -vmax, vmax, seed + 1)
+    return dict(X=X, V=V, Om=np.zeros((n, 3)), R=R)
+
+
 def polydisperse(box, n, r_range, seed, vmax=0.01):
     X, R = rsa_spheres(box, n, r_range, seed)
     V = uniform_vectors(n, -vmax, vmax, seed + 1)

@@ -145,3 +145,40 @@ def test_friction_parameters_are_checked():
     for bad in (dict(kt=-1.0), dict(mu=-0.1), dict(restitution_t=0.0), dict(restitution_t=1.5)):
         with pytest.raises(Exception):
             L.Lattice(32, 32, 16, tau0=0.6, max_particles=1, max_radius=4.0, **bad)
+
+
+def test_full_size_dense_slurry_with_friction_sampled():
+    """256^3 at the solid fraction 0.13 the production box names (8136
+    spheres of radius 4) with friction, the launch configuration of
+    bench.py --workload dense, two steps: geometry identical everywhere,
+    forces of every sphere, populations at 200k sampled nodes, motion."""
+    p = inputs.phi_matched_slurry()
+    n = len(p["R"])
+    assert abs(inputs.solid_fraction((256, 256, 256), p["R"]) - 0.13) < 1e-3
+    kw = dict(tau0=0.51, cs=0.17, u_hi=(0.05, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16,
+              kt=500.0, mu=0.3, restitution_t=0.6)
+    lat = lbm().Lattice(256, 256, 256, max_particles=n, max_radius=4.0, **kw)
+    orc = oracle.Oracle(256, 256, 256, **kw)
+    for o in (lat, orc):
+        place(o, p)
+    lat.step(2)
+    orc.step(2)
+    assert np.array_equal(lat.owner(), orc.owner())
+    Fg, _ = lat.forces()
+    Fo, _ = orc.forces()
+    # relative to max(|F_p|, median |F|): in a box this dense a few spheres
+    # feel loads that cancel to 1e-3 of the typical one, below the FP32
+    # level of their ~300 link terms (absolute errors stay ~1e-7 everywhere)
+    no = np.linalg.norm(Fo, axis=1)
+    assert (np.linalg.norm(Fg - Fo, axis=1) / np.maximum(no, np.median(no))).max() <= FORCE_TOL
+    fo = orc.populations().reshape(19, -1)
+    fg = lat.populations().reshape(19, -1)
+    fluid = (orc.owner() < 0).reshape(-1)
+    idx = np.flatnonzero(fluid)
+    idx = idx[inputs.rng(5).choice(len(idx), 200000, replace=False)]
+    assert (np.abs(fg[:, idx] - fo[:, idx]) / np.abs(fo[:, idx])).max() <= POP_TOL
+    m = 2.5 * 4.0 / 3.0 * np.pi * p["R"] ** 3
+    a = np.linalg.norm(Fo + orc.contact_forces(), axis=1) / m
+    (Xg, Vg, _), (Xo, Vo, _) = lat.particles(), orc.particles()
+    assert np.abs(Xg - Xo).max() < FORCE_TOL * a.max() * 2.0 + 1e-12
+    assert np.abs(Vg - Vo).max() < FORCE_TOL * a.max() * 2.0 + 1e-14

@@ -73,21 +73,29 @@ def test_sheared_box_with_spheres(precision):
         (np.linalg.norm(Fg - Fo, axis=1) / np.linalg.norm(Fo, axis=1)).max())))
 
 
-def test_full_precision_workload_against_the_fp32_path():
+@pytest.mark.parametrize("variant", ["4000_spheres", "phi_matched_friction"])
+def test_full_precision_workload_against_the_fp32_path(variant):
     """The precision workload at full size: a 512 x 256 x 256 channel with
     walls in z, body force 5e-6, Cs 0.17, tau0 0.51 and 4000 spheres with
-    radii uniform in [3, 6]; 100 steps in FP16 and BF16 storage against the
-    FP32 path on the same inputs (relative L2 velocity difference over nodes
-    fluid in both)."""
+    radii uniform in [3, 6] (solid fraction 0.051), or the count that gives
+    the solid fraction 0.10 it names (7911) with tangential friction; 100
+    steps in FP16 and BF16 storage against the FP32 path on the same inputs
+    (relative L2 velocity difference over nodes fluid in both)."""
     from paper_1703_05158_gb300 import lbm
 
     lbm.load()
     shape = (512, 256, 256)
-    parts = inputs.polydisperse(shape, 4000, (3.0, 6.0), seed=inputs.SEED_BASE + 3)
     kw = dict(tau0=0.51, cs=0.17, g=(5e-6, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16)
+    if variant == "4000_spheres":
+        n = 4000
+        parts = inputs.polydisperse(shape, n, (3.0, 6.0), seed=inputs.SEED_BASE + 3)
+    else:
+        n = inputs.phi_matched_count(shape, 0.10, (3.0, 6.0))
+        parts = inputs.polydisperse(shape, n, (3.0, 6.0), seed=inputs.SEED_BASE + 7)
+        kw.update(kt=500.0, mu=0.3, restitution_t=0.6)
     u, own = {}, {}
     for prec in ("fp32", "fp16", "bf16"):
-        lat = lbm.Lattice(*shape, precision=prec, max_particles=4000, max_radius=6.0, **kw)
+        lat = lbm.Lattice(*shape, precision=prec, max_particles=n, max_radius=6.0, **kw)
         lat.set_particles(parts["X"], V=parts["V"], R=parts["R"])
         lat.step(100)
         u[prec] = lat.fields()[1]
@@ -98,6 +106,6 @@ def test_full_precision_workload_against_the_fp32_path():
         fluid = (own[prec] < 0) & (own["fp32"] < 0)
         a, b = u[prec][:, fluid].astype(np.float64), u["fp32"][:, fluid].astype(np.float64)
         err[prec] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
-        print("%s vs fp32 at 512x256x256: relative velocity difference %.2e" % (prec, err[prec]))
+        print("%s vs fp32 at 512x256x256, %s: relative velocity difference %.2e" % (prec, variant, err[prec]))
     assert err["fp16"] <= VEL_TOL["fp16"]
     assert err["bf16"] <= VEL_TOL["bf16"]
