@@ -33,6 +33,8 @@ class OrcParams(ctypes.Structure):
         ("dem_substeps", ctypes.c_int), ("les", ctypes.c_int), ("fluid", ctypes.c_int),
         ("periodic_z", ctypes.c_int), ("momentum_correction", ctypes.c_int),
         ("kt", ctypes.c_double), ("mu", ctypes.c_double), ("restitution_t", ctypes.c_double),
+        ("zieb", ctypes.c_int), ("zieb_area", ctypes.c_double), ("zieb_volume", ctypes.c_double),
+        ("zieb_vp", ctypes.c_double),
     ]
 
 
@@ -66,6 +68,8 @@ def _load():
         lib.orc_contact_torques.argtypes = [vp, dp]
         lib.orc_contact_overflow.restype = ctypes.c_int
         lib.orc_contact_overflow.argtypes = [vp]
+        lib.orc_zieb_state.argtypes = [vp, dp]
+        lib.orc_zieb_set_piston.argtypes = [vp, ctypes.c_double]
         lib.orc_particles.argtypes = [vp, dp, dp, dp]
         lib.orc_fields.argtypes = [vp, dp, dp]
         lib.orc_tau_eff.argtypes = [vp, dp]
@@ -102,7 +106,7 @@ class Oracle:
     def __init__(self, nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0),
                  u_hi=(0.0, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16,
                  les=True, fluid=True, periodic_z=False, momentum_correction=False, kt=0.0, mu=0.0,
-                 restitution_t=1.0, threads=None):
+                 restitution_t=1.0, zieb=None, threads=None):
         if threads is not None:
             os.environ["OMP_NUM_THREADS"] = str(threads)
         lib = _load()
@@ -117,6 +121,8 @@ class Oracle:
         p.periodic_z = int(bool(periodic_z))
         p.momentum_correction = int(bool(momentum_correction))
         p.kt, p.mu, p.restitution_t = kt, mu, restitution_t
+        if zieb is not None:  # dict(area=A_p, volume=V_0, vp=v_p)
+            p.zieb, p.zieb_area, p.zieb_volume, p.zieb_vp = 1, zieb["area"], zieb["volume"], zieb.get("vp", 0.0)
         self._h = lib.orc_create(ctypes.byref(p))
         if not self._h:
             raise MemoryError("oracle allocation failed")
@@ -177,6 +183,15 @@ class Oracle:
         if self.np:
             self.lib.orc_contact_forces(self._h, _dp(F))
         return F
+
+    def zieb_state(self):
+        """(cylinder density rho^n, piston displacement H_p^n, mean inflow v_f^n)."""
+        out = np.empty(3)
+        self.lib.orc_zieb_state(self._h, _dp(out))
+        return out
+
+    def zieb_set_piston(self, vp):
+        self.lib.orc_zieb_set_piston(self._h, float(vp))
 
     def contact_torques(self):
         T = np.empty((self.np, 3))

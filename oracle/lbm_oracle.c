@@ -80,6 +80,10 @@ typedef struct {
     double kt;              /* tangential contact stiffness (Eq. 2); friction is on when kt > 0 and mu > 0 */
     double mu;              /* Coulomb friction coefficient mu_s (Eq. 2) */
     double restitution_t;   /* tangential restitution, sets gamma_t (Eq. 2); 1: no tangential damping */
+    int zieb;               /* 1: the plane z = 0 is a ZIEB face (Sect. 2.6) onto a virtual cylinder below */
+    double zieb_area;       /* piston (and cylinder) cross-section A_p */
+    double zieb_volume;     /* cylinder volume V_0 */
+    double zieb_vp;         /* piston velocity v_p (H_p advances by v_p per step) */
 } orc_params;
 
 #define CT_MAX 64
@@ -113,6 +117,7 @@ typedef struct {
     unsigned char *fixed;   /* 1: prescribed motion, X += V dt; V, Om constant */
     long step;
     long refilled;          /* nodes refilled in the last step */
+    double zrho, zH, zvf;   /* ZIEB: cylinder density rho^n, piston displacement H_p^n, mean inflow v_f^n */
 } orc_state;
 
 /* ------------------------------------------------------------------ */
@@ -513,6 +518,58 @@ static void refill(orc_state *s) {
             }
 }
 
+/* Zoom-in with Effective Boundaries (Sect. 2.6): the plane z = 0 is the
+ * first simulated plane x_S next to a virtual cylinder of volume V_0 and
+ * cross-section A_p below it, whose piston has moved by H_p^n.  After the
+ * streaming of step n (and the momentum exchange):
+ *   rho^{n+1} = rho^n exp[(v_p A_p - v_f^n A_p) / (V_0 - A_p H_p^n)]   (Eq. 8)
+ * with rho^n the cylinder density and v_f^n the mean inflow velocity over
+ * the face at time n; then at every fluid node of the face the five
+ * populations that would enter from the cylinder (c_z = +1) are unknown:
+ * rho* is the sum of the 14 streamed populations and of the five
+ * unknown ones at their post-collision values of time n at the node
+ * (reading of "f^n": what the node holds for them after its collision, as
+ * nothing streamed in); the one normal to the face takes
+ *   f_12 = rho^{n+1} - (rho* - f_12)                                    (Eq. 9)
+ * so that the density is rho^{n+1}; u = sum_i f_i c_i / rho^{n+1}; and all 19
+ * populations are replaced by f^eq(rho^{n+1}, u) (Eq. 9 of the LBM section).
+ * readings: v_f^n is the mean of u_z over the fluid nodes of the face as
+ * the previous update left them (0 at the start, fluid at rest), rho^0 = 1,
+ * H_p^0 = 0, H_p advances by v_p per step; u carries no force shift; the
+ * face replaces the wall z = -1/2 for the fluid only (spheres keep their
+ * contact with that plane). */
+static void zieb(orc_state *s) {
+    const orc_params *P = &s->p;
+    const double A = P->zieb_area;
+    const double rho1 = s->zrho * exp((P->zieb_vp * A - s->zvf * A) / (P->zieb_volume - A * s->zH));
+    double sum_uz = 0.0;
+    long count = 0;
+    for (int y = 0; y < P->ny; ++y)
+        for (int x = 0; x < P->nx; ++x) {
+            long n = node_of(s, x, y, 0);
+            if (s->owner[n] >= 0) continue;
+            double f[NQ], rstar = 0.0;
+            for (int i = 0; i < NQ; ++i) {
+                f[i] = CZ[i] == 1 ? s->fc[(long)i * s->N + n] : s->fn[(long)i * s->N + n];
+                rstar += f[i];
+            }
+            f[12] = rho1 - (rstar - f[12]);
+            double u[3] = {0.0, 0.0, 0.0};
+            for (int i = 0; i < NQ; ++i) {
+                u[0] += CX[i] * f[i];
+                u[1] += CY[i] * f[i];
+                u[2] += CZ[i] * f[i];
+            }
+            for (int a = 0; a < 3; ++a) u[a] /= rho1;
+            for (int i = 0; i < NQ; ++i) s->fn[(long)i * s->N + n] = feq(s, i, rho1, u);
+            sum_uz += u[2];
+            ++count;
+        }
+    s->zrho = rho1;
+    s->zH += P->zieb_vp;
+    s->zvf = count ? sum_uz / count : 0.0;
+}
+
 /* ------------------------------------------------------------------ */
 /* DEM                                                                 */
 /* ------------------------------------------------------------------ */
@@ -785,6 +842,7 @@ orc_state *orc_create(const orc_params *p) {
             for (long n = 0; n < s->N; ++n) s->f[(long)i * s->N + n] = s->w[i];
         for (long n = 0; n < s->N; ++n) s->owner[n] = s->owner_prev[n] = -1;
     }
+    s->zrho = 1.0;
     return s;
 }
 
@@ -841,6 +899,9 @@ int orc_set_particles(orc_state *s, int n, const double *X, const double *V, con
     }
     contact_forces(s, s->X, s->V, s->Om, s->Fc, s->Tc, 0.0);
     s->step = 0;
+    s->zrho = 1.0;
+    s->zH = 0.0;
+    s->zvf = 0.0;
     s->refilled = 0;
     return 0;
 }
@@ -879,6 +940,7 @@ void orc_step(orc_state *s, int nsteps) {
                 s->Fh[k] += s->Fcorr[k];
                 s->Th[k] += s->Tcorr[k];
             }
+            if (s->p.zieb) zieb(s);
             double *t = s->f;
             s->f = s->fn;
             s->fn = t;
@@ -898,6 +960,15 @@ void orc_contact_forces(const orc_state *s, double *Fc) { memcpy(Fc, s->Fc, size
 void orc_contact_torques(const orc_state *s, double *Tc) { memcpy(Tc, s->Tc, sizeof(double) * 3 * s->np); }
 
 int orc_contact_overflow(const orc_state *s) { return s->ct_overflow; }
+
+/* ZIEB state: cylinder density, piston displacement, mean inflow velocity. */
+void orc_zieb_state(const orc_state *s, double *out) {
+    out[0] = s->zrho;
+    out[1] = s->zH;
+    out[2] = s->zvf;
+}
+
+void orc_zieb_set_piston(orc_state *s, double vp) { s->p.zieb_vp = vp; }
 
 void orc_particles(const orc_state *s, double *X, double *V, double *Om) {
     memcpy(X, s->X, sizeof(double) * 3 * s->np);
