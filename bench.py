@@ -196,6 +196,14 @@ def friction_params(args):
     return dict(kt=0.5 * PHYS["kn"], mu=0.3, restitution_t=0.6)
 
 
+def zieb_params(args):
+    """ZIEB face of the --zieb runs (none by default)."""
+    if not getattr(args, "zieb", False):
+        return {}
+    A = float(BOX[0] * BOX[1])
+    return dict(zieb=dict(area=A, volume=40.0 * A, vp=0.005))
+
+
 def run_reference(args, rank, world):
     """--impl reference: the FP64 oracle on the host, each step a bounded
     sample of the workload (a 48^3 box at the same solid fraction: 13 spheres
@@ -242,7 +250,8 @@ def run_ours(args, rank, world, local_rank):
     dense = args.workload == "dense"
     lat = lbm.Lattice(*BOX, precision=args.precision, max_particles=nsph, max_radius=4.0,
                       stream=ctypes_stream(stream), device=dev, schedule=args.schedule,
-                      momentum_correction=args.momentum_correction, **PHYS, **friction_params(args))
+                      momentum_correction=args.momentum_correction, **PHYS, **friction_params(args),
+                      **zieb_params(args))
     lat.set_particles(p["X"], V=p["V"], Om=p["Om"], R=p["R"])
     N = BOX[0] * BOX[1] * BOX[2]
 
@@ -315,6 +324,7 @@ def run_ours(args, rank, world, local_rank):
                    "radius": 4.0, "solid_fraction": round(float(np.sum(4 / 3 * np.pi * p["R"] ** 3)) / N, 4),
                    "storage": args.precision, "schedule": args.schedule, "fluid_nodes": nf, "links": info["links"],
                    "momentum_correction": args.momentum_correction, "friction": friction_params(args) or None,
+                   "zieb": zieb_params(args).get("zieb"),
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (populations %.2f GB)" % (19 * N * s / 1e9)},
         "roofline": {"bound": "hbm", "kernel": "k_stream_collide" + (" (near + far launches)" if args.schedule == "overlap" else ""),
@@ -330,7 +340,7 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": int((oF.numel() + oT.numel() + oX.numel()) * 8)},
         # per step with spheres: overlapped = far collide, near marks, near list, marks, refill,
         # near collide, links, neighbours, DEM; serial = marks, refill, collide, links, neighbours, DEM
-        "gpu_launches": args.steps * ((9 if args.schedule == "overlap" else 6) if nsph else 1),
+        "gpu_launches": args.steps * (((9 if args.schedule == "overlap" else 6) if nsph else 1) + int(args.zieb)),
     }
     if world == 1 and not args.no_cpu_baseline and not dense:
         line["cpu_baseline"] = cpu_baseline()
@@ -486,6 +496,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", choices=["serial", "overlap"], default="serial",
                     help="order of the kernels inside a step (same results)")
+    ap.add_argument("--zieb", action="store_true",
+                    help="ZIEB face on z = 0 onto a piston cylinder (A_p = nx ny, V_0 = 40 A_p, v_p = 0.005)")
     ap.add_argument("--friction", action="store_true",
                     help="tangential contact law (Eqs. 2, 3) with k_t = k_n / 2, mu = 0.3, e_t = 0.6 (slurry workload)")
     ap.add_argument("--momentum-correction", action="store_true",

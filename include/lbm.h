@@ -111,6 +111,14 @@ typedef struct {
                                   thread-block cluster of the DEM holds) */
     double restitution_t;      /* tangential restitution in (0, 1], sets the dashpot gamma_t of
                                   Eq. 2 like restitution sets gamma_n; 1: no tangential damping */
+    int32_t zieb;              /* 1: the plane z = 0 is a ZIEB face (Sect. 2.6) onto a virtual
+                                  piston cylinder below it, in place of the wall z = -1/2 for the
+                                  fluid (spheres still touch that plane); needs
+                                  LBM_SCHEDULE_SERIAL and no batch (else LBM_ERR_UNSUPPORTED);
+                                  0: off; other values: LBM_ERR_ARG */
+    double zieb_area;          /* piston / cylinder cross-section A_p > 0 (lattice units) */
+    double zieb_volume;        /* cylinder volume V_0 > zieb_area * (piston travel) */
+    double zieb_piston_velocity; /* v_p: the piston displacement H_p grows by v_p per step */
 } lbm_params;
 
 typedef struct {
@@ -130,6 +138,19 @@ typedef struct {
  * cannot hold a sphere of max_radius, ...), LBM_ERR_UNSUPPORTED for
  * periodic_z != 0, LBM_ERR_NOMEM / LBM_ERR_CUDA on device failure. */
 int lbm_create(const lbm_params *params, lbm_handle *out);
+
+/* ZIEB face (Sect. 2.6, Eqs. 8, 9): after each step the cylinder density
+ * rho follows rho <- rho exp[(v_p A_p - v_f A_p) / (V_0 - A_p H_p)], with v_f
+ * the mean inflow velocity u_z over the face's fluid nodes, and every fluid
+ * node of the face takes the equilibrium at density rho and at the velocity
+ * left once the population normal to the face has restored that density.
+ * out[3] (host) receives rho, H_p and v_f after the last step (synchronises).
+ * LBM_ERR_ARG when the handle has no ZIEB face. */
+int lbm_zieb_state(lbm_handle h, double *out);
+
+/* Piston velocity v_p for the following steps (synchronises).  LBM_ERR_ARG
+ * when the handle has no ZIEB face or vp is not finite. */
+int lbm_zieb_set_piston(lbm_handle h, double vp);
 
 /* Free everything the handle holds (synchronises its stream first). */
 int lbm_destroy(lbm_handle h);

@@ -56,7 +56,8 @@ void release(lbm_s *h) {
                     (void *)h->pt.fixed, h->pt.Fh, h->pt.Th, h->pt.Fc, h->pt.Fx, h->pt.Tx, h->pt.Xf,
                     h->pt.Xb[0], h->pt.Xb[1], h->pt.Vh[0], h->pt.Vh[1], h->pt.nbr, h->pt.nbr_cnt, h->pt.pairA,
                     h->pt.pairB, h->pt.Xbuild, h->pt.rebuild, h->pt.frame[0], h->pt.frame[1], h->pt.Fcorr,
-                    h->pt.Tcorr, h->pt.Tc, h->pt.pairC, h->pt.tdisp, h->pt.tmask, h->pt.twall};
+                    h->pt.Tcorr, h->pt.Tc, h->pt.pairC, h->pt.tdisp, h->pt.tmask, h->pt.twall, h->zs,
+                    h->zpart, h->zcnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->status_host) cudaFreeHost(h->status_host);
@@ -146,6 +147,20 @@ int copy_out(lbm_s *h, void *dst, const void *src, size_t n, int where) {
     return cudaMemcpyAsync(dst, src, n, k, h->stream) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
+// ZIEB cylinder at rest: rho = 1 and H_p = 0 in both parity slots, piston
+// velocity vp, inflow sums 0 (synchronous).
+int zieb_reset(lbm_s *h, double vp) {
+    const double z[5] = {1.0, 1.0, 0.0, 0.0, vp};
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess ||
+        cudaMemcpy(h->zs, z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(h->zpart, 0, sizeof(double) * 2 * (size_t)h->zblocks) != cudaSuccess ||
+        cudaMemset(h->zcnt, 0, sizeof(int) * 2 * (size_t)h->zblocks) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}
+
 // Run fn(device pointer) on a device buffer of n bytes: the caller's own if
 // where == LBM_DEVICE, else a stream-ordered temporary copied to the host.
 template <class Fn>
@@ -204,6 +219,13 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     if (!(p.kt >= 0.0) || !(p.mu >= 0.0) || !(p.restitution_t > 0.0 && p.restitution_t <= 1.0) ||
         !std::isfinite(p.kt) || !std::isfinite(p.mu))
         return LBM_ERR_ARG;
+    if (p.zieb != 0 && p.zieb != 1) return LBM_ERR_ARG;
+    if (p.zieb && (!(p.zieb_area > 0.0) || !(p.zieb_volume > 0.0) || !std::isfinite(p.zieb_area) ||
+                   !std::isfinite(p.zieb_volume) || !std::isfinite(p.zieb_piston_velocity)))
+        return LBM_ERR_ARG;
+    // the face update runs between steps; the overlapped schedule collides
+    // far nodes (the face among them) of the next step meanwhile
+    if (p.zieb && p.schedule != LBM_SCHEDULE_SERIAL) return LBM_ERR_UNSUPPORTED;
     if (p.max_particles > 0) {
         if (!(p.max_radius > 0.0 && p.max_radius <= 16.0)) return LBM_ERR_ARG;
         // a sphere's bounding box and link tile must not wrap onto itself
@@ -308,6 +330,17 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     if (!rc) rc = dalloc(h, &pt.Fcorr, 3 * (size_t)M);
     if (!rc) rc = dalloc(h, &pt.Tcorr, 3 * (size_t)M);
     if (!rc) rc = dalloc(h, &pt.Tc, 3 * (size_t)M);
+    if (!rc && p.zieb) {
+        h->zieb = 1;
+        h->zA = p.zieb_area;
+        h->zV0 = p.zieb_volume;
+        h->zblocks = (int)(((long long)p.nx * p.ny + 255) / 256);
+        rc = dalloc(h, &h->zs, 5);
+        if (!rc) rc = dalloc(h, &h->zpart, 2 * (size_t)h->zblocks);
+        if (!rc) rc = dalloc(h, &h->zcnt, 2 * (size_t)h->zblocks);
+        h->zvp = p.zieb_piston_velocity;
+        if (!rc) rc = zieb_reset(h, h->zvp);
+    }
     if (!rc && pt.fric) {
         rc = dalloc(h, &pt.pairC, (size_t)M * kMaxNbr);
         if (!rc) rc = dalloc(h, &pt.tdisp, (size_t)M * kMaxNbr);
@@ -474,6 +507,7 @@ int lbm_set_particles(lbm_handle h, int32_t n, const double *pos, const double *
     pt.np = n;
     h->parity = 0;
     h->steps = 0;
+    if (!rc && h->zieb) rc = zieb_reset(h, h->zvp);  // the cylinder starts at rest with the fluid
     if (!rc && n) rc = launch_neighbours(h, 1);
     if (!rc && n) rc = launch_mark(h, h->parity, 0);
     if (!rc && n) rc = launch_contact(h);
@@ -558,6 +592,7 @@ int serial_step_launches(lbm_s *h) {
     if (!rc) rc = launch_refill(h, P);
     if (!rc) rc = launch_stream_collide(h, P);
     if (!rc) rc = launch_links(h, P);
+    if (!rc && h->zieb) rc = launch_zieb(h, P);
     if (!rc) rc = ok(cudaStreamWaitEvent(h->stream, h->ev_nbr, 0));
     if (!rc) rc = launch_dem(h);
     return rc;
@@ -696,6 +731,7 @@ int lbm_step(lbm_handle h, int32_t nsteps) {
         }
         if (!rc) rc = prof_mark(h, E3, A);
         if (!rc && parts) rc = launch_links(h, P);
+        if (!rc && h->zieb) rc = launch_zieb(h, P);
         if (!rc) rc = prof_mark(h, E4, A);
         if (!rc && parts) rc = launch_neighbours(h, 0);
         if (!rc && parts) rc = launch_dem(h);
@@ -799,6 +835,39 @@ int lbm_info(lbm_handle h, lbm_info_t *info) {
     info->particles = h->pt.np;
     info->precision = h->precision;
     info->device_bytes = (int64_t)h->bytes;
+    return rc ? rc : s;
+}
+
+int lbm_zieb_state(lbm_handle h, double *out) {
+    if (!h || !out || !h->zieb) return LBM_ERR_ARG;
+    DeviceScope ds(h->device);
+    const int P = h->parity;  // the slot the last step wrote
+    double z[5];
+    std::vector<double> part(h->zblocks);
+    std::vector<int> cnt(h->zblocks);
+    int rc = copy_out(h, z, h->zs, sizeof(z), LBM_HOST);
+    if (!rc) rc = copy_out(h, part.data(), h->zpart + (size_t)P * h->zblocks, sizeof(double) * h->zblocks, LBM_HOST);
+    if (!rc) rc = copy_out(h, cnt.data(), h->zcnt + (size_t)P * h->zblocks, sizeof(int) * h->zblocks, LBM_HOST);
+    const int s = settle(h);
+    if (rc || s) return rc ? rc : s;
+    double su = 0.0;
+    long long sc = 0;
+    for (int b = 0; b < h->zblocks; ++b) {
+        su += part[b];
+        sc += cnt[b];
+    }
+    out[0] = z[P];
+    out[1] = z[2 + P];
+    out[2] = sc ? su / (double)sc : 0.0;
+    return LBM_OK;
+}
+
+int lbm_zieb_set_piston(lbm_handle h, double vp) {
+    if (!h || !h->zieb || !std::isfinite(vp)) return LBM_ERR_ARG;
+    DeviceScope ds(h->device);
+    int rc = copy_in(h, h->zs + 4, &vp, sizeof(double), LBM_HOST);
+    const int s = settle(h);  // vp lives on this stack frame until the copy is done
+    if (!rc && !s) h->zvp = vp;
     return rc ? rc : s;
 }
 
@@ -1049,6 +1118,10 @@ int lbm_batch_create(const lbm_params *params, int32_t count, lbm_batch *out) {
             break;
         }
         b->m[i]->batch = b;
+        if (b->m[i]->zieb) {  // the face update is not part of the batched step
+            rc = LBM_ERR_UNSUPPORTED;
+            break;
+        }
         if (p.max_particles > 0) {
             b->ext = std::max(b->ext, b->m[i]->tile_ext);
             b->cap = std::max(b->cap, b->m[i]->link_cap);

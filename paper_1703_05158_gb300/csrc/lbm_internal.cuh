@@ -253,6 +253,12 @@ struct lbm_s {
     int sticky;              // first device error seen
     int dem_blocks, dem_threads;  // cooperative fallback grid
     int dem_cluster;              // CTAs of the one-cluster DEM kernel (0: use the fallback)
+    // ZIEB face on z = 0: zs = [rho, rho, H_p, H_p, v_p] (rho and H_p ping-pong by
+    // step parity), zpart / zcnt = [2][zblocks] per-block sums of u_z and node counts
+    int zieb = 0, zblocks = 0;
+    double zA = 0.0, zV0 = 0.0, zvp = 0.0;
+    double *zs = nullptr, *zpart = nullptr;
+    int *zcnt = nullptr;
     int tile_ext;            // half width of the per-sphere link tile
     int link_cap;            // link-list capacity per sphere (shared memory)
     size_t bytes;
@@ -329,6 +335,7 @@ int launch_stream_collide(lbm_s *h, int parity, int mode = 0, const uint8_t *nea
 int launch_near_mark(lbm_s *h, uint8_t *near, uint8_t tag, const SFrame *frames, int *list, int *count,
                      cudaStream_t stream);
 int launch_collide_list(lbm_s *h, int parity, const int *list, const int *count, cudaStream_t stream);
+int launch_zieb(lbm_s *h, int P);  // ZIEB face after the step of parity P
 int launch_mark(lbm_s *h, int P, int corr);  // corr: momentum correction of the covered nodes
 int launch_refill(lbm_s *h, int parity);
 int launch_links(lbm_s *h, int parity);

@@ -38,7 +38,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_particles", "lbm_set_particle_l
            "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_handle", "lbm_batch_tune", "lbm_batch_step",
            "lbm_batch_sync", "lbm_channel_create", "lbm_channel_destroy", "lbm_channel_set_theta",
            "lbm_channel_forward", "lbm_channel_backward", "lbm_channel_drag", "lbm_channel_populations",
-           "lbm_channel_geometry")
+           "lbm_channel_geometry", "lbm_zieb_state", "lbm_zieb_set_piston")
 
 
 SCHEDULES = {"serial": 0, "overlap": 1}
@@ -56,6 +56,8 @@ class lbm_params(ctypes.Structure):
         ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int32), ("schedule", ctypes.c_int32),
         ("momentum_correction", ctypes.c_int32),
         ("kt", ctypes.c_double), ("mu", ctypes.c_double), ("restitution_t", ctypes.c_double),
+        ("zieb", ctypes.c_int32), ("zieb_area", ctypes.c_double), ("zieb_volume", ctypes.c_double),
+        ("zieb_piston_velocity", ctypes.c_double),
     ]
 
 
@@ -125,6 +127,8 @@ def load(build=True):
         lib.lbm_channel_drag.argtypes = [vp, dp]
         lib.lbm_channel_populations.argtypes = [vp, dp]
         lib.lbm_channel_geometry.argtypes = [vp, vp]
+        lib.lbm_zieb_state.argtypes = [vp, dp]
+        lib.lbm_zieb_set_piston.argtypes = [vp, ctypes.c_double]
         lib.lbm_error_string.argtypes = [ctypes.c_int]
         lib.lbm_error_string.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -254,6 +258,16 @@ def lbm_sync(h):
     return _check(load().lbm_sync(h), "lbm_sync")
 
 
+def lbm_zieb_state(h):
+    out = np.empty(3)
+    _check(load().lbm_zieb_state(h, out.ctypes.data), "lbm_zieb_state")
+    return out
+
+
+def lbm_zieb_set_piston(h, vp):
+    return _check(load().lbm_zieb_set_piston(h, float(vp)), "lbm_zieb_set_piston")
+
+
 PHASES = ("geometry", "collide", "links", "dem", "collide_far", "wait_far")
 
 
@@ -304,8 +318,9 @@ def lbm_batch_sync(b):
 def make_params(nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0), u_hi=(0.0, 0.0, 0.0),
                 rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16, precision="fp32", max_particles=0,
                 max_radius=4.0, stream=None, device=0, schedule="serial", momentum_correction=False, kt=0.0,
-                mu=0.0, restitution_t=1.0):
-    """lbm_params from keyword arguments (the Lattice constructor's)."""
+                mu=0.0, restitution_t=1.0, zieb=None):
+    """lbm_params from keyword arguments (the Lattice constructor's); zieb:
+    None or dict(area=A_p, volume=V_0, vp=v_p) for a ZIEB face on z = 0."""
     p = lbm_params()
     p.nx, p.ny, p.nz, p.periodic_z = nx, ny, nz, 0
     p.tau0, p.cs_smag = tau0, cs
@@ -321,6 +336,9 @@ def make_params(nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0
     p.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
     p.momentum_correction = int(bool(momentum_correction))
     p.kt, p.mu, p.restitution_t = kt, mu, restitution_t
+    if zieb is not None:
+        p.zieb, p.zieb_area, p.zieb_volume = 1, zieb["area"], zieb["volume"]
+        p.zieb_piston_velocity = zieb.get("vp", 0.0)
     return p
 
 
@@ -336,10 +354,10 @@ class Lattice:
     def __init__(self, nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0), u_hi=(0.0, 0.0, 0.0),
                  rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16, precision="fp32", max_particles=0,
                  max_radius=4.0, stream=None, device=0, schedule="serial", momentum_correction=False, kt=0.0,
-                 mu=0.0, restitution_t=1.0):
+                 mu=0.0, restitution_t=1.0, zieb=None):
         p = make_params(nx, ny, nz, tau0, cs, g, u_lo, u_hi, rho_s, kn, restitution, dem_substeps, precision,
                         max_particles, max_radius, stream, device, schedule, momentum_correction, kt, mu,
-                        restitution_t)
+                        restitution_t, zieb)
         self.params = p
         self.h = lbm_create(p)
         self.shape = (nz, ny, nx)
@@ -378,6 +396,13 @@ class Lattice:
         Om = np.zeros((n, 3)) if Om is None else Om
         lbm_set_particles(self.h, X, V, Om, R, fixed)
         self.np = n
+
+    def zieb_state(self):
+        """(cylinder density, piston displacement, mean inflow velocity)."""
+        return lbm_zieb_state(self.h)
+
+    def zieb_set_piston(self, vp):
+        lbm_zieb_set_piston(self.h, vp)
 
     def set_load(self, F=None, T=None):
         F = None if F is None else np.ascontiguousarray(F, dtype=np.float64).reshape(self.np, 3)

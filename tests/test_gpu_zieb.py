@@ -1,0 +1,99 @@
+"""ZIEB face (Sect. 2.6, Eqs. 8, 9) on the GPU against the FP64 oracle,
+whose pins (tests/test_oracle_zieb.py) fix its behaviour: populations within
+1e-5, the cylinder density within 1e-6 relative, the piston displacement
+exact, the mean inflow velocity within 1e-5 of the inflow scale."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1703_05158_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+POP_TOL = 1e-5
+
+
+def lbm():
+    from paper_1703_05158_gb300 import lbm as mod
+
+    mod.load()
+    return mod
+
+
+def pair(shape, zieb, parts=None, **kw):
+    lat = lbm().Lattice(*shape, max_particles=max(1, 0 if parts is None else len(parts["R"])), max_radius=5.0,
+                        zieb=zieb, **kw)
+    orc = oracle.Oracle(*shape, zieb=zieb, **kw)
+    if parts is not None:
+        for o in (lat, orc):
+            o.set_particles(parts["X"], V=parts["V"], Om=parts.get("Om"), R=parts["R"])
+    return lat, orc
+
+
+def check(lat, orc, scale):
+    fo, fg = orc.populations(), lat.populations()
+    fluid = orc.owner() < 0
+    assert np.array_equal(lat.owner(), orc.owner())
+    assert float((np.abs(fg - fo)[:, fluid] / np.abs(fo[:, fluid])).max()) <= POP_TOL
+    zg, zo = lat.zieb_state(), orc.zieb_state()
+    assert abs(zg[0] - zo[0]) <= 1e-6 * zo[0]
+    assert zg[1] == pytest.approx(zo[1], abs=1e-12)
+    assert abs(zg[2] - zo[2]) <= 1e-5 * scale
+
+
+def test_rest_state_stays_exact():
+    A = 24 * 20
+    lat, _ = pair((24, 20, 16), dict(area=A, volume=30.0 * A, vp=0.0), tau0=0.7, cs=0.17)
+    lat.step(40)
+    _, w, _ = oracle.tables()
+    assert np.array_equal(lat.populations(), np.broadcast_to(w[:, None, None, None], (19, 16, 20, 24)))
+    z = lat.zieb_state()
+    assert z[0] == 1.0 and z[1] == 0.0 and z[2] == 0.0
+
+
+def test_piston_stroke_matches_the_oracle():
+    shape = (24, 20, 32)
+    A = shape[0] * shape[1]
+    zieb = dict(area=A, volume=40.0 * A, vp=0.02)
+    kw = dict(tau0=0.8, cs=0.17, u_hi=(0.02, 0.0, 0.0))
+    lat, orc = pair(shape, zieb, **kw)
+    for n in (1, 2, 47, 50):
+        lat.step(n)
+        orc.step(n)
+        check(lat, orc, 0.02)
+    for o in (lat, orc):  # the piston stops: the column rings and settles
+        o.zieb_set_piston(0.0)
+    lat.step(100)
+    orc.step(100)
+    check(lat, orc, 0.02)
+
+
+def test_piston_with_moving_spheres_matches_the_oracle():
+    shape = (40, 36, 32)
+    A = shape[0] * shape[1]
+    zieb = dict(area=0.5 * A, volume=20.0 * A, vp=0.03)
+    kw = dict(tau0=0.7, cs=0.17, rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16)
+    parts = inputs.polydisperse(shape, 6, (2.5, 4.0), seed=inputs.SEED_BASE + 90, vmax=0.02)
+    lat, orc = pair(shape, zieb, parts=parts, **kw)
+    for n in (1, 9, 40, 50):
+        lat.step(n)
+        orc.step(n)
+        check(lat, orc, 0.03)
+        Fg, _ = lat.forces()
+        Fo, _ = orc.forces()
+        assert (np.linalg.norm(Fg - Fo, axis=1) / np.linalg.norm(Fo, axis=1)).max() <= 1e-4
+
+
+def test_zieb_needs_the_serial_schedule_and_no_batch():
+    L = lbm()
+    zieb = dict(area=100.0, volume=4000.0, vp=0.01)
+    with pytest.raises(Exception):
+        L.Lattice(24, 20, 16, tau0=0.7, max_particles=1, schedule="overlap", zieb=zieb)
+    with pytest.raises(Exception):
+        L.Batch([dict(nx=24, ny=20, nz=16, tau0=0.7, zieb=zieb)])
+    for bad in (dict(area=0.0, volume=10.0), dict(area=1.0, volume=-1.0)):
+        with pytest.raises(Exception):
+            L.Lattice(24, 20, 16, tau0=0.7, zieb=bad)
+    lat = L.Lattice(24, 20, 16, tau0=0.7)
+    with pytest.raises(Exception):
+        lat.zieb_state()
