@@ -78,6 +78,10 @@ typedef struct lbm_s *lbm_handle;
 #define LBM_SCHEDULE_SERIAL 0
 #define LBM_SCHEDULE_OVERLAP 1
 
+/* Momentum exchange on sphere links. */
+#define LBM_MEA_PAPER 0
+#define LBM_MEA_GALILEAN 1
+
 /* Memory space of a caller buffer. */
 #define LBM_HOST 0
 #define LBM_DEVICE 1
@@ -119,6 +123,9 @@ typedef struct {
     double zieb_area;          /* piston / cylinder cross-section A_p > 0 (lattice units) */
     double zieb_volume;        /* cylinder volume V_0 > zieb_area * (piston travel) */
     double zieb_piston_velocity; /* v_p: the piston displacement H_p grows by v_p per step */
+    int32_t mea;               /* momentum exchange: LBM_MEA_PAPER (Eqs. 25, 26) or LBM_MEA_GALILEAN
+                                  (populations carry c - u_b, Wen, Zhang & Fang 2014; not in the
+                                  paper); other values: LBM_ERR_ARG */
 } lbm_params;
 
 typedef struct {

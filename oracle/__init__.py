@@ -34,7 +34,7 @@ class OrcParams(ctypes.Structure):
         ("periodic_z", ctypes.c_int), ("momentum_correction", ctypes.c_int),
         ("kt", ctypes.c_double), ("mu", ctypes.c_double), ("restitution_t", ctypes.c_double),
         ("zieb", ctypes.c_int), ("zieb_area", ctypes.c_double), ("zieb_volume", ctypes.c_double),
-        ("zieb_vp", ctypes.c_double),
+        ("zieb_vp", ctypes.c_double), ("mea", ctypes.c_int),
     ]
 
 
@@ -106,7 +106,7 @@ class Oracle:
     def __init__(self, nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0),
                  u_hi=(0.0, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16,
                  les=True, fluid=True, periodic_z=False, momentum_correction=False, kt=0.0, mu=0.0,
-                 restitution_t=1.0, zieb=None, threads=None):
+                 restitution_t=1.0, zieb=None, mea="paper", threads=None):
         if threads is not None:
             os.environ["OMP_NUM_THREADS"] = str(threads)
         lib = _load()
@@ -121,6 +121,7 @@ class Oracle:
         p.periodic_z = int(bool(periodic_z))
         p.momentum_correction = int(bool(momentum_correction))
         p.kt, p.mu, p.restitution_t = kt, mu, restitution_t
+        p.mea = {"paper": 0, "galilean": 1}[mea]
         if zieb is not None:  # dict(area=A_p, volume=V_0, vp=v_p)
             p.zieb, p.zieb_area, p.zieb_volume, p.zieb_vp = 1, zieb["area"], zieb["volume"], zieb.get("vp", 0.0)
         self._h = lib.orc_create(ctypes.byref(p))

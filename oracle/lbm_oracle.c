@@ -84,6 +84,7 @@ typedef struct {
     double zieb_area;       /* piston (and cylinder) cross-section A_p */
     double zieb_volume;     /* cylinder volume V_0 */
     double zieb_vp;         /* piston velocity v_p (H_p advances by v_p per step) */
+    int mea;                /* 0: momentum exchange of Eqs. 25, 26; 1: its Galilean-invariant form */
 } orc_params;
 
 #define CT_MAX 64
@@ -413,6 +414,12 @@ static void momentum_exchange(orc_state *s) {
                     arm(s, p, x, y, z, j, q, l);
                     double m = s->fc[(long)j * s->N + n] + s->fn[(long)k * s->N + n];
                     double dP[3] = {m * CX[j], m * CY[j], m * CZ[j]};
+                    if (P->mea) {
+                        /* Galilean-invariant form (Wen, Zhang & Fang 2014; not in the paper): the
+                         * populations carry c - u_b, so dP = fc_j (c_j - u_b) - f_k (c_k - u_b) */
+                        double e = s->fc[(long)j * s->N + n] - s->fn[(long)k * s->N + n];
+                        for (int a = 0; a < 3; ++a) dP[a] -= e * ub[a];
+                    }
                     double *F = s->Fh + 3 * p, *T = s->Th + 3 * p;
                     F[0] += dP[0];
                     F[1] += dP[1];

@@ -220,6 +220,7 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
         !std::isfinite(p.kt) || !std::isfinite(p.mu))
         return LBM_ERR_ARG;
     if (p.zieb != 0 && p.zieb != 1) return LBM_ERR_ARG;
+    if (p.mea != LBM_MEA_PAPER && p.mea != LBM_MEA_GALILEAN) return LBM_ERR_ARG;
     if (p.zieb && (!(p.zieb_area > 0.0) || !(p.zieb_volume > 0.0) || !std::isfinite(p.zieb_area) ||
                    !std::isfinite(p.zieb_volume) || !std::isfinite(p.zieb_piston_velocity)))
         return LBM_ERR_ARG;
@@ -292,6 +293,7 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     pt.skin = kSkin;
     pt.max_step = kMaxStep;
     pt.fric = p.kt > 0.0 && p.mu > 0.0;
+    pt.gimea = p.mea == LBM_MEA_GALILEAN;
     pt.kt = p.kt;
     pt.mu = p.mu;
     {

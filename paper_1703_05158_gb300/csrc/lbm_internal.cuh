@@ -199,6 +199,7 @@ struct Parts {
     unsigned long long *tmask;     // per sphere: bit m set = list entry m was in contact
     float4 *twall;                 // [np][2]: tangential displacement against the lower / upper wall
     float ulo[3], uhi[3];          // wall velocities
+    int gimea;                     // 1: Galilean-invariant momentum exchange
 };
 
 // Makes device d current for the lifetime of the object, then restores the

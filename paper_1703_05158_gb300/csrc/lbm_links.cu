@@ -17,7 +17,9 @@
 // and all outputs are slots no other link reads, so links are independent.
 //
 // Momentum exchange (Eqs. 25, 26): the sphere receives
-//   dP = (f^c_j(x) + f_k(x, t+1)) c_j,   torque (x_b - X) x dP.
+//   dP = (f^c_j(x) + f_k(x, t+1)) c_j,   torque (x_b - X) x dP,
+// and with the Galilean-invariant option (Wen, Zhang & Fang 2014; not in the
+// paper) also -(f^c_j(x) - f_k(x, t+1)) u_b.
 // With f = w + d this splits into the deviation part (d^c_j + d_k) c_j,
 // summed in FP32 per thread and per warp (shuffles), and the rest part
 // 2 w_j c_j = (36 w_j / 18) c_j, counted exactly in integers; (x_b - X) x c_j
@@ -45,7 +47,7 @@ __device__ __forceinline__ void tile_xyz(int t, int B, int B2, unsigned mB, unsi
     oz = z - ext;
 }
 
-template <typename T>
+template <typename T, bool GI>
 __device__ __forceinline__ void links_body(const Lat &L, const Parts &pt, const SFrame *__restrict__ fcur,
                                            T *__restrict__ f, uint8_t *__restrict__ flag,
                                            const int32_t *__restrict__ owner, const int P, const int ext,
@@ -274,6 +276,15 @@ __device__ __forceinline__ void links_body(const Lat &L, const Parts &pt, const 
             Td[0] += m * (dy * cjz - dz * cjy);
             Td[1] += m * (dz * cjx - dx * cjz);
             Td[2] += m * (dx * cjy - dy * cjx);
+            if (GI && pt.gimea) {  // Galilean-invariant form: - (f^c_j - f_k) u_b, the weights cancel
+                const float e = dcj - dn;
+                Fd[0] -= e * ubx;
+                Fd[1] -= e * uby;
+                Fd[2] -= e * ubz;
+                Td[0] -= e * (ly * ubz - lz * uby);
+                Td[1] -= e * (lz * ubx - lx * ubz);
+                Td[2] -= e * (lx * uby - ly * ubx);
+            }
             const int w = rw36(j);
             I[0] += w * cjx;
             I[1] += w * cjy;
@@ -341,23 +352,25 @@ __device__ __forceinline__ void links_body(const Lat &L, const Parts &pt, const 
     }
 }
 
-template <typename T>
+// GI: compiled with the Galilean-invariant momentum exchange (taken where
+// the handle asks for it).
+template <typename T, bool GI>
 __global__ void __launch_bounds__(256, 3) k_links(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
                                                T *__restrict__ f,
                                                uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
                                                const int P, const int ext, const unsigned mB, const unsigned mB2,
                                                const int cap, int *__restrict__ status,
                                                unsigned long long *__restrict__ ctr) {
-    links_body<T>(L, pt, fcur, f, flag, owner, P, ext, mB, mB2, cap, status, ctr);
+    links_body<T, GI>(L, pt, fcur, f, flag, owner, P, ext, mB, mB2, cap, status, ctr);
 }
 
 // Batched: instance blockIdx.y; parity P is also the step parity.
-template <typename T>
+template <typename T, bool GI>
 __global__ void __launch_bounds__(256, 3) k_links_b(const Inst *__restrict__ I, const int P, const int ext,
                                                  const unsigned mB, const unsigned mB2, const int cap) {
     const Inst &a = I[blockIdx.y];
     if ((int)blockIdx.x >= a.pt.np) return;
-    links_body<T>(a.L, a.pt, a.pt.frame[P], (T *)a.f, a.flag, a.owner, P, ext, mB, mB2, cap, a.status, a.ctr);
+    links_body<T, GI>(a.L, a.pt, a.pt.frame[P], (T *)a.f, a.flag, a.owner, P, ext, mB, mB2, cap, a.status, a.ctr);
 }
 
 int link_capacity(double max_radius) {
@@ -381,13 +394,37 @@ static cudaError_t raise_smem(K kernel, size_t smem) {
     return e;
 }
 
+template <bool GI>
+static cudaError_t raise_all(size_t smem) {
+    cudaError_t e = raise_smem(k_links<float, GI>, smem);
+    if (e == cudaSuccess) e = raise_smem(k_links<__nv_bfloat16, GI>, smem);
+    if (e == cudaSuccess) e = raise_smem(k_links<__half, GI>, smem);
+    if (e == cudaSuccess) e = raise_smem(k_links_b<float, GI>, smem);
+    if (e == cudaSuccess) e = raise_smem(k_links_b<__nv_bfloat16, GI>, smem);
+    if (e == cudaSuccess) e = raise_smem(k_links_b<__half, GI>, smem);
+    return e;
+}
+
 int links_setup(int ext, int cap) {
     const size_t smem = link_smem(ext, cap);
-    cudaError_t e = raise_smem(k_links<float>, smem);
-    if (e == cudaSuccess) e = raise_smem(k_links<__nv_bfloat16>, smem);
-    if (e == cudaSuccess) e = raise_smem(k_links<__half>, smem);
+    cudaError_t e = raise_all<false>(smem);
+    if (e == cudaSuccess) e = raise_all<true>(smem);
     if (e != cudaSuccess) cudaGetLastError();
     return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+template <typename T, bool GI>
+static void links_launch(lbm_s *h, int parity, size_t smem, const SFrame *fcur, int ext, unsigned mB, unsigned mB2,
+                         int cap) {
+    k_links<T, GI><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, fcur, (T *)h->f, h->flag, h->owner, parity, ext,
+                                                       mB, mB2, cap, h->status, h->ctr);
+}
+
+template <typename T>
+static void links_launch_t(lbm_s *h, int parity, size_t smem, const SFrame *fcur, int ext, unsigned mB, unsigned mB2,
+                           int cap) {
+    if (h->pt.gimea) links_launch<T, true>(h, parity, smem, fcur, ext, mB, mB2, cap);
+    else links_launch<T, false>(h, parity, smem, fcur, ext, mB, mB2, cap);
 }
 
 int launch_links(lbm_s *h, int parity) {
@@ -396,31 +433,25 @@ int launch_links(lbm_s *h, int parity) {
     const SFrame *fcur = h->pt.frame[h->steps & 1];
     const unsigned B = 2u * ext + 1u, mB = 0xFFFFFFFFu / B + 1u, mB2 = 0xFFFFFFFFu / (B * B) + 1u;
     switch (h->precision) {
-        case LBM_FP32:
-            k_links<float><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, fcur, (float *)h->f, h->flag, h->owner,
-                                                                parity, ext, mB, mB2, cap, h->status, h->ctr);
-            break;
-        case LBM_BF16_DEV:
-            k_links<__nv_bfloat16><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, fcur, (__nv_bfloat16 *)h->f,
-                                                                        h->flag, h->owner, parity, ext, mB, mB2, cap,
-                                                                        h->status, h->ctr);
-            break;
-        case LBM_FP16_DEV:
-            k_links<__half><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, fcur, (__half *)h->f, h->flag, h->owner,
-                                                                 parity, ext, mB, mB2, cap, h->status, h->ctr);
-            break;
+        case LBM_FP32: links_launch_t<float>(h, parity, smem, fcur, ext, mB, mB2, cap); break;
+        case LBM_BF16_DEV: links_launch_t<__nv_bfloat16>(h, parity, smem, fcur, ext, mB, mB2, cap); break;
+        case LBM_FP16_DEV: links_launch_t<__half>(h, parity, smem, fcur, ext, mB, mB2, cap); break;
         default: return LBM_ERR_ARG;
     }
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
-int links_setup_batch(int ext, int cap) {
-    const size_t smem = link_smem(ext, cap);
-    cudaError_t e = raise_smem(k_links_b<float>, smem);
-    if (e == cudaSuccess) e = raise_smem(k_links_b<__nv_bfloat16>, smem);
-    if (e == cudaSuccess) e = raise_smem(k_links_b<__half>, smem);
-    if (e != cudaSuccess) cudaGetLastError();
-    return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+int links_setup_batch(int ext, int cap) { return links_setup(ext, cap); }
+
+// A batch with any member on the Galilean-invariant exchange takes the GI
+// kernels; each instance still follows its own setting.
+template <typename T>
+static void links_launch_batch(const lbm_batch_s *b, int P, size_t smem, int ext, unsigned mB, unsigned mB2, int cap) {
+    bool gi = false;
+    for (int i = 0; i < b->n; ++i) gi = gi || b->m[i]->pt.gimea != 0;
+    const dim3 grid(b->max_np, b->n);
+    if (gi) k_links_b<T, true><<<grid, 256, smem, b->stream>>>(b->dinst, P, ext, mB, mB2, cap);
+    else k_links_b<T, false><<<grid, 256, smem, b->stream>>>(b->dinst, P, ext, mB, mB2, cap);
 }
 
 int launch_links_batch(const lbm_batch_s *b, int P) {
@@ -428,13 +459,10 @@ int launch_links_batch(const lbm_batch_s *b, int P) {
     const int ext = b->ext, cap = b->cap;
     const size_t smem = link_smem(ext, cap);
     const unsigned B = 2u * ext + 1u, mB = 0xFFFFFFFFu / B + 1u, mB2 = 0xFFFFFFFFu / (B * B) + 1u;
-    const dim3 grid(b->max_np, b->n);
     switch (b->precision) {
-        case LBM_FP32: k_links_b<float><<<grid, 256, smem, b->stream>>>(b->dinst, P, ext, mB, mB2, cap); break;
-        case LBM_BF16_DEV:
-            k_links_b<__nv_bfloat16><<<grid, 256, smem, b->stream>>>(b->dinst, P, ext, mB, mB2, cap);
-            break;
-        case LBM_FP16_DEV: k_links_b<__half><<<grid, 256, smem, b->stream>>>(b->dinst, P, ext, mB, mB2, cap); break;
+        case LBM_FP32: links_launch_batch<float>(b, P, smem, ext, mB, mB2, cap); break;
+        case LBM_BF16_DEV: links_launch_batch<__nv_bfloat16>(b, P, smem, ext, mB, mB2, cap); break;
+        case LBM_FP16_DEV: links_launch_batch<__half>(b, P, smem, ext, mB, mB2, cap); break;
         default: return LBM_ERR_ARG;
     }
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;

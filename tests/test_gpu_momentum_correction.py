@@ -137,3 +137,31 @@ def test_correction_with_16_bit_storage(precision):
     Fr, _ = ref.forces()
     Fl, _ = low.forces()
     assert np.abs(Fl - Fr).max() <= 2e-2 * np.abs(Fr).max()
+
+
+@pytest.mark.parametrize("corr", [False, True])
+def test_galilean_invariant_exchange_matches_the_oracle(corr):
+    """The Galilean-invariant momentum exchange (Wen, Zhang & Fang 2014),
+    alone and with the covered / uncovered correction."""
+    shape = (48, 40, 36)
+    p = suspension(shape, seed=inputs.SEED_BASE + 66)
+    lat = lbm().Lattice(*shape, max_particles=len(p["R"]), max_radius=5.0, momentum_correction=corr,
+                        mea="galilean", **KW)
+    orc = oracle.Oracle(*shape, momentum_correction=corr, mea="galilean", **KW)
+    for o in (lat, orc):
+        place(o, p)
+    done = 0
+    for n in (1, 9, 40, 50):
+        lat.step(n)
+        orc.step(n)
+        done += n
+        assert np.array_equal(lat.owner(), orc.owner()), done
+        fo, fg = orc.populations(), lat.populations()
+        fluid = orc.owner() < 0
+        assert float((np.abs(fg - fo)[:, fluid] / np.abs(fo[:, fluid])).max()) <= POP_TOL, done
+        Fg, Tg = lat.forces()
+        Fo, To = orc.forces()
+        ef = np.linalg.norm(Fg - Fo, axis=1) / np.linalg.norm(Fo, axis=1)
+        dt = np.linalg.norm(Tg - To, axis=1)
+        assert ef.max() <= FORCE_TOL, (done, ef.max())
+        assert np.all((dt <= 1e-3 * np.linalg.norm(To, axis=1)) | (dt < 1e-7)), (done, dt, To)
