@@ -250,7 +250,7 @@ def run_ours(args, rank, world, local_rank):
     dense = args.workload == "dense"
     lat = lbm.Lattice(*BOX, precision=args.precision, max_particles=nsph, max_radius=4.0,
                       stream=ctypes_stream(stream), device=dev, schedule=args.schedule,
-                      momentum_correction=args.momentum_correction, **PHYS, **friction_params(args),
+                      momentum_correction=args.momentum_correction, mea=args.mea, **PHYS, **friction_params(args),
                       **zieb_params(args))
     lat.set_particles(p["X"], V=p["V"], Om=p["Om"], R=p["R"])
     N = BOX[0] * BOX[1] * BOX[2]
@@ -324,7 +324,7 @@ def run_ours(args, rank, world, local_rank):
                    "radius": 4.0, "solid_fraction": round(float(np.sum(4 / 3 * np.pi * p["R"] ** 3)) / N, 4),
                    "storage": args.precision, "schedule": args.schedule, "fluid_nodes": nf, "links": info["links"],
                    "momentum_correction": args.momentum_correction, "friction": friction_params(args) or None,
-                   "zieb": zieb_params(args).get("zieb"),
+                   "zieb": zieb_params(args).get("zieb"), "mea": args.mea,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (populations %.2f GB)" % (19 * N * s / 1e9)},
         "roofline": {"bound": "hbm", "kernel": "k_stream_collide" + (" (near + far launches)" if args.schedule == "overlap" else ""),
@@ -496,6 +496,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", choices=["serial", "overlap"], default="serial",
                     help="order of the kernels inside a step (same results)")
+    ap.add_argument("--mea", choices=["paper", "galilean"], default="paper",
+                    help="momentum exchange on sphere links (Eqs. 25, 26, or its Galilean-invariant form)")
     ap.add_argument("--zieb", action="store_true",
                     help="ZIEB face on z = 0 onto a piston cylinder (A_p = nx ny, V_0 = 40 A_p, v_p = 0.005)")
     ap.add_argument("--friction", action="store_true",
