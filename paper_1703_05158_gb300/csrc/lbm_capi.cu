@@ -56,7 +56,7 @@ void release(lbm_s *h) {
                     (void *)h->pt.fixed, h->pt.Fh, h->pt.Th, h->pt.Fc, h->pt.Fx, h->pt.Tx, h->pt.Xf,
                     h->pt.Xb[0], h->pt.Xb[1], h->pt.Vh[0], h->pt.Vh[1], h->pt.nbr, h->pt.nbr_cnt, h->pt.pairA,
                     h->pt.pairB, h->pt.Xbuild, h->pt.rebuild, h->pt.frame[0], h->pt.frame[1], h->pt.Fcorr,
-                    h->pt.Tcorr, h->pt.Tc, h->pt.pairC, h->pt.tdisp, h->pt.tmask, h->pt.twall, h->zs,
+                    h->pt.Tcorr, h->pt.Tc, h->pt.pairC, h->pt.tdisp, h->pt.tmask, h->pt.twall, h->zs, h->pt.pairBM, h->pt.nact,
                     h->zpart, h->zcnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -354,6 +354,8 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     if (!rc) rc = dalloc(h, &pt.frame[1], (size_t)M);
     if (!rc) rc = dalloc(h, &pt.pairA, (size_t)M * kMaxNbr);
     if (!rc) rc = dalloc(h, &pt.pairB, (size_t)M * kMaxNbr);
+    if (!rc) rc = dalloc(h, &pt.pairBM, (size_t)M * kMaxNbr);
+    if (!rc) rc = dalloc(h, &pt.nact, (size_t)M);
     if (!rc) rc = dalloc(h, &pt.Xf, (size_t)M);
     for (int b = 0; b < 2 && !rc; ++b) {
         rc = dalloc(h, &pt.Xb[b], 3 * (size_t)M);

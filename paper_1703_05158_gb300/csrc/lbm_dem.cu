@@ -73,10 +73,11 @@ __device__ __forceinline__ void min_image(const Lat &L, double d[3]) {
 // One warp per sphere, step parity sp.  If a rebuild is due (or forced),
 // list every b != a
 // with |X_a - X_b| < R_a + R_b + skin in increasing b (centres staged through
-// shared memory); then compute the pair constants of every list entry for
-// the current centres and velocities:
+// shared memory); then compute, for the entries that can touch within the
+// step (compacted in list order), the pair constants for the current
+// centres and velocities:
 //   pairA = (d0, c0),  d0 = X_a - X_b (minimum image), c0 = (R_a+R_b)^2 - |d0|^2
-//   pairB = (V_a - V_b, gamma_n)
+//   pairB = (V_a - V_b, gamma_n),  pairBM = (b, list position)
 constexpr int kNbrTile = 1024;
 
 constexpr int kMaxNbrFric = 64;  // list length the 64-bit contact mask covers
@@ -164,24 +165,46 @@ __device__ __forceinline__ void neighbours_body(const Lat &L, const Parts &pt, c
         }
     }
     if (!live) return;
+    // the step's contact candidates: listed pairs whose gap can close within
+    // the step (each sphere moves less than max_step, so pairs further apart
+    // than R_a + R_b + 2 max_step cannot touch, nor did they touch at the end
+    // of the last step), compacted in list order with their list position
     const int cnt = pt.nbr_cnt[a];
-    for (int m = lane; m < cnt; m += 32) {
-        const int b = pt.nbr[(long long)a * pt.max_nbr + m];
-        double d[3] = {pt.X[3 * a] - pt.X[3 * b], pt.X[3 * a + 1] - pt.X[3 * b + 1], pt.X[3 * a + 2] - pt.X[3 * b + 2]};
-        min_image(L, d);
-        const double Rs = pt.R[a] + pt.R[b];
-        const double c0 = Rs * Rs - (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        const double ma = sphere_mass(pt, a), mb = sphere_mass(pt, b);
-        const double meff = pt.fixed[b] ? ma : (pt.fixed[a] ? mb : ma * mb / (ma + mb));
-        const float gam = (float)pt.ce * sqrtf((float)(meff * pt.kn));
-        const long long e = (long long)a * pt.max_nbr + m;
-        pt.pairA[e] = make_float4((float)d[0], (float)d[1], (float)d[2], (float)c0);
-        pt.pairB[e] = make_float4((float)(pt.V[3 * a] - pt.V[3 * b]), (float)(pt.V[3 * a + 1] - pt.V[3 * b + 1]),
-                                  (float)(pt.V[3 * a + 2] - pt.V[3 * b + 2]), gam);
-        if (pt.fric)
-            pt.pairC[e] = make_float4((float)pt.W[3 * b], (float)pt.W[3 * b + 1], (float)pt.W[3 * b + 2],
-                                      (float)pt.ct * sqrtf((float)(meff * pt.kt)));
+    const double reach = 2.0 * pt.max_step + 1e-3;
+    int nact = 0;
+    for (int m0 = 0; m0 < cnt; m0 += 32) {
+        const int m = m0 + lane;
+        bool act = false;
+        int b = 0;
+        double d[3] = {0.0, 0.0, 0.0}, Rs = 0.0, d2 = 0.0;
+        if (m < cnt) {
+            b = pt.nbr[(long long)a * pt.max_nbr + m];
+            d[0] = pt.X[3 * a] - pt.X[3 * b];
+            d[1] = pt.X[3 * a + 1] - pt.X[3 * b + 1];
+            d[2] = pt.X[3 * a + 2] - pt.X[3 * b + 2];
+            min_image(L, d);
+            Rs = pt.R[a] + pt.R[b];
+            d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            act = d2 < (Rs + reach) * (Rs + reach);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, act);
+        if (act) {
+            const double c0 = Rs * Rs - d2;
+            const double ma = sphere_mass(pt, a), mb = sphere_mass(pt, b);
+            const double meff = pt.fixed[b] ? ma : (pt.fixed[a] ? mb : ma * mb / (ma + mb));
+            const float gam = (float)pt.ce * sqrtf((float)(meff * pt.kn));
+            const long long e = (long long)a * pt.max_nbr + nact + __popc(bal & ((1u << lane) - 1u));
+            pt.pairA[e] = make_float4((float)d[0], (float)d[1], (float)d[2], (float)c0);
+            pt.pairB[e] = make_float4((float)(pt.V[3 * a] - pt.V[3 * b]), (float)(pt.V[3 * a + 1] - pt.V[3 * b + 1]),
+                                      (float)(pt.V[3 * a + 2] - pt.V[3 * b + 2]), gam);
+            pt.pairBM[e] = make_int2(b, m);
+            if (pt.fric)
+                pt.pairC[e] = make_float4((float)pt.W[3 * b], (float)pt.W[3 * b + 1], (float)pt.W[3 * b + 2],
+                                          (float)pt.ct * sqrtf((float)(meff * pt.kt)));
+        }
+        nact += __popc(bal);
     }
+    if (lane == 0) pt.nact[a] = nact;
 }
 
 // Tangential force of one contact (Eqs. 2, 3), FP64, delta_t = 0 (a contact
@@ -428,7 +451,7 @@ __device__ __forceinline__ void dem_cluster_body(const Lat &L, const Parts &pt, 
         Llo[q] = (float)(R - (z0 + 0.5));
         Lhi[q] = (float)(R - ((L.nz - 0.5) - z0));
         gw[q] = ce * sqrtf((float)m * kn);
-        nc[q] = pt.nbr_cnt[a];
+        nc[q] = pt.nact[a];
         dx[q] = make_float3(0.f, 0.f, 0.f);
         dv[q] = make_float3(0.f, 0.f, 0.f);
         if constexpr (FRIC) {
@@ -486,11 +509,14 @@ __device__ __forceinline__ void dem_cluster_body(const Lat &L, const Parts &pt, 
                 float4 A[kNbrGroup], Bv[kNbrGroup], ox[kNbrGroup], ov[kNbrGroup];
                 float4 C[FRIC ? kNbrGroup : 1], ow[FRIC ? kNbrGroup : 1];
                 float Rb[kNbrGroup];
+                int lm[kNbrGroup];  // list position of the candidate (its contact state)
 #pragma unroll
                 for (int u = 0; u < kNbrGroup; ++u) {
                     if (m0 + u >= nc[q]) break;
                     const long long e = (long long)a * pt.max_nbr + m0 + u;
-                    const int b = __ldg(pt.nbr + e);
+                    const int2 bm = __ldg(pt.pairBM + e);
+                    const int b = bm.x;
+                    lm[u] = bm.y;
                     A[u] = __ldg(pt.pairA + e);
                     Bv[u] = __ldg(pt.pairB + e);
                     Rb[u] = __ldg(&pt.Xf[b].w);
@@ -510,7 +536,7 @@ __device__ __forceinline__ void dem_cluster_body(const Lat &L, const Parts &pt, 
                     const float c =
                         A[u].w - 2.f * (A[u].x * Dx + A[u].y * Dy + A[u].z * Dz) - (Dx * Dx + Dy * Dy + Dz * Dz);
                     if (!(c > 0.f)) {
-                        if constexpr (FRIC) msk[q] &= ~(1ull << (m0 + u));  // the contact opened
+                        if constexpr (FRIC) msk[q] &= ~(1ull << lm[u]);  // the contact opened
                         continue;
                     }
                     const float ex = A[u].x + Dx, ey = A[u].y + Dy, ez = A[u].z + Dz;
@@ -526,7 +552,7 @@ __device__ __forceinline__ void dem_cluster_body(const Lat &L, const Parts &pt, 
                     F.y += fn * ny;
                     F.z += fn * nz;
                     if constexpr (FRIC) {
-                        const int m = m0 + u;
+                        const int m = lm[u];
                         const long long e = (long long)a * pt.max_nbr + m;
                         const float la = Rf[q] - 0.5f * delta, lb = Rb[u] - 0.5f * delta;
                         const float3 n = make_float3(nx, ny, nz);

@@ -180,7 +180,9 @@ struct Parts {
     double *Xb[2], *Vh[2];         // DEM sub-step buffers
     int *nbr, *nbr_cnt;            // neighbour lists [np][max_nbr]
     int max_nbr;
-    float4 *pairA, *pairB;         // per list entry: (d0, c0) and (dv0, gamma), see lbm_dem.cu
+    float4 *pairA, *pairB;         // per contact candidate: (d0, c0) and (dv0, gamma), see lbm_dem.cu
+    int2 *pairBM;                  // per contact candidate: (b, list position)
+    int *nact;                     // [np] contact candidates of the step
     double *Xbuild;                // centres when the lists were built
     int *rebuild;                  // [2]: rebuild[s & 1] = 1 asks the neighbour pass of step s to rebuild
     SFrame *frame[2];              // frames of the centres of even / odd steps
@@ -194,7 +196,7 @@ struct Parts {
     int fric;
     double kt, mu, ct;             // ct = -2 ln e_t / sqrt(pi^2 + ln^2 e_t) (0 for e_t = 1)
     double *Tc;                    // contact torque at the current position [np][3]
-    float4 *pairC;                 // per list entry: (spin of b at the start of the step, gamma_t)
+    float4 *pairC;                 // per contact candidate: (spin of b at the start of the step, gamma_t)
     float4 *tdisp;                 // per list entry: tangential displacement of the contact (xyz)
     unsigned long long *tmask;     // per sphere: bit m set = list entry m was in contact
     float4 *twall;                 // [np][2]: tangential displacement against the lower / upper wall
