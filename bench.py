@@ -146,6 +146,36 @@ def oracle_sample(box, nsph, seed_offset=0):
     return inputs.slurry_box(box=box, n=nsph, seed=inputs.SEED_BASE + 2 + seed_offset)
 
 
+def error_vs_fp64(precision, steps=200):
+    """Relative L2 velocity error (nodes fluid on both sides) and largest
+    relative sphere-force error of the GPU path at this storage precision
+    against the FP64 oracle, on a 64^3 sub-box of the production physics at
+    the same sphere density (31 spheres of radius 4), after 200 steps."""
+    import numpy as np
+
+    import oracle
+    from paper_1703_05158_gb300 import inputs, lbm
+
+    box = (64, 64, 64)
+    p = inputs.slurry_box(box=box, n=31, radius=4.0, seed=inputs.SEED_BASE + 8)
+    lat = lbm.Lattice(*box, precision=precision, max_particles=31, max_radius=4.0, **PHYS)
+    orc = oracle.Oracle(*box, **PHYS)
+    for o in (lat, orc):
+        o.set_particles(p["X"], V=p["V"], Om=p["Om"], R=p["R"])
+    lat.step(steps)
+    orc.step(steps)
+    _, ug = lat.fields()
+    _, uo = orc.fields()
+    fluid = (orc.owner() < 0) & (lat.owner() < 0)
+    a, b = ug[:, fluid].astype(np.float64), uo[:, fluid]
+    Fg, _ = lat.forces()
+    Fo, _ = orc.forces()
+    lat.close()
+    return {"relative_l2_velocity": float(np.linalg.norm(a - b) / np.linalg.norm(b)),
+            "max_relative_force": float((np.linalg.norm(Fg - Fo, axis=1) / np.linalg.norm(Fo, axis=1)).max()),
+            "case": "64^3 sub-box, 31 spheres R=4, %d steps, against the FP64 oracle" % steps}
+
+
 def cpu_baseline(steps=2):
     """The oracle as it stands on the host cores, on the full workload for a
     couple of steps (bounded sample)."""
@@ -313,6 +343,7 @@ def run_ours(args, rank, world, local_rank):
     # 19 + 19 populations of every fluid node once
     bytes_collide = nf * 2 * 19 * s + (2 if args.schedule == "overlap" else 1) * N + walls
     collide_ms = (phases["collide"] + phases["collide_far"]) / max(psteps, 1)
+    step_bytes = bytes_collide + 16 * info["links"]
     achieved = bytes_collide / (collide_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     traffic = profiled_traffic(args.precision)
@@ -332,7 +363,10 @@ def run_ours(args, rank, world, local_rank):
                      "peak": peak,
                      "peak_kind": "%s hbm_gbs" % peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": bytes_collide,
-                     "avg_launch_ms": collide_ms},
+                     "avg_launch_ms": collide_ms, "frac_of_nominal_7900": achieved / 7900.0,
+                     # the whole step: the collide bytes plus 16 B per cut link
+                     "step_bytes": step_bytes, "step_frac": step_bytes / (ms_max / args.steps * 1e-3) / 1e9 / peak},
+        "mflups_fluid": value * nf / N,
         "phases_ms_per_step": {k: v / max(psteps, 1) for k, v in phases.items()},
         "clocks": clk.summary(),
         "e2e": {"value": e2e_val, "unit": "MLUPS", "steps": ke,
@@ -344,6 +378,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if world == 1 and not args.no_cpu_baseline and not dense:
         line["cpu_baseline"] = cpu_baseline()
+    if world == 1 and not args.no_error_check and not dense:
+        line["error_vs_fp64"] = error_vs_fp64(args.precision)
     print(json.dumps(line), flush=True)
     lat.close()
 
@@ -494,6 +530,8 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "bf16", "fp16"], default="fp32")
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-error-check", action="store_true",
+                    help="skip the 64^3 velocity / force error against the FP64 oracle")
     ap.add_argument("--schedule", choices=["serial", "overlap"], default="serial",
                     help="order of the kernels inside a step (same results)")
     ap.add_argument("--mea", choices=["paper", "galilean"], default="paper",
