@@ -159,6 +159,14 @@ int lbm_zieb_state(lbm_handle h, double *out);
  * when the handle has no ZIEB face or vp is not finite. */
 int lbm_zieb_set_piston(lbm_handle h, double vp);
 
+/* Self-test of the failure path of the device-side waits (no compute):
+ * runs the bounded grid barrier of the cooperative DEM with a partner block
+ * that never arrives.  The wait gives up after its poll limit (about a
+ * second), the kernel returns, and the call returns LBM_ERR_TIMEOUT, which
+ * stays the handle's sticky status; the device context stays usable for
+ * other handles. */
+int lbm_selftest_wait(lbm_handle h);
+
 /* Free everything the handle holds (synchronises its stream first). */
 int lbm_destroy(lbm_handle h);
 

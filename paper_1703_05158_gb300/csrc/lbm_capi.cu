@@ -919,6 +919,14 @@ int lbm_sync(lbm_handle h) {
     return settle(h);
 }
 
+int lbm_selftest_wait(lbm_handle h) {
+    if (!h) return LBM_ERR_ARG;
+    DeviceScope ds(h->device);
+    const int rc = launch_wait_probe(h);
+    const int s = settle(h);
+    return rc ? rc : s;
+}
+
 }  // extern "C"
 
 // ---- batched form -----------------------------------------------------------

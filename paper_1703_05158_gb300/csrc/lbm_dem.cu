@@ -715,6 +715,17 @@ __device__ bool grid_barrier(unsigned *bar, unsigned target, int *status) {
     return ok != 0;
 }
 
+// Self-test of the bounded wait: one block waits at the grid barrier for a
+// second block that does not exist, so the wait runs out of polls, sets the
+// timeout status and returns.
+__global__ void k_wait_probe(unsigned *bar, int *status) { grid_barrier(bar, 2u, status); }
+
+int launch_wait_probe(lbm_s *h) {
+    if (cudaMemsetAsync(h->bar, 0, sizeof(unsigned), h->stream) != cudaSuccess) return LBM_ERR_CUDA;
+    k_wait_probe<<<1, 32, 0, h->stream>>>(h->bar, h->status);
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
 // FP64 velocity Verlet with centres and half-step velocities exchanged
 // through global memory (any number of spheres).  pt.V holds the full-step
 // velocity between sub-steps; pt.X stays the start-of-step centre until the

@@ -339,6 +339,7 @@ int launch_near_mark(lbm_s *h, uint8_t *near, uint8_t tag, const SFrame *frames,
                      cudaStream_t stream);
 int launch_collide_list(lbm_s *h, int parity, const int *list, const int *count, cudaStream_t stream);
 int launch_zieb(lbm_s *h, int P);  // ZIEB face after the step of parity P
+int launch_wait_probe(lbm_s *h);   // a bounded device wait that runs out (self-test)
 int launch_mark(lbm_s *h, int P, int corr);  // corr: momentum correction of the covered nodes
 int launch_refill(lbm_s *h, int parity);
 int launch_links(lbm_s *h, int parity);

@@ -38,7 +38,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_particles", "lbm_set_particle_l
            "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_handle", "lbm_batch_tune", "lbm_batch_step",
            "lbm_batch_sync", "lbm_channel_create", "lbm_channel_destroy", "lbm_channel_set_theta",
            "lbm_channel_forward", "lbm_channel_backward", "lbm_channel_drag", "lbm_channel_populations",
-           "lbm_channel_geometry", "lbm_zieb_state", "lbm_zieb_set_piston")
+           "lbm_channel_geometry", "lbm_zieb_state", "lbm_zieb_set_piston", "lbm_selftest_wait")
 
 
 SCHEDULES = {"serial": 0, "overlap": 1}
@@ -128,6 +128,7 @@ def load(build=True):
         lib.lbm_channel_drag.argtypes = [vp, dp]
         lib.lbm_channel_populations.argtypes = [vp, dp]
         lib.lbm_channel_geometry.argtypes = [vp, vp]
+        lib.lbm_selftest_wait.argtypes = [vp]
         lib.lbm_zieb_state.argtypes = [vp, dp]
         lib.lbm_zieb_set_piston.argtypes = [vp, ctypes.c_double]
         lib.lbm_error_string.argtypes = [ctypes.c_int]
@@ -257,6 +258,10 @@ def lbm_info(h):
 
 def lbm_sync(h):
     return _check(load().lbm_sync(h), "lbm_sync")
+
+
+def lbm_selftest_wait(h):
+    return _check(load().lbm_selftest_wait(h), "lbm_selftest_wait")
 
 
 def lbm_zieb_state(h):
