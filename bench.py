@@ -190,7 +190,25 @@ def cpu_baseline(steps=2):
     n = BOX[0] * BOX[1] * BOX[2]
     return {"value": n * steps / dt / 1e6, "unit": "MLUPS", "cores": int(os.environ.get("OMP_NUM_THREADS",
                                                                                         os.cpu_count())),
-            "kind": "oracle", "sample": "%d steps of the full 256^3 + 2000-sphere workload, FP64, %.1f s" % (steps, dt)}
+            "kind": "oracle", "sample": "%d steps of the full 256^3 + 2000-sphere workload, FP64, %.1f s" % (steps, dt),
+            "single_thread": single_thread_baseline()}
+
+
+def single_thread_baseline(steps=3):
+    """The oracle on one host thread (a child process with OMP_NUM_THREADS=1)
+    on a 64^3 box at the workload's sphere density (31 spheres of radius 4)."""
+    code = ("import time, bench, oracle\n"
+            "from paper_1703_05158_gb300 import inputs\n"
+            "p = inputs.slurry_box(box=(64, 64, 64), n=31, radius=4.0, seed=inputs.SEED_BASE + 8)\n"
+            "o = oracle.Oracle(64, 64, 64, **bench.PHYS)\n"
+            "o.set_particles(p['X'], V=p['V'], Om=p['Om'], R=p['R'])\n"
+            "t = time.perf_counter(); o.step(%d); print(time.perf_counter() - t)\n" % steps)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, stdout=subprocess.PIPE,
+                       stderr=subprocess.DEVNULL, text=True, timeout=600)
+    dt = float(r.stdout.strip().splitlines()[-1])
+    return {"value": 64 ** 3 * steps / dt / 1e6, "unit": "MLUPS", "cores": 1,
+            "sample": "%d steps of a 64^3 box with 31 spheres R=4 (the workload's density), %.1f s" % (steps, dt)}
 
 
 def max_over_ranks(x, world):
