@@ -78,6 +78,11 @@ typedef struct lbm_s *lbm_handle;
 #define LBM_SCHEDULE_SERIAL 0
 #define LBM_SCHEDULE_OVERLAP 1
 
+/* Execution of the DEM sub-steps. */
+#define LBM_DEM_AUTO 0
+#define LBM_DEM_CLUSTER 1
+#define LBM_DEM_GRID 2
+
 /* Momentum exchange on sphere links. */
 #define LBM_MEA_PAPER 0
 #define LBM_MEA_GALILEAN 1
@@ -110,9 +115,7 @@ typedef struct {
                                     other values: LBM_ERR_ARG */
     double kt;                 /* tangential contact stiffness (Eq. 2), >= 0 */
     double mu;                 /* Coulomb friction coefficient mu_s (Eq. 2), >= 0; friction acts
-                                  between spheres and against the walls when kt > 0 and mu > 0
-                                  (then LBM_ERR_UNSUPPORTED if max_particles exceeds what one
-                                  thread-block cluster of the DEM holds) */
+                                  between spheres and against the walls when kt > 0 and mu > 0 */
     double restitution_t;      /* tangential restitution in (0, 1], sets the dashpot gamma_t of
                                   Eq. 2 like restitution sets gamma_n; 1: no tangential damping */
     int32_t zieb;              /* 1: the plane z = 0 is a ZIEB face (Sect. 2.6) onto a virtual
@@ -126,6 +129,10 @@ typedef struct {
     int32_t mea;               /* momentum exchange: LBM_MEA_PAPER (Eqs. 25, 26) or LBM_MEA_GALILEAN
                                   (populations carry c - u_b, Wen, Zhang & Fang 2014; not in the
                                   paper); other values: LBM_ERR_ARG */
+    int32_t dem_mode;          /* how the DEM sub-steps run: LBM_DEM_AUTO (one thread-block
+                                  cluster up to 4096 spheres, else a cooperative grid),
+                                  LBM_DEM_CLUSTER or LBM_DEM_GRID; the same arithmetic either way;
+                                  other values: LBM_ERR_ARG */
 } lbm_params;
 
 typedef struct {

@@ -57,6 +57,7 @@ void release(lbm_s *h) {
                     h->pt.Xb[0], h->pt.Xb[1], h->pt.Vh[0], h->pt.Vh[1], h->pt.nbr, h->pt.nbr_cnt, h->pt.pairA,
                     h->pt.pairB, h->pt.Xbuild, h->pt.rebuild, h->pt.frame[0], h->pt.frame[1], h->pt.Fcorr,
                     h->pt.Tcorr, h->pt.Tc, h->pt.pairC, h->pt.tdisp, h->pt.tmask, h->pt.twall, h->zs, h->pt.pairBM, h->pt.nact,
+                    h->xbuf,
                     h->zpart, h->zcnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -221,6 +222,8 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
         return LBM_ERR_ARG;
     if (p.zieb != 0 && p.zieb != 1) return LBM_ERR_ARG;
     if (p.mea != LBM_MEA_PAPER && p.mea != LBM_MEA_GALILEAN) return LBM_ERR_ARG;
+    if (p.dem_mode != LBM_DEM_AUTO && p.dem_mode != LBM_DEM_CLUSTER && p.dem_mode != LBM_DEM_GRID)
+        return LBM_ERR_ARG;
     if (p.zieb && (!(p.zieb_area > 0.0) || !(p.zieb_volume > 0.0) || !std::isfinite(p.zieb_area) ||
                    !std::isfinite(p.zieb_volume) || !std::isfinite(p.zieb_piston_velocity)))
         return LBM_ERR_ARG;
@@ -355,6 +358,7 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     if (!rc) rc = dalloc(h, &pt.pairA, (size_t)M * kMaxNbr);
     if (!rc) rc = dalloc(h, &pt.pairB, (size_t)M * kMaxNbr);
     if (!rc) rc = dalloc(h, &pt.pairBM, (size_t)M * kMaxNbr);
+    if (!rc) rc = dalloc(h, &h->xbuf, 2 * 3 * (size_t)M);
     if (!rc) rc = dalloc(h, &pt.nact, (size_t)M);
     if (!rc) rc = dalloc(h, &pt.Xf, (size_t)M);
     for (int b = 0; b < 2 && !rc; ++b) {
@@ -409,8 +413,14 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
         h->sms = sms;
         if (!rc && h->dem_blocks < 1) rc = LBM_ERR_CUDA;
         h->dem_cluster = M > 0 ? dem_cluster_setup(M, false, h->pt.fric != 0) : 0;
-        // the tangential contact state lives in the cluster kernel only
-        if (!rc && M > 0 && h->pt.fric && h->dem_cluster == 0) rc = LBM_ERR_UNSUPPORTED;
+        h->dem_mode = p.dem_mode;
+        h->dem_grid_blocks = M > 0 ? dem_grid_setup(h->pt.fric != 0, sms) : 0;
+        const bool grid_fits = h->dem_grid_blocks > 0 && dem_grid_capacity(h->pt.fric != 0, h->dem_grid_blocks) >= M;
+        if (!grid_fits) h->dem_grid_blocks = 0;
+        // the tangential contact state lives in the cluster and grid forms only
+        if (!rc && M > 0 && h->pt.fric && h->dem_cluster == 0 && !grid_fits) rc = LBM_ERR_UNSUPPORTED;
+        if (!rc && M > 0 && p.dem_mode == LBM_DEM_CLUSTER && h->dem_cluster == 0) rc = LBM_ERR_UNSUPPORTED;
+        if (!rc && M > 0 && p.dem_mode == LBM_DEM_GRID && !grid_fits) rc = LBM_ERR_UNSUPPORTED;
     }
     if (!rc) {
         *h->status_host = 0;

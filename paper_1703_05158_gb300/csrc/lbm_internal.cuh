@@ -256,6 +256,9 @@ struct lbm_s {
     int sticky;              // first device error seen
     int dem_blocks, dem_threads;  // cooperative fallback grid
     int dem_cluster;              // CTAs of the one-cluster DEM kernel (0: use the fallback)
+    int dem_mode = 0;             // LBM_DEM_AUTO, LBM_DEM_CLUSTER or LBM_DEM_GRID
+    int dem_grid_blocks = 0;      // co-resident blocks of the grid form (0: unavailable)
+    float4 *xbuf = nullptr;       // grid form: [2][max_particles][3] sub-step exchange buffer
     // ZIEB face on z = 0: zs = [rho, rho, H_p, H_p, v_p] (rho and H_p ping-pong by
     // step parity), zpart / zcnt = [2][zblocks] per-block sums of u_z and node counts
     int zieb = 0, zblocks = 0;
@@ -353,6 +356,8 @@ int launch_owner(lbm_s *h, int32_t *owner);
 int launch_count_fluid(lbm_s *h);
 int dem_max_blocks(int threads, int *blocks_per_sm);
 int dem_cluster_setup(int max_particles, bool small = false, bool fric = false);
+int dem_grid_setup(bool fric, int sms);
+long long dem_grid_capacity(bool fric, int blocks);
 int link_capacity(double max_radius);
 size_t link_smem(int ext, int cap);
 int links_setup(int ext, int cap);

@@ -43,6 +43,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_particles", "lbm_set_particle_l
 
 SCHEDULES = {"serial": 0, "overlap": 1}
 MEAS = {"paper": 0, "galilean": 1}
+DEM_MODES = {"auto": 0, "cluster": 1, "grid": 2}
 
 
 class lbm_params(ctypes.Structure):
@@ -58,7 +59,7 @@ class lbm_params(ctypes.Structure):
         ("momentum_correction", ctypes.c_int32),
         ("kt", ctypes.c_double), ("mu", ctypes.c_double), ("restitution_t", ctypes.c_double),
         ("zieb", ctypes.c_int32), ("zieb_area", ctypes.c_double), ("zieb_volume", ctypes.c_double),
-        ("zieb_piston_velocity", ctypes.c_double), ("mea", ctypes.c_int32),
+        ("zieb_piston_velocity", ctypes.c_double), ("mea", ctypes.c_int32), ("dem_mode", ctypes.c_int32),
     ]
 
 
@@ -324,10 +325,11 @@ def lbm_batch_sync(b):
 def make_params(nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0), u_hi=(0.0, 0.0, 0.0),
                 rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16, precision="fp32", max_particles=0,
                 max_radius=4.0, stream=None, device=0, schedule="serial", momentum_correction=False, kt=0.0,
-                mu=0.0, restitution_t=1.0, zieb=None, mea="paper"):
+                mu=0.0, restitution_t=1.0, zieb=None, mea="paper", dem_mode="auto"):
     """lbm_params from keyword arguments (the Lattice constructor's); zieb:
     None or dict(area=A_p, volume=V_0, vp=v_p) for a ZIEB face on z = 0; mea:
-    "paper" or "galilean" (momentum exchange)."""
+    "paper" or "galilean" (momentum exchange); dem_mode: "auto", "cluster" or
+    "grid" (how the DEM sub-steps run)."""
     p = lbm_params()
     p.nx, p.ny, p.nz, p.periodic_z = nx, ny, nz, 0
     p.tau0, p.cs_smag = tau0, cs
@@ -344,6 +346,7 @@ def make_params(nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0
     p.momentum_correction = int(bool(momentum_correction))
     p.kt, p.mu, p.restitution_t = kt, mu, restitution_t
     p.mea = MEAS[mea] if isinstance(mea, str) else int(mea)
+    p.dem_mode = DEM_MODES[dem_mode] if isinstance(dem_mode, str) else int(dem_mode)
     if zieb is not None:
         p.zieb, p.zieb_area, p.zieb_volume = 1, zieb["area"], zieb["volume"]
         p.zieb_piston_velocity = zieb.get("vp", 0.0)
@@ -362,10 +365,10 @@ class Lattice:
     def __init__(self, nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0), u_hi=(0.0, 0.0, 0.0),
                  rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16, precision="fp32", max_particles=0,
                  max_radius=4.0, stream=None, device=0, schedule="serial", momentum_correction=False, kt=0.0,
-                 mu=0.0, restitution_t=1.0, zieb=None, mea="paper"):
+                 mu=0.0, restitution_t=1.0, zieb=None, mea="paper", dem_mode="auto"):
         p = make_params(nx, ny, nz, tau0, cs, g, u_lo, u_hi, rho_s, kn, restitution, dem_substeps, precision,
                         max_particles, max_radius, stream, device, schedule, momentum_correction, kt, mu,
-                        restitution_t, zieb, mea)
+                        restitution_t, zieb, mea, dem_mode)
         self.params = p
         self.h = lbm_create(p)
         self.shape = (nz, ny, nx)
