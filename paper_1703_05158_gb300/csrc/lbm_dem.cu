@@ -246,7 +246,11 @@ __device__ void contact_force(const Lat &L, const Parts &pt, int a, const double
     const int cnt = pt.nbr_cnt[a];
     for (int m = 0; m < cnt; ++m) {
         const int b = pt.nbr[(long long)a * pt.max_nbr + m];
-        double d[3] = {xa[0] - Xs[3 * b], xa[1] - Xs[3 * b + 1], xa[2] - Xs[3 * b + 2]};
+        // other blocks of the cooperative fallback write Xs / Vs within the
+        // kernel: read them through L2 (__ldcg), never from a stale L1 line
+        const double xb[3] = {__ldcg(Xs + 3 * b), __ldcg(Xs + 3 * b + 1), __ldcg(Xs + 3 * b + 2)};
+        const double vb[3] = {__ldcg(Vs + 3 * b), __ldcg(Vs + 3 * b + 1), __ldcg(Vs + 3 * b + 2)};
+        double d[3] = {xa[0] - xb[0], xa[1] - xb[1], xa[2] - xb[2]};
         min_image(L, d);
         const double Rs = Ra + pt.R[b];
         const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -256,8 +260,7 @@ __device__ void contact_force(const Lat &L, const Parts &pt, int a, const double
         if (!(delta > 0.0) || dist == 0.0) continue;
         const float id = (float)(1.0 / dist);
         const float nx = (float)d[0] * id, ny = (float)d[1] * id, nz = (float)d[2] * id;
-        const float vn = (float)(va[0] - Vs[3 * b]) * nx + (float)(va[1] - Vs[3 * b + 1]) * ny +
-                         (float)(va[2] - Vs[3 * b + 2]) * nz;
+        const float vn = (float)(va[0] - vb[0]) * nx + (float)(va[1] - vb[1]) * ny + (float)(va[2] - vb[2]) * nz;
         const double mb = sphere_mass(pt, b);
         const double meff = pt.fixed[b] ? ma : (pt.fixed[a] ? mb : ma * mb / (ma + mb));
         const float fn = kn * (float)delta - ce * sqrtf((float)meff * kn) * vn;
@@ -269,9 +272,9 @@ __device__ void contact_force(const Lat &L, const Parts &pt, int a, const double
             const double la = Ra - 0.5 * delta, lb = pt.R[b] - 0.5 * delta;
             double S[3], vr[3];
             for (int c = 0; c < 3; ++c) S[c] = la * wa[c] + lb * Ws[3 * b + c];
-            vr[0] = va[0] - Vs[3 * b] - (S[1] * n[2] - S[2] * n[1]);
-            vr[1] = va[1] - Vs[3 * b + 1] - (S[2] * n[0] - S[0] * n[2]);
-            vr[2] = va[2] - Vs[3 * b + 2] - (S[0] * n[1] - S[1] * n[0]);
+            vr[0] = va[0] - vb[0] - (S[1] * n[2] - S[2] * n[1]);
+            vr[1] = va[1] - vb[1] - (S[2] * n[0] - S[0] * n[2]);
+            vr[2] = va[2] - vb[2] - (S[0] * n[1] - S[1] * n[0]);
             open_contact_friction(pt, n, vr, (double)fn, pt.ct * sqrt(meff * pt.kt), la, F, T);
         }
     }
