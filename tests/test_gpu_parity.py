@@ -288,3 +288,33 @@ def test_full_size_slurry_box_sampled():
     idx = np.flatnonzero(fluid)
     idx = idx[inputs.rng(3).choice(len(idx), 200000, replace=False)]
     assert (np.abs(fg[:, idx] - fo[:, idx]) / np.abs(fo[:, idx])).max() <= POP_TOL
+
+
+def test_full_size_slurry_with_every_option_sampled():
+    """The benchmark box (256^3, 2000 spheres of radius 4) with every option
+    of the extra bench lines at once: momentum correction, the
+    Galilean-invariant exchange, tangential friction and a ZIEB face; three
+    steps (spheres move, so nodes are covered and uncovered) against the
+    oracle: geometry everywhere, every sphere's load, 200k sampled
+    populations, the cylinder density."""
+    p = inputs.slurry_box()
+    A = 256.0 * 256.0
+    zieb = dict(area=A, volume=40.0 * A, vp=0.005)
+    kw = dict(tau0=0.51, cs=0.17, u_hi=(0.05, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16,
+              kt=500.0, mu=0.3, restitution_t=0.6, momentum_correction=True, mea="galilean", zieb=zieb)
+    lat = lbm().Lattice(256, 256, 256, max_particles=len(p["R"]), max_radius=4.0, **kw)
+    orc = oracle.Oracle(256, 256, 256, **kw)
+    for o in (lat, orc):
+        o.set_particles(p["X"], V=p["V"], R=p["R"])
+    lat.step(3)
+    orc.step(3)
+    assert np.array_equal(lat.owner(), orc.owner())
+    ef, _, Fo, _ = force_error(lat, orc)
+    assert ef <= FORCE_TOL, ef
+    fo = orc.populations().reshape(19, -1)
+    fg = lat.populations().reshape(19, -1)
+    fluid = (orc.owner() < 0).reshape(-1)
+    idx = np.flatnonzero(fluid)
+    idx = idx[inputs.rng(7).choice(len(idx), 200000, replace=False)]
+    assert (np.abs(fg[:, idx] - fo[:, idx]) / np.abs(fo[:, idx])).max() <= POP_TOL
+    assert abs(lat.zieb_state()[0] - orc.zieb_state()[0]) <= 1e-6
