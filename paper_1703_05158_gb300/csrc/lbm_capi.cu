@@ -688,8 +688,10 @@ int lbm_step(lbm_handle h, int32_t nsteps) {
     }
     cudaStream_t A = h->stream, Bs = h->stream2;
     // Serial steps with spheres, unprofiled: replay the captured step graphs
-    // (the captures need a stream other than the legacy default stream).
-    if (!rc && parts && !ovl && !h->prof && nsteps >= 2 && h->stream) {
+    // (the captures need a stream other than the legacy default stream; they
+    // are kept until the spheres are set again, so single steps replay them
+    // too).
+    if (!rc && parts && !ovl && !h->prof && nsteps >= 1 && h->stream) {
         if (h->graph_stale || !h->graph[0] || !h->graph[1]) rc = capture_step_graphs(h);
         for (int it = 0; it < nsteps && !rc; ++it) {
             // the link / refill counters report the last step of the call
