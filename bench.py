@@ -213,7 +213,7 @@ def single_thread_baseline(steps=3):
 
 def max_over_ranks(x, world):
     """Maximum of a host float over the ranks of the job (every rank calls
-    it; NCCL on the GPU machine, gloo in the CPU tests)."""
+    it; NCCL with GPUs, gloo in the CPU tests)."""
     if world == 1:
         return float(x)
     import torch
