@@ -953,6 +953,8 @@ void batch_release(lbm_batch_s *b) {
         }
     if (b->dinst) cudaFree(b->dinst);
     if (b->chunks) cudaFree(b->chunks);
+    delete b->ctab;
+    b->ctab = nullptr;
     b->dinst = nullptr;
     b->chunks = nullptr;
     if (b->m) {
@@ -1012,6 +1014,20 @@ int batch_descriptors(lbm_batch_s *b) {
     if (cudaMemcpy(b->dinst, I.data(), I.size() * sizeof(Inst), cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
         return LBM_ERR_CUDA;
+    }
+    if (b->n <= kCollideTable) {
+        if (!b->ctab) b->ctab = new (std::nothrow) CollideTable();
+        if (!b->ctab) return LBM_ERR_NOMEM;
+        for (int i = 0; i < b->n; ++i) {
+            CInst &c = b->ctab->c[i];
+            c.L = I[i].L;
+            c.ph = I[i].ph;
+            c.f = I[i].f;
+            c.flag = I[i].flag;
+            c.status = I[i].status;
+            c.dnx = I[i].dnx;
+            c.dny = I[i].dny;
+        }
     }
     return LBM_OK;
 }
@@ -1240,7 +1256,7 @@ int lbm_batch_tune(lbm_batch b, int32_t *threads, int32_t *blocks, float *ms) {
         int2 *ch = nullptr;
         int nch = 0, bps = 0;
         rc = batch_chunks(b, tpb, &ch, &nch);
-        if (!rc) rc = collide_batch_occupancy(b->precision, P, tpb, minb, &bps);
+        if (!rc) rc = collide_batch_occupancy(b->precision, P, tpb, minb, &bps, b->ctab != nullptr);
         if (!rc && nch > 0 && bps > 0) {
             // persistent grids of 1/2 and 1 times the resident blocks, and one block per chunk
             const int cands[3] = {std::max(1, b->sms * bps / 2), b->sms * bps, nch};

@@ -168,6 +168,27 @@ __global__ void __launch_bounds__(TPB, MINB) k_collide_batch(const Inst *__restr
     }
 }
 
+// The same with the instances' parameters in a kernel-parameter table (up to
+// kCollideTable members): no shared-memory staging, and the constants are
+// read through the constant cache as in the single-instance kernel.
+template <int ODD, typename T, int TPB, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) k_collide_batch_tab(const __grid_constant__ CollideTable tab,
+                                                                  const int2 *__restrict__ chunks,
+                                                                  const int nchunks) {
+    const int c0 = (int)((long long)nchunks * blockIdx.x / gridDim.x);
+    const int c1 = (int)((long long)nchunks * (blockIdx.x + 1) / gridDim.x);
+    for (int c = c0; c < c1; ++c) {
+        const int2 ch = chunks[c];
+        const CInst &ci = tab.c[ch.x];
+        const int n = ch.y + (int)threadIdx.x;
+        if (n >= (int)ci.L.N) continue;
+        const int row = (int)ci.dnx.div((unsigned)n);
+        const int z = (int)ci.dny.div((unsigned)row);
+        sc_node<ODD, T>(ci.L, ci.ph, (T *)ci.f, ci.flag, ci.status, n - row * ci.L.nx, row - z * ci.L.ny, z, n,
+                        ci.flag[n]);
+    }
+}
+
 // 16-bit storage, two nodes (x, x+1), x even, per thread: each slot pair is
 // one aligned 32-bit word.  Even steps read and write the node's own words.
 // Odd steps read slot opp(i) at x - c_i: for c_x(i) = 0 that is again one
@@ -396,7 +417,10 @@ int launch_collide_list(lbm_s *h, int parity, const int *list, const int *count,
 
 template <int ODD, typename T, int TPB, int MINB>
 static cudaError_t collide_batch_t(const lbm_batch_s *b, int grid, const int2 *chunks, int nchunks) {
-    k_collide_batch<ODD, T, TPB, MINB><<<grid, TPB, 0, b->stream>>>(b->dinst, chunks, nchunks);
+    if (b->ctab)
+        k_collide_batch_tab<ODD, T, TPB, MINB><<<grid, TPB, 0, b->stream>>>(*b->ctab, chunks, nchunks);
+    else
+        k_collide_batch<ODD, T, TPB, MINB><<<grid, TPB, 0, b->stream>>>(b->dinst, chunks, nchunks);
     return cudaGetLastError();
 }
 
@@ -434,25 +458,26 @@ int launch_collide_batch(const lbm_batch_s *b, int P, int tpb, int minb, int gri
 }
 
 template <int ODD, typename T, int TPB, int MINB>
-static cudaError_t occ_t(int *bps) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_collide_batch<ODD, T, TPB, MINB>, TPB, 0);
+static cudaError_t occ_t(int *bps, bool table) {
+    return table ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_collide_batch_tab<ODD, T, TPB, MINB>, TPB, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_collide_batch<ODD, T, TPB, MINB>, TPB, 0);
 }
 
 template <typename T>
-static cudaError_t occ_ty(int P, int tpb, int minb, int *bps) {
+static cudaError_t occ_ty(int P, int tpb, int minb, int *bps, bool table) {
 #define LBM_CASE(t, m) \
-    if (tpb == t && minb == m) return P ? occ_t<1, T, t, m>(bps) : occ_t<0, T, t, m>(bps);
+    if (tpb == t && minb == m) return P ? occ_t<1, T, t, m>(bps, table) : occ_t<0, T, t, m>(bps, table);
     LBM_BATCH_SHAPES(LBM_CASE)
 #undef LBM_CASE
     return cudaErrorInvalidValue;
 }
 
-int collide_batch_occupancy(int precision, int P, int tpb, int minb, int *blocks_per_sm) {
+int collide_batch_occupancy(int precision, int P, int tpb, int minb, int *blocks_per_sm, bool table) {
     cudaError_t e = cudaErrorInvalidValue;
     switch (precision) {
-        case LBM_FP32: e = occ_ty<float>(P, tpb, minb, blocks_per_sm); break;
-        case LBM_BF16_DEV: e = occ_ty<__nv_bfloat16>(P, tpb, minb, blocks_per_sm); break;
-        case LBM_FP16_DEV: e = occ_ty<__half>(P, tpb, minb, blocks_per_sm); break;
+        case LBM_FP32: e = occ_ty<float>(P, tpb, minb, blocks_per_sm, table); break;
+        case LBM_BF16_DEV: e = occ_ty<__nv_bfloat16>(P, tpb, minb, blocks_per_sm, table); break;
+        case LBM_FP16_DEV: e = occ_ty<__half>(P, tpb, minb, blocks_per_sm, table); break;
     }
     if (e != cudaSuccess) cudaGetLastError();
     return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;

@@ -311,6 +311,23 @@ struct Inst {
     FastDiv dnx, dny;
 };
 
+// What the batched collide needs of one instance.  Up to kCollideTable
+// instances travel as one kernel-parameter table (read through the constant
+// cache, like the single-instance kernel's parameters).
+struct CInst {
+    Lat L;
+    Phys ph;
+    void *f;
+    uint8_t *flag;
+    int *status;
+    FastDiv dnx, dny;
+};
+constexpr int kCollideTable = 192;
+struct CollideTable {
+    CInst c[kCollideTable];
+};
+static_assert(sizeof(CollideTable) <= 32000, "kernel parameters are limited to 32764 bytes");
+
 }  // namespace lbm
 
 // A batch of independent simulations stepped together (lbm_batch_*).
@@ -325,6 +342,7 @@ struct lbm_batch_s {
     int ext = 0, cap = 0;         // link tile half width and list capacity (largest over members)
     int dem_cluster = 0;          // CTAs per instance cluster of the DEM kernel
     bool fric = false;            // a member has tangential friction: the DEM kernel that keeps its state
+    lbm::CollideTable *ctab = nullptr;  // host copy of the collide's parameter table (n <= kCollideTable)
     int precision = 0, device = 0, sms = 0;
     bool dirty = true;            // descriptors / graphs to be rebuilt
     cudaStream_t stream = nullptr;
@@ -366,7 +384,7 @@ int settle_handle(lbm_s *h);
 int launch_mark_batch(const lbm_batch_s *b, int sp);
 int launch_refill_batch(const lbm_batch_s *b, int P);
 int launch_collide_batch(const lbm_batch_s *b, int P, int tpb, int minb, int grid, const int2 *chunks, int nchunks);
-int collide_batch_occupancy(int precision, int P, int tpb, int minb, int *blocks_per_sm);
+int collide_batch_occupancy(int precision, int P, int tpb, int minb, int *blocks_per_sm, bool table);
 int launch_links_batch(const lbm_batch_s *b, int P);
 int links_setup_batch(int ext, int cap);
 int launch_neighbours_batch(const lbm_batch_s *b, int sp);
