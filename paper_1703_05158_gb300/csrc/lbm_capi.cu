@@ -112,14 +112,12 @@ inline int prof_mark(lbm_s *h, int k, cudaStream_t st) {
     return cudaEventRecord(h->ev[kProfEv * h->ev_used + k], st) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
-// Sync the stream and fold the device status into the sticky error.
+// Sync the stream and fold the device status into the sticky error (the
+// status word comes back to pinned host memory on the same stream, so one
+// synchronisation covers both).
 int settle(lbm_s *h) {
-    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
-        cudaGetLastError();
-        if (!h->sticky) h->sticky = LBM_ERR_CUDA;
-        return h->sticky;
-    }
-    if (cudaMemcpy(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    if (cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
         cudaGetLastError();
         if (!h->sticky) h->sticky = LBM_ERR_CUDA;
         return h->sticky;
