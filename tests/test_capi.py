@@ -1,6 +1,7 @@
 """Host-side checks of the C ABI that need no GPU: the library builds, loads
 and exports every entry point include/lbm.h declares, the binding names them
 all, and lbm_create rejects invalid parameters before touching the device."""
+import ctypes
 import os
 import re
 import subprocess
@@ -45,12 +46,12 @@ def test_error_strings():
 
 
 @pytest.mark.parametrize("field,value", [("tau0", 0.5), ("nx", 0), ("restitution", 0.0), ("dem_substeps", 0),
-                                         ("precision", 7), ("max_radius", 20.0)])
+                                         ("precision", 7), ("max_radius", 20.0), ("schedule", 9),
+                                         ("momentum_correction", 2), ("kt", -1.0), ("mu", -0.5),
+                                         ("restitution_t", 0.0), ("restitution_t", 1.5), ("zieb", 2),
+                                         ("mea", 5), ("dem_mode", 7)])
 def test_create_rejects_invalid_parameters(field, value):
-    p = lbm.lbm_params()
-    p.nx = p.ny = p.nz = 32
-    p.tau0, p.rho_particle, p.kn, p.restitution = 0.8, 2.5, 1e3, 0.8
-    p.dem_substeps, p.max_particles, p.max_radius = 4, 4, 4.0
+    p = lbm.make_params(32, 32, 32, 0.8, max_particles=4, max_radius=4.0, dem_substeps=4)
     setattr(p, field, value)
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_create(p)
@@ -70,3 +71,40 @@ def test_create_rejects_moving_wall_normal_and_periodic_z():
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_create(p)
     assert e.value.code == lbm.LBM_ERR_UNSUPPORTED
+
+
+def test_zieb_face_needs_a_cylinder_and_the_serial_schedule():
+    for zieb in (dict(area=0.0, volume=100.0), dict(area=10.0, volume=-1.0)):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_create(lbm.make_params(16, 16, 8, 0.8, zieb=zieb))
+        assert e.value.code == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(lbm.make_params(16, 16, 8, 0.8, schedule="overlap", zieb=dict(area=10.0, volume=100.0)))
+    assert e.value.code == lbm.LBM_ERR_UNSUPPORTED
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Compile a C program against include/lbm.h that prints the offset of
+    every field of the ABI structs, and compare with the ctypes layout."""
+    structs = {"lbm_params": lbm.lbm_params, "lbm_channel_params": lbm.lbm_channel_params,
+               "lbm_info_t": lbm.lbm_info_t}
+    lines = ['#include <stdio.h>', '#include "lbm.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line.strip():
+            a, b, c = line.split()
+            got[(a, b)] = int(c)
+    for cname, cls in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
