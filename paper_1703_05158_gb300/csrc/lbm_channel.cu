@@ -55,6 +55,10 @@ struct ChanGeo {
     const uint8_t *cut;     // [N]: 1 if some link x -> x + c_j is cut (then q is read)
     const float *q;         // [Q][N]: fraction of the cut link x -> x + c_j, -1 if not cut
     const uint32_t *plate;  // [N]: bit j set if x -> x + c_j ends in the plate
+    // neighbour masks (static geometry, for the reverse gather): bit i set if
+    // x + c_i is in the box and is an interior fluid node (mfl), also has a
+    // cut link (mcut), or is any fluid class, inlet / outlet included (many)
+    const uint32_t *mfl, *mcut, *many;
 };
 
 __device__ __forceinline__ int wrapy(int y, int ny) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); }
@@ -163,6 +167,28 @@ __global__ void k_chan_links(const int nx, const int ny, const int nz, const int
     }
     plate[n] = pm;
     cut[n] = any ? 1 : 0;
+}
+
+// Neighbour masks of every node (see ChanGeo).
+__global__ void k_chan_masks(const ChanGeo G, uint32_t *__restrict__ mfl, uint32_t *__restrict__ mcut,
+                             uint32_t *__restrict__ many) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    const int x = n % G.nx, y = (n / G.nx) % G.ny, z = n / (G.nx * G.ny);
+    uint32_t a = 0u, b = 0u, c = 0u;
+    for (int i = 0; i < Q; ++i) {
+        const int tn = nbr(G, x, y, z, rcx(i), rcy(i), rcz(i));
+        if (tn < 0) continue;
+        const uint8_t t = G.type[tn];
+        if (t == CH_FLUID) {
+            a |= 1u << i;
+            if (G.cut[tn]) b |= 1u << i;
+        }
+        if (is_fluid_type(t)) c |= 1u << i;
+    }
+    mfl[n] = a;
+    mcut[n] = b;
+    many[n] = c;
 }
 
 // ---- forward -----------------------------------------------------------------
@@ -476,7 +502,7 @@ __device__ __forceinline__ float eff(const ChanGeo &G, const float *__restrict__
 
 // Reverse step s: lambda^s from lambda^{s+1} (lam1) and f^s (fs; null for
 // the rest state f^0 = w), weight wd of D^s in J (0 outside the window).
-__global__ void __launch_bounds__(256) k_chan_adj(const ChanGeo G, const Phys ph, const float *__restrict__ lam1,
+__global__ void __launch_bounds__(256, 3) k_chan_adj(const ChanGeo G, const Phys ph, const float *__restrict__ lam1,
                                                   const float *__restrict__ fs, const float *__restrict__ rho_bar,
                                                   const float *__restrict__ ext, const float wd,
                                                   float *__restrict__ lam0, double *__restrict__ grad) {
@@ -493,14 +519,15 @@ __global__ void __launch_bounds__(256) k_chan_adj(const ChanGeo G, const Phys ph
             const uint32_t pm = G.plate[n];
             const bool cut = G.cut[n] != 0;
             const int yz0 = y + G.ny * z;
+            const uint32_t mf = G.mfl[n], mc = G.mcut[n], ma = G.many[n];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 float v = 0.f;
-                const int tn = nbr(G, x, y, z, rcx(i), rcy(i), rcz(i));
-                if (tn >= 0 && G.type[tn] == CH_FLUID) {
+                if ((mf >> i) & 1u) {  // x + c_i is an interior fluid node
+                    const int tn = nbr(G, x, y, z, rcx(i), rcy(i), rcz(i));
                     const int xt = x + rcx(i), yzt = wrapy(y + rcy(i), G.ny) + G.ny * (z + rcz(i));
                     v += eff(G, lam1, rho_bar, ext, tn, xt, yzt, i);  // regular pull of x + c_i
-                    const float qt = G.cut[tn] ? G.q[(size_t)i * G.N + tn] : -1.f;
+                    const float qt = ((mc >> i) & 1u) ? G.q[(size_t)i * G.N + tn] : -1.f;
                     if (qt >= 0.f && qt < 0.5f)
                         v += (1.f - 2.f * qt) * eff(G, lam1, rho_bar, ext, tn, xt, yzt, ropp(i));
                 }
@@ -509,8 +536,7 @@ __global__ void __launch_bounds__(256) k_chan_adj(const ChanGeo G, const Phys ph
                     if (qi >= 0.f) {
                         float a;
                         if (qi < 0.5f) {
-                            const int n2 = nbr(G, x, y, z, -rcx(i), -rcy(i), -rcz(i));
-                            a = (n2 >= 0 && is_fluid_type(G.type[n2])) ? 2.f * qi : 1.f;
+                            a = ((ma >> ropp(i)) & 1u) ? 2.f * qi : 1.f;  // x - c_i fluid
                         } else {
                             a = 1.f / (2.f * qi);
                         }
@@ -552,6 +578,7 @@ struct lbm_channel_s {
     uint8_t *type = nullptr, *cut = nullptr;
     float *q = nullptr;
     uint32_t *plate = nullptr;
+    uint32_t *mfl = nullptr, *mcut = nullptr, *many = nullptr;
     double *X = nullptr, *R = nullptr;
     float *G[2] = {nullptr, nullptr}, *lam[2] = {nullptr, nullptr};
     float *seg = nullptr;   // K states f^s of a segment
@@ -580,6 +607,9 @@ ChanGeo geo_of(const lbm_channel_s *c) {
     g.cut = c->cut;
     g.q = c->q;
     g.plate = c->plate;
+    g.mfl = c->mfl;
+    g.mcut = c->mcut;
+    g.many = c->many;
     return g;
 }
 
@@ -604,7 +634,7 @@ int calloc_dev(lbm_channel_s *c, T **p, size_t n) {
 }
 
 void chan_release(lbm_channel_s *c) {
-    void *ptrs[] = {c->type, c->cut, c->q, c->plate, c->X, c->R, c->G[0], c->G[1], c->lam[0], c->lam[1], c->seg, c->ckpt,
+    void *ptrs[] = {c->type, c->cut, c->q, c->plate, c->mfl, c->mcut, c->many, c->X, c->R, c->G[0], c->G[1], c->lam[0], c->lam[1], c->seg, c->ckpt,
                     c->fend, c->rho_bar, c->ext, c->drag, c->grad, c->status};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -700,6 +730,9 @@ int lbm_channel_create(const lbm_channel_params *prm, int32_t n, const double *p
     if (!rc) rc = calloc_dev(c, &c->cut, (size_t)c->N);
     if (!rc) rc = calloc_dev(c, &c->q, NQs);
     if (!rc) rc = calloc_dev(c, &c->plate, (size_t)c->N);
+    if (!rc) rc = calloc_dev(c, &c->mfl, (size_t)c->N);
+    if (!rc) rc = calloc_dev(c, &c->mcut, (size_t)c->N);
+    if (!rc) rc = calloc_dev(c, &c->many, (size_t)c->N);
     if (!rc) rc = calloc_dev(c, &c->X, 3 * (size_t)n);
     if (!rc) rc = calloc_dev(c, &c->R, (size_t)n);
     for (int k = 0; k < 2 && !rc; ++k) {
@@ -731,6 +764,10 @@ int lbm_channel_create(const lbm_channel_params *prm, int32_t n, const double *p
             k_chan_links<<<blocks, 256, 0, c->stream>>>(p.nx, p.ny, p.nz, n, c->X, c->R, c->type, c->q, c->plate,
                                                         c->cut);
         if (!rc) rc = launch_ok();
+        if (!rc) {
+            k_chan_masks<<<blocks, 256, 0, c->stream>>>(geo_of(c), c->mfl, c->mcut, c->many);
+            rc = launch_ok();
+        }
     }
     rc = chan_check(c, rc);
     if (rc) {
