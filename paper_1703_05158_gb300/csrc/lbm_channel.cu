@@ -257,7 +257,7 @@ __device__ __forceinline__ void warp_add(double v, double *dst) {
 // plate drag of G^s added to *drag (may be null).  With PULL the inlet and
 // outlet planes are k_chan_bc_step's.
 template <bool PULL>
-__global__ void __launch_bounds__(256) k_chan_step(const ChanGeo G, const Phys ph, const float *__restrict__ Gin,
+__global__ void __launch_bounds__(256, 4) k_chan_step(const ChanGeo G, const Phys ph, const float *__restrict__ Gin,
                                                    const float *__restrict__ fin, float *__restrict__ frec,
                                                    float *__restrict__ Gout, double *__restrict__ drag,
                                                    int *__restrict__ status) {
@@ -273,8 +273,22 @@ __global__ void __launch_bounds__(256) k_chan_step(const ChanGeo G, const Phys p
             } else {
                 const int x = n % G.nx, y = (n / G.nx) % G.ny, z = n / (G.nx * G.ny);
                 const bool cut = G.cut[n] != 0;
+                if (!cut) {
+                    // no cut link: every x - c_i is in the box (walls and the plate
+                    // cut the links that would leave it; x is interior), plain pull
+                    // with y periodic
+                    const int ym = y == 0 ? G.nx * (G.ny - 1) : -G.nx;
+                    const int yp = y == G.ny - 1 ? -G.nx * (G.ny - 1) : G.nx;
+                    const int zp = G.nx * G.ny;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) d[i] = pull(G, Gin, x, y, z, n, i, cut);
+                    for (int i = 0; i < Q; ++i) {
+                        const int off = -rcx(i) + (rcy(i) > 0 ? ym : (rcy(i) < 0 ? yp : 0)) - rcz(i) * zp;
+                        d[i] = Gin[(size_t)i * G.N + n + off];
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) d[i] = pull(G, Gin, x, y, z, n, i, cut);
+                }
             }
             if (frec)
 #pragma unroll
