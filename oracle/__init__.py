@@ -9,7 +9,12 @@ momentum balance, rest-state invariance, Couette and Poiseuille closed forms,
 the Smagorinsky reduction to BGK and its strain-rate relation, the lattice
 point count of a sphere, brute-force link fractions, bounce-back exactness on
 uniform flow, refill on a shifted sphere, drag on a periodic sphere array
-against Hasimoto/Sangani-Acrivos, and the DEM restitution and contact time.
+against Hasimoto/Sangani-Acrivos, and the DEM restitution and contact time;
+for the options: exact total-momentum conservation with the covered /
+uncovered momentum correction, the Coulomb sliding / rolling closed forms
+and exact linear and angular momentum of frictional collisions, the ZIEB
+face's rest state, face density and mass balance of a piston stroke, and
+the reduction of the Galilean-invariant exchange to Eqs. 25, 26 at rest.
 The coupled free-sphere trajectory itself has no closed form: parity
 unpinned beyond those invariants.
 """

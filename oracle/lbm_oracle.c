@@ -20,6 +20,12 @@
  *   6. DEM: linear spring-dashpot normal contact, Eq. (1), integrated by
  *      velocity Verlet (Sect. 2.1) in dem_substeps sub-steps
  *
+ * Options (off by default; the paper's own where marked): the tangential
+ * spring, dashpot and Coulomb cap of Eqs. (2), (3) (paper's); the ZIEB face
+ * of Sect. 2.6, Eqs. (8), (9), after step 5 (paper's); momentum correction
+ * of covered / uncovered nodes (Aidun, Lu & Ding 1998); the
+ * Galilean-invariant momentum exchange (Wen, Zhang & Fang 2014).
+ *
  * Arithmetic is FP64, except the geometric decisions (is a node inside a
  * sphere, which sphere owns it, the link fraction q and so which branch of
  * Eq. (19) applies) which are taken in FP32 from FP32 relative positions:
