@@ -984,7 +984,7 @@ int launch_dem(lbm_s *h) {
                                    : cudaLaunchKernelEx(&cfg, k_dem_cluster<false>, L, pt, fnext, sp, status);
         return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
     }
-    if (pt.fric) return LBM_ERR_UNSUPPORTED;  // the tangential state lives in the cluster kernel only
+    if (pt.fric) return LBM_ERR_UNSUPPORTED;  // the FP64 fallback keeps no tangential contact state
     if (cudaMemsetAsync(h->bar, 0, sizeof(unsigned), h->stream) != cudaSuccess) return LBM_ERR_CUDA;
     int blocks = (h->pt.np + h->dem_threads - 1) / h->dem_threads;
     if (blocks > h->dem_blocks) blocks = h->dem_blocks;
