@@ -14,9 +14,11 @@ for the options: exact total-momentum conservation with the covered /
 uncovered momentum correction, the Coulomb sliding / rolling closed forms
 and exact linear and angular momentum of frictional collisions, the ZIEB
 face's rest state, face density and mass balance of a piston stroke, and
-the reduction of the Galilean-invariant exchange to Eqs. 25, 26 at rest.
-The coupled free-sphere trajectory itself has no closed form: parity
-unpinned beyond those invariants.
+for the Galilean-invariant exchange its reduction to Eqs. 25, 26 at rest and
+its extra force on a translating sphere (the velocity times the fluid mass
+the moving bounce-back creates).  The coupled free-sphere trajectory itself
+has no closed form: parity unpinned beyond those invariants, as for the
+torque and the rotational part of the Galilean-invariant extra term.
 """
 import ctypes
 import os
