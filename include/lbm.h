@@ -31,10 +31,11 @@
  *                inputs during the call and keeps no caller pointer.
  *   Errors       0 on success, a negative LBM_ERR_* code otherwise.  Argument
  *                errors leave the state untouched.  Errors the device detects
- *                while stepping (capacity, divergence, a particle moving more
- *                than half a node per step, a wait that ran out) are sticky:
- *                lbm_step returns at once and lbm_sync, lbm_forces,
- *                lbm_fields, ... report them until the handle is destroyed.
+ *                while stepping (capacity, divergence, a particle moving a
+ *                quarter of a node or more in one step, a wait that ran
+ *                out) are sticky: lbm_step returns at once and lbm_sync,
+ *                lbm_forces, lbm_fields, ... report them until the handle
+ *                is destroyed.
  *   Threads      a handle is not thread-safe; all its work goes to its
  *                stream in call order.
  */
@@ -59,7 +60,7 @@ typedef struct lbm_s *lbm_handle;
 #define LBM_ERR_DIVERGED (-5)     /* non-positive or non-finite density found */
 #define LBM_ERR_UNSUPPORTED (-6)  /* valid request this build does not implement */
 #define LBM_ERR_TIMEOUT (-7)      /* a device-side wait gave up */
-#define LBM_ERR_GEOMETRY (-8)     /* a sphere moved >= 1/2 node in one step or left the box */
+#define LBM_ERR_GEOMETRY (-8)     /* a sphere moved >= 1/4 node in one step or left the box */
 
 /* Storage of the populations (arithmetic is FP32 in every case). */
 #define LBM_FP32 0       /* f_i - w_i stored as FP32 */
@@ -182,8 +183,10 @@ int lbm_destroy(lbm_handle h);
  * omega[n][3], radii radius[n] in (0, max_radius], and fixed[n] (NULL = none
  * fixed; 1 = prescribed motion: the centre moves with the given constant
  * velocity, velocity and spin never change).  Resets the fluid to rest, the
- * step counter to 0 and the external load to 0, and computes the node
- * geometry (Sect. 2.3).  LBM_ERR_CAPACITY if n > max_particles. */
+ * step counter to 0, the external load to 0, the tangential contact state
+ * (Eq. 2) and a ZIEB cylinder (density 1, H_p = 0, the piston velocity kept),
+ * and computes the node geometry (Sect. 2.3).  LBM_ERR_CAPACITY if
+ * n > max_particles. */
 int lbm_set_particles(lbm_handle h, int32_t n, const double *pos, const double *vel,
                       const double *omega, const double *radius, const uint8_t *fixed);
 
@@ -203,7 +206,9 @@ int lbm_set_populations(lbm_handle h, const double *f, int32_t where);
 int lbm_step(lbm_handle h, int32_t nsteps);
 
 /* Hydrodynamic force F[n][3] and torque T[n][3] (about the centre) of the
- * last step (Eqs. 25, 26); zero before the first step. */
+ * last step (Eqs. 25, 26, or their Galilean-invariant form under
+ * LBM_MEA_GALILEAN, plus the covered / uncovered-node momentum under
+ * momentum_correction); zero before the first step. */
 int lbm_forces(lbm_handle h, double *F, double *T, int32_t where);
 
 /* Current sphere centres, velocities and angular velocities ([n][3] each;
@@ -291,9 +296,11 @@ const char *lbm_error_string(int code);
  * Results are bitwise those of stepping each member alone with lbm_step. */
 typedef struct lbm_batch_s *lbm_batch;
 
-/* Create count >= 1 members.  LBM_ERR_ARG if the params differ in device,
- * precision or stream or one is invalid (as lbm_create), LBM_ERR_UNSUPPORTED
- * if the DEM cluster cannot hold the largest max_particles. */
+/* Create count >= 1 members.  Members run the serial order with one DEM
+ * cluster each: their schedule and dem_mode fields are not used.  LBM_ERR_ARG
+ * if the params differ in device, precision or stream or one is invalid (as
+ * lbm_create), LBM_ERR_UNSUPPORTED if the DEM cluster cannot hold the largest
+ * max_particles or a member has a ZIEB face. */
 int lbm_batch_create(const lbm_params *params, int32_t count, lbm_batch *out);
 
 /* Destroy the batch and its members (synchronises the stream first). */

@@ -194,7 +194,7 @@ const char *lbm_error_string(int code) {
         case LBM_ERR_DIVERGED: return "lattice diverged (non-positive or non-finite density)";
         case LBM_ERR_UNSUPPORTED: return "unsupported configuration";
         case LBM_ERR_TIMEOUT: return "device-side wait timed out";
-        case LBM_ERR_GEOMETRY: return "a sphere moved half a lattice unit in one step or left the box";
+        case LBM_ERR_GEOMETRY: return "a sphere moved a quarter of a lattice unit or more in one step, or left the box";
     }
     return "unknown error";
 }
