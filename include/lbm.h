@@ -125,7 +125,8 @@ typedef struct {
                                   LBM_SCHEDULE_SERIAL and no batch (else LBM_ERR_UNSUPPORTED);
                                   0: off; other values: LBM_ERR_ARG */
     double zieb_area;          /* piston / cylinder cross-section A_p > 0 (lattice units) */
-    double zieb_volume;        /* cylinder volume V_0 > zieb_area * (piston travel) */
+    double zieb_volume;        /* cylinder volume V_0 > zieb_area * (piston travel); a step at which
+                                  V_0 - A_p H_p <= 0 sets LBM_ERR_DIVERGED (sticky) */
     double zieb_piston_velocity; /* v_p: the piston displacement H_p grows by v_p per step */
     int32_t mea;               /* momentum exchange: LBM_MEA_PAPER (Eqs. 25, 26) or LBM_MEA_GALILEAN
                                   (populations carry c - u_b, Wen, Zhang & Fang 2014; not in the

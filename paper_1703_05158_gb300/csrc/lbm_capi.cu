@@ -209,7 +209,9 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     if (!(p.cs_smag >= 0.0) || !std::isfinite(p.cs_smag)) return LBM_ERR_ARG;
     if (!finite3(p.body_accel, 1) || !finite3(p.wall_vel_lo, 1) || !finite3(p.wall_vel_hi, 1)) return LBM_ERR_ARG;
     if (p.wall_vel_lo[2] != 0.0 || p.wall_vel_hi[2] != 0.0) return LBM_ERR_ARG;
-    if (!(p.rho_particle > 0.0) || !(p.kn >= 0.0) || !(p.restitution > 0.0 && p.restitution <= 1.0)) return LBM_ERR_ARG;
+    if (!(p.rho_particle > 0.0) || !(p.kn >= 0.0) || !(p.restitution > 0.0 && p.restitution <= 1.0) ||
+        !std::isfinite(p.rho_particle) || !std::isfinite(p.kn))
+        return LBM_ERR_ARG;
     if (p.dem_substeps < 1) return LBM_ERR_ARG;
     if (p.precision != LBM_FP32 && p.precision != LBM_BF16_DEV && p.precision != LBM_FP16_DEV) return LBM_ERR_ARG;
     if (p.max_particles < 0) return LBM_ERR_ARG;

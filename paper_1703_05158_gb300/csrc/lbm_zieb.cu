@@ -13,6 +13,10 @@
 // 19 populations become f^eq(rho^{n+1}, u).  The halfway bounce-back the
 // collide kernel pushed for the wall z = -1/2 is overwritten.
 //
+// A step at which V_0 - A_p H_p is no longer positive (the piston has
+// swept the cylinder) or rho^{n+1} is not finite sets the sticky divergence
+// status and keeps rho^n.
+//
 // One thread per face node.  Every block recomputes rho^{n+1} from the
 // state of the previous update (the per-block sums of u_z, reduced in block
 // order, so the result does not depend on timing); block 0 stores it.  The
@@ -29,7 +33,7 @@ __global__ void __launch_bounds__(kZiebThreads) k_zieb(const Lat L, T *__restric
                                                       const uint8_t *__restrict__ flag, const int P,
                                                       double *__restrict__ zs, double *__restrict__ zpart,
                                                       int *__restrict__ zcnt, const int nblk, const double A,
-                                                      const double V0) {
+                                                      const double V0, int *__restrict__ status) {
     __shared__ double s_rho1;
     __shared__ double red[kZiebThreads / 32];
     __shared__ int redc[kZiebThreads / 32];
@@ -51,7 +55,11 @@ __global__ void __launch_bounds__(kZiebThreads) k_zieb(const Lat L, T *__restric
         if (lane == 0) {
             const double vf = sc ? su / sc : 0.0;
             const double rho0 = zs[P], H = zs[2 + P], vp = zs[4];
-            const double rho1 = rho0 * exp((vp * A - vf * A) / (V0 - A * H));
+            double rho1 = rho0 * exp((vp * A - vf * A) / (V0 - A * H));
+            if (!(V0 - A * H > 0.0) || !isfinite(rho1)) {  // the piston has emptied the cylinder
+                if (blockIdx.x == 0) atomicOr(status, ST_DIVERGED);
+                rho1 = rho0;
+            }
             s_rho1 = rho1;
             if (blockIdx.x == 0) {
                 zs[P ^ 1] = rho1;
@@ -126,16 +134,16 @@ int launch_zieb(lbm_s *h, int P) {
     switch (h->precision) {
         case LBM_FP32:
             k_zieb<float><<<g, kZiebThreads, 0, h->stream>>>(h->L, (float *)h->f, h->flag, P, h->zs, h->zpart,
-                                                             h->zcnt, h->zblocks, h->zA, h->zV0);
+                                                             h->zcnt, h->zblocks, h->zA, h->zV0, h->status);
             break;
         case LBM_BF16_DEV:
             k_zieb<__nv_bfloat16><<<g, kZiebThreads, 0, h->stream>>>(h->L, (__nv_bfloat16 *)h->f, h->flag, P,
                                                                      h->zs, h->zpart, h->zcnt, h->zblocks, h->zA,
-                                                                     h->zV0);
+                                                                     h->zV0, h->status);
             break;
         case LBM_FP16_DEV:
             k_zieb<__half><<<g, kZiebThreads, 0, h->stream>>>(h->L, (__half *)h->f, h->flag, P, h->zs, h->zpart,
-                                                              h->zcnt, h->zblocks, h->zA, h->zV0);
+                                                              h->zcnt, h->zblocks, h->zA, h->zV0, h->status);
             break;
         default: return LBM_ERR_ARG;
     }

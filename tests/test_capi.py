@@ -49,7 +49,10 @@ def test_error_strings():
                                          ("precision", 7), ("max_radius", 20.0), ("schedule", 9),
                                          ("momentum_correction", 2), ("kt", -1.0), ("mu", -0.5),
                                          ("restitution_t", 0.0), ("restitution_t", 1.5), ("zieb", 2),
-                                         ("mea", 5), ("dem_mode", 7)])
+                                         ("mea", 5), ("dem_mode", 7), ("tau0", float("inf")),
+                                         ("cs_smag", float("nan")), ("kn", float("inf")),
+                                         ("rho_particle", float("inf")), ("kt", float("inf")),
+                                         ("max_radius", float("nan")), ("max_radius", 0.0), ("nx", 14)])
 def test_create_rejects_invalid_parameters(field, value):
     p = lbm.make_params(32, 32, 32, 0.8, max_particles=4, max_radius=4.0, dem_substeps=4)
     setattr(p, field, value)
@@ -73,8 +76,22 @@ def test_create_rejects_moving_wall_normal_and_periodic_z():
     assert e.value.code == lbm.LBM_ERR_UNSUPPORTED
 
 
+def test_create_rejects_non_finite_vectors_and_lattices_beyond_32_bit_offsets():
+    for field in ("body_accel", "wall_vel_lo", "wall_vel_hi"):
+        p = lbm.make_params(32, 32, 32, 0.8)
+        getattr(p, field)[0] = float("nan")
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_create(p)
+        assert e.value.code == lbm.LBM_ERR_ARG
+    # 19 slots of 1024^2 * 2050 nodes exceed the kernels' 32-bit element offsets
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(lbm.make_params(1024, 1024, 2048, 0.8))
+    assert e.value.code == lbm.LBM_ERR_UNSUPPORTED
+
+
 def test_zieb_face_needs_a_cylinder_and_the_serial_schedule():
-    for zieb in (dict(area=0.0, volume=100.0), dict(area=10.0, volume=-1.0)):
+    for zieb in (dict(area=0.0, volume=100.0), dict(area=10.0, volume=-1.0),
+                 dict(area=10.0, volume=100.0, vp=float("nan"))):
         with pytest.raises(lbm.LbmError) as e:
             lbm.lbm_create(lbm.make_params(16, 16, 8, 0.8, zieb=zieb))
         assert e.value.code == lbm.LBM_ERR_ARG

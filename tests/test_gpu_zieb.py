@@ -99,6 +99,26 @@ def test_zieb_needs_the_serial_schedule_and_no_batch():
         lat.zieb_state()
 
 
+def test_an_emptied_cylinder_sets_the_divergence_status():
+    """Eq. 8 divides by the cylinder volume left, V_0 - A_p H_p.  A piston
+    that passes the bottom of the cylinder (here after one step: V_0 = A_p,
+    v_p = 2) makes the next update report LBM_ERR_DIVERGED, which stays
+    sticky; without the check the second update would silently shrink the
+    density back to about 1."""
+    L = lbm()
+    shape = (24, 20, 16)
+    A = float(shape[0] * shape[1])
+    lat = L.Lattice(*shape, tau0=0.8, zieb=dict(area=A, volume=A, vp=2.0))
+    lat.step(1)
+    lat.sync()  # the first update sees V_0 - A_p H_p = A_p > 0
+    with pytest.raises(L.LbmError) as e:
+        lat.step(1)
+        lat.sync()
+    assert e.value.code == L.LBM_ERR_DIVERGED
+    with pytest.raises(L.LbmError):
+        lat.step(1)  # sticky
+
+
 @pytest.mark.parametrize("precision", ["fp16", "bf16"])
 def test_zieb_with_16_bit_storage_follows_the_fp32_path(precision):
     """16-bit deviation storage under a piston stroke: the cylinder density
