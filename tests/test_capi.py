@@ -1,11 +1,13 @@
 """Host-side checks of the C ABI that need no GPU: the library builds, loads
 and exports every entry point include/lbm.h declares, the binding names them
-all, and lbm_create rejects invalid parameters before touching the device."""
+all, lbm_create rejects invalid parameters before touching the device, and
+the link kernel's tile index arithmetic is exact for every radius it takes."""
 import ctypes
 import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_1703_05158_gb300 import build as libbuild
@@ -125,3 +127,23 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_link_tile_decode_by_multiply_high_is_exact_for_every_allowed_radius():
+    """The link kernel splits a tile index t < B^3 into (x, y, z) with
+    __umulhi(t, 2^32 / B + 1) in place of t / B (B = 2 ext + 1, ext =
+    ceil(max_radius) + 2); check the quotients for every t and every radius
+    the ABI accepts (max_radius <= 16), and that the kernel still uses this
+    form.  The 16-bit list of a sphere's own tile nodes needs B^3 <= 2^16."""
+    src = open(os.path.join(ROOT, "paper_1703_05158_gb300", "csrc", "lbm_links.cu")).read()
+    assert src.count("mB = 0xFFFFFFFFu / B + 1u, mB2 = 0xFFFFFFFFu / (B * B) + 1u") == 2
+    for R in range(1, 17):
+        B = 2 * (R + 2) + 1
+        B2 = B * B
+        assert B2 * B <= 1 << 16
+        mB, mB2 = 0xFFFFFFFF // B + 1, 0xFFFFFFFF // B2 + 1
+        t = np.arange(B2 * B, dtype=np.uint64)
+        z = (t * np.uint64(mB2)) >> np.uint64(32)
+        assert np.array_equal(z, t // np.uint64(B2))
+        r = t - z * np.uint64(B2)
+        assert np.array_equal((r * np.uint64(mB)) >> np.uint64(32), r // np.uint64(B))
