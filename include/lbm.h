@@ -301,7 +301,9 @@ typedef struct lbm_batch_s *lbm_batch;
  * cluster each: their schedule and dem_mode fields are not used.  LBM_ERR_ARG
  * if the params differ in device, precision or stream or one is invalid (as
  * lbm_create), LBM_ERR_UNSUPPORTED if the DEM cluster cannot hold the largest
- * max_particles or a member has a ZIEB face. */
+ * max_particles, a member has a ZIEB face, or a member with spheres has nx or
+ * ny below 2 (ceil(r) + 2) + 3 for r the largest max_radius of the batch (the
+ * link kernel tiles every member's spheres with the batch's largest tile). */
 int lbm_batch_create(const lbm_params *params, int32_t count, lbm_batch *out);
 
 /* Destroy the batch and its members (synchronises the stream first). */

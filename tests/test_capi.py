@@ -147,3 +147,20 @@ def test_link_tile_decode_by_multiply_high_is_exact_for_every_allowed_radius():
         assert np.array_equal(z, t // np.uint64(B2))
         r = t - z * np.uint64(B2)
         assert np.array_equal((r * np.uint64(mB)) >> np.uint64(32), r // np.uint64(B))
+
+
+def test_batch_rejects_a_member_box_narrower_than_the_shared_link_tile():
+    """Alone, a 20 x 20 box takes spheres up to radius 4 (tile 2 (4 + 2) + 3
+    = 15 nodes); batched with a radius-8 member, whose tile of 23 nodes the
+    link kernel uses for every member, it is refused before any device
+    work.  A member without spheres is not tiled and stays accepted."""
+    small = lbm.make_params(20, 20, 16, 0.8, max_particles=2, max_radius=4.0)
+    large = lbm.make_params(64, 64, 32, 0.8, max_particles=2, max_radius=8.0)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_batch_create([small, large])
+    assert e.value.code == lbm.LBM_ERR_UNSUPPORTED
+    fluid_only = lbm.make_params(20, 20, 16, 0.8)
+    try:  # passes the check; creating the members then needs a device
+        lbm.lbm_batch_destroy(lbm.lbm_batch_create([fluid_only, large]))
+    except lbm.LbmError as e:
+        assert e.code != lbm.LBM_ERR_UNSUPPORTED
