@@ -179,8 +179,9 @@ int lbm_selftest_wait(lbm_handle h);
 /* Free everything the handle holds (synchronises its stream first). */
 int lbm_destroy(lbm_handle h);
 
-/* Place n spheres (host arrays): centres pos[n][3] (x, y in [0, n) after
- * wrapping; z in (-1/2, nz - 1/2)), velocities vel[n][3], angular velocities
+/* Place n spheres (host arrays): centres pos[n][3] (x in [0, nx), y in
+ * [0, ny): the caller wraps periodic coordinates; z in (-1/2, nz - 1/2);
+ * else LBM_ERR_ARG), velocities vel[n][3], angular velocities
  * omega[n][3], radii radius[n] in (0, max_radius], and fixed[n] (NULL = none
  * fixed; 1 = prescribed motion: the centre moves with the given constant
  * velocity, velocity and spin never change).  Resets the fluid to rest, the
