@@ -706,6 +706,9 @@ int lbm_channel_create(const lbm_channel_params *prm, int32_t n, const double *p
     *out = nullptr;
     const lbm_channel_params &p = *prm;
     if (p.nx < 8 || p.ny < 1 || p.nz < 2 || !(p.tau0 > 0.5) || !(p.cs_smag >= 0.0)) return LBM_ERR_ARG;
+    if (!std::isfinite(p.tau0) || !std::isfinite(p.cs_smag) || !std::isfinite(p.inlet_peak) ||
+        !std::isfinite(p.body_accel_x))
+        return LBM_ERR_ARG;
     if (p.steps < 1 || p.avg_from < 1 || p.avg_from > p.steps || p.checkpoint_every < 1) return LBM_ERR_ARG;
     if ((long long)p.nx * p.ny * p.nz * Q >= (1ll << 31)) return LBM_ERR_UNSUPPORTED;
     // obstacles stay clear of the inlet / outlet planes and their neighbours
@@ -803,7 +806,9 @@ int lbm_channel_destroy(lbm_channel c) {
 }
 
 int lbm_channel_set_theta(lbm_channel c, const double *theta) {
-    if (!c || !theta || !std::isfinite(theta[0]) || !std::isfinite(theta[1]) || !(theta[2] >= 0.0)) return LBM_ERR_ARG;
+    if (!c || !theta || !std::isfinite(theta[0]) || !std::isfinite(theta[1]) || !(theta[2] >= 0.0) ||
+        !std::isfinite(theta[2]))
+        return LBM_ERR_ARG;
     for (int k = 0; k < 3; ++k) c->theta[k] = theta[k];
     set_phys(c);
     c->have_forward = false;

@@ -164,3 +164,45 @@ def test_batch_rejects_a_member_box_narrower_than_the_shared_link_tile():
         lbm.lbm_batch_destroy(lbm.lbm_batch_create([fluid_only, large]))
     except lbm.LbmError as e:
         assert e.code != lbm.LBM_ERR_UNSUPPORTED
+
+
+def _channel_params(**kw):
+    p = lbm.lbm_channel_params()
+    p.nx, p.ny, p.nz = 48, 20, 24
+    p.tau0, p.cs_smag, p.body_accel_x, p.inlet_peak = 0.6, 0.15, 1e-6, 0.04
+    p.plate_lo[:] = [20, 4, 6]
+    p.plate_hi[:] = [23, 15, 17]
+    p.steps, p.avg_from, p.checkpoint_every = 40, 21, 10
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("field,value", [("nx", 7), ("nz", 1), ("tau0", 0.5), ("tau0", float("inf")),
+                                         ("cs_smag", -0.1), ("cs_smag", float("inf")),
+                                         ("inlet_peak", float("nan")), ("body_accel_x", float("inf")),
+                                         ("steps", 0), ("avg_from", 0), ("avg_from", 41),
+                                         ("checkpoint_every", 0)])
+def test_channel_create_rejects_invalid_parameters(field, value):
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_channel_create(_channel_params(**{field: value}), np.zeros((0, 3)), np.zeros(0))
+    assert e.value.code == lbm.LBM_ERR_ARG
+
+
+def test_channel_create_keeps_obstacles_clear_of_the_inlet_and_outlet():
+    """The plate and every sphere stay off the inlet / outlet planes and their
+    neighbours (x - R > 1, x + R < nx - 2; plate 2 <= x <= nx - 3)."""
+    cases = [(_channel_params(), np.array([[4.0, 10.0, 12.0]]), np.array([3.0])),  # x - R = 1
+             (_channel_params(), np.array([[43.5, 10.0, 12.0]]), np.array([3.0])),  # x + R = nx - 1.5
+             (_channel_params(), np.array([[20.0, float("nan"), 12.0]]), np.array([3.0])),
+             (_channel_params(), np.array([[20.0, 10.0, 12.0]]), np.array([0.0]))]
+    p = _channel_params()
+    p.plate_lo[0] = 1
+    cases.append((p, np.zeros((0, 3)), np.zeros(0)))
+    p = _channel_params()
+    p.plate_hi[0] = 46
+    cases.append((p, np.zeros((0, 3)), np.zeros(0)))
+    for prm, X, R in cases:
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_channel_create(prm, X, R)
+        assert e.value.code == lbm.LBM_ERR_ARG
