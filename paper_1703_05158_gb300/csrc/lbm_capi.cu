@@ -548,6 +548,9 @@ int lbm_set_particles(lbm_handle h, int32_t n, const double *pos, const double *
 
 int lbm_set_particle_load(lbm_handle h, const double *force, const double *torque, int32_t where) {
     if (!h || (where != LBM_HOST && where != LBM_DEVICE)) return LBM_ERR_ARG;
+    if (where == LBM_HOST && h->pt.np > 0 &&
+        ((force && !finite3(force, h->pt.np)) || (torque && !finite3(torque, h->pt.np))))
+        return LBM_ERR_ARG;
     if (h->sticky) return h->sticky;
     DeviceScope ds(h->device);
     const size_t v3 = 3 * sizeof(double) * (size_t)h->pt.np;
