@@ -15,6 +15,10 @@ tangential spring and dashpot, Coulomb cap), dry (no lattice).
   which fixes the contact point at the middle of the overlap and the sign of
   every tangential term; the contact dissipates energy.
 * Friction off (mu = 0) leaves the frictionless oracle bit for bit.
+* The tangential force lies in the contact's tangent plane even while the
+  normal turns under a loaded displacement (a sphere sliding, then rolling,
+  over a fixed sphere): with an elastic normal law the contact force along
+  n is exactly k_n delta at every step.
 """
 import numpy as np
 import pytest
@@ -168,3 +172,39 @@ def test_a_contact_that_opens_forgets_its_tangential_displacement():
     assert second
     for u, v in zip(a.particles(), b.particles()):
         assert np.array_equal(u, v)
+
+
+def test_tangential_force_stays_in_the_tangent_plane_while_the_normal_turns():
+    """A sphere pressed onto the top of a fixed sphere by a constant load
+    m g along -z and launched sideways slides, rolls and is carried round
+    the fixed sphere, so the contact normal turns by tens of degrees while
+    the stored displacement delta_t carries a load of up to mu f_n.  With
+    e = 1 the normal law is k_n delta alone, so at every step in contact the
+    force along n = (X_a - X_b) / |X_a - X_b| must be k_n delta, which holds
+    only if delta_t is turned into the tangent plane as n moves (a
+    displacement kept as a fixed vector would tilt the spring force out of
+    that plane by about |f_t| times the angle turned)."""
+    Ra, Rb, kt, g = 3.0, 4.0, 500.0, 1e-2
+    m = RHO_S * 4.0 / 3.0 * np.pi * Ra ** 3
+    o = oracle.Oracle(32, 32, 40, tau0=1.0, rho_s=RHO_S, kn=KN, restitution=1.0, dem_substeps=16, fluid=False,
+                      kt=kt, mu=0.3, restitution_t=0.6)
+    X = np.array([[16.0, 16.0, 20.0 + Ra + Rb - m * g / KN], [16.0, 16.0, 20.0]])
+    o.set_particles(X, V=np.array([[0.02, 0.0, 0.0], [0.0, 0.0, 0.0]]), R=np.array([Ra, Rb]),
+                    fixed=np.array([0, 1], dtype=np.uint8))
+    o.set_load(F=np.array([[0.0, 0.0, -m * g], [0.0, 0.0, 0.0]]))
+    tilt, ft_ratio, touching = [], 0.0, 0
+    for _ in range(400):
+        o.step(1)
+        Xs = o.particles()[0]
+        d = Xs[0] - Xs[1]
+        delta = Ra + Rb - np.linalg.norm(d)
+        if delta <= 0.0 or Xs[0, 2] - Ra <= -0.5:
+            continue  # contact open (or the wall touched)
+        n = d / np.linalg.norm(d)
+        F = o.contact_forces()[0]
+        fn = F @ n
+        assert abs(fn - KN * delta) <= 1e-10 * np.linalg.norm(F), (fn, KN * delta)
+        touching += 1
+        tilt.append(np.degrees(np.arccos(n[2])))
+        ft_ratio = max(ft_ratio, np.linalg.norm(F - fn * n) / fn)
+    assert touching >= 50 and max(tilt) - min(tilt) > 30.0 and ft_ratio > 0.1
