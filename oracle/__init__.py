@@ -11,8 +11,9 @@ point count of a sphere, brute-force link fractions, bounce-back exactness on
 uniform flow, refill on a shifted sphere, drag on a periodic sphere array
 against Hasimoto/Sangani-Acrivos, and the DEM restitution and contact time;
 for the options: exact total-momentum conservation with the covered /
-uncovered momentum correction, the Coulomb sliding / rolling closed forms
-and exact linear and angular momentum of frictional collisions, the ZIEB
+uncovered momentum correction, the Coulomb sliding / rolling closed forms,
+exact linear and angular momentum of frictional collisions and a tangential
+force confined to the tangent plane as the contact normal turns, the ZIEB
 face's rest state, face density and mass balance of a piston stroke, and
 for the Galilean-invariant exchange its reduction to Eqs. 25, 26 at rest and
 its extra force on a translating sphere (the velocity times the fluid mass
