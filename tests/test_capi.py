@@ -1,7 +1,8 @@
 """Host-side checks of the C ABI that need no GPU: the library builds, loads
 and exports every entry point include/lbm.h declares, the binding names them
 all, lbm_create rejects invalid parameters before touching the device, and
-the link kernel's tile index arithmetic is exact for every radius it takes."""
+the link kernel's tile index arithmetic is exact and the per-sphere link and
+refill capacities hold the worst case for every radius the ABI takes."""
 import ctypes
 import os
 import re
@@ -206,3 +207,45 @@ def test_channel_create_keeps_obstacles_clear_of_the_inlet_and_outlet():
         with pytest.raises(lbm.LbmError) as e:
             lbm.lbm_channel_create(prm, X, R)
         assert e.value.code == lbm.LBM_ERR_ARG
+
+
+def _d3q19_moving():
+    c = [v for v in np.ndindex(3, 3, 3) if 0 < sum(abs(k - 1) for k in v) <= 2]
+    return np.array(c) - 1
+
+
+def _ball_nodes(R, X):
+    e = int(np.ceil(R)) + 2
+    b = np.floor(X).astype(int)
+    g = np.stack(np.meshgrid(*[np.arange(b[k] - e, b[k] + e + 1) for k in range(3)], indexing="ij"), -1)
+    return g.reshape(-1, 3)
+
+
+def test_per_sphere_capacities_hold_the_worst_case_up_to_radius_16():
+    """The link kernel keeps a sphere's cut links in shared memory (capacity
+    ceil(80 r^2) + 64) and the refill kernel its uncovered nodes (a fixed
+    list); brute-force counts at sampled sub-node centre offsets (and the
+    symmetric ones) stay below both, with the sphere moving just under the
+    0.25 nodes a step allows, for radii up to the ABI's 16."""
+    src_links = open(os.path.join(ROOT, "paper_1703_05158_gb300", "csrc", "lbm_links.cu")).read()
+    a, b = re.search(r"std::ceil\(([\d.]+) \* r \* r\) \+ (\d+)", src_links).groups()
+    src_geo = open(os.path.join(ROOT, "paper_1703_05158_gb300", "csrc", "lbm_geometry.cu")).read()
+    refill_cap = int(re.search(r"constexpr int kRefillCap = (\d+);", src_geo).group(1))
+    c = _d3q19_moving()
+    assert len(c) == 18
+    rng = np.random.default_rng(11)
+    for R in (2.5, 4.0, 8.0, 16.0):
+        cap = int(np.ceil(float(a) * R * R)) + int(b)
+        offsets = [np.zeros(3), np.full(3, 0.5)] + [rng.uniform(0.0, 1.0, 3) for _ in range(12)]
+        most_links, most_uncovered = 0, 0
+        for off in offsets:
+            X = 40.0 + off
+            g = _ball_nodes(R, X)
+            inside = ((g - X) ** 2).sum(1) < R * R
+            fluid = g[~inside]
+            most_links = max(most_links, sum(int((((fluid + cj) - X) ** 2).sum(1).__lt__(R * R).sum()) for cj in c))
+            v = rng.normal(size=3)
+            d = 0.2499 * v / np.linalg.norm(v)
+            most_uncovered = max(most_uncovered, int((inside & (((g - X - d) ** 2).sum(1) >= R * R)).sum()))
+        assert most_links < cap, (R, most_links, cap)
+        assert most_uncovered < refill_cap, (R, most_uncovered)
