@@ -263,18 +263,22 @@ int lbm_profile_read(lbm_handle h, double *ms, int64_t *steps);
 /* lbm_fields to host memory without allocating device memory.  lbm_fields
  * with host outputs stages the data through a stream-ordered temporary
  * (cudaMallocAsync); some callers cannot allow that: an application whose
- * framework allocator already holds the device's memory, or a loop that
- * must not allocate (a real-time step loop, code run inside CUDA stream
- * capture).  This entry point stages through a fixed 16 MiB array built into
- * the library instead, which every GPU that loads the library holds until the
- * process exits; it calls no device allocation routine.  The paper has no
- * counterpart: this is a service of the library.
+ * framework allocator already holds the device's memory, or a step loop
+ * that must not allocate (a real-time loop).  This entry point stages
+ * through a fixed 16 MiB array built into the library instead; it calls no
+ * device allocation routine.  The paper has no counterpart: this is a
+ * service of the library.
  *   rho[N], u[3][N]: host buffers (either may be NULL), as lbm_fields.
  *   LBM_ERR_CAPACITY if nx*ny*nz > LBM_NOALLOC_MAX_NODES.
- * The first call on a device looks up the array's device address there, so
- * make one call before any stream capture.  All calls on a device share the
- * array; calls whose work overlaps on the same GPU (handles on different
- * streams used from different threads) race on it. */
+ * The first call on a device looks up the array's device address there.
+ * With lazy module loading (the CUDA default) the driver commits the
+ * array's 16 MiB on that device at this first call, not when the library
+ * loads, and holds it until the process exits: make the first call at
+ * start-up, before a framework allocator takes the device's memory (if the
+ * driver cannot commit it, the call returns LBM_ERR_NOMEM).  Synchronises the
+ * handle's stream, like lbm_fields to host memory.  All calls on a device
+ * share the array; calls whose work overlaps on the same GPU (handles on
+ * different streams used from different threads) race on it. */
 int lbm_fields_noalloc(lbm_handle h, float *rho, float *u);
 
 /* Wait for the handle's stream and return its sticky device status. */

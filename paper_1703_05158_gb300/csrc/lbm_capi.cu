@@ -67,7 +67,8 @@ void release(lbm_s *h) {
         std::free(h->ev);
         h->ev = nullptr;
     }
-    void *ovl[] = {h->near[0], h->near[1], h->near_list[0], h->near_list[1], h->near_cnt};
+    void *ovl[] = {h->near[0], h->near[1], h->near_list[0], h->near_list[1], h->near_cnt,
+                   h->far_list[0], h->far_list[1], h->far_cnt};
     for (void *p : ovl)
         if (p) cudaFree(p);
     cudaEvent_t evs[] = {h->ev_cf, h->ev_nm[0], h->ev_nm[1], h->ev_join};
@@ -375,8 +376,9 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
     // overlapped schedule (spheres only): near tags, second stream, events
     h->overlap = M > 0 && p.schedule == LBM_SCHEDULE_OVERLAP;
     if (!rc && h->overlap) {
-        // groups of one 32-byte sector of a slot row
-        h->near_shift = h->esize == 4 ? 3 : 4;
+        // groups of 64 bytes of a slot row (the DRAM access granularity), so
+        // the near and far collides never share one
+        h->near_shift = h->esize == 4 ? 4 : 5;
         h->near_ngx = (p.nx + (1 << h->near_shift) - 1) >> h->near_shift;
         h->near_groups = (long long)h->near_ngx * p.ny * p.nz;
         const long long NG = h->near_groups;
@@ -388,6 +390,9 @@ int lbm_create(const lbm_params *prm, lbm_handle *out) {
         if (!rc) rc = dalloc(h, &h->near_list[0], (size_t)cap);
         if (!rc) rc = dalloc(h, &h->near_list[1], (size_t)cap);
         if (!rc) rc = dalloc(h, &h->near_cnt, 2);
+        if (!rc) rc = dalloc(h, &h->far_list[0], (size_t)NG);
+        if (!rc) rc = dalloc(h, &h->far_list[1], (size_t)NG);
+        if (!rc) rc = dalloc(h, &h->far_cnt, 2);
         bool ok = !rc && cudaStreamCreateWithPriority(&h->stream2, cudaStreamNonBlocking, prio_low) == cudaSuccess;
         cudaEvent_t *evs[] = {&h->ev_cf, &h->ev_nm[0], &h->ev_nm[1], &h->ev_join};
         for (cudaEvent_t *e : evs) ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
@@ -532,7 +537,7 @@ int lbm_set_particles(lbm_handle h, int32_t n, const double *pos, const double *
             rc = LBM_ERR_CUDA;
         if (!rc)
             rc = launch_near_mark(h, h->near[0], near_tag(0), h->pt.frame[0], h->near_list[0], h->near_cnt,
-                                  h->stream);
+                                  h->far_list[0], h->far_cnt, h->stream);
         cudaEvent_t evs[] = {h->ev_cf, h->ev_nm[0], h->ev_nm[1]};
         for (cudaEvent_t e : evs)
             if (!rc && cudaEventRecord(e, h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
@@ -723,7 +728,7 @@ int lbm_step(lbm_handle h, int32_t nsteps) {
             // work of steps s-1, s and the near collisions of step s touch
             if (!rc) rc = ok(cudaStreamWaitEvent(Bs, h->ev_nm[cur], 0));
             if (!rc) rc = prof_mark(h, E6, Bs);
-            if (!rc) rc = launch_stream_collide(h, P, 1, h->near[cur], near_tag(s), Bs);
+            if (!rc) rc = launch_collide_list(h, P, h->far_list[cur], h->far_cnt + cur, Bs);
             if (!rc) rc = prof_mark(h, E7, Bs);
             if (!rc) rc = ok(cudaEventRecord(h->ev_cf, Bs));
         }
@@ -739,7 +744,7 @@ int lbm_step(lbm_handle h, int32_t nsteps) {
             if (!rc && near_tag(s + 1) == 1) rc = ok(cudaMemsetAsync(h->near[nxt], 0, (size_t)h->near_groups, A));
             if (!rc)
                 rc = launch_near_mark(h, h->near[nxt], near_tag(s + 1), h->pt.frame[cur], h->near_list[nxt],
-                                      h->near_cnt + nxt, A);
+                                      h->near_cnt + nxt, h->far_list[nxt], h->far_cnt + nxt, A);
             if (!rc) rc = ok(cudaEventRecord(h->ev_nm[nxt], A));
             if (!rc) rc = ok(cudaStreamWaitEvent(A, h->ev_cf, 0));
         } else {

@@ -1,20 +1,24 @@
 // Node geometry and refill (Sect. 2.3), one CTA per sphere over its bounding
 // box.
 //
-// flag[n] (bit 0 = solid for every kernel that reads it):
-//   0 fluid
-//   1 solid, owner[n] = sphere of the current geometry
-//   3 solid at the previous geometry, not yet re-marked (the link kernel of
-//     the previous step turns its sphere's nodes from 1 to 3)
-//   2 fluid now, solid at the previous step (the refill turns 3 into 2; the
-//     collide kernel turns 2 into 0)
+// flag[n] (bit 0 = solid):
+//   0       fluid
+//   1 or 3  solid, owner[n] = its sphere: the marks of a step of even step
+//           count write 1, those of an odd step 3 (the mark value `cur` of
+//           the step), so a solid node of the previous geometry that the
+//           current marks did not take keeps the other value
+//   2       fluid now, solid at the previous step (the refill turns nodes of
+//           the other mark value into 2; the collide kernel turns 2 into 0)
 //
 //   mark:   nodes inside sphere p at the current centre, unless a
 //           neighbouring sphere that also contains the node has a smaller
-//           |x - X| - R (ties to the smaller index) -> 1, owner p
-//   refill: nodes left at 3 take the equilibrium (Eq. 9) at the surface
-//           velocity of their previous sphere and at the mean density of the
-//           neighbours fluid before and after (flag 0), then become 2.
+//           |x - X| - R (ties to the smaller index) -> cur, owner p
+//   refill: nodes of sphere p left at the previous step's mark value take
+//           the equilibrium (Eq. 9) at the surface velocity of p and at the
+//           mean density of the neighbours fluid before and after (flag 0),
+//           then become 2.
+// After the refill every solid node carries the current mark value, and
+// bit 0 is the fluid / solid class for every reader.
 //
 // Inside tests and keys are FP32 on relative coordinates
 // (float)(x - b) - (float)(X - b), b = floor(X) (the sphere frames written
@@ -85,9 +89,9 @@ __device__ __forceinline__ int mark_node(const Lat &L, const SFrame &F, const SF
     return x + L.nx * (y + L.ny * z);
 }
 
-// The plain marks: flag 1 and owner p on every node sphere p wins.
+// The plain marks: flag cur and owner p on every node sphere p wins.
 __device__ __forceinline__ void mark_body(const Lat &L, const Parts &pt, const SFrame *__restrict__ fcur,
-                                          uint8_t *__restrict__ flag, int32_t *__restrict__ owner) {
+                                          uint8_t *__restrict__ flag, int32_t *__restrict__ owner, const uint8_t cur) {
     const int p = blockIdx.x;
     __shared__ SFrame nf[MAX_NBR_SMEM];
     __shared__ int nid[MAX_NBR_SMEM];
@@ -103,7 +107,7 @@ __device__ __forceinline__ void mark_body(const Lat &L, const Parts &pt, const S
     for (int t = threadIdx.x; t < B3; t += blockDim.x) {
         const int n = mark_node(L, F, nf, nid, cnt, p, e, B, t);
         if (n < 0) continue;
-        flag[n] = 1;
+        flag[n] = cur;
         owner[n] = p;
     }
 }
@@ -121,7 +125,7 @@ __device__ __forceinline__ void mark_body(const Lat &L, const Parts &pt, const S
 template <typename T>
 __device__ __forceinline__ void mark_corr_body(const Lat &L, const Parts &pt, const SFrame *__restrict__ fcur,
                                                uint8_t *__restrict__ flag, int32_t *__restrict__ owner,
-                                               const T *__restrict__ f, const int P) {
+                                               const T *__restrict__ f, const int P, const uint8_t cur) {
     constexpr int kCovRound = 1024;
     const int p = blockIdx.x;
     __shared__ SFrame nf[MAX_NBR_SMEM];
@@ -153,7 +157,7 @@ __device__ __forceinline__ void mark_corr_body(const Lat &L, const Parts &pt, co
             const int n = mark_node(L, F, nf, nid, cnt, p, e, B, t);
             if (n < 0) continue;
             if (prev[t - t0] == 0) clist[atomicAdd(&ccount, 1)] = n;
-            flag[n] = 1;
+            flag[n] = cur;
             owner[n] = p;
         }
         __syncthreads();
@@ -215,9 +219,10 @@ __device__ __forceinline__ void mark_corr_body(const Lat &L, const Parts &pt, co
 template <typename T, bool CORR>
 __global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
                                               uint8_t *__restrict__ flag, int32_t *__restrict__ owner,
-                                              const T *__restrict__ f, const int P, const int corr) {
-    if (CORR && corr) mark_corr_body<T>(L, pt, fcur, flag, owner, f, P);
-    else mark_body(L, pt, fcur, flag, owner);
+                                              const T *__restrict__ f, const int P, const int corr,
+                                              const uint8_t cur) {
+    if (CORR && corr) mark_corr_body<T>(L, pt, fcur, flag, owner, f, P, cur);
+    else mark_body(L, pt, fcur, flag, owner, cur);
 }
 
 // Batched: instance blockIdx.y at step parity sp (also the population
@@ -227,8 +232,9 @@ __global__ void __launch_bounds__(256) k_mark_b(const Inst *__restrict__ I, cons
     const Inst &a = I[blockIdx.y];
     if (blockIdx.x == 0 && threadIdx.x < 2) a.ctr[threadIdx.x] = 0ull;
     if ((int)blockIdx.x >= a.pt.np) return;
-    if (CORR && a.pt.corr) mark_corr_body<T>(a.L, a.pt, a.pt.frame[sp], a.flag, a.owner, (const T *)a.f, sp);
-    else mark_body(a.L, a.pt, a.pt.frame[sp], a.flag, a.owner);
+    const uint8_t cur = mark_value(sp);
+    if (CORR && a.pt.corr) mark_corr_body<T>(a.L, a.pt, a.pt.frame[sp], a.flag, a.owner, (const T *)a.f, sp, cur);
+    else mark_body(a.L, a.pt, a.pt.frame[sp], a.flag, a.owner, cur);
 }
 
 // One CTA per sphere: collect the uncovered nodes of its previous bounding
@@ -242,8 +248,9 @@ __device__ __forceinline__ void refill_body(const Lat &L, const SFrame *__restri
                                             const SFrame *__restrict__ fprev, T *__restrict__ f,
                                             uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
                                             const int P, unsigned long long *__restrict__ ctr,
-                                            int *__restrict__ status, const Parts &pt) {
+                                            int *__restrict__ status, const Parts &pt, const uint8_t cur) {
     __shared__ int list[kRefillCap];
+    const uint8_t prev_mark = (uint8_t)(4 - cur);  // the other mark value: the previous step's geometry
     __shared__ int count;
     const int p = blockIdx.x;
     const SFrame Fp = fprev[p];  // the node geometry of the previous step was built from this centre
@@ -256,7 +263,7 @@ __device__ __forceinline__ void refill_body(const Lat &L, const SFrame *__restri
         if (z < 0 || z >= L.nz) continue;
         const int y = wrapi(by + (t / B) % B - e, L.ny), x = wrapi(bx + t % B - e, L.nx);
         const int n = x + L.nx * (y + L.ny * z);
-        if (flag[n] != 3 || owner[n] != p) continue;
+        if (flag[n] != prev_mark || owner[n] != p) continue;
         const int k = atomicAdd(&count, 1);
         if (k < kRefillCap) list[k] = n;
         else atomicOr(status, ST_TILE);
@@ -363,8 +370,8 @@ __global__ void __launch_bounds__(256, 4) k_refill(const Lat L, const SFrame *__
                                                 const SFrame *__restrict__ fprev, T *__restrict__ f,
                                                 uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
                                                 const int P, unsigned long long *__restrict__ ctr,
-                                                int *__restrict__ status, const Parts pt) {
-    refill_body<T, CORR>(L, fcur, fprev, f, flag, owner, P, ctr, status, pt);
+                                                int *__restrict__ status, const Parts pt, const uint8_t cur) {
+    refill_body<T, CORR>(L, fcur, fprev, f, flag, owner, P, ctr, status, pt, cur);
 }
 
 // Batched: instance blockIdx.y; parity P is also the step parity.
@@ -373,7 +380,7 @@ __global__ void __launch_bounds__(256, 4) k_refill_b(const Inst *__restrict__ I,
     const Inst &a = I[blockIdx.y];
     if ((int)blockIdx.x >= a.pt.np) return;
     refill_body<T, CORR>(a.L, a.pt.frame[P], a.pt.frame[P ^ 1], (T *)a.f, a.flag, a.owner, P, a.ctr, a.status,
-                         a.pt);
+                         a.pt, mark_value(P));
 }
 
 // Near set of step s+1, from the centres the geometry of step s uses.
@@ -393,13 +400,17 @@ __global__ void __launch_bounds__(256, 4) k_refill_b(const Inst *__restrict__ I,
 // centred at X has sum_a max(0, |x_a - X_a| - 2)^2 < R^2; the test below
 // adds `margin` to R for the FP32 rounding of the sphere test of k_mark.
 // A group (2^shift nodes along x) is tagged when any of its nodes passes.
-// Thread (0, 0) also clears the count of the list the same stream builds
-// next.
+// Thread (0, 0) also clears the counts of the near and far lists the same
+// stream builds next.
 __global__ void __launch_bounds__(256) k_near_mark(const Lat L, const SFrame *__restrict__ fr, const float margin,
                                                    uint8_t *__restrict__ near, const uint8_t tag, const int ngx,
-                                                   const int shift, int *__restrict__ count) {
+                                                   const int shift, int *__restrict__ count,
+                                                   int *__restrict__ far_count) {
     const int p = blockIdx.x;
-    if (p == 0 && threadIdx.x == 0) *count = 0;
+    if (p == 0 && threadIdx.x == 0) {
+        *count = 0;
+        *far_count = 0;
+    }
     const SFrame F = fr[p];
     const float Rg = F.R + margin, R2 = Rg * Rg;
     // |ox - fr| < Rg + 2 with fr in [0, 1): ox in [-(ceil(Rg) + 2), ceil(Rg) + 2]
@@ -417,17 +428,19 @@ __global__ void __launch_bounds__(256) k_near_mark(const Lat L, const SFrame *__
     }
 }
 
-// Compaction of the entries tagged `tag` into list[0 .. *count), ascending
-// within each 4096-entry chunk (one chunk per block, one atomic per block;
-// the chunks land in any order).  *count must be 0 on entry.
+// Compaction of the entries tagged `tag` into list[0 .. *count) and of the
+// others into far[0 .. *far_count), each ascending within each 4096-entry
+// chunk (one chunk per block, one atomic per list and block; the chunks land
+// in any order).  Both counts must be 0 on entry.
 constexpr int kListPerThread = 16;
 __global__ void __launch_bounds__(256) k_near_list(const uint8_t *__restrict__ near, const uint8_t tag,
                                                    const long long N, int *__restrict__ list,
-                                                   int *__restrict__ count) {
-    __shared__ int warp_sum[8];
-    __shared__ int base;
+                                                   int *__restrict__ count, int *__restrict__ far,
+                                                   int *__restrict__ far_count) {
+    __shared__ int warp_sum[2][8];
+    __shared__ int base[2];
     const long long n0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * kListPerThread;
-    unsigned bits = 0;
+    unsigned bits = 0, valid = 0;
     if (n0 + kListPerThread <= N) {
         const uint4 v = *(const uint4 *)(near + n0);  // chunk starts are multiples of 16 bytes
         const unsigned t4 = 0x01010101u * tag;
@@ -437,63 +450,79 @@ __global__ void __launch_bounds__(256) k_near_list(const uint8_t *__restrict__ n
             const unsigned m = __vcmpeq4(w[k], t4);  // 0xff in each matching byte
             bits |= (((m >> 7) & 1u) | ((m >> 14) & 2u) | ((m >> 21) & 4u) | ((m >> 28) & 8u)) << (4 * k);
         }
+        valid = 0xffffu;
     } else {
-        for (int k = 0; k < kListPerThread && n0 + k < N; ++k)
+        for (int k = 0; k < kListPerThread && n0 + k < N; ++k) {
+            valid |= 1u << k;
             if (near[n0 + k] == tag) bits |= 1u << k;
+        }
     }
-    const int c = __popc(bits);
+    unsigned sel[2] = {bits, valid & ~bits};  // near, far
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int inc = c;  // inclusive scan over the warp
+    int c[2], inc[2];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += v;
+    for (int a = 0; a < 2; ++a) {
+        c[a] = __popc(sel[a]);
+        inc[a] = c[a];  // inclusive scan over the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc[a], o);
+            if (lane >= o) inc[a] += v;
+        }
+        if (lane == 31) warp_sum[a][wid] = inc[a];
     }
-    if (lane == 31) warp_sum[wid] = inc;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 2) {
+        const int a = threadIdx.x;
         int tot = 0;
         for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-            const int v = warp_sum[k];
-            warp_sum[k] = tot;
+            const int v = warp_sum[a][k];
+            warp_sum[a][k] = tot;
             tot += v;
         }
-        base = tot ? atomicAdd(count, tot) : 0;
+        base[a] = tot ? atomicAdd(a == 0 ? count : far_count, tot) : 0;
     }
     __syncthreads();
-    int o = base + warp_sum[wid] + inc - c;
-    while (bits) {
-        const int k = __ffs(bits) - 1;
-        bits &= bits - 1;
-        list[o++] = (int)(n0 + k);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        int *out = a == 0 ? list : far;
+        int o = base[a] + warp_sum[a][wid] + inc[a] - c[a];
+        unsigned b = sel[a];
+        while (b) {
+            const int k = __ffs(b) - 1;
+            b &= b - 1;
+            out[o++] = (int)(n0 + k);
+        }
     }
 }
 
-int launch_near_mark(lbm_s *h, uint8_t *near, uint8_t tag, const SFrame *frames, int *list, int *count,
-                     cudaStream_t stream) {
-    k_near_mark<<<h->pt.np, 256, 0, stream>>>(h->L, frames, 0.05f, near, tag, h->near_ngx, h->near_shift, count);
+int launch_near_mark(lbm_s *h, uint8_t *near, uint8_t tag, const SFrame *frames, int *list, int *count, int *far,
+                     int *far_count, cudaStream_t stream) {
+    k_near_mark<<<h->pt.np, 256, 0, stream>>>(h->L, frames, 0.05f, near, tag, h->near_ngx, h->near_shift, count,
+                                              far_count);
     const long long per_block = 256ll * kListPerThread;
     const long long blocks = (h->near_groups + per_block - 1) / per_block;
-    k_near_list<<<(unsigned)blocks, 256, 0, stream>>>(near, tag, h->near_groups, list, count);
+    k_near_list<<<(unsigned)blocks, 256, 0, stream>>>(near, tag, h->near_groups, list, count, far, far_count);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
 template <bool CORR>
 int mark_launch(lbm_s *h, int P, int corr) {
     const SFrame *fcur = h->pt.frame[h->steps & 1];
+    const uint8_t cur = mark_value((int)(h->steps & 1));
     const dim3 g(h->pt.np);
     switch (h->precision) {
         case LBM_FP32:
             k_mark<float, CORR><<<g, 256, 0, h->stream>>>(h->L, h->pt, fcur, h->flag, h->owner,
-                                                           (const float *)h->f, P, corr);
+                                                           (const float *)h->f, P, corr, cur);
             break;
         case LBM_BF16_DEV:
             k_mark<__nv_bfloat16, CORR><<<g, 256, 0, h->stream>>>(h->L, h->pt, fcur, h->flag, h->owner,
-                                                                   (const __nv_bfloat16 *)h->f, P, corr);
+                                                                   (const __nv_bfloat16 *)h->f, P, corr, cur);
             break;
         case LBM_FP16_DEV:
             k_mark<__half, CORR><<<g, 256, 0, h->stream>>>(h->L, h->pt, fcur, h->flag, h->owner,
-                                                            (const __half *)h->f, P, corr);
+                                                            (const __half *)h->f, P, corr, cur);
             break;
         default: return LBM_ERR_ARG;
     }
@@ -508,7 +537,7 @@ template <typename T, bool CORR>
 void refill_launch(lbm_s *h, int parity) {
     const SFrame *fcur = h->pt.frame[h->steps & 1], *fprev = h->pt.frame[(h->steps + 1) & 1];
     k_refill<T, CORR><<<h->pt.np, 256, 0, h->stream>>>(h->L, fcur, fprev, (T *)h->f, h->flag, h->owner, parity,
-                                                         h->ctr, h->status, h->pt);
+                                                         h->ctr, h->status, h->pt, mark_value((int)(h->steps & 1)));
 }
 
 int launch_refill(lbm_s *h, int parity) {

@@ -62,6 +62,10 @@ __device__ __forceinline__ int rw36(int i) {
     return i == 0 ? 12 : (rcx(i) * rcx(i) + rcy(i) * rcy(i) + rcz(i) * rcz(i) == 1 ? 2 : 1);
 }
 
+// Flag value of the solid nodes marked by a step of step parity sp (1 or
+// 3, bit 0 set); the other value marks the previous step's geometry.
+__host__ __device__ constexpr uint8_t mark_value(int sp) { return (uint8_t)(1 + 2 * (sp & 1)); }
+
 // Device status bits (sticky, OR-ed by kernels).
 enum : int {
     ST_DIVERGED = 1,
@@ -77,18 +81,25 @@ struct Store;
 template <>
 struct Store<float> {
     static __device__ __forceinline__ float ld(const float *p) { return *p; }
+    static __device__ __forceinline__ float ldcg(const float *p) { return __ldcg(p); }  // through L2 only
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
     static __device__ __forceinline__ float rt(float v) { return v; }  // v as stored and read back
 };
 template <>
 struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ float ldcg(const __nv_bfloat16 *p) {
+        return __uint_as_float((unsigned)__ldcg((const unsigned short *)p) << 16);
+    }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
     static __device__ __forceinline__ float rt(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 };
 template <>
 struct Store<__half> {
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
+    static __device__ __forceinline__ float ldcg(const __half *p) {
+        return __half2float(__ushort_as_half(__ldcg((const unsigned short *)p)));
+    }
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
     static __device__ __forceinline__ float rt(float v) { return __half2float(__float2half_rn(v)); }
 };
@@ -275,13 +286,15 @@ struct lbm_s {
     cudaStream_t chain;      // highest priority; runs lbm_step's main-stream work when the caller's stream
                              // does not have that priority (null otherwise)
     cudaEvent_t ev_join;     // hand-over between the caller's stream and `chain`
-    // Tags are kept per group of 2^near_shift consecutive nodes along x (one
-    // 32-byte sector of a slot row): group (x >> near_shift) of row
-    // y + ny z is tag entry row * near_ngx + (x >> near_shift).
+    // Tags are kept per group of 2^near_shift consecutive nodes along x (64
+    // bytes of a slot row, the DRAM access granularity): group (x >>
+    // near_shift) of row y + ny z is tag entry row * near_ngx + (x >> near_shift).
     int near_shift, near_ngx;
     long long near_groups;   // rows * near_ngx
     int *near_list[2];       // near groups of step parity 0 / 1, compacted
     int *near_cnt;           // [2] their counts
+    int *far_list[2];        // the other groups of step parity 0 / 1, compacted
+    int *far_cnt;            // [2] their counts
     int sms;                 // multiprocessors of the device
     cudaEvent_t ev_cf;                 // after the far collisions
     bool overlap;
@@ -352,12 +365,11 @@ struct lbm_batch_s {
 
 // Launchers (one per translation unit).
 namespace lbm {
-// mode 0: every fluid node; 1: nodes whose group is not tagged near
-int launch_stream_collide(lbm_s *h, int parity, int mode = 0, const uint8_t *near = nullptr, uint8_t tag = 0,
-                          cudaStream_t stream = nullptr);
-// near tags of one step into `near`, the tagged groups compacted into list / *count
-int launch_near_mark(lbm_s *h, uint8_t *near, uint8_t tag, const SFrame *frames, int *list, int *count,
-                     cudaStream_t stream);
+int launch_stream_collide(lbm_s *h, int parity, cudaStream_t stream = nullptr);
+// near tags of one step into `near`, the tagged groups compacted into list / *count and the
+// other groups into far / *far_count
+int launch_near_mark(lbm_s *h, uint8_t *near, uint8_t tag, const SFrame *frames, int *list, int *count, int *far,
+                     int *far_count, cudaStream_t stream);
 int launch_collide_list(lbm_s *h, int parity, const int *list, const int *count, cudaStream_t stream);
 int launch_zieb(lbm_s *h, int P);  // ZIEB face after the step of parity P
 int launch_wait_probe(lbm_s *h);   // a bounded device wait that runs out (self-test)

@@ -2,10 +2,11 @@
 // memory, staged through a fixed device array instead of a temporary
 // allocation, for callers that must not allocate device memory.
 //
-// The staging array below is part of the library image: every GPU that loads
-// the library holds it (16 MiB) until the process exits.  Its address is
+// The staging array below is part of the library image.  Its address is
 // looked up once per device, with that device current, on the first call
-// there.  All calls on a device share the array and it keeps the last call's
+// there; under lazy module loading that lookup is when the driver commits
+// the array's 16 MiB on the device, which then holds it until the process
+// exits (an allocation failure there is reported as LBM_ERR_NOMEM).  All calls on a device share the array and it keeps the last call's
 // contents; the fields kernel writes every element it later copies, so
 // nothing needs clearing.  Two calls whose work overlaps on the same GPU
 // (handles on different streams) race on the array.
@@ -30,9 +31,10 @@ int staging_for(int device, float **out) {
     std::lock_guard<std::mutex> lock(g_mutex);
     if (!g_staging[device]) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_fields_staging) != cudaSuccess || !p) {
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_fields_staging);
+        if (e != cudaSuccess || !p) {
             cudaGetLastError();
-            return LBM_ERR_CUDA;
+            return e == cudaErrorMemoryAllocation ? LBM_ERR_NOMEM : LBM_ERR_CUDA;
         }
         g_staging[device] = (float *)p;
     }

@@ -159,6 +159,58 @@ def test_many_spheres_moving_lid_contacts_periodic_edges():
     assert info["fluid_nodes"] == int((orc.owner() < 0).sum())
 
 
+def test_headline_physics_forces_until_the_first_switch_event():
+    """The production physics (tau0 = 0.51, Cs = 0.17, lid 0.05, spheres of
+    radius 4 at the 256^3 workload's density: 31 in a 64^3 sub-box).  After
+    100 steps: populations within 1e-5, every sphere's force within 1e-4,
+    identical owners.  Then step by step to 200: the force bound holds for as
+    long as both sides have classified every node alike.  Both sides take
+    the inside test in the same FP32 operations, but on centres that differ
+    by the integrated effect of FP32-level load differences (~1e-6 here); a
+    node that the surface crosses within that distance of a step boundary is
+    covered or uncovered one step apart on the two sides (a switch event of
+    the method), and the refill then differs locally by O(1e-2) of that
+    sphere's load.  The oracle started from FP32-level perturbed populations
+    (6e-8 relative) stays within 5e-6 of itself in force over 200 steps, so
+    the departure is the switch event, not a growth of rounding noise."""
+    shape = (64, 64, 64)
+    p = inputs.slurry_box(box=shape, n=31, radius=4.0, seed=inputs.SEED_BASE + 8)
+    kw = dict(tau0=0.51, cs=0.17, u_hi=(0.05, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16)
+    lat, orc = make_pair(shape, parts=p, **kw)
+    # control: the oracle from rest populations perturbed at the FP32 level
+    ctl = oracle.Oracle(*shape, **kw)
+    ctl.set_particles(p["X"], V=p["V"], Om=p["Om"], R=p["R"])
+    ctl.set_populations(perturbed(shape, 6e-8, 12345))
+    lat.step(100)
+    orc.step(100)
+    ctl.step(100)
+    assert np.array_equal(lat.owner(), orc.owner())
+    pe = pop_error(lat, orc)
+    ef, _, Fo, _ = force_error(lat, orc)
+    print("tau0 = 0.51, 100 steps: populations %.2e, forces %.2e" % (pe, ef))
+    assert pe <= POP_TOL
+    assert ef <= FORCE_TOL, (ef, Fo)
+    first_flip = None
+    for s in range(101, 201):
+        lat.step(1)
+        orc.step(1)
+        if first_flip is None and not np.array_equal(lat.owner(), orc.owner()):
+            Xg, _, _ = lat.particles()
+            Xo, _, _ = orc.particles()
+            first_flip = s
+            print("first switch event on one side only at step %d (centres differ by %.1e)" % (s, np.abs(Xg - Xo).max()))
+        if first_flip is None:
+            ef, _, Fo, _ = force_error(lat, orc)
+            assert ef <= FORCE_TOL, (s, ef, Fo)
+    print("forces within %.0e up to step %s" % (FORCE_TOL, first_flip - 1 if first_flip else 200))
+    ctl.step(100)
+    Fc, _ = ctl.forces()
+    Fo, _ = orc.forces()
+    self_div = float((np.linalg.norm(Fc - Fo, axis=1) / np.linalg.norm(Fo, axis=1)).max())
+    print("control: oracle against its FP32-level perturbed copy after 200 steps: forces %.2e" % self_div)
+    assert self_div <= 0.1 * FORCE_TOL
+
+
 def test_mostly_far_nodes_overlapped_schedule():
     """A large box with a few spheres: most nodes are collided by the second
     stream while the link / DEM / geometry work runs; 100 steps must still

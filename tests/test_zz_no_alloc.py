@@ -44,6 +44,25 @@ def test_noalloc_fields_match_lbm_fields_on_consecutive_calls():
     lat.close()
 
 
+def test_noalloc_fields_take_no_device_memory():
+    """After the first call on the device (which has the driver commit the
+    built-in array), a call leaves the device's free memory unchanged."""
+    import torch
+
+    lbm, lat = _lattice()
+    lat.step(3)
+    rho = np.zeros(lat.N, dtype=np.float32)
+    u = np.zeros(3 * lat.N, dtype=np.float32)
+    lbm.lbm_fields_noalloc(lat.h, rho, u)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(0)
+    lbm.lbm_fields_noalloc(lat.h, rho, u)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(0)
+    assert free1 == free0, (free0, free1)
+    lat.close()
+
+
 def test_noalloc_rejects_lattices_beyond_its_array():
     from paper_1703_05158_gb300 import lbm
 
