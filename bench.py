@@ -63,7 +63,7 @@ def collide_source_sha():
     import hashlib
 
     h = hashlib.sha256()
-    for name in ("lbm_collide.cu", "lbm_collide_node.cuh"):
+    for name in ("lbm_collide.cu", "lbm_collide_node.cuh", "lbm_stream.cuh"):
         with open(os.path.join(ROOT, "paper_1703_05158_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -174,6 +174,36 @@ def error_vs_fp64(precision, steps=200):
     return {"relative_l2_velocity": float(np.linalg.norm(a - b) / np.linalg.norm(b)),
             "max_relative_force": float((np.linalg.norm(Fg - Fo, axis=1) / np.linalg.norm(Fo, axis=1)).max()),
             "case": "64^3 sub-box, 31 spheres R=4, %d steps, against the FP64 oracle" % steps}
+
+
+def precision_form(args, prec, p, stream, dev, fp32_ms):
+    """The same workload with populations stored as 16-bit deviations: MLUPS
+    over the same number of timed steps (after the same warm-up), the ratio
+    to the FP32 line, and the velocity / force error against the FP64 oracle
+    on the 64^3 sub-box."""
+    import torch
+
+    from paper_1703_05158_gb300 import lbm
+
+    lat = lbm.Lattice(*BOX, precision=prec, max_particles=len(p["R"]), max_radius=4.0, stream=ctypes_stream(stream),
+                      device=dev, schedule=args.schedule, **PHYS)
+    lat.set_particles(p["X"], V=p["V"], Om=p["Om"], R=p["R"])
+    lat.step(args.warmup)
+    lat.sync()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    lat.step(args.steps)
+    end.record(stream)
+    torch.cuda.synchronize()
+    lat.sync()
+    ms = start.elapsed_time(end) / args.steps
+    lat.close()
+    out = {"value": BOX[0] * BOX[1] * BOX[2] / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
+           "ratio_to_fp32": fp32_ms / ms}
+    if not args.no_error_check:
+        out["error_vs_fp64"] = error_vs_fp64(prec)
+    return out
 
 
 def cpu_baseline(steps=2):
@@ -382,8 +412,9 @@ def run_ours(args, rank, world, local_rank):
                      "peak_kind": "%s hbm_gbs" % peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": bytes_collide,
                      "avg_launch_ms": collide_ms, "frac_of_nominal_7900": achieved / 7900.0,
-                     # the whole step: the collide bytes plus 16 B per cut link
-                     "step_bytes": step_bytes, "step_frac": step_bytes / (ms_max / args.steps * 1e-3) / 1e9 / peak},
+                     # the whole step: the collide bytes plus 16 B per cut link, over the step time
+                     "step_bytes": step_bytes, "step_frac": step_bytes / (ms_max / args.steps * 1e-3) / 1e9 / peak,
+                     "path_frac": step_bytes / (ms_max / args.steps * 1e-3) / 1e9 / peak},
         "mflups_fluid": value * nf / N,
         "phases_ms_per_step": {k: v / max(psteps, 1) for k, v in phases.items()},
         "clocks": clk.summary(),
@@ -398,8 +429,11 @@ def run_ours(args, rank, world, local_rank):
         line["cpu_baseline"] = cpu_baseline()
     if world == 1 and not args.no_error_check and not dense:
         line["error_vs_fp64"] = error_vs_fp64(args.precision)
-    print(json.dumps(line), flush=True)
     lat.close()
+    if world == 1 and args.precision == "fp32" and not dense and not args.no_precision_forms:
+        line["precision_forms"] = {q: precision_form(args, q, p, stream, dev, ms_max / args.steps)
+                                   for q in ("bf16", "fp16")}
+    print(json.dumps(line), flush=True)
 
 
 def run_batched(args, rank, world, local_rank):
@@ -550,6 +584,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error-check", action="store_true",
                     help="skip the 64^3 velocity / force error against the FP64 oracle")
+    ap.add_argument("--no-precision-forms", action="store_true",
+                    help="skip the BF16 / FP16 storage lines of the FP32 run")
     ap.add_argument("--schedule", choices=["serial", "overlap"], default="serial",
                     help="order of the kernels inside a step (same results)")
     ap.add_argument("--mea", choices=["paper", "galilean"], default="paper",

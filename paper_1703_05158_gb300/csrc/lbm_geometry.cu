@@ -216,6 +216,13 @@ __device__ __forceinline__ void mark_corr_body(const Lat &L, const Parts &pt, co
 
 // CORR = false: the plain marks (no population reads); true: with the
 // momentum correction where the argument corr (per instance) asks for it.
+// Threads of the plain marks and refill (the momentum-correction forms keep
+// 256: their node sorts assume it).
+#ifndef LBM_GEOM_THREADS
+#define LBM_GEOM_THREADS 128
+#endif
+constexpr int kGeomThreads = LBM_GEOM_THREADS;
+
 template <typename T, bool CORR>
 __global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
                                               uint8_t *__restrict__ flag, int32_t *__restrict__ owner,
@@ -511,17 +518,18 @@ int mark_launch(lbm_s *h, int P, int corr) {
     const SFrame *fcur = h->pt.frame[h->steps & 1];
     const uint8_t cur = mark_value((int)(h->steps & 1));
     const dim3 g(h->pt.np);
+    const int nt = CORR ? 256 : kGeomThreads;
     switch (h->precision) {
         case LBM_FP32:
-            k_mark<float, CORR><<<g, 256, 0, h->stream>>>(h->L, h->pt, fcur, h->flag, h->owner,
+            k_mark<float, CORR><<<g, nt, 0, h->stream>>>(h->L, h->pt, fcur, h->flag, h->owner,
                                                            (const float *)h->f, P, corr, cur);
             break;
         case LBM_BF16_DEV:
-            k_mark<__nv_bfloat16, CORR><<<g, 256, 0, h->stream>>>(h->L, h->pt, fcur, h->flag, h->owner,
+            k_mark<__nv_bfloat16, CORR><<<g, nt, 0, h->stream>>>(h->L, h->pt, fcur, h->flag, h->owner,
                                                                    (const __nv_bfloat16 *)h->f, P, corr, cur);
             break;
         case LBM_FP16_DEV:
-            k_mark<__half, CORR><<<g, 256, 0, h->stream>>>(h->L, h->pt, fcur, h->flag, h->owner,
+            k_mark<__half, CORR><<<g, nt, 0, h->stream>>>(h->L, h->pt, fcur, h->flag, h->owner,
                                                             (const __half *)h->f, P, corr, cur);
             break;
         default: return LBM_ERR_ARG;
@@ -536,7 +544,7 @@ int launch_mark(lbm_s *h, int P, int corr) {
 template <typename T, bool CORR>
 void refill_launch(lbm_s *h, int parity) {
     const SFrame *fcur = h->pt.frame[h->steps & 1], *fprev = h->pt.frame[(h->steps + 1) & 1];
-    k_refill<T, CORR><<<h->pt.np, 256, 0, h->stream>>>(h->L, fcur, fprev, (T *)h->f, h->flag, h->owner, parity,
+    k_refill<T, CORR><<<h->pt.np, CORR ? 256 : kGeomThreads, 0, h->stream>>>(h->L, fcur, fprev, (T *)h->f, h->flag, h->owner, parity,
                                                          h->ctr, h->status, h->pt, mark_value((int)(h->steps & 1)));
 }
 

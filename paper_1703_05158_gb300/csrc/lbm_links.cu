@@ -8,14 +8,21 @@ namespace lbm {
 
 // GI: compiled with the Galilean-invariant momentum exchange (taken where
 // the handle asks for it).
+#ifndef LBM_LINK_MINB
+#define LBM_LINK_MINB 4  // resident CTAs per SM the register budget is set for (64 registers)
+#endif
+#ifndef LBM_LINK_BATCH
+#define LBM_LINK_BATCH 3  // links per thread whose populations are loaded together (no spills at 64)
+#endif
+
 template <typename T, bool GI>
-__global__ void __launch_bounds__(256, 3) k_links(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
+__global__ void __launch_bounds__(256, LBM_LINK_MINB) k_links(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
                                                T *__restrict__ f,
                                                uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
                                                const int P, const int ext, const unsigned mB, const unsigned mB2,
                                                const int cap, int *__restrict__ status,
                                                unsigned long long *__restrict__ ctr) {
-    links_body<T, GI>(L, pt, fcur, f, flag, owner, P, ext, mB, mB2, cap, status, ctr, blockIdx.x);
+    links_body<T, GI, LBM_LINK_BATCH>(L, pt, fcur, f, flag, owner, P, ext, mB, mB2, cap, status, ctr, blockIdx.x);
 }
 
 // Batched: instance blockIdx.y; parity P is also the step parity.
