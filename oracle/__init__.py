@@ -43,6 +43,8 @@ class OrcParams(ctypes.Structure):
         ("kt", ctypes.c_double), ("mu", ctypes.c_double), ("restitution_t", ctypes.c_double),
         ("zieb", ctypes.c_int), ("zieb_area", ctypes.c_double), ("zieb_volume", ctypes.c_double),
         ("zieb_vp", ctypes.c_double), ("mea", ctypes.c_int),
+        ("channel", ctypes.c_int), ("u_peak", ctypes.c_double),
+        ("plate_lo", ctypes.c_int * 3), ("plate_hi", ctypes.c_int * 3),
     ]
 
 
@@ -93,6 +95,10 @@ def _load():
         lib.orc_feq.argtypes = [ctypes.c_double, dp, dp]
         lib.orc_refill_only.argtypes = [vp]
         lib.orc_set_load.argtypes = [vp, ctypes.c_void_p, ctypes.c_void_p]
+        lib.orc_plate_drag.restype = ctypes.c_double
+        lib.orc_plate_drag.argtypes = [vp]
+        lib.orc_channel_violation.restype = ctypes.c_int
+        lib.orc_channel_violation.argtypes = [vp]
         lib.chan_run.restype = ctypes.c_int
         lib.chan_run.argtypes = [ctypes.POINTER(ChanParams), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -114,7 +120,7 @@ class Oracle:
     def __init__(self, nx, ny, nz, tau0, cs=0.0, g=(0.0, 0.0, 0.0), u_lo=(0.0, 0.0, 0.0),
                  u_hi=(0.0, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16,
                  les=True, fluid=True, periodic_z=False, momentum_correction=False, kt=0.0, mu=0.0,
-                 restitution_t=1.0, zieb=None, mea="paper", threads=None):
+                 restitution_t=1.0, zieb=None, mea="paper", channel=None, threads=None):
         if threads is not None:
             os.environ["OMP_NUM_THREADS"] = str(threads)
         lib = _load()
@@ -132,6 +138,10 @@ class Oracle:
         p.mea = {"paper": 0, "galilean": 1}[mea]
         if zieb is not None:  # dict(area=A_p, volume=V_0, vp=v_p)
             p.zieb, p.zieb_area, p.zieb_volume, p.zieb_vp = 1, zieb["area"], zieb["volume"], zieb.get("vp", 0.0)
+        if channel is not None:  # dict(u_peak=..., plate_lo=(x, y, z), plate_hi=(x, y, z)): x open
+            p.channel, p.u_peak = 1, channel["u_peak"]
+            p.plate_lo[:] = list(channel.get("plate_lo", (1, 0, 0)))
+            p.plate_hi[:] = list(channel.get("plate_hi", (0, -1, -1)))
         self._h = lib.orc_create(ctypes.byref(p))
         if not self._h:
             raise MemoryError("oracle allocation failed")
@@ -238,6 +248,14 @@ class Oracle:
         self.lib.orc_links(self._h, n, node.ctypes.data, d.ctypes.data, q.ctypes.data, pid.ctypes.data)
         return node, d, q, pid
 
+    def plate_drag(self):
+        """Channel option: the plate drag (x) of the last step's collided populations."""
+        return float(self.lib.orc_plate_drag(self._h))
+
+    def channel_violation(self):
+        """Channel option: whether a sphere ever covered a node of the planes x <= 1 or x >= nx - 2."""
+        return bool(self.lib.orc_channel_violation(self._h))
+
     def refill_only(self):
         """Run only geometry and refill of the next step (test hook)."""
         self.lib.orc_refill_only(self._h)
@@ -301,3 +319,31 @@ def channel(nx, ny, nz, tau0, cs, gx, u_peak, plate_lo, plate_hi, steps, avg_fro
     if f is not None:
         out["f"] = f.reshape(NQ, nz, ny, nx)
     return out
+
+
+def free_channel(nx, ny, nz, tau0, cs, gx, u_peak, plate_lo, plate_hi, steps, avg_from, X, R, free=True,
+                 rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16):
+    """The differentiation-form channel run by the coupled oracle (lbm_oracle.c,
+    channel option), with the spheres free (moved by the momentum exchange
+    and the contacts of the coupled step, starting at rest) or held fixed.
+    Returns dict(J, drag [steps], X [n, 3] final centres).
+
+    The step order of the coupled oracle collides first, so its step k
+    (k = 0 .. steps) collides f^k into G^k and its plate links give D^k;
+    J is the mean of D^s over s in [avg_from, steps], as in channel()."""
+    o = Oracle(nx, ny, nz, tau0, cs=cs, g=(gx, 0.0, 0.0), rho_s=rho_s, kn=kn, restitution=restitution,
+               dem_substeps=dem_substeps, channel=dict(u_peak=u_peak, plate_lo=plate_lo, plate_hi=plate_hi))
+    try:
+        X = np.asarray(X, dtype=np.float64).reshape(-1, 3)
+        n = X.shape[0]
+        o.set_particles(X, R=R, fixed=None if free else np.ones(n, dtype=np.uint8))
+        drag = np.zeros(steps + 1)
+        for k in range(steps + 1):
+            o.step(1)
+            drag[k] = o.plate_drag()
+        if o.channel_violation():
+            raise RuntimeError("a sphere reached the planes next to the inlet or the outlet")
+        Xf = o.particles()[0]
+    finally:
+        o.close()
+    return dict(J=float(drag[avg_from:steps + 1].mean()), drag=drag[1:], X=Xf)

@@ -24,7 +24,10 @@
  * spring, dashpot and Coulomb cap of Eqs. (2), (3) (paper's); the ZIEB face
  * of Sect. 2.6, Eqs. (8), (9), after step 5 (paper's); momentum correction
  * of covered / uncovered nodes (Aidun, Lu & Ding 1998); the
- * Galilean-invariant momentum exchange (Wen, Zhang & Fang 2014).
+ * Galilean-invariant momentum exchange (Wen, Zhang & Fang 2014); an open
+ * channel in x with a velocity inlet, a pressure outlet and a fixed plate,
+ * the boundaries of the differentiation form, so that its objective (the
+ * plate drag) can be evaluated with the spheres free.
  *
  * Arithmetic is FP64, except the geometric decisions (is a node inside a
  * sphere, which sphere owns it, the link fraction q and so which branch of
@@ -93,6 +96,10 @@ typedef struct {
     double zieb_volume;     /* cylinder volume V_0 */
     double zieb_vp;         /* piston velocity v_p (H_p advances by v_p per step) */
     int mea;                /* 0: momentum exchange of Eqs. 25, 26; 1: its Galilean-invariant form */
+    int channel;            /* 1: open channel in x (differentiation form): inlet plane x = 0, outlet x = nx-1 */
+    double u_peak;          /* channel inlet peak velocity */
+    int plate_lo[3];        /* channel plate node box, inclusive (no plate when lo[0] > hi[0]) */
+    int plate_hi[3];
 } orc_params;
 
 #define CT_MAX 64
@@ -127,6 +134,8 @@ typedef struct {
     long step;
     long refilled;          /* nodes refilled in the last step */
     double zrho, zH, zvf;   /* ZIEB: cylinder density rho^n, piston displacement H_p^n, mean inflow v_f^n */
+    double plate_drag;      /* channel: x momentum the plate took in the last step (Eq. 25 over its links) */
+    int channel_violation;  /* channel: a sphere covered a node of the planes x <= 1 or x >= nx-2 */
 } orc_state;
 
 /* ------------------------------------------------------------------ */
@@ -161,6 +170,25 @@ static int wrap(int x, int n) {
     return r < 0 ? r + n : r;
 }
 
+/* Channel option (the differentiation form, Sect. 2.3 applied to an open
+ * channel): x is not periodic; the planes x = 0 (velocity inlet) and
+ * x = nx - 1 (pressure outlet) are not collided and take an equilibrium
+ * after streaming; a plate (node box) is a static solid with halfway
+ * bounce-back at rest.  Plate nodes carry the owner index np (one past the
+ * spheres), so that every test "owner >= 0" treats them as solid; the
+ * sphere-specific steps skip that index. */
+static int x_periodic(const orc_state *s) { return !s->p.channel; }
+
+static int is_plate_owner(const orc_state *s, int p) { return s->p.channel && p == s->np; }
+
+static int in_plate(const orc_params *P, int x, int y, int z) {
+    return P->channel && x >= P->plate_lo[0] && x <= P->plate_hi[0] && y >= P->plate_lo[1] &&
+           y <= P->plate_hi[1] && z >= P->plate_lo[2] && z <= P->plate_hi[2];
+}
+
+/* Inlet or outlet node of the channel (never collided). */
+static int open_plane(const orc_state *s, int x) { return s->p.channel && (x == 0 || x == s->p.nx - 1); }
+
 /* Step 1.  A node is inside sphere p when |x - X_p|^2 < R_p^2 (strict).
  * reading: a node inside several overlapping spheres belongs to the one with
  * the smallest |x - X_p| - R_p, ties to the smallest p. */
@@ -170,6 +198,15 @@ static void geometry(orc_state *s) {
         s->owner[n] = -1;
         s->key[n] = INFINITY;
     }
+    if (P->channel)
+        for (int z = 0; z < P->nz; ++z)
+            for (int y = 0; y < P->ny; ++y)
+                for (int x = 0; x < P->nx; ++x)
+                    if (in_plate(P, x, y, z)) {
+                        long n = x + (long)P->nx * (y + (long)P->ny * z);
+                        s->owner[n] = s->np; /* static: no sphere takes a plate node */
+                        s->key[n] = -INFINITY;
+                    }
     for (int p = 0; p < s->np; ++p) {
         const double *X = s->X + 3 * p;
         float Rf = (float)s->R[p];
@@ -186,6 +223,11 @@ static void geometry(orc_state *s) {
                     float dx = rel32(xi, X[0]), dy = rel32(yi, X[1]), dz = rel32(zi, X[2]);
                     float d2 = dist2_32(dx, dy, dz);
                     if (!(d2 < R2)) continue;
+                    if (P->channel && (xi <= 1 || xi >= P->nx - 2)) {
+                        /* the open planes and the planes they read stay fluid */
+                        s->channel_violation = 1;
+                        continue;
+                    }
                     float key = sqrtf(d2) - Rf;
                     long n = wrap(xi, P->nx) + (long)P->nx * (wrap(yi, P->ny) + (long)P->ny * wrap(zi, P->nz));
                     if (key < s->key[n]) {
@@ -303,6 +345,7 @@ static long node_of(const orc_state *s, int x, int y, int z) {
 
 static int is_fluid(const orc_state *s, int x, int y, int z) {
     if (!in_z(s, z)) return 0;
+    if (s->p.channel && (x < 0 || x >= s->p.nx)) return 0;
     return s->owner[node_of(s, x, y, z)] < 0;
 }
 
@@ -310,7 +353,7 @@ static int is_fluid(const orc_state *s, int x, int y, int z) {
  * taken at its image nearest to the centre. */
 static void arm(const orc_state *s, int p, int x, int y, int z, int j, double q, double l[3]) {
     const double *X = s->X + 3 * p;
-    int xi = image(x, X[0], s->p.nx, 1), yi = image(y, X[1], s->p.ny, 1);
+    int xi = image(x, X[0], s->p.nx, x_periodic(s)), yi = image(y, X[1], s->p.ny, 1);
     int zi = image(z, X[2], s->p.nz, s->p.periodic_z);
     l[0] = ((double)xi - X[0]) + q * CX[j];
     l[1] = ((double)yi - X[1]) + q * CY[j];
@@ -319,7 +362,8 @@ static void arm(const orc_state *s, int p, int x, int y, int z, int j, double q,
 
 /* Describe the boundary met by the link from fluid node (x,y,z) along c_j:
  * fraction q and boundary velocity u_b.  Returns the owning sphere, -1 for a
- * z wall (q = 1/2, u_b = wall velocity; the halfway wall of Eq. 19). */
+ * z wall (q = 1/2, u_b = wall velocity; the halfway wall of Eq. 19) or the
+ * channel's plate (q = 1/2, u_b = 0). */
 static int boundary(const orc_state *s, int x, int y, int z, int j, double *q, double ub[3]) {
     int zz = z + CZ[j];
     if (!in_z(s, zz)) {
@@ -331,8 +375,13 @@ static int boundary(const orc_state *s, int x, int y, int z, int j, double *q, d
         return -1;
     }
     int p = s->owner[node_of(s, x + CX[j], y + CY[j], zz)];
+    if (is_plate_owner(s, p)) { /* the plate: halfway wall at rest */
+        *q = 0.5;
+        ub[0] = ub[1] = ub[2] = 0.0;
+        return -1;
+    }
     const double *X = s->X + 3 * p;
-    int xi = image(x, X[0], s->p.nx, 1), yi = image(y, X[1], s->p.ny, 1);
+    int xi = image(x, X[0], s->p.nx, x_periodic(s)), yi = image(y, X[1], s->p.ny, 1);
     int zi = image(z, X[2], s->p.nz, s->p.periodic_z);
     *q = (double)link_q(s, p, xi, yi, zi, j);
     double l[3];
@@ -378,7 +427,7 @@ static void stream(orc_state *s) {
         for (int y = 0; y < P->ny; ++y) {
             for (int x = 0; x < P->nx; ++x) {
                 long n = node_of(s, x, y, z);
-                if (s->owner[n] >= 0) continue;
+                if (s->owner[n] >= 0 || open_plane(s, x)) continue;
                 for (int k = 0; k < NQ; ++k) {
                     int j = s->opp[k];
                     double v;
@@ -396,16 +445,41 @@ static void stream(orc_state *s) {
     }
 }
 
+/* Channel option, after streaming: the inlet node (0, y, z) takes
+ * f^eq(rho(1, y, z), u_in(z)) with u_in = u_peak 4 zh (1 - zh) x^,
+ * zh = (z + 1/2)/nz, and the outlet node (nx-1, y, z) takes f^eq(1,
+ * u(nx-2, y, z)), both moments (Eqs. 5, 6, with the force shift) of the
+ * populations just streamed into the neighbouring plane (the readings of
+ * the differentiation form's boundaries). */
+static void channel_planes(orc_state *s) {
+    const orc_params *P = &s->p;
+    for (int z = 0; z < P->nz; ++z)
+        for (int y = 0; y < P->ny; ++y) {
+            double zh = (z + 0.5) / P->nz;
+            double u_in[3] = {P->u_peak * 4.0 * zh * (1.0 - zh), 0.0, 0.0};
+            double rho1, u1[3], rho2, u2[3];
+            moments(s, s->fn, node_of(s, 1, y, z), &rho1, u1);
+            moments(s, s->fn, node_of(s, P->nx - 2, y, z), &rho2, u2);
+            long n0 = node_of(s, 0, y, z), n1 = node_of(s, P->nx - 1, y, z);
+            for (int i = 0; i < NQ; ++i) {
+                s->fn[(long)i * s->N + n0] = feq(s, i, rho1, u_in);
+                s->fn[(long)i * s->N + n1] = feq(s, i, 1.0, u2);
+            }
+        }
+}
+
 /* Step 5: momentum exchange (Eqs. 25, 26).  Every cut link from fluid node x
  * along j into sphere p carries fc_j(x) c_j into the solid and takes back
  * f_k(x, n+1) c_k, k = opposite(j); the solid receives
  *   dP = (fc_j(x) + f_k(x, n+1)) c_j,    F_p += dP,   T_p += l x dP,
  * l = x_b - X_p, x_b = x + q c_j (reading of "l" as the arm to the boundary
- * point of the link).  Summed in (node index, j) order. */
+ * point of the link).  Summed in (node index, j) order.  Channel option:
+ * the plate's links give its drag, the x component of the same sum. */
 static void momentum_exchange(orc_state *s) {
     const orc_params *P = &s->p;
     memset(s->Fh, 0, sizeof(double) * 3 * s->np);
     memset(s->Th, 0, sizeof(double) * 3 * s->np);
+    s->plate_drag = 0.0;
     for (int z = 0; z < P->nz; ++z)
         for (int y = 0; y < P->ny; ++y)
             for (int x = 0; x < P->nx; ++x) {
@@ -414,9 +488,14 @@ static void momentum_exchange(orc_state *s) {
                 for (int j = 1; j < NQ; ++j) {
                     int zz = z + CZ[j];
                     if (!in_z(s, zz)) continue;
+                    if (P->channel && (x + CX[j] < 0 || x + CX[j] >= P->nx)) continue;
                     int p = s->owner[node_of(s, x + CX[j], y + CY[j], zz)];
                     if (p < 0) continue;
                     int k = s->opp[j];
+                    if (is_plate_owner(s, p)) {
+                        s->plate_drag += (s->fc[(long)j * s->N + n] + s->fn[(long)k * s->N + n]) * CX[j];
+                        continue;
+                    }
                     double q, ub[3], l[3];
                     boundary(s, x, y, z, j, &q, ub);
                     arm(s, p, x, y, z, j, q, l);
@@ -449,7 +528,7 @@ static void momentum_exchange(orc_state *s) {
  * and walls.  This part: the nodes covered at step n. */
 static void arm_of(const orc_state *s, int p, int x, int y, int z, double l[3]) {
     const double *X = s->X + 3 * p;
-    l[0] = (double)image(x, X[0], s->p.nx, 1) - X[0];
+    l[0] = (double)image(x, X[0], s->p.nx, x_periodic(s)) - X[0];
     l[1] = (double)image(y, X[1], s->p.ny, 1) - X[1];
     l[2] = (double)image(z, X[2], s->p.nz, s->p.periodic_z) - X[2];
 }
@@ -482,7 +561,7 @@ static void covered_correction(orc_state *s) {
             for (int x = 0; x < P->nx; ++x) {
                 long n = node_of(s, x, y, z);
                 int p = s->owner[n];
-                if (p < 0 || s->owner_prev[n] >= 0) continue;
+                if (p < 0 || s->owner_prev[n] >= 0 || is_plate_owner(s, p)) continue;
                 double m[3], l[3];
                 node_momentum(s, n, m);
                 arm_of(s, p, x, y, z, l);
@@ -503,7 +582,7 @@ static void refill(orc_state *s) {
             for (int x = 0; x < P->nx; ++x) {
                 long n = node_of(s, x, y, z);
                 int p = s->owner_prev[n];
-                if (p < 0 || s->owner[n] >= 0) continue;
+                if (p < 0 || s->owner[n] >= 0 || is_plate_owner(s, p)) continue;
                 double sum = 0.0;
                 int cnt = 0;
                 for (int i = 1; i < NQ; ++i) {
@@ -518,7 +597,7 @@ static void refill(orc_state *s) {
                 }
                 double rho = cnt > 0 ? sum / cnt : 1.0;
                 const double *X = s->X + 3 * p, *V = s->V + 3 * p, *W = s->Om + 3 * p;
-                double l[3] = {(double)image(x, X[0], P->nx, 1) - X[0],
+                double l[3] = {(double)image(x, X[0], P->nx, x_periodic(s)) - X[0],
                                (double)image(y, X[1], P->ny, 1) - X[1],
                                (double)image(z, X[2], P->nz, P->periodic_z) - X[2]};
                 double us[3] = {V[0] + (W[1] * l[2] - W[2] * l[1]), V[1] + (W[2] * l[0] - W[0] * l[2]),
@@ -682,8 +761,8 @@ static void contact_forces(orc_state *s, const double *X, const double *v, const
             if (b == a) continue;
             double stv[3] = {0.0, 0.0, 0.0}, *st = stv;
             double d[3] = {X[3 * a] - X[3 * b], X[3 * a + 1] - X[3 * b + 1], X[3 * a + 2] - X[3 * b + 2]};
-            if (d[0] > 0.5 * P->nx) d[0] -= P->nx;
-            if (d[0] < -0.5 * P->nx) d[0] += P->nx;
+            if (!P->channel && d[0] > 0.5 * P->nx) d[0] -= P->nx;
+            if (!P->channel && d[0] < -0.5 * P->nx) d[0] += P->nx;
             if (d[1] > 0.5 * P->ny) d[1] -= P->ny;
             if (d[1] < -0.5 * P->ny) d[1] += P->ny;
             if (P->periodic_z && d[2] > 0.5 * P->nz) d[2] -= P->nz;
@@ -771,6 +850,31 @@ static void contact_forces(orc_state *s, const double *X, const double *v, const
                 for (int c = 0; c < 3; ++c) T[c] += tq[c];
             }
         }
+        if (P->channel && P->plate_lo[0] <= P->plate_hi[0]) {
+            /* channel plate: normal contact (Eq. 1, m_eff = m) with its surface,
+             * the node box grown by 1/2 (its halfway bounce-back planes), at
+             * the closest point of that box to the centre (y minimum image) */
+            double d[3], dist2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                double xc = X[3 * a + c];
+                if (c == 1) {
+                    double mid = 0.5 * (P->plate_lo[1] + P->plate_hi[1]);
+                    if (xc - mid > 0.5 * P->ny) xc -= P->ny;
+                    if (xc - mid < -0.5 * P->ny) xc += P->ny;
+                }
+                double lo = P->plate_lo[c] - 0.5, hi = P->plate_hi[c] + 0.5;
+                double pc = xc < lo ? lo : (xc > hi ? hi : xc);
+                d[c] = xc - pc;
+                dist2 += d[c] * d[c];
+            }
+            double dist = sqrt(dist2), pen = s->R[a] - dist;
+            if (pen > 0.0 && dist > 0.0) {
+                double nv[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+                double vn = v[3 * a] * nv[0] + v[3 * a + 1] * nv[1] + v[3 * a + 2] * nv[2];
+                double fn = P->kn * pen - gamma_n(s, ma) * vn;
+                for (int c = 0; c < 3; ++c) F[c] += fn * nv[c];
+            }
+        }
         for (int c = 0; c < 3; ++c) {
             Fc[3 * a + c] = F[c];
             Tc[3 * a + c] = T[c];
@@ -804,8 +908,8 @@ static void dem(orc_state *s) {
                 }
                 s->X[3 * a + c] += s->V[3 * a + c] * h;
             }
-            if (s->X[3 * a] >= P->nx) s->X[3 * a] -= P->nx;
-            if (s->X[3 * a] < 0.0) s->X[3 * a] += P->nx;
+            if (!P->channel && s->X[3 * a] >= P->nx) s->X[3 * a] -= P->nx;
+            if (!P->channel && s->X[3 * a] < 0.0) s->X[3 * a] += P->nx;
             if (s->X[3 * a + 1] >= P->ny) s->X[3 * a + 1] -= P->ny;
             if (s->X[3 * a + 1] < 0.0) s->X[3 * a + 1] += P->ny;
             if (P->periodic_z && s->X[3 * a + 2] >= P->nz) s->X[3 * a + 2] -= P->nz;
@@ -947,9 +1051,15 @@ void orc_step(orc_state *s, int nsteps) {
             covered_correction(s);
             refill(s);
 #pragma omp parallel for schedule(static)
-            for (long n = 0; n < s->N; ++n)
-                if (s->owner[n] < 0) collide_node(s, n);
+            for (long n = 0; n < s->N; ++n) {
+                if (s->owner[n] >= 0) continue;
+                if (open_plane(s, (int)(n % s->p.nx))) /* channel inlet / outlet: not collided */
+                    for (int i = 0; i < NQ; ++i) s->fc[(long)i * s->N + n] = s->f[(long)i * s->N + n];
+                else
+                    collide_node(s, n);
+            }
             stream(s);
+            if (s->p.channel) channel_planes(s);
             momentum_exchange(s);
             for (long k = 0; k < 3 * (long)s->np; ++k) {
                 s->Fh[k] += s->Fcorr[k];
@@ -1038,12 +1148,12 @@ long orc_links(const orc_state *s, long cap, long *node, int *dir, float *q, int
                     int zz = z + CZ[j];
                     if (!in_z(s, zz)) continue;
                     int p = s->owner[node_of(s, x + CX[j], y + CY[j], zz)];
-                    if (p < 0) continue;
+                    if (p < 0 || is_plate_owner(s, p)) continue;
                     if (cnt < cap) {
                         const double *X = s->X + 3 * p;
                         node[cnt] = n;
                         dir[cnt] = j;
-                        q[cnt] = link_q(s, p, image(x, X[0], P->nx, 1), image(y, X[1], P->ny, 1),
+                        q[cnt] = link_q(s, p, image(x, X[0], P->nx, x_periodic(s)), image(y, X[1], P->ny, 1),
                                         image(z, X[2], P->nz, P->periodic_z), j);
                         pid[cnt] = p;
                     }
@@ -1054,6 +1164,10 @@ long orc_links(const orc_state *s, long cap, long *node, int *dir, float *q, int
 }
 
 long orc_refilled(const orc_state *s) { return s->refilled; }
+
+/* Channel option: the plate drag of the last step and the violation flag. */
+double orc_plate_drag(const orc_state *s) { return s->plate_drag; }
+int orc_channel_violation(const orc_state *s) { return s->channel_violation; }
 long orc_step_count(const orc_state *s) { return s->step; }
 
 /* ------------------------------------------------------------------ */

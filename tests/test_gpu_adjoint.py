@@ -107,7 +107,10 @@ def test_autograd_function_gives_the_adjoint_gradient():
 def test_full_differentiation_workload_against_stored_oracle_values():
     """128 x 64 x 64, plate 4 x 40 x 40 at x = 80, 200 fixed spheres of
     radius 3, 500 steps, checkpoints every 50, drag averaged over steps
-    301..500; the oracle values come from tests/golden/make_channel_golden.py."""
+    301..500; the oracle values come from tests/golden/make_channel_golden.py.
+    Also prints the discrepancy of this gradient against central differences
+    of the objective with the spheres free (stored by
+    tests/golden/make_free_sphere_report.py)."""
     with open(os.path.join(HERE, "golden", "channel_config5.json")) as fh:
         gold = json.load(fh)
     c = gold["config"]
@@ -123,3 +126,15 @@ def test_full_differentiation_workload_against_stored_oracle_values():
     for k in range(3):
         assert abs(g[k] - gold["grad_tangent_linear"][k]) <= GRAD_TOL * abs(gold["grad_tangent_linear"][k])
         assert abs(g[k] - gold["grad_central_difference"][k]) <= GRAD_TOL * abs(gold["grad_central_difference"][k])
+    # The same workload with the 200 spheres free (tests/golden/make_free_sphere_report.py, the
+    # coupled oracle): how far this fixed-sphere gradient is from central differences of the
+    # free-sphere objective.  Reported, not asserted: the adjoint leaves the sphere motion out.
+    with open(os.path.join(HERE, "golden", "channel_config5_free.json")) as fh:
+        free = json.load(fh)
+    print("J with the spheres free %.9g (fixed %.9g); sphere displacement max %.3g, mean %.3g" % (
+        free["J_free"], free["J_fixed"], free["displacement_max"], free["displacement_mean"]))
+    for k, name in enumerate(("u_peak", "gx", "cs")):
+        fd = free["grad_free_central_difference"][name]
+        print("%s: adjoint (fixed spheres) %.9g; free-sphere central differences %s at relative steps %s;"
+              " relative discrepancy %s" % (name, g[k], ["%.9g" % v for v in fd], free["fd_relative_steps"],
+                                             ["%.3g" % ((g[k] - v) / abs(v)) for v in fd]))
