@@ -544,9 +544,10 @@ def run_adjoint(args, rank, world, local_rank):
         return
     N, S = 128 * 64 * 64, 500
     ms = (tf + tb) / args.steps
-    # reverse sweep, per node and step: recompute (read G, write G and f, read the 19 link fractions)
-    # and adjoint step (read lambda^{s+1}, f^s and the link fractions, write lambda^s), FP32
-    bytes_bwd = N * S * (4 * 19 * 4 + 4 * 19 * 4)
+    # reverse sweep, per node and step, FP32: recompute (read G^{s-1}, write G^s and f^s) and adjoint
+    # step (read lambda^{s+1} and f^s, write lambda^s): 6 x 19 x 4 B; the link fractions are read at
+    # cut nodes only and the per-node masks (16 B) are left out
+    bytes_bwd = N * S * (6 * 19 * 4)
     achieved = bytes_bwd / (tb / args.steps * 1e-3) / 1e9
     peak, peak_kind = peaks()
     line = {
@@ -563,10 +564,23 @@ def run_adjoint(args, rank, world, local_rank):
                      "frac": achieved / peak, "traffic": None, "algorithmic_bytes_per_launch": bytes_bwd // S},
         "clocks": clk.summary(),
         "e2e": None,
-        "gpu_launches": args.steps * (S + 1 + (S // 50 + 1) + S + 2 * S),
+        "gpu_launches": args.steps * chan_launches(S, 50),
     }
     print(json.dumps(line), flush=True)
     ch.close()
+
+
+def chan_launches(S, K):
+    """Kernel launches of one gradient evaluation of the differentiation form:
+    the forward run (one launch for the initial collision, one per step; the
+    boundary planes ride in the same launches), then per checkpoint segment
+    the recompute (as the forward) and one adjoint launch per step, and the
+    final sum of the gradient parts."""
+    n = S + 1
+    for seg in range(S // K, -1, -1):
+        s0, s1 = seg * K, min(seg * K + K - 1, S)
+        n += (s1 - s0 + 1 if s1 > s0 else 0) + (s1 - s0 + 1)
+    return n + 1
 
 
 def ctypes_stream(stream):

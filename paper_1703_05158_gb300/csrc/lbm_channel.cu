@@ -33,12 +33,16 @@
 // x + c_i, by the bounce-back of x's own cut links and by the Bouzidi rule
 // of the fluid node x + c_i whose link along c_i is cut with q < 1/2; the
 // inlet and outlet rows add the adjoint of rho(1, y, z) and u(nx-2, y, z)
-// to the nodes they read (k_chan_bc_adj).  C^T is the analytic
-// vector-Jacobian product of collide_node (chan_collide_vjp).  The forward
-// run keeps f^s every K steps; the reverse sweep recomputes each K-step
-// segment from its checkpoint, keeping its f^s, and runs the segment
-// backwards.  Parameter gradients are summed per block in FP64 and added
-// with FP64 atomics.
+// to the nodes they read (bc_adj_row).  C^T is the analytic vector-Jacobian
+// product of collide_node (chan_collide_vjp).  The forward run keeps f^s
+// every K steps; the reverse sweep recomputes each K-step segment from its
+// checkpoint, keeping its f^s, and runs the segment backwards, one launch
+// per step.  The boundary planes ride in extra blocks of the same launches:
+// the inlet / outlet equilibria of a forward step, and the inlet / outlet
+// adjoint that the next reverse step needs (it depends only on the step's
+// inputs, lambda^{s+1} and f^s).  Parameter gradients are summed per block
+// in FP64 into the block's own slots and added up once at the end of the
+// sweep.
 #include <cmath>
 #include <vector>
 
@@ -52,13 +56,14 @@ enum : uint8_t { CH_FLUID = 0, CH_SOLID = 1, CH_INLET = 2, CH_OUTLET = 3, CH_PLA
 struct ChanGeo {
     int nx, ny, nz, N;
     const uint8_t *type;    // [N]
-    const uint8_t *cut;     // [N]: 1 if some link x -> x + c_j is cut (then q is read)
+    const uint32_t *cutm;   // [N]: bit j set if the link x -> x + c_j is cut (q is read only then)
     const float *q;         // [Q][N]: fraction of the cut link x -> x + c_j, -1 if not cut
     const uint32_t *plate;  // [N]: bit j set if x -> x + c_j ends in the plate
-    // neighbour masks (static geometry, for the reverse gather): bit i set if
-    // x + c_i is in the box and is an interior fluid node (mfl), also has a
-    // cut link (mcut), or is any fluid class, inlet / outlet included (many)
-    const uint32_t *mfl, *mcut, *many;
+    // neighbour masks (static geometry): bit i set if x + c_i is in the box
+    // and is an interior fluid node (mfl), is an interior fluid node whose
+    // link along c_i is cut with q < 1/2 (mbq: the Bouzidi rule there reads
+    // x), or is any fluid class, inlet / outlet included (many)
+    const uint32_t *mfl, *mbq, *many;
 };
 
 __device__ __forceinline__ int wrapy(int y, int ny) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); }
@@ -120,13 +125,12 @@ __global__ void k_chan_types(const int nx, const int ny, const int nz, const Pla
 // kept when q is rounded to FP32).
 __global__ void k_chan_links(const int nx, const int ny, const int nz, const int np, const double *__restrict__ X,
                              const double *__restrict__ R, const uint8_t *__restrict__ type, float *__restrict__ qout,
-                             uint32_t *__restrict__ plate, uint8_t *__restrict__ cut) {
+                             uint32_t *__restrict__ plate, uint32_t *__restrict__ cutm) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = nx * ny * nz;
     if (n >= N) return;
     const int x = n % nx, y = (n / nx) % ny, z = n / (nx * ny);
-    uint32_t pm = 0;
-    bool any = false;
+    uint32_t pm = 0, cm = 0;
     qout[n] = -1.f;  // j = 0
     for (int j = 1; j < Q; ++j) {
         float qf = -1.f;
@@ -163,14 +167,14 @@ __global__ void k_chan_links(const int nx, const int ny, const int nz, const int
             }
         }
         qout[(size_t)j * N + n] = qf;
-        any |= qf >= 0.f;
+        if (qf >= 0.f) cm |= 1u << j;
     }
     plate[n] = pm;
-    cut[n] = any ? 1 : 0;
+    cutm[n] = cm;
 }
 
 // Neighbour masks of every node (see ChanGeo).
-__global__ void k_chan_masks(const ChanGeo G, uint32_t *__restrict__ mfl, uint32_t *__restrict__ mcut,
+__global__ void k_chan_masks(const ChanGeo G, uint32_t *__restrict__ mfl, uint32_t *__restrict__ mbq,
                              uint32_t *__restrict__ many) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= G.N) return;
@@ -182,12 +186,12 @@ __global__ void k_chan_masks(const ChanGeo G, uint32_t *__restrict__ mfl, uint32
         const uint8_t t = G.type[tn];
         if (t == CH_FLUID) {
             a |= 1u << i;
-            if (G.cut[tn]) b |= 1u << i;
+            if (((G.cutm[tn] >> i) & 1u) && G.q[(size_t)i * G.N + tn] < 0.5f) b |= 1u << i;
         }
         if (is_fluid_type(t)) c |= 1u << i;
     }
     mfl[n] = a;
-    mcut[n] = b;
+    mbq[n] = b;
     many[n] = c;
 }
 
@@ -198,15 +202,15 @@ __global__ void k_chan_masks(const ChanGeo G, uint32_t *__restrict__ mfl, uint32
 __device__ __forceinline__ float pull(const ChanGeo &G, const float *__restrict__ Gin, int x, int y, int z, int n,
                                       int i, bool cut) {
     const int j = ropp(i);
-    const float q = cut ? G.q[(size_t)j * G.N + n] : -1.f;
-    if (q < 0.f) return Gin[(size_t)i * G.N + nbr(G, x, y, z, -rcx(i), -rcy(i), -rcz(i))];
-    const float gj = Gin[(size_t)j * G.N + n];
+    const float q = cut ? G.q[j * G.N + n] : -1.f;
+    if (q < 0.f) return Gin[i * G.N + nbr(G, x, y, z, -rcx(i), -rcy(i), -rcz(i))];
+    const float gj = Gin[j * G.N + n];
     if (q < 0.5f) {
         const int n2 = nbr(G, x, y, z, -rcx(j), -rcy(j), -rcz(j));
-        if (n2 >= 0 && is_fluid_type(G.type[n2])) return 2.f * q * gj + (1.f - 2.f * q) * Gin[(size_t)j * G.N + n2];
+        if (n2 >= 0 && is_fluid_type(G.type[n2])) return 2.f * q * gj + (1.f - 2.f * q) * Gin[j * G.N + n2];
         return gj;
     }
-    return gj / (2.f * q) + (2.f * q - 1.f) / (2.f * q) * Gin[(size_t)i * G.N + n];
+    return gj / (2.f * q) + (2.f * q - 1.f) / (2.f * q) * Gin[i * G.N + n];
 }
 
 // Deviation of f^eq_i(rho, u) (Eq. 9) from w_i.
@@ -228,18 +232,20 @@ __device__ __forceinline__ void moments(const float *d, float &rho, float &jx, f
     }
 }
 
-__device__ __forceinline__ void block_add(double v, double *dst) {
-    __shared__ double part[32];
+// Warp sums of three values added to the warp's own slots dst[0..2] (the
+// same warp of the same block adds to them every reverse step, on one
+// stream; no block barrier).
+__device__ __forceinline__ void warp_part(double a, double b, double c, double *dst) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) part[w] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += part[k];
-        if (s != 0.0) atomicAdd(dst, s);
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        dst[0] += a;
+        dst[1] += b;
+        dst[2] += c;
     }
 }
 
@@ -251,76 +257,49 @@ __device__ __forceinline__ void warp_add(double v, double *dst) {
     if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(dst, v);
 }
 
-// One step at the interior fluid nodes (PULL: f^s pulled from G^{s-1}) or at
-// every fluid node (!PULL: f^s = fin, the stored state): record f^s in frec
-// (may be null), G^s = C(f^s) into Gout (G = f at inlet and outlet nodes),
-// plate drag of G^s added to *drag (may be null).  With PULL the inlet and
-// outlet planes are k_chan_bc_step's.
-template <bool PULL>
-__global__ void __launch_bounds__(256, 4) k_chan_step(const ChanGeo G, const Phys ph, const float *__restrict__ Gin,
-                                                   const float *__restrict__ fin, float *__restrict__ frec,
-                                                   float *__restrict__ Gout, double *__restrict__ drag,
-                                                   int *__restrict__ status) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    double D = 0.0;
-    if (n < G.N) {
-        const uint8_t t = G.type[n];
-        if (PULL ? t == CH_FLUID : is_fluid_type(t)) {
-            float d[Q];
-            if (!PULL) {
-#pragma unroll
-                for (int i = 0; i < Q; ++i) d[i] = fin[(size_t)i * G.N + n];
-            } else {
-                const int x = n % G.nx, y = (n / G.nx) % G.ny, z = n / (G.nx * G.ny);
-                const bool cut = G.cut[n] != 0;
-                if (!cut) {
-                    // no cut link: every x - c_i is in the box (walls and the plate
-                    // cut the links that would leave it; x is interior), plain pull
-                    // with y periodic
-                    const int ym = y == 0 ? G.nx * (G.ny - 1) : -G.nx;
-                    const int yp = y == G.ny - 1 ? -G.nx * (G.ny - 1) : G.nx;
-                    const int zp = G.nx * G.ny;
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        const int off = -rcx(i) + (rcy(i) > 0 ? ym : (rcy(i) < 0 ? yp : 0)) - rcz(i) * zp;
-                        d[i] = Gin[(size_t)i * G.N + n + off];
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) d[i] = pull(G, Gin, x, y, z, n, i, cut);
-                }
-            }
-            if (frec)
-#pragma unroll
-                for (int i = 0; i < Q; ++i) frec[(size_t)i * G.N + n] = d[i];
-            if (t == CH_FLUID) collide_node(ph, d, status);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) Gout[(size_t)i * G.N + n] = d[i];
-            const uint32_t pm = G.plate[n];
-            if (pm)
-#pragma unroll
-                for (int j = 1; j < Q; ++j)
-                    if (((pm >> j) & 1u) && rcx(j) != 0)
-                        D += 2.0 * rcx(j) * ((double)d[j] + (double)rw36(j) / 36.0);
-        }
+// Launch shape of the per-node kernels: a block covers kChanTx consecutive
+// nodes of one x row; grid (ceil(nx / kChanTx), ny, nz), so that (x, y, z)
+// come from the block and thread indices without integer division.
+constexpr int kChanTx = 128;
+#ifndef LBM_CHAN_ADJ_MINB
+#define LBM_CHAN_ADJ_MINB 8  // resident blocks per SM of k_chan_adj (register budget 64)
+#endif
+
+// Row neighbours of (y, z): y periodic; z - 1 and z + 1 clamped into the
+// box (a pull from outside the box is replaced by the bounce-back of the cut
+// wall link, so the clamped value is never used).
+struct RowNb {
+    int ym, yp, zm, zp;
+    __device__ __forceinline__ RowNb(const ChanGeo &G, int y, int z) {
+        ym = y == 0 ? G.ny - 1 : y - 1;
+        yp = y == G.ny - 1 ? 0 : y + 1;
+        zm = z == 0 ? 0 : z - 1;
+        zp = z == G.nz - 1 ? z : z + 1;
     }
-    if (drag) warp_add(D, drag);
-}
+    // row index y' + ny z' of (y, z) + s (c_iy, c_iz), s = +1 or -1
+    __device__ __forceinline__ int row(const ChanGeo &G, int y, int z, int i, int s) const {
+        const int dy = s * rcy(i), dz = s * rcz(i);
+        const int yy = dy > 0 ? yp : (dy < 0 ? ym : y), zz = dz > 0 ? zp : (dz < 0 ? zm : z);
+        return yy + G.ny * zz;
+    }
+    // node index of (x, y, z) + s c_i (x + s c_ix must be in the box)
+    __device__ __forceinline__ int at(const ChanGeo &G, int x, int y, int z, int i, int s) const {
+        return x + s * rcx(i) + G.nx * row(G, y, z, i, s);
+    }
+};
 
 // Inlet (x = 0) and outlet (x = nx - 1) planes of a pulled step, one thread
-// per (y, z, side): the equilibrium of Eq. (9) from the populations pulled at
-// the neighbour plane; G = f there (not collided).
-__global__ void __launch_bounds__(128) k_chan_bc_step(const ChanGeo G, const Phys ph, const float u_peak,
-                                                      const float *__restrict__ Gin, float *__restrict__ frec,
-                                                      float *__restrict__ Gout) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+// per (y, z, side), k in [0, 2 ny nz): the equilibrium of Eq. (9) from the
+// populations pulled at the neighbour plane; G = f there (not collided).
+__device__ __noinline__ void bc_step_body(const ChanGeo G, const Phys ph, const float u_peak,
+                                          const float *__restrict__ Gin, float *__restrict__ frec,
+                                          float *__restrict__ Gout, const int k) {
     const int P = G.ny * G.nz;
-    if (k >= 2 * P) return;
     const bool inlet = k < P;
     const int yz = inlet ? k : k - P, y = yz % G.ny, z = yz / G.ny;
     const int xs = inlet ? 1 : G.nx - 2, ns = xs + G.nx * yz, n = (inlet ? 0 : G.nx - 1) + G.nx * yz;
     float e[Q], d[Q];
-    const bool cut = G.cut[ns] != 0;
+    const bool cut = G.cutm[ns] != 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) e[i] = pull(G, Gin, xs, y, z, ns, i, cut);
     float rho, jx, jy, jz;
@@ -337,100 +316,191 @@ __global__ void __launch_bounds__(128) k_chan_bc_step(const ChanGeo G, const Phy
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        if (frec) frec[(size_t)i * G.N + n] = d[i];
-        Gout[(size_t)i * G.N + n] = d[i];
+        if (frec) frec[i * G.N + n] = d[i];
+        Gout[i * G.N + n] = d[i];
     }
+}
+
+// Index of a thread of the blocks beyond the lattice (blockIdx.z >= nz: the
+// slabs of extra blocks that a launch carries for the boundary planes).
+__device__ __forceinline__ int extra_index(const ChanGeo &G) {
+    return (((blockIdx.z - G.nz) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * kChanTx + threadIdx.x;
+}
+
+// One step at the interior fluid nodes (PULL: f^s pulled from G^{s-1}) or at
+// every fluid node (!PULL: f^s = fin, the stored state): record f^s in frec
+// (may be null), G^s = C(f^s) into Gout (G = f at inlet and outlet nodes),
+// plate drag of G^s added to *drag (may be null).  With PULL the inlet and
+// outlet planes are computed by the launch's extra blocks (blockIdx.z >= nz,
+// bc_step_body).  The pull reads x - c_i for every direction, then replaces
+// the populations of the node's cut links (bounce-back; Eq. 19 with q from
+// the geometry, walls and plate q = 1/2).
+template <bool PULL>
+__global__ void __launch_bounds__(kChanTx, 8) k_chan_step(const ChanGeo G, const Phys ph, const float u_peak,
+                                                       const float *__restrict__ Gin, const float *__restrict__ fin,
+                                                       float *__restrict__ frec, float *__restrict__ Gout,
+                                                       double *__restrict__ drag, int *__restrict__ status) {
+    if (PULL && (int)blockIdx.z >= G.nz) {  // the inlet and outlet planes (independent of the other blocks)
+        const int k = extra_index(G);
+        if (k < 2 * G.ny * G.nz) bc_step_body(G, ph, u_peak, Gin, frec, Gout, k);
+        return;
+    }
+    const int x = blockIdx.x * kChanTx + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    const int n = x + G.nx * (y + G.ny * z);
+    double D = 0.0;
+    if (x < G.nx) {
+        const uint8_t t = G.type[n];
+        if (PULL ? t == CH_FLUID : is_fluid_type(t)) {
+            float d[Q];
+            if (!PULL) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) d[i] = fin[i * G.N + n];
+            } else {
+                const RowNb nb(G, y, z);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) d[i] = Gin[i * G.N + nb.at(G, x, y, z, i, -1)];
+                const uint32_t cm = G.cutm[n];
+                if (cm) {
+                    const uint32_t ma = G.many[n];
+#pragma unroll
+                    for (int i = 1; i < Q; ++i) {
+                        const int j = ropp(i);  // population i arrives from the cut link along c_j
+                        if ((cm >> j) & 1u) {
+                            const float q = G.q[j * G.N + n], gj = Gin[j * G.N + n];
+                            if (q < 0.5f) {
+                                // x - c_j = x + c_i: the second point of the rule, if it is fluid
+                                d[i] = ((ma >> i) & 1u)
+                                           ? 2.f * q * gj + (1.f - 2.f * q) * Gin[j * G.N + nb.at(G, x, y, z, i, 1)]
+                                           : gj;
+                            } else {
+                                d[i] = gj / (2.f * q) + (2.f * q - 1.f) / (2.f * q) * Gin[i * G.N + n];
+                            }
+                        }
+                    }
+                }
+            }
+            if (frec)
+#pragma unroll
+                for (int i = 0; i < Q; ++i) frec[i * G.N + n] = d[i];
+            if (t == CH_FLUID) collide_node(ph, d, status);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) Gout[i * G.N + n] = d[i];
+            const uint32_t pm = G.plate[n];
+            if (pm)
+#pragma unroll
+                for (int j = 1; j < Q; ++j)
+                    if (((pm >> j) & 1u) && rcx(j) != 0)
+                        D += 2.0 * rcx(j) * ((double)d[j] + (double)rw36(j) / 36.0);
+        }
+    }
+    if (drag && __any_sync(0xffffffffu, D != 0.0)) warp_add(D, drag);
 }
 
 // ---- reverse -----------------------------------------------------------------
 
-// Adjoint of the inlet and outlet rows of P at step s + 1, one thread per
-// (y, z):  rho_bar(y, z) is added to the adjoint of every population pulled
-// at (1, y, z), ext[k](y, z) to that of population k pulled at (nx-2, y, z);
-// the u_peak and g_x terms go to grad.
-__global__ void __launch_bounds__(128) k_chan_bc_adj(const ChanGeo G, const Phys ph, const float u_peak,
-                                                     const float *__restrict__ lam1, const float *__restrict__ f1,
-                                                     float *__restrict__ rho_bar, float *__restrict__ ext,
-                                                     double *__restrict__ grad) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;  // y + ny z
-    const int P = G.ny * G.nz;
-    double gu = 0.0, gg = 0.0;
-    if (k < P) {
-        const int y = k % G.ny, z = k / G.ny;
-        const int n0 = G.nx * k, n1 = 1 + G.nx * k, n2 = G.nx - 2 + G.nx * k, nl = G.nx - 1 + G.nx * k;
-        (void)y;
-        // inlet: f_i(0) = rho_1 fe_i(1, u_in)
-        const float zh = (z + 0.5f) / G.nz, sh = 4.f * zh * (1.f - zh), ux = u_peak * sh;
-        float e[Q];
+// Adjoint of the inlet and outlet rows of P at step s + 1 for one row
+// k = y + ny z, given lambda^{s+1} at the row's inlet node (li; bc_adj_inlet)
+// or outlet node (lo; bc_adj_outlet) and f^{s+1} (f1):  rho_bar(y, z) is
+// added to the adjoint of every population pulled at (1, y, z), ext[i](y, z)
+// to that of population i pulled at (nx-2, y, z); gu and gg are the row's
+// parts of dJ/du_peak and dJ/dg_x.
+__device__ __forceinline__ void bc_adj_inlet(const ChanGeo &G, const float u_peak, const float (&li)[Q],
+                                             const float *__restrict__ f1, const int k, float *__restrict__ rho_bar,
+                                             double &gu) {
+    const int z = k / G.ny, n1 = 1 + G.nx * k;
+    // inlet: f_i(0) = rho_1 fe_i(1, u_in)
+    const float zh = (z + 0.5f) / G.nz, sh = 4.f * zh * (1.f - zh), ux = u_peak * sh;
+    float e[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) e[i] = f1[(size_t)i * G.N + n1];
-        float rho1, jx, jy, jz;
-        moments(e, rho1, jx, jy, jz);
-        float rb = 0.f, ub = 0.f;
+    for (int i = 0; i < Q; ++i) e[i] = f1[i * G.N + n1];
+    float rho1, jx, jy, jz;
+    moments(e, rho1, jx, jy, jz);
+    float rb = 0.f, ub = 0.f;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const float w = (float)rw36(i) / 36.f, cu = rcx(i) * ux, l = lam1[(size_t)i * G.N + n0];
-            rb += l * w * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * ux * ux);
-            ub += l * w * (3.f * rcx(i) + 9.f * cu * rcx(i) - 3.f * ux);
-        }
-        rho_bar[k] = rb;
-        gu = (double)ub * rho1 * sh;
-        // outlet: f_i(nx-1) = f^eq_i(1, u(nx-2)), u = j / rho + g / 2
-#pragma unroll
-        for (int i = 0; i < Q; ++i) e[i] = f1[(size_t)i * G.N + n2];
-        float rho2;
-        moments(e, rho2, jx, jy, jz);
-        const float ir = 1.f / rho2;
-        const float u[3] = {jx * ir + 0.5f * ph.g[0], jy * ir + 0.5f * ph.g[1], jz * ir + 0.5f * ph.g[2]};
-        float uba[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const float w = (float)rw36(i) / 36.f, l = lam1[(size_t)i * G.N + nl];
-            const float cu = rcx(i) * u[0] + rcy(i) * u[1] + rcz(i) * u[2];
-            uba[0] += l * w * (3.f * rcx(i) + 9.f * cu * rcx(i) - 3.f * u[0]);
-            uba[1] += l * w * (3.f * rcy(i) + 9.f * cu * rcy(i) - 3.f * u[1]);
-            uba[2] += l * w * (3.f * rcz(i) + 9.f * cu * rcz(i) - 3.f * u[2]);
-        }
-        const float v[3] = {jx * ir, jy * ir, jz * ir};
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-            ext[(size_t)i * P + k] = ir * (uba[0] * (rcx(i) - v[0]) + uba[1] * (rcy(i) - v[1]) + uba[2] * (rcz(i) - v[2]));
-        gg = 0.5 * (double)uba[0];
+    for (int i = 0; i < Q; ++i) {
+        const float w = (float)rw36(i) / 36.f, cu = rcx(i) * ux, l = li[i];
+        rb += l * w * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * ux * ux);
+        ub += l * w * (3.f * rcx(i) + 9.f * cu * rcx(i) - 3.f * ux);
     }
-    block_add(gu, grad + 0);
-    block_add(gg, grad + 1);
+    rho_bar[k] = rb;
+    gu = (double)ub * rho1 * sh;
+}
+
+__device__ __forceinline__ void bc_adj_outlet(const ChanGeo &G, const Phys &ph, const float (&lo)[Q],
+                                              const float *__restrict__ f1, const int k, float *__restrict__ ext,
+                                              double &gg) {
+    const int P = G.ny * G.nz, n2 = G.nx - 2 + G.nx * k;
+    // outlet: f_i(nx-1) = f^eq_i(1, u(nx-2)), u = j / rho + g / 2
+    float e[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) e[i] = f1[i * G.N + n2];
+    float rho2, jx, jy, jz;
+    moments(e, rho2, jx, jy, jz);
+    const float ir = 1.f / rho2;
+    const float u[3] = {jx * ir + 0.5f * ph.g[0], jy * ir + 0.5f * ph.g[1], jz * ir + 0.5f * ph.g[2]};
+    float uba[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float w = (float)rw36(i) / 36.f, l = lo[i];
+        const float cu = rcx(i) * u[0] + rcy(i) * u[1] + rcz(i) * u[2];
+        uba[0] += l * w * (3.f * rcx(i) + 9.f * cu * rcx(i) - 3.f * u[0]);
+        uba[1] += l * w * (3.f * rcy(i) + 9.f * cu * rcy(i) - 3.f * u[1]);
+        uba[2] += l * w * (3.f * rcz(i) + 9.f * cu * rcz(i) - 3.f * u[2]);
+    }
+    const float v[3] = {jx * ir, jy * ir, jz * ir};
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        ext[i * P + k] = ir * (uba[0] * (rcx(i) - v[0]) + uba[1] * (rcy(i) - v[1]) + uba[2] * (rcz(i) - v[2]));
+    gg = 0.5 * (double)uba[0];
 }
 
 // Vector-Jacobian product of collide_node at deviations d: lam = C'(d)^T gb,
 // and the products with dC/dg_x and dC/dsmag (smag = 18 sqrt(2) C^2).
-__device__ __forceinline__ void chan_collide_vjp(const Phys &ph, const float (&d)[Q], const float (&gb)[Q],
-                                                 float (&lam)[Q], float &gx_bar, float &smag_bar) {
-    // forward intermediates
-    float drho = 0.f, j[3] = {0.f, 0.f, 0.f};
+//
+// The collision is g_k = (1 - om) d_k + om E_k + sk S_k with
+//   E_k = w_k (drho - 1.5 rho u.u + 4.5 rho (c_k.u)^2 + 3 rho c_k.u),
+//   S_k = w_k rho g_x (3 c_kx - 3 u_x + 9 (c_k.u) c_kx),  sk = 1 - om/2,
+// and E, S and om depend on d only through drho, j and Pi.  So every sum
+// over k that the chain rule needs is a moment of gb: with
+//   N0 = sum w_k gb_k,  N1 = sum w_k gb_k c_k,  N2 = sum w_k gb_k c_k c_k,
+// sum w gb (c.u) = u.N1, sum w gb (c.u)^2 = u.N2.u, sum w gb (c.u) c = N2 u.
+// The result is lam_i = (1 - om) gb_i + A + B.c_i + M:c_i c_i, taken by
+// opposite pairs (i, i + 9) like the forward collision.  Divisions and
+// square roots use the hardware approximations (a few ulp): the adjoint
+// only has to carry the gradient to well within its 1e-3 tolerance.  The deviations are
+// read pair by pair from f (node n of [Q][N] arrays; null: the rest state)
+// and the result is written to lam (same layout), so that only gb is held
+// whole.
+__device__ __forceinline__ void chan_collide_vjp(const Phys &ph, const float *__restrict__ f, const int n,
+                                                 const int N, const float (&gb)[Q], float *__restrict__ lam,
+                                                 float &gx_bar, float &smag_bar) {
+    // forward intermediates (the moments of d, by opposite pairs)
+    const float d0 = f ? f[n] : 0.f;
+    float drho = d0, j[3] = {0.f, 0.f, 0.f}, m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // m: xx yy zz xy xz yz
+    float N0 = wf(0) * gb[0], N1[3] = {0.f, 0.f, 0.f}, N2[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gd = gb[0] * d0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        drho += d[i];
-        j[0] += rcx(i) * d[i];
-        j[1] += rcy(i) * d[i];
-        j[2] += rcz(i) * d[i];
+    for (int i = 1; i <= 9; ++i) {
+        const int k = i + 9;  // opp(i)
+        const float di = f ? f[i * N + n] : 0.f, dk = f ? f[k * N + n] : 0.f;
+        const float sp = di + dk, dm = di - dk;
+        const float gs = wf(i) * (gb[i] + gb[k]), gm = wf(i) * (gb[i] - gb[k]);
+        drho += sp;
+        N0 += gs;
+        gd += gb[i] * di + gb[k] * dk;
+        if (cx(i)) { j[0] += cx(i) * dm; N1[0] += cx(i) * gm; m[0] += sp; N2[0] += gs; }
+        if (cy(i)) { j[1] += cy(i) * dm; N1[1] += cy(i) * gm; m[1] += sp; N2[1] += gs; }
+        if (cz(i)) { j[2] += cz(i) * dm; N1[2] += cz(i) * gm; m[2] += sp; N2[2] += gs; }
+        if (cx(i) * cy(i)) { m[3] += cx(i) * cy(i) * sp; N2[3] += cx(i) * cy(i) * gs; }
+        if (cx(i) * cz(i)) { m[4] += cx(i) * cz(i) * sp; N2[4] += cx(i) * cz(i) * gs; }
+        if (cy(i) * cz(i)) { m[5] += cy(i) * cz(i) * sp; N2[5] += cy(i) * cz(i) * gs; }
     }
-    const float rho = 1.f + drho, ir = 1.f / rho;
+    const float rho = 1.f + drho, ir = __fdividef(1.f, rho);
     const float u[3] = {j[0] * ir + 0.5f * ph.g[0], j[1] * ir + 0.5f * ph.g[1], j[2] * ir + 0.5f * ph.g[2]};
     const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // xx yy zz xy xz yz
     float P6[6], Qn = 0.f, inner = ph.tau0 * ph.tau0, tau = ph.tau0;
     const bool les = ph.smag > 0.f;
     if (les) {
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            m[0] += rcx(i) * rcx(i) * d[i];
-            m[1] += rcy(i) * rcy(i) * d[i];
-            m[2] += rcz(i) * rcz(i) * d[i];
-            m[3] += rcx(i) * rcy(i) * d[i];
-            m[4] += rcx(i) * rcz(i) * d[i];
-            m[5] += rcy(i) * rcz(i) * d[i];
-        }
-        const float t3 = drho / 3.f;
+        const float t3 = drho * (1.f / 3.f);
         P6[0] = m[0] - t3 - rho * u[0] * u[0];
         P6[1] = m[1] - t3 - rho * u[1] * u[1];
         P6[2] = m[2] - t3 - rho * u[2] * u[2];
@@ -439,57 +509,50 @@ __device__ __forceinline__ void chan_collide_vjp(const Phys &ph, const float (&d
         P6[5] = m[5] - rho * u[1] * u[2];
         const float q2 = P6[0] * P6[0] + P6[1] * P6[1] + P6[2] * P6[2] +
                          2.f * (P6[3] * P6[3] + P6[4] * P6[4] + P6[5] * P6[5]);
-        Qn = sqrtf(q2);
+        Qn = q2 > 0.f ? q2 * rsqrtf(q2) : 0.f;
         inner = ph.smag * Qn * ir + ph.tau0 * ph.tau0;
-        tau = ph.tau0 + 0.5f * (sqrtf(inner) - ph.tau0);
+        tau = ph.tau0 + 0.5f * (inner * rsqrtf(inner) - ph.tau0);
     }
-    const float om = 1.f / tau, sk = 1.f - 0.5f * om, gx = ph.g[0];
-    // g_i = (1 - om) d_i + om E_i + sk S_i,
-    // E_i = w_i (drho - 1.5 rho uu + 4.5 rho cu^2 + 3 rho cu),
-    // S_i = w_i rho g_x (3 c_ix - 3 u_x + 9 cu c_ix)
-    float om_bar = 0.f, drho_bar = 0.f, rho_bar = 0.f, ub[3] = {0.f, 0.f, 0.f};
-    gx_bar = 0.f;
+    const float om = __fdividef(1.f, tau), sk = 1.f - 0.5f * om, gx = ph.g[0];
+    // moments of gb contracted with u
+    const float N2u[3] = {N2[0] * u[0] + N2[3] * u[1] + N2[4] * u[2], N2[3] * u[0] + N2[1] * u[1] + N2[5] * u[2],
+                          N2[4] * u[0] + N2[5] * u[1] + N2[2] * u[2]};
+    const float uN1 = u[0] * N1[0] + u[1] * N1[1] + u[2] * N1[2];
+    const float uN2u = u[0] * N2u[0] + u[1] * N2u[1] + u[2] * N2u[2];
+    const float eq = -1.5f * uu * N0 + 4.5f * uN2u + 3.f * uN1;  // sum w gb (E/w - drho)/rho
+    const float sx = 3.f * N1[0] - 3.f * u[0] * N0 + 9.f * N2u[0];  // sum gb S / (rho g_x)
+    // om_bar = sum gb (E - d - S/2)
+    const float om_bar = drho * N0 + rho * eq - gd - 0.5f * rho * gx * sx;
+    float drho_bar = om * N0;
+    float rho_bar = om * eq + sk * gx * sx;
+    float ub[3];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const float w = (float)rw36(i) / 36.f;
-        const float cu = rcx(i) * u[0] + rcy(i) * u[1] + rcz(i) * u[2];
-        const float E = w * (drho - 1.5f * rho * uu + 4.5f * rho * cu * cu + 3.f * rho * cu);
-        const float sb = w * rho * (3.f * rcx(i) - 3.f * u[0] + 9.f * cu * rcx(i));  // S_i / g_x
-        const float S = sb * gx;
-        lam[i] = (1.f - om) * gb[i];
-        om_bar += gb[i] * (E - d[i] - 0.5f * S);
-        const float Eb = om * gb[i], Sb = sk * gb[i];
-        drho_bar += Eb * w;
-        rho_bar += Eb * w * (-1.5f * uu + 4.5f * cu * cu + 3.f * cu) + Sb * sb * gx * ir;
-        const float ke = Eb * w * rho, ks = Sb * w * rho * gx;
-        ub[0] += ke * (-3.f * u[0] + 9.f * cu * rcx(i) + 3.f * rcx(i)) + ks * (-3.f + 9.f * rcx(i) * rcx(i));
-        ub[1] += ke * (-3.f * u[1] + 9.f * cu * rcy(i) + 3.f * rcy(i)) + ks * (9.f * rcx(i) * rcy(i));
-        ub[2] += ke * (-3.f * u[2] + 9.f * cu * rcz(i) + 3.f * rcz(i)) + ks * (9.f * rcx(i) * rcz(i));
-        gx_bar += Sb * sb;
-    }
+    for (int a = 0; a < 3; ++a) ub[a] = om * rho * (-3.f * u[a] * N0 + 9.f * N2u[a] + 3.f * N1[a]);
+    const float ks = sk * rho * gx;
+    ub[0] += ks * (-3.f * N0 + 9.f * N2[0]);
+    ub[1] += ks * 9.f * N2[3];
+    ub[2] += ks * 9.f * N2[4];
+    gx_bar = sk * rho * sx;
     // om = 1 / tau, tau = tau0 + (sqrt(inner) - tau0) / 2, inner = smag Q / rho + tau0^2
     float ir_bar = 0.f, mb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     smag_bar = 0.f;
     if (les) {
         const float tau_bar = -om_bar * om * om;
-        const float in_bar = tau_bar * 0.25f / sqrtf(inner);
+        const float in_bar = tau_bar * 0.25f * rsqrtf(inner);
         smag_bar = in_bar * Qn * ir;
         ir_bar += in_bar * ph.smag * Qn;
         const float Q_bar = in_bar * ph.smag * ir;
-        const float q2_bar = Qn > 0.f ? Q_bar / (2.f * Qn) : 0.f;
-        float Pb[6];
+        const float q2_bar = Qn > 0.f ? __fdividef(Q_bar, 2.f * Qn) : 0.f;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) Pb[k] = 2.f * P6[k] * q2_bar;
+        for (int k = 0; k < 3; ++k) mb[k] = 2.f * P6[k] * q2_bar;
 #pragma unroll
-        for (int k = 3; k < 6; ++k) Pb[k] = 4.f * P6[k] * q2_bar;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) mb[k] = Pb[k];
-        drho_bar -= (Pb[0] + Pb[1] + Pb[2]) / 3.f;
-        rho_bar -= Pb[0] * u[0] * u[0] + Pb[1] * u[1] * u[1] + Pb[2] * u[2] * u[2] + Pb[3] * u[0] * u[1] +
-                   Pb[4] * u[0] * u[2] + Pb[5] * u[1] * u[2];
-        ub[0] -= rho * (2.f * Pb[0] * u[0] + Pb[3] * u[1] + Pb[4] * u[2]);
-        ub[1] -= rho * (2.f * Pb[1] * u[1] + Pb[3] * u[0] + Pb[5] * u[2]);
-        ub[2] -= rho * (2.f * Pb[2] * u[2] + Pb[4] * u[0] + Pb[5] * u[1]);
+        for (int k = 3; k < 6; ++k) mb[k] = 4.f * P6[k] * q2_bar;
+        drho_bar -= (mb[0] + mb[1] + mb[2]) * (1.f / 3.f);
+        rho_bar -= mb[0] * u[0] * u[0] + mb[1] * u[1] * u[1] + mb[2] * u[2] * u[2] + mb[3] * u[0] * u[1] +
+                   mb[4] * u[0] * u[2] + mb[5] * u[1] * u[2];
+        ub[0] -= rho * (2.f * mb[0] * u[0] + mb[3] * u[1] + mb[4] * u[2]);
+        ub[1] -= rho * (2.f * mb[1] * u[1] + mb[3] * u[0] + mb[5] * u[2]);
+        ub[2] -= rho * (2.f * mb[2] * u[2] + mb[4] * u[0] + mb[5] * u[1]);
     }
     // u = j / rho + g / 2
     const float jb[3] = {ub[0] * ir, ub[1] * ir, ub[2] * ir};
@@ -497,88 +560,165 @@ __device__ __forceinline__ void chan_collide_vjp(const Phys &ph, const float (&d
     gx_bar += 0.5f * ub[0];
     rho_bar -= ir_bar * ir * ir;
     const float dtot = drho_bar + rho_bar;  // rho = 1 + drho
+    const float keep = 1.f - om;
+    lam[n] = keep * gb[0] + dtot;
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-        lam[i] += dtot + jb[0] * rcx(i) + jb[1] * rcy(i) + jb[2] * rcz(i) + mb[0] * rcx(i) * rcx(i) +
-                  mb[1] * rcy(i) * rcy(i) + mb[2] * rcz(i) * rcz(i) + mb[3] * rcx(i) * rcy(i) +
-                  mb[4] * rcx(i) * rcz(i) + mb[5] * rcy(i) * rcz(i);
+    for (int i = 1; i <= 9; ++i) {
+        const int k = i + 9;
+        float even = dtot, odd = 0.f;
+        if (cx(i)) { even += mb[0]; odd += cx(i) * jb[0]; }
+        if (cy(i)) { even += mb[1]; odd += cy(i) * jb[1]; }
+        if (cz(i)) { even += mb[2]; odd += cz(i) * jb[2]; }
+        if (cx(i) * cy(i)) even += cx(i) * cy(i) * mb[3];
+        if (cx(i) * cz(i)) even += cx(i) * cz(i) * mb[4];
+        if (cy(i) * cz(i)) even += cy(i) * cz(i) * mb[5];
+        lam[i * N + n] = keep * gb[i] + even + odd;
+        lam[k * N + n] = keep * gb[k] + even - odd;
+    }
 }
 
-// Adjoint of the population pulled as k at interior fluid node t (at x = xt,
-// row yz = y + ny z), with the inlet / outlet rows folded in.
-__device__ __forceinline__ float eff(const ChanGeo &G, const float *__restrict__ lam1, const float *__restrict__ rho_bar,
-                                     const float *__restrict__ ext, int t, int xt, int yz, int k) {
-    float v = lam1[(size_t)k * G.N + t];
+// The inlet / outlet part of the adjoint of the population pulled as k at
+// interior fluid node t at x = xt (row yz): the inlet and outlet rows of P
+// read the pulls at x = 1 and x = nx - 2.
+__device__ __forceinline__ float edge_adj(const ChanGeo &G, const float *__restrict__ rho_bar,
+                                          const float *__restrict__ ext, int xt, int yz, int k) {
+    float v = 0.f;
     if (xt == 1) v += rho_bar[yz];
-    if (xt == G.nx - 2) v += ext[(size_t)k * (G.ny * G.nz) + yz];
+    if (xt == G.nx - 2) v += ext[k * (G.ny * G.nz) + yz];
     return v;
 }
 
+// Adjoint of the population pulled as k at interior fluid node t (at x = xt,
+// row yz), with the inlet / outlet rows folded in.
+__device__ __forceinline__ float eff(const ChanGeo &G, const float *__restrict__ lam1, const float *__restrict__ rho_bar,
+                                     const float *__restrict__ ext, int t, int xt, int yz, int k) {
+    return lam1[k * G.N + t] + edge_adj(G, rho_bar, ext, xt, yz, k);
+}
+
+// The adjoint gb of G^s at fluid-class node (x, y, z), index n, that the
+// pulls of step s + 1 at the neighbours give: the regular pull of x + c_i
+// (an interior fluid node) and the Bouzidi rule of x + c_i whose link along
+// c_i is cut with q < 1/2 (it reads x).
+__device__ __forceinline__ void gather_adj(const ChanGeo &G, const float *__restrict__ lam1,
+                                           const float *__restrict__ rho_bar, const float *__restrict__ ext, int x,
+                                           int y, int z, int n, float (&gb)[Q]) {
+    const RowNb nb(G, y, z);
+    const uint32_t mf = G.mfl[n], mb = G.mbq[n];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        float v = 0.f;
+        if ((mf >> i) & 1u) {
+            const int xt = x + rcx(i), yzt = nb.row(G, y, z, i, 1), tn = xt + G.nx * yzt;
+            v = eff(G, lam1, rho_bar, ext, tn, xt, yzt, i);
+            if ((mb >> i) & 1u)
+                v += (1.f - 2.f * G.q[i * G.N + tn]) * eff(G, lam1, rho_bar, ext, tn, xt, yzt, ropp(i));
+        }
+        gb[i] = v;
+    }
+}
+
+// The inlet / outlet adjoint of step s - 1 for row k (k_chan_adj's extra
+// blocks): lambda^s at the row's inlet and outlet nodes is their gathered gb.
+// Not inlined, so that the node kernel's instruction stream stays short.
+__device__ __noinline__ void adj_extra_row(const ChanGeo G, const Phys ph, const float u_peak,
+                                           const float *__restrict__ lam1, const float *__restrict__ fs,
+                                           const float *__restrict__ rho_bar, const float *__restrict__ ext,
+                                           float *__restrict__ rho_nx, float *__restrict__ ext_nx, const int k,
+                                           double &gup, double &ggx) {
+    const int y = k % G.ny, z = k / G.ny;
+    float l[Q];
+    gather_adj(G, lam1, rho_bar, ext, 0, y, z, G.nx * k, l);
+    bc_adj_inlet(G, u_peak, l, fs, k, rho_nx, gup);
+    gather_adj(G, lam1, rho_bar, ext, G.nx - 1, y, z, G.nx - 1 + G.nx * k, l);
+    bc_adj_outlet(G, ph, l, fs, k, ext_nx, ggx);
+}
+
 // Reverse step s: lambda^s from lambda^{s+1} (lam1) and f^s (fs; null for
-// the rest state f^0 = w), weight wd of D^s in J (0 outside the window).
-__global__ void __launch_bounds__(256, 3) k_chan_adj(const ChanGeo G, const Phys ph, const float *__restrict__ lam1,
-                                                  const float *__restrict__ fs, const float *__restrict__ rho_bar,
-                                                  const float *__restrict__ ext, const float wd,
-                                                  float *__restrict__ lam0, double *__restrict__ grad) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    double ggx = 0.0, gsm = 0.0;
-    if (n < G.N) {
-        const int x = n % G.nx, y = (n / G.nx) % G.ny, z = n / (G.nx * G.ny);
-        const uint8_t t = G.type[n];
-        if (!is_fluid_type(t)) {
+// the rest state f^0 = w), weight wd of D^s in J (0 outside the window),
+// with the inlet / outlet adjoint of step s + 1 in rho_bar and ext.  The
+// parts of dJ/d(u_peak, g_x, smag) of each warp are added to its own slots
+// of gpart (3 per warp, summed over the steps; no atomics).  The launch's
+// extra blocks (blockIdx.z >= nz, present when rho_nx is not null) compute
+// the inlet / outlet adjoint of step s that the next reverse step reads
+// (rho_nx, ext_nx; from lambda^s at the inlet and outlet nodes, where it is
+// the gathered gb, and f^s), independently of the other blocks.
+__global__ void __launch_bounds__(kChanTx, LBM_CHAN_ADJ_MINB) k_chan_adj(
+    const ChanGeo G, const Phys ph, const float u_peak, const float *__restrict__ lam1, const float *__restrict__ fs,
+    const float *__restrict__ rho_bar, const float *__restrict__ ext, const float wd, float *__restrict__ lam0,
+    float *__restrict__ rho_nx, float *__restrict__ ext_nx, double *__restrict__ gpart) {
+    double gup = 0.0, ggx = 0.0, gsm = 0.0;
+    if ((int)blockIdx.z >= G.nz) {
+        const int k = extra_index(G);  // row y + ny z
+        if (k < G.ny * G.nz) adj_extra_row(G, ph, u_peak, lam1, fs, rho_bar, ext, rho_nx, ext_nx, k, gup, ggx);
+    } else {
+        const int x = blockIdx.x * kChanTx + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+        const int n = x + G.nx * (y + G.ny * z);
+        if (x < G.nx) {
+            const uint8_t t = G.type[n];
+            if (!is_fluid_type(t)) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) lam0[(size_t)i * G.N + n] = 0.f;
-        } else {
-            float gb[Q];
-            const uint32_t pm = G.plate[n];
-            const bool cut = G.cut[n] != 0;
-            const int yz0 = y + G.ny * z;
-            const uint32_t mf = G.mfl[n], mc = G.mcut[n], ma = G.many[n];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                float v = 0.f;
-                if ((mf >> i) & 1u) {  // x + c_i is an interior fluid node
-                    const int tn = nbr(G, x, y, z, rcx(i), rcy(i), rcz(i));
-                    const int xt = x + rcx(i), yzt = wrapy(y + rcy(i), G.ny) + G.ny * (z + rcz(i));
-                    v += eff(G, lam1, rho_bar, ext, tn, xt, yzt, i);  // regular pull of x + c_i
-                    const float qt = ((mc >> i) & 1u) ? G.q[(size_t)i * G.N + tn] : -1.f;
-                    if (qt >= 0.f && qt < 0.5f)
-                        v += (1.f - 2.f * qt) * eff(G, lam1, rho_bar, ext, tn, xt, yzt, ropp(i));
-                }
-                if (t == CH_FLUID && cut) {
-                    const float qi = G.q[(size_t)i * G.N + n];  // own link along c_i
-                    if (qi >= 0.f) {
-                        float a;
-                        if (qi < 0.5f) {
-                            a = ((ma >> ropp(i)) & 1u) ? 2.f * qi : 1.f;  // x - c_i fluid
-                        } else {
-                            a = 1.f / (2.f * qi);
-                        }
-                        v += a * eff(G, lam1, rho_bar, ext, n, x, yz0, ropp(i));
-                    }
-                    const float qo = G.q[(size_t)ropp(i) * G.N + n];  // own link along -c_i
-                    if (qo >= 0.5f) v += (2.f * qo - 1.f) / (2.f * qo) * eff(G, lam1, rho_bar, ext, n, x, yz0, i);
-                }
-                if (wd != 0.f && ((pm >> i) & 1u)) v += wd * 2.f * rcx(i);
-                gb[i] = v;
-            }
-            if (t == CH_FLUID) {
-                float d[Q], lam[Q], gxb, smb;
-#pragma unroll
-                for (int i = 0; i < Q; ++i) d[i] = fs ? fs[(size_t)i * G.N + n] : 0.f;
-                chan_collide_vjp(ph, d, gb, lam, gxb, smb);
-#pragma unroll
-                for (int i = 0; i < Q; ++i) lam0[(size_t)i * G.N + n] = lam[i];
-                ggx = gxb;
-                gsm = smb;
+                for (int i = 0; i < Q; ++i) lam0[i * G.N + n] = 0.f;
             } else {
+                float gb[Q];
+                gather_adj(G, lam1, rho_bar, ext, x, y, z, n, gb);
+                const int yz0 = y + G.ny * z;
+                // the node's own cut links (the adjoint of the populations it pulls itself)
+                const uint32_t cm = t == CH_FLUID ? G.cutm[n] : 0u;
+                if (cm) {
+                    const uint32_t ma = G.many[n];
 #pragma unroll
-                for (int i = 0; i < Q; ++i) lam0[(size_t)i * G.N + n] = gb[i];
+                    for (int i = 1; i < Q; ++i) {
+                        if ((cm >> i) & 1u) {  // link along c_i: population opp(i) reads G_i(x)
+                            const float qi = G.q[i * G.N + n];
+                            const float a = qi < 0.5f ? (((ma >> ropp(i)) & 1u) ? 2.f * qi : 1.f) : 1.f / (2.f * qi);
+                            gb[i] += a * eff(G, lam1, rho_bar, ext, n, x, yz0, ropp(i));
+                        }
+                        if ((cm >> ropp(i)) & 1u) {  // link along -c_i with q >= 1/2: population i reads G_i(x)
+                            const float qo = G.q[ropp(i) * G.N + n];
+                            if (qo >= 0.5f) gb[i] += (2.f * qo - 1.f) / (2.f * qo) * eff(G, lam1, rho_bar, ext, n, x, yz0, i);
+                        }
+                    }
+                }
+                const uint32_t pm = G.plate[n];
+                if (wd != 0.f && pm)
+#pragma unroll
+                    for (int i = 0; i < Q; ++i)
+                        if ((pm >> i) & 1u) gb[i] += wd * 2.f * rcx(i);
+                if (t == CH_FLUID) {
+                    float gxb, smb;
+                    chan_collide_vjp(ph, fs, n, G.N, gb, lam0, gxb, smb);
+                    ggx = gxb;
+                    gsm = smb;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) lam0[i * G.N + n] = gb[i];
+                }
             }
         }
     }
-    block_add(ggx, grad + 1);
-    block_add(gsm, grad + 2);
+    const int warp = (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)) * (kChanTx / 32) + (threadIdx.x >> 5);
+    warp_part(gup, ggx, gsm, gpart + 3 * warp);
+}
+
+// grad[0..2] += the sum of the nb warps' parts.
+__global__ void __launch_bounds__(256) k_chan_gsum(const double *__restrict__ gpart, int nb, double *__restrict__ grad) {
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int k = threadIdx.x; k < nb; k += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a[c] += gpart[3 * k + c];
+    __shared__ double sh[3][8];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+        if ((threadIdx.x & 31) == 0) sh[c][threadIdx.x >> 5] = a[c];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) a[c] += sh[c][w];
+            grad[c] += a[c];
+        }
 }
 
 }  // namespace
@@ -589,16 +729,18 @@ using namespace lbm;
 struct lbm_channel_s {
     lbm_channel_params p;
     int N = 0, np = 0, K = 0, nck = 0;
-    uint8_t *type = nullptr, *cut = nullptr;
+    uint8_t *type = nullptr;
+    uint32_t *cutm = nullptr;
     float *q = nullptr;
     uint32_t *plate = nullptr;
-    uint32_t *mfl = nullptr, *mcut = nullptr, *many = nullptr;
+    uint32_t *mfl = nullptr, *mbq = nullptr, *many = nullptr;
+    double *gpart = nullptr;  // per-warp parts of dJ/d(u_peak, g_x, smag) (k_chan_adj)
     double *X = nullptr, *R = nullptr;
     float *G[2] = {nullptr, nullptr}, *lam[2] = {nullptr, nullptr};
     float *seg = nullptr;   // K states f^s of a segment
     float *ckpt = nullptr;  // f^s at s = 0, K, 2K, ...
     float *fend = nullptr;  // f^S of the last forward
-    float *rho_bar = nullptr, *ext = nullptr;
+    float *rho_bar[2] = {nullptr, nullptr}, *ext[2] = {nullptr, nullptr};  // inlet / outlet adjoint, by step parity
     double *drag = nullptr, *grad = nullptr;
     int *status = nullptr;
     cudaStream_t stream = nullptr;
@@ -618,11 +760,11 @@ ChanGeo geo_of(const lbm_channel_s *c) {
     g.nz = c->p.nz;
     g.N = c->N;
     g.type = c->type;
-    g.cut = c->cut;
+    g.cutm = c->cutm;
     g.q = c->q;
     g.plate = c->plate;
     g.mfl = c->mfl;
-    g.mcut = c->mcut;
+    g.mbq = c->mbq;
     g.many = c->many;
     return g;
 }
@@ -648,8 +790,8 @@ int calloc_dev(lbm_channel_s *c, T **p, size_t n) {
 }
 
 void chan_release(lbm_channel_s *c) {
-    void *ptrs[] = {c->type, c->cut, c->q, c->plate, c->mfl, c->mcut, c->many, c->X, c->R, c->G[0], c->G[1], c->lam[0], c->lam[1], c->seg, c->ckpt,
-                    c->fend, c->rho_bar, c->ext, c->drag, c->grad, c->status};
+    void *ptrs[] = {c->type, c->cutm, c->q, c->plate, c->mfl, c->mbq, c->many, c->gpart, c->X, c->R, c->G[0], c->G[1], c->lam[0], c->lam[1], c->seg, c->ckpt,
+                    c->fend, c->rho_bar[0], c->rho_bar[1], c->ext[0], c->ext[1], c->drag, c->grad, c->status};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -674,24 +816,34 @@ int chan_check(lbm_channel_s *c, int rc) {
 
 int launch_ok() { return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; }
 
+// Grid of the per-node kernels (see kChanTx) with extra slabs of blocks for
+// `extra` more threads (the boundary-plane work), and its block count.
+dim3 chan_grid(const lbm_channel_params &p, long long extra) {
+    const long long gx = (p.nx + kChanTx - 1) / kChanTx, per_slab = gx * p.ny * kChanTx;
+    return dim3((unsigned)gx, p.ny, p.nz + (unsigned)((extra + per_slab - 1) / per_slab));
+}
+int chan_warps(const lbm_channel_params &p, long long extra) {
+    const dim3 g = chan_grid(p, extra);
+    return (int)(g.x * g.y * g.z) * (kChanTx / 32);
+}
+
 // Forward from f^{s0} (fin) over steps s0 + 1 .. s1: f^s recorded into
 // rec(s) when it returns non-null; drag of G^s into drag[s - 1] when
 // with_drag.
 template <typename Rec>
 int chan_run(lbm_channel_s *c, const float *fin, int s0, int s1, Rec rec, bool with_drag) {
     const ChanGeo g = geo_of(c);
-    const int blocks = (c->N + 255) / 256, bblocks = (2 * c->p.ny * c->p.nz + 127) / 128;
+    const dim3 grid = chan_grid(c->p, 0), grid_bc = chan_grid(c->p, 2ll * c->p.ny * c->p.nz);
     const float up = (float)c->theta[0];
-    k_chan_step<false><<<blocks, 256, 0, c->stream>>>(g, c->ph, nullptr, fin, nullptr, c->G[s0 & 1],
+    k_chan_step<false><<<grid, kChanTx, 0, c->stream>>>(g, c->ph, up, nullptr, fin, nullptr, c->G[s0 & 1],
                                                       with_drag && s0 >= 1 ? c->drag + (s0 - 1) : nullptr, c->status);
     int rc = launch_ok();
     for (int s = s0 + 1; s <= s1 && !rc; ++s) {
         float *fr = rec(s);
-        k_chan_step<true><<<blocks, 256, 0, c->stream>>>(g, c->ph, c->G[(s - 1) & 1], nullptr, fr, c->G[s & 1],
-                                                         with_drag ? c->drag + (s - 1) : nullptr, c->status);
+        k_chan_step<true><<<grid_bc, kChanTx, 0, c->stream>>>(g, c->ph, up, c->G[(s - 1) & 1], nullptr, fr,
+                                                              c->G[s & 1], with_drag ? c->drag + (s - 1) : nullptr,
+                                                              c->status);
         rc = launch_ok();
-        if (!rc) k_chan_bc_step<<<bblocks, 128, 0, c->stream>>>(g, c->ph, up, c->G[(s - 1) & 1], fr, c->G[s & 1]);
-        if (!rc) rc = launch_ok();
     }
     return rc;
 }
@@ -710,7 +862,8 @@ int lbm_channel_create(const lbm_channel_params *prm, int32_t n, const double *p
         !std::isfinite(p.body_accel_x))
         return LBM_ERR_ARG;
     if (p.steps < 1 || p.avg_from < 1 || p.avg_from > p.steps || p.checkpoint_every < 1) return LBM_ERR_ARG;
-    if ((long long)p.nx * p.ny * p.nz * Q >= (1ll << 31)) return LBM_ERR_UNSUPPORTED;
+    if ((long long)p.nx * p.ny * p.nz * Q >= (1ll << 31)) return LBM_ERR_UNSUPPORTED;  // kernels index [Q][N] in int
+    if (p.ny > 65535 || p.nz > 65535) return LBM_ERR_UNSUPPORTED;  // grid rows (y, z) of the per-node kernels
     // obstacles stay clear of the inlet / outlet planes and their neighbours
     const bool plate = p.plate_lo[0] <= p.plate_hi[0] && p.plate_lo[1] <= p.plate_hi[1] && p.plate_lo[2] <= p.plate_hi[2];
     if (plate && (p.plate_lo[0] < 2 || p.plate_hi[0] > p.nx - 3)) return LBM_ERR_ARG;
@@ -744,11 +897,12 @@ int lbm_channel_create(const lbm_channel_params *prm, int32_t n, const double *p
     }
     const size_t NQs = (size_t)c->N * Q, P = (size_t)p.ny * p.nz;
     if (!rc) rc = calloc_dev(c, &c->type, (size_t)c->N);
-    if (!rc) rc = calloc_dev(c, &c->cut, (size_t)c->N);
+    if (!rc) rc = calloc_dev(c, &c->cutm, (size_t)c->N);
     if (!rc) rc = calloc_dev(c, &c->q, NQs);
     if (!rc) rc = calloc_dev(c, &c->plate, (size_t)c->N);
     if (!rc) rc = calloc_dev(c, &c->mfl, (size_t)c->N);
-    if (!rc) rc = calloc_dev(c, &c->mcut, (size_t)c->N);
+    if (!rc) rc = calloc_dev(c, &c->mbq, (size_t)c->N);
+    if (!rc) rc = calloc_dev(c, &c->gpart, 3 * (size_t)chan_warps(p, (long long)p.ny * p.nz));
     if (!rc) rc = calloc_dev(c, &c->many, (size_t)c->N);
     if (!rc) rc = calloc_dev(c, &c->X, 3 * (size_t)n);
     if (!rc) rc = calloc_dev(c, &c->R, (size_t)n);
@@ -759,8 +913,10 @@ int lbm_channel_create(const lbm_channel_params *prm, int32_t n, const double *p
     if (!rc) rc = calloc_dev(c, &c->seg, NQs * c->K);
     if (!rc) rc = calloc_dev(c, &c->ckpt, NQs * c->nck);
     if (!rc) rc = calloc_dev(c, &c->fend, NQs);
-    if (!rc) rc = calloc_dev(c, &c->rho_bar, P);
-    if (!rc) rc = calloc_dev(c, &c->ext, P * Q);
+    for (int k = 0; k < 2 && !rc; ++k) {
+        rc = calloc_dev(c, &c->rho_bar[k], P);
+        if (!rc) rc = calloc_dev(c, &c->ext[k], P * Q);
+    }
     if (!rc) rc = calloc_dev(c, &c->drag, (size_t)p.steps);
     if (!rc) rc = calloc_dev(c, &c->grad, 3);
     if (!rc) rc = calloc_dev(c, &c->status, 1);
@@ -779,10 +935,10 @@ int lbm_channel_create(const lbm_channel_params *prm, int32_t n, const double *p
         rc = launch_ok();
         if (!rc)
             k_chan_links<<<blocks, 256, 0, c->stream>>>(p.nx, p.ny, p.nz, n, c->X, c->R, c->type, c->q, c->plate,
-                                                        c->cut);
+                                                        c->cutm);
         if (!rc) rc = launch_ok();
         if (!rc) {
-            k_chan_masks<<<blocks, 256, 0, c->stream>>>(geo_of(c), c->mfl, c->mcut, c->many);
+            k_chan_masks<<<blocks, 256, 0, c->stream>>>(geo_of(c), c->mfl, c->mbq, c->many);
             rc = launch_ok();
         }
     }
@@ -849,39 +1005,42 @@ int lbm_channel_backward(lbm_channel c, double *grad) {
     if (!c->have_forward) return LBM_ERR_ARG;  // the checkpoints belong to another theta
     DeviceScope ds(c->p.device);
     const size_t NQs = (size_t)c->N * Q, P = (size_t)c->p.ny * c->p.nz;
-    const int S = c->p.steps, K = c->K, blocks = (c->N + 255) / 256, pblocks = (int)((P + 127) / 128);
+    const int S = c->p.steps, K = c->K;
+    const dim3 grid = chan_grid(c->p, 0), grid_bc = chan_grid(c->p, (long long)P);
+    const int nwarps = chan_warps(c->p, (long long)P);
     const ChanGeo g = geo_of(c);
     const float up = (float)c->theta[0];
     const float wd = (float)(1.0 / (S - c->p.avg_from + 1));
     int rc = cudaMemsetAsync(c->grad, 0, 3 * sizeof(double), c->stream) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+    if (!rc && cudaMemsetAsync(c->gpart, 0, 3 * sizeof(double) * nwarps, c->stream) != cudaSuccess)
+        rc = LBM_ERR_CUDA;
     if (!rc && cudaMemsetAsync(c->lam[(S + 1) & 1], 0, sizeof(float) * NQs, c->stream) != cudaSuccess)
         rc = LBM_ERR_CUDA;  // lambda^{S+1} = 0
+    // lambda^{S+1} = 0: no inlet / outlet adjoint enters reverse step S
+    if (!rc && (cudaMemsetAsync(c->rho_bar[S & 1], 0, sizeof(float) * P, c->stream) != cudaSuccess ||
+                cudaMemsetAsync(c->ext[S & 1], 0, sizeof(float) * P * Q, c->stream) != cudaSuccess))
+        rc = LBM_ERR_CUDA;
     for (int seg = S / K; seg >= 0 && !rc; --seg) {
         const int s0 = seg * K, s1 = std::min(s0 + K - 1, S);  // reverse steps s1 .. s0
         const float *f0 = c->ckpt + NQs * seg;                   // f^{s0}
-        // f^{s0+1} .. f^{min(s1+1, S)} into seg slots 0 .. K-1 (drag not needed again)
-        const int last = std::min(s1 + 1, S);
+        // f^{s0+1} .. f^{s1} into seg slots 0 .. K-2 (drag not needed again)
         auto rec = [&](int s) -> float * { return c->seg + NQs * (size_t)(s - s0 - 1); };
-        rc = chan_run(c, f0, s0, last, rec, false);
+        if (s1 > s0) rc = chan_run(c, f0, s0, s1, rec, false);
         for (int s = s1; s >= s0 && !rc; --s) {
             const float *fs = s == s0 ? f0 : c->seg + NQs * (size_t)(s - s0 - 1);
-            const float *lam1 = c->lam[(s + 1) & 1];
-            float *lam0 = c->lam[s & 1];
-            if (s < S) {
-                const float *f1 = c->seg + NQs * (size_t)(s - s0);  // f^{s+1}
-                k_chan_bc_adj<<<pblocks, 128, 0, c->stream>>>(g, c->ph, up, lam1, f1, c->rho_bar, c->ext, c->grad);
-            } else {
-                if (cudaMemsetAsync(c->rho_bar, 0, sizeof(float) * P, c->stream) != cudaSuccess ||
-                    cudaMemsetAsync(c->ext, 0, sizeof(float) * P * Q, c->stream) != cudaSuccess)
-                    rc = LBM_ERR_CUDA;
-            }
-            if (!rc) rc = launch_ok();
             const float w = (s >= c->p.avg_from && s >= 1) ? wd : 0.f;
-            if (!rc)
-                k_chan_adj<<<blocks, 256, 0, c->stream>>>(g, c->ph, lam1, s == 0 ? nullptr : fs, c->rho_bar, c->ext, w,
-                                                          lam0, c->grad);
-            if (!rc) rc = launch_ok();
+            // the extra blocks of reverse step s > 0 prepare the inlet / outlet adjoint of step s - 1
+            const bool nxt = s > 0;
+            k_chan_adj<<<nxt ? grid_bc : grid, kChanTx, 0, c->stream>>>(
+                g, c->ph, up, c->lam[(s + 1) & 1], s == 0 ? nullptr : fs, c->rho_bar[s & 1], c->ext[s & 1], w,
+                c->lam[s & 1], nxt ? c->rho_bar[(s - 1) & 1] : nullptr, nxt ? c->ext[(s - 1) & 1] : nullptr,
+                c->gpart);
+            rc = launch_ok();
         }
+    }
+    if (!rc) {
+        k_chan_gsum<<<1, 256, 0, c->stream>>>(c->gpart, nwarps, c->grad);
+        rc = launch_ok();
     }
     double gr[3] = {0.0, 0.0, 0.0};
     if (!rc && cudaMemcpyAsync(gr, c->grad, sizeof(gr), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
