@@ -372,7 +372,9 @@ typedef struct {
 } lbm_channel_params;
 
 /* Create; n fixed spheres (host arrays pos[n][3], radius[n]; x - R > 1 and
- * x + R < nx - 2).  Decides the node classes and link fractions once. */
+ * x + R < nx - 2).  Decides the node classes and link fractions once.
+ * LBM_ERR_UNSUPPORTED when 19 nx ny nz >= 2^31, ny > 65535 or nz > 64000
+ * (the kernels index in 32 bits and run one block row per (y, z)). */
 int lbm_channel_create(const lbm_channel_params *params, int32_t n, const double *pos, const double *radius,
                        lbm_channel *out);
 int lbm_channel_destroy(lbm_channel c);

@@ -863,7 +863,8 @@ int lbm_channel_create(const lbm_channel_params *prm, int32_t n, const double *p
         return LBM_ERR_ARG;
     if (p.steps < 1 || p.avg_from < 1 || p.avg_from > p.steps || p.checkpoint_every < 1) return LBM_ERR_ARG;
     if ((long long)p.nx * p.ny * p.nz * Q >= (1ll << 31)) return LBM_ERR_UNSUPPORTED;  // kernels index [Q][N] in int
-    if (p.ny > 65535 || p.nz > 65535) return LBM_ERR_UNSUPPORTED;  // grid rows (y, z) of the per-node kernels
+    // grid rows (y, z) of the per-node kernels, plus at most nz / 64 + 1 slabs of extra blocks in z
+    if (p.ny > 65535 || p.nz > 64000) return LBM_ERR_UNSUPPORTED;
     // obstacles stay clear of the inlet / outlet planes and their neighbours
     const bool plate = p.plate_lo[0] <= p.plate_hi[0] && p.plate_lo[1] <= p.plate_hi[1] && p.plate_lo[2] <= p.plate_hi[2];
     if (plate && (p.plate_lo[0] < 2 || p.plate_hi[0] > p.nx - 3)) return LBM_ERR_ARG;
