@@ -11,7 +11,11 @@ Pins of the channel option:
   outlet equilibrium, a plate link counted with the wrong sign or step, or a
   collided boundary plane fails;
 * free spheres of very large density (1e9) give the fixed-sphere objective:
-  the momentum exchange moves them by ~1e-9 lattice units.
+  the momentum exchange moves them by ~1e-9 lattice units;
+* the plate contact (Eq. 1 against the plate's halfway surface, the node
+  box grown by 1/2): a sphere meeting a face head-on, or an edge along the
+  diagonal, leaves along the contact normal with the normal restitution
+  (DEM only, no fluid), which a wrong surface offset, normal or sign fails.
 
 The report: central differences of the free-sphere J (Sect. 2.3, Eqs. 19,
 21, 25, 26 and the DEM of Sect. 2.1 moving the spheres) against the
@@ -24,6 +28,7 @@ full-size numbers come from tests/golden/make_free_sphere_report.py and are
 printed by the GPU adjoint test.
 """
 import numpy as np
+import pytest
 
 import oracle
 from paper_1703_05158_gb300 import inputs
@@ -44,6 +49,21 @@ def test_channel_option_with_fixed_spheres_is_the_channel_oracle():
     assert np.abs(fx["drag"] - ref["drag"]).max() <= 1e-8 * scale
     assert abs(fx["J"] - ref["J"]) <= 1e-8 * abs(ref["J"])
     assert np.array_equal(fx["X"], X)
+
+
+@pytest.mark.parametrize("case", ["face_x", "face_z", "edge"])
+def test_plate_contact_restitution_along_the_contact_normal(case):
+    R, v, e = 4.0, 0.02, 0.8
+    r2 = np.sqrt(0.5)
+    X0, V0 = {"face_x": ([19.5 - R - 0.05, 10.0, 20.0], [v, 0.0, 0.0]),
+              "face_z": ([21.5, 10.0, 14.5 - R - 0.05], [0.0, 0.0, v]),
+              "edge": ([19.5 - (R + 0.05) * r2, 10.0, 14.5 - (R + 0.05) * r2], [v * r2, 0.0, v * r2])}[case]
+    o = oracle.Oracle(48, 24, 40, tau0=0.8, rho_s=2.5, kn=10.0, restitution=e, dem_substeps=32, fluid=False,
+                      channel=dict(u_peak=0.0, plate_lo=(20, 5, 15), plate_hi=(23, 14, 24)))
+    o.set_particles(np.array([X0]), V=np.array([V0]), R=[R])
+    o.step(60)
+    V = o.particles()[1][0]
+    assert np.abs(V - (-e) * np.array(V0)).max() <= 1e-3 * v
 
 
 def test_very_heavy_free_spheres_give_the_fixed_objective():
