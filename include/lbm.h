@@ -195,7 +195,10 @@ int lbm_set_particles(lbm_handle h, int32_t n, const double *pos, const double *
 /* External force and torque on every sphere ([n][3] each, NULL = zero), added
  * to the hydrodynamic load during the DEM sub-steps of every following step
  * until set again (e.g. the load of another solver coupled to the spheres).
- * Non-finite host values: LBM_ERR_ARG. */
+ * Host values are copied into the library's pinned staging buffers before the
+ * call returns (the caller may reuse its arrays at once) and reach the device
+ * in stream order, without waiting for the stream.  Non-finite host values:
+ * LBM_ERR_ARG; LBM_ERR_NOMEM if the staging buffers cannot be allocated. */
 int lbm_set_particle_load(lbm_handle h, const double *force, const double *torque, int32_t where);
 
 /* Overwrite the populations of the fluid nodes with f[19][N] (FP64, the

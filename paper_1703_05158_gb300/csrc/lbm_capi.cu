@@ -62,6 +62,10 @@ void release(lbm_s *h) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->status_host) cudaFreeHost(h->status_host);
+    for (int k = 0; k < 2; ++k) {
+        if (h->load_stage[k]) cudaFreeHost(h->load_stage[k]);
+        if (h->load_ev[k]) cudaEventDestroy(h->load_ev[k]);
+    }
     if (h->ev) {
         for (int i = 0; i < kProfEv * h->ev_cap; ++i) cudaEventDestroy(h->ev[i]);
         std::free(h->ev);
@@ -560,18 +564,40 @@ int lbm_set_particle_load(lbm_handle h, const double *force, const double *torqu
     DeviceScope ds(h->device);
     const size_t v3 = 3 * sizeof(double) * (size_t)h->pt.np;
     int rc = LBM_OK;
+    // host values: staged in pinned memory first (the caller may reuse its
+    // buffers as soon as we return), copied to the device in stream order
+    double *stage = nullptr;
+    if (where == LBM_HOST && v3 && (force || torque)) {
+        const int k = h->load_slot;
+        if (!h->load_stage[k]) {
+            const size_t cap = 6 * sizeof(double) * (size_t)(h->p.max_particles > 0 ? h->p.max_particles : 1);
+            if (cudaMallocHost((void **)&h->load_stage[k], cap) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->load_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                return LBM_ERR_NOMEM;
+            }
+        } else if (cudaEventSynchronize(h->load_ev[k]) != cudaSuccess) {  // its last copy is done
+            return LBM_ERR_CUDA;
+        }
+        stage = h->load_stage[k];
+        if (force) std::memcpy(stage, force, v3);
+        if (torque) std::memcpy(stage + 3 * (size_t)h->pt.np, torque, v3);
+    }
     if (force)
-        rc = copy_in(h, h->pt.Fx, force, v3, where);
+        rc = copy_in(h, h->pt.Fx, stage ? stage : force, v3, where);
     else if (v3 && cudaMemsetAsync(h->pt.Fx, 0, v3, h->stream) != cudaSuccess)
         rc = LBM_ERR_CUDA;
     if (!rc) {
         if (torque)
-            rc = copy_in(h, h->pt.Tx, torque, v3, where);
+            rc = copy_in(h, h->pt.Tx, stage ? stage + 3 * (size_t)h->pt.np : torque, v3, where);
         else if (v3 && cudaMemsetAsync(h->pt.Tx, 0, v3, h->stream) != cudaSuccess)
             rc = LBM_ERR_CUDA;
     }
-    // the caller may reuse its buffer as soon as we return
-    if (!rc && where == LBM_HOST && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+    if (!rc && stage) {
+        if (cudaEventRecord(h->load_ev[h->load_slot], h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+        h->load_slot ^= 1;
+    }
+    if (rc) cudaGetLastError();
     return rc;
 }
 

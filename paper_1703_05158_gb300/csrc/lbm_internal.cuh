@@ -276,6 +276,12 @@ struct lbm_s {
     double zA = 0.0, zV0 = 0.0, zvp = 0.0;
     double *zs = nullptr, *zpart = nullptr;
     int *zcnt = nullptr;
+    // host loads staged in pinned memory (two slots, each [2][max_particles][3]:
+    // force, torque) so that lbm_set_particle_load returns without waiting for
+    // the stream; load_ev[k] follows the last copy out of slot k
+    double *load_stage[2] = {nullptr, nullptr};
+    cudaEvent_t load_ev[2] = {nullptr, nullptr};
+    int load_slot = 0;
     int tile_ext;            // half width of the per-sphere link tile
     int link_cap;            // link-list capacity per sphere (shared memory)
     size_t bytes;
