@@ -170,7 +170,28 @@ __device__ __forceinline__ void sc_pair(const Lat &L, const Phys &ph, T *__restr
 #pragma unroll
         for (int i = 0; i < Q; ++i) wv[i] = __byte_perm(wv[i], (unsigned)Pack2<T>::bits(d[i]), 0x5410);
     }
-    // write: even -> slot opp(i) of the pair; odd -> slot i at (x, x+1) + c_i
+    // write: even -> slot opp(i) of the pair; odd -> slot i at (x, x+1) + c_i.
+    // Both nodes fluid (the common case): whole words where the pair stays
+    // aligned, no per-direction tests.
+    if (liveA && liveB) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (!ODD) {
+                ((unsigned *)f)[(opp(i) * S >> 1) + sw] = wv[i];
+            } else {
+                const int wbase = (i * S >> 1) + sw + roff(cy(i), cz(i));
+                if (cx(i) == 0) {
+                    ((unsigned *)f)[wbase] = wv[i];
+                } else if (cx(i) > 0) {  // nodes x+1 (high half of this word), x+2 (low half of the right word)
+                    fh[2 * wbase + 1] = (unsigned short)(wv[i] & 0xffffu);
+                    fh[2 * (wbase + wr)] = (unsigned short)(wv[i] >> 16);
+                } else {  // nodes x-1 (high half of the left word), x (low half of this word)
+                    fh[2 * (wbase + wl) + 1] = (unsigned short)(wv[i] & 0xffffu);
+                    fh[2 * wbase] = (unsigned short)(wv[i] >> 16);
+                }
+            }
+        }
+    } else
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const unsigned short oa = (unsigned short)(wv[i] & 0xffffu), ob = (unsigned short)(wv[i] >> 16);
