@@ -70,23 +70,35 @@ __device__ __forceinline__ void collide_node(const Phys &ph, float (&d)[Q], int 
     const float om = __fdiv_rn(1.f, tau);
 
     // Relaxation towards Eq. (9) (deviation form), by opposite pairs (i, i+9):
-    // f^eq - w = w [drho + rho (4.5 (c.u)^2 - 1.5 u^2)]  +/-  3 w rho (c.u)
+    // f^eq - w = w [drho + rho (4.5 (c.u)^2 - 1.5 u^2)]  +/-  3 w rho (c.u),
+    // written d' = (1 - om) d + om (f^eq - w) with om folded into the two
+    // weight classes' factors (w = 1/18 for the axes, 1/36 for the diagonals)
     const float base = __fmaf_rn(-__fmul_rn(1.5f, rho), uu, drho);
-    d[0] = __fmaf_rn(om, __fmaf_rn(wf(0), base, -d[0]), d[0]);
+    const float keep = __fsub_rn(1.f, om);
+    d[0] = __fmaf_rn(keep, d[0], __fmul_rn(__fmul_rn(om, wf(0)), base));
     const bool forced = ph.g[0] != 0.f || ph.g[1] != 0.f || ph.g[2] != 0.f;
     const float fx = __fmul_rn(rho, ph.g[0]), fy = __fmul_rn(rho, ph.g[1]), fz = __fmul_rn(rho, ph.g[2]);
     const float uF = __fmaf_rn(uz, fz, __fmaf_rn(uy, fy, __fmul_rn(ux, fx)));
     const float sk = __fmaf_rn(-0.5f, om, 1.f);
-    const float r45 = __fmul_rn(4.5f, rho);
     if (forced) d[0] = __fmaf_rn(__fmul_rn(sk, wf(0)), __fmul_rn(-3.f, uF), d[0]);
+    // per weight class c (0: 1/18, 1: 1/36): om w, om w 4.5 rho, om w base, om 3 w rho
+    float ow45[2], owb[2], ow3[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const float ow = __fmul_rn(om, c == 0 ? wf(1) : wf(4));
+        ow45[c] = __fmul_rn(ow, __fmul_rn(4.5f, rho));
+        owb[c] = __fmul_rn(ow, base);
+        ow3[c] = __fmul_rn(__fmul_rn(3.f, ow), rho);
+    }
 #pragma unroll
     for (int i = 1; i <= 9; ++i) {
         const int k = i + 9;  // opp(i)
+        const int c = w36(i) == 2 ? 0 : 1;
         const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-        const float sym = __fmul_rn(wf(i), __fmaf_rn(__fmul_rn(r45, cu), cu, base));
-        const float asym = __fmul_rn(__fmul_rn(3.f * wf(i), rho), cu);
-        d[i] = __fmaf_rn(om, __fsub_rn(__fadd_rn(sym, asym), d[i]), d[i]);
-        d[k] = __fmaf_rn(om, __fsub_rn(__fsub_rn(sym, asym), d[k]), d[k]);
+        const float sym = __fmaf_rn(__fmul_rn(ow45[c], cu), cu, owb[c]);  // om (f^eq - w), even part
+        const float asym = __fmul_rn(ow3[c], cu);                           // odd part
+        d[i] = __fmaf_rn(keep, d[i], __fadd_rn(sym, asym));
+        d[k] = __fmaf_rn(keep, d[k], __fsub_rn(sym, asym));
         if (forced) {
             // Guo source: w [3 (c - u).F + 9 (c.u)(c.F)], even and odd parts
             const float cF = cx(i) * fx + cy(i) * fy + cz(i) * fz;
