@@ -74,6 +74,24 @@ def test_gradient_matches_tangent_linear_and_central_differences():
         assert abs(g[k] - fd) <= GRAD_TOL * abs(fd)
 
 
+def test_gradient_with_two_blocks_per_row_and_odd_ny():
+    """nx = 160 (two 128-thread blocks per row, the second partly idle), odd
+    ny and nz, and a checkpoint interval that does not divide the step count:
+    the gradient against the oracle's tangent-linear pass."""
+    cfg = dict(nx=160, ny=19, nz=21, tau0=0.6, cs=0.15, gx=2e-6, u_peak=0.04, plate_lo=(30, 4, 5),
+               plate_hi=(32, 13, 15), steps=90, avg_from=51)
+    X, R = inputs.channel_spheres(seed=inputs.SEED_BASE + 31, n=4, radius=2.5, box=(160, 19, 21),
+                                  x_range=(6.0, 26.0))
+    ch = gpu_channel(cfg, X, R, 13)
+    J = ch.forward()
+    g = ch.backward()
+    ref = oracle.channel(**cfg, X=X, R=R)
+    assert abs(J - ref["J"]) <= 1e-4 * abs(ref["J"])
+    for k in range(3):
+        tl = oracle.channel(**cfg, X=X, R=R, dtheta=np.eye(3)[k])["dJ"]
+        assert abs(g[k] - tl) <= GRAD_TOL * abs(tl), (k, g[k], tl)
+
+
 def test_checkpoint_interval_does_not_change_the_gradient():
     X, R = medium_spheres()
     grads = []
