@@ -376,8 +376,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(ke):
         lbm.lbm_set_particle_load(lat.h, hF, hT)
         lbm.lbm_step(lat.h, 1)
-        lbm.lbm_forces(lat.h, oF, oT)
-        lbm.lbm_particles(lat.h, oX)
+        lbm.lbm_particle_state(lat.h, oF, oT, oX)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_val = whole_job_mlups(N * ke, world, max_over_ranks(e2e_s, world))

@@ -221,6 +221,13 @@ int lbm_forces(lbm_handle h, double *F, double *T, int32_t where);
  * any pointer may be NULL to skip it). */
 int lbm_particles(lbm_handle h, double *pos, double *vel, double *omega, int32_t where);
 
+/* lbm_forces and lbm_particles in one call with one stream synchronisation
+ * (a coupling loop reads both after every step): F, T the hydrodynamic load
+ * of the last step, pos, vel, omega the current state ([n][3] each; any
+ * pointer may be NULL to skip it). */
+int lbm_particle_state(lbm_handle h, double *F, double *T, double *pos, double *vel, double *omega,
+                       int32_t where);
+
 /* Density rho[N] and velocity u[3][N] of the current state (Eqs. 5, 6 with
  * the half-force shift); solid nodes give rho = 0 and u = 0.  Either pointer
  * may be NULL. */

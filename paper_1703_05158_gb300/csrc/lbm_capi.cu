@@ -828,6 +828,20 @@ int lbm_particles(lbm_handle h, double *pos, double *vel, double *omega, int32_t
     return rc ? rc : s;
 }
 
+int lbm_particle_state(lbm_handle h, double *F, double *T, double *pos, double *vel, double *omega,
+                       int32_t where) {
+    if (!h || (where != LBM_HOST && where != LBM_DEVICE)) return LBM_ERR_ARG;
+    DeviceScope ds(h->device);
+    const size_t v3 = 3 * sizeof(double) * (size_t)h->pt.np;
+    int rc = copy_out(h, F, h->pt.Fh, v3, where);
+    if (!rc) rc = copy_out(h, T, h->pt.Th, v3, where);
+    if (!rc) rc = copy_out(h, pos, h->pt.X, v3, where);
+    if (!rc) rc = copy_out(h, vel, h->pt.V, v3, where);
+    if (!rc) rc = copy_out(h, omega, h->pt.W, v3, where);
+    const int s = settle(h);
+    return rc ? rc : s;
+}
+
 int lbm_fields(lbm_handle h, float *rho, float *u, int32_t where) {
     if (!h || (where != LBM_HOST && where != LBM_DEVICE)) return LBM_ERR_ARG;
     DeviceScope ds(h->device);

@@ -33,7 +33,7 @@ LBM_DEVICE = 1
 PRECISIONS = {"fp32": LBM_FP32, "bf16": LBM_BF16_DEV, "fp16": LBM_FP16_DEV}
 
 EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_particles", "lbm_set_particle_load", "lbm_set_populations",
-           "lbm_step", "lbm_forces", "lbm_particles", "lbm_fields", "lbm_populations", "lbm_geometry", "lbm_info",
+           "lbm_step", "lbm_forces", "lbm_particles", "lbm_particle_state", "lbm_fields", "lbm_populations", "lbm_geometry", "lbm_info",
            "lbm_sync", "lbm_error_string", "lbm_profile", "lbm_profile_read", "lbm_fields_noalloc",
            "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_handle", "lbm_batch_tune", "lbm_batch_step",
            "lbm_batch_sync", "lbm_channel_create", "lbm_channel_destroy", "lbm_channel_set_theta",
@@ -106,6 +106,7 @@ def load(build=True):
         lib.lbm_step.argtypes = [vp, ip]
         lib.lbm_forces.argtypes = [vp, dp, dp, ip]
         lib.lbm_particles.argtypes = [vp, dp, dp, dp, ip]
+        lib.lbm_particle_state.argtypes = [vp, dp, dp, dp, dp, dp, ip]
         lib.lbm_fields.argtypes = [vp, fp, fp, ip]
         lib.lbm_populations.argtypes = [vp, dp, ip]
         lib.lbm_geometry.argtypes = [vp, vp, ip]
@@ -221,6 +222,13 @@ def lbm_particles(h, pos, vel=None, omega=None):
     p2, _ = _ptr(vel)
     p3, _ = _ptr(omega)
     return _check(load().lbm_particles(h, p1, p2, p3, where), "lbm_particles")
+
+
+def lbm_particle_state(h, F=None, T=None, pos=None, vel=None, omega=None):
+    arrays = (F, T, pos, vel, omega)
+    ptrs = [_ptr(a) for a in arrays]
+    where = next((w for a, (_, w) in zip(arrays, ptrs) if a is not None), LBM_HOST)
+    return _check(load().lbm_particle_state(h, *[p for p, _ in ptrs], where), "lbm_particle_state")
 
 
 def lbm_fields(h, rho, u):

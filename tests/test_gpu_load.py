@@ -1,4 +1,6 @@
-"""lbm_set_particle_load from host arrays: the values are taken at the call.
+"""Per-step host I/O of the sphere state: lbm_set_particle_load from host
+arrays takes the values at the call, and lbm_particle_state returns what
+lbm_forces and lbm_particles return, with one synchronisation.
 
 The library stages host values in pinned memory before it returns (the copy
 to the device then runs in stream order, without a stream synchronisation),
@@ -61,3 +63,21 @@ def test_host_loads_are_taken_at_the_call():
     assert np.abs(Xg - Xo).max() <= 1e-6
     assert np.abs(Vg - Vo).max() <= 1e-4 * np.abs(Vo).max()
     assert np.abs(Wg - Wo).max() <= 1e-4 * np.abs(Wo).max()
+
+
+def test_particle_state_is_forces_and_particles_in_one_call():
+    L = lbm()
+    lat = L.Lattice(*SHAPE, max_particles=2, max_radius=3.0, **KW)
+    lat.set_particles(np.array([[10.3, 12.1, 14.7], [21.6, 18.2, 15.4]]), R=np.array([3.0, 2.5]))
+    L.lbm_set_particle_load(lat.h, *loads(0))
+    lat.step(5)
+    F, T = lat.forces()
+    X, V, W = lat.particles()
+    out = [np.empty((2, 3)) for _ in range(5)]
+    L.lbm_particle_state(lat.h, *out)
+    for a, b in zip(out, (F, T, X, V, W)):
+        assert np.array_equal(a, b)
+    Fo = np.empty((2, 3))
+    L.lbm_particle_state(lat.h, F=Fo)  # any output may be left out
+    assert np.array_equal(Fo, F)
+    lat.close()
