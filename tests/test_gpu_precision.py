@@ -2,7 +2,7 @@
 (arithmetic FP32), against the FP64 oracle on the same seeded inputs.
 
 Relative velocity error is ||u - u_64|| / ||u_64|| (L2 over nodes fluid on
-both sides) after 200 steps; the bound is the benchmark spec's 1e-3 for both 16-bit
+both sides) after 200 steps; the bound is 1e-3 for both 16-bit
 forms.  FP16 storage (11-bit significand) meets it (measured ~5e-4).  BF16
 storage (8-bit significand) rounds each deviation to ~0.4%, and in these
 low-viscosity (tau0 = 0.51) flows the rounding noise is weakly damped: it
