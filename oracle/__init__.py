@@ -18,8 +18,10 @@ face's rest state, face density and mass balance of a piston stroke, and
 for the Galilean-invariant exchange its reduction to Eqs. 25, 26 at rest and
 its extra force on a translating sphere (the velocity times the fluid mass
 the moving bounce-back creates).  The coupled free-sphere trajectory itself
-has no closed form: parity unpinned beyond those invariants, as for the
-torque and the rotational part of the Galilean-invariant extra term.
+has no closed form: parity unpinned beyond those invariants.  The
+Galilean-invariant extra term is pinned in force (a translating sphere:
+the fluid mass the moving bounce-back creates) and in force and torque (a
+sphere spinning in place: the term formed from the streamed populations).
 """
 import ctypes
 import os

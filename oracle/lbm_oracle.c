@@ -38,9 +38,7 @@
  *
  * Readings of passages the paper leaves open are marked "reading:".
  * Parity pins: every function below is pinned by tests in tests/ except the
- * full coupled moving-sphere trajectory, which has no closed form, and, in
- * the Galilean-invariant exchange, the torque and the rotational part of the
- * extra term (its force on a translating sphere is pinned).
+ * full coupled moving-sphere trajectory, which has no closed form.
  */
 #include <math.h>
 #include <stdint.h>

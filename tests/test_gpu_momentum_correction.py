@@ -143,10 +143,10 @@ def test_correction_with_16_bit_storage(precision):
 def test_galilean_invariant_exchange_matches_the_oracle(corr):
     """The Galilean-invariant momentum exchange (Wen, Zhang & Fang 2014),
     alone and with the covered / uncovered correction, against the oracle.
-    Parity unpinned for part of it: the oracle's extra force on a translating
-    sphere is pinned (to the fluid mass the moving bounce-back creates), but
-    the torque of the extra term and its rotational part are pinned by no
-    independent value; for those this test checks GPU against oracle only."""
+    The oracle's extra term is pinned in test_oracle_mea.py: its force on a
+    translating sphere (the fluid mass the moving bounce-back creates) and
+    its force and torque on a sphere spinning in place (formed from the
+    streamed populations and the link list)."""
     shape = (48, 40, 36)
     p = suspension(shape, seed=inputs.SEED_BASE + 66)
     lat = lbm().Lattice(*shape, max_particles=len(p["R"]), max_radius=5.0, momentum_correction=corr,

@@ -10,9 +10,16 @@ nothing else in a step changes the fluid mass of a fully periodic box
 (collision and streaming conserve it) unless a node changes owner.  For a
 sphere in pure translation every link has u_b = V, so on a step without
 owner changes the Galilean force minus the paper's is V times the fluid
-mass gained, a total read from the populations alone.  The torque of the
-extra term and its rotational part (u_b = Omega x l) are not isolated by
-any pin.
+mass gained, a total read from the populations alone.
+
+The rotational part and the torque are pinned on the first step of a sphere
+spinning in place in a fully periodic box at rest: every post-collision
+population is then exactly w (the rest state collides into itself), the
+populations after the step's streaming come from the oracle's stream alone,
+and the test forms -sum (w_j - f_k(x, t+1)) u_b and -sum (w_j - f_k) (l x u_b)
+itself from the oracle's link list (node, direction, q), with
+u_b = Omega x l and l = x + q c_j - X at the image nearest to the centre:
+they equal the Galilean force and torque minus the paper's to rounding.
 """
 import numpy as np
 
@@ -92,3 +99,32 @@ def test_extra_force_of_a_translating_sphere_is_its_velocity_times_the_created_m
             assert np.abs(dF - V * (M1 - M0)).max() <= tol, (dF, V * (M1 - M0))
             strong += bool(np.abs(dF).max() > 1e3 * tol)
     assert strong >= 3
+
+
+def test_extra_load_of_a_spinning_sphere_from_the_streamed_populations():
+    c, w, opp = oracle.tables()
+    nx, ny, nz = 24, 22, 20
+    Xs = np.array([[11.3, 10.6, 9.8]])
+    Om = np.array([[0.004, -0.007, 0.011]])
+    out = {}
+    for mea in ("paper", "galilean"):
+        o = oracle.Oracle(nx, ny, nz, tau0=1.0, cs=0.0, periodic_z=True, mea=mea, rho_s=2.5)
+        o.set_particles(Xs, V=np.zeros((1, 3)), Om=Om, R=np.array([4.1]), fixed=np.ones(1, dtype=np.uint8))
+        o.step(1)
+        out[mea] = (*o.forces(), o.populations().reshape(19, -1), o.links())
+    Fp, Tp, f1, (node, d, q, _) = out["paper"]
+    Fg, Tg = out["galilean"][:2]
+    assert len(node) > 100
+    dF, dT = np.zeros(3), np.zeros(3)
+    for n, j, qj in zip(node, d, q):
+        xi = np.array([n % nx, (n // nx) % ny, n // (nx * ny)], dtype=float)
+        for a, L in enumerate((nx, ny, nz)):  # image nearest to the centre
+            xi[a] -= L * np.round((xi[a] - Xs[0, a]) / L)
+        l = xi + float(qj) * c[j] - Xs[0]
+        ub = np.cross(Om[0], l)
+        e = w[j] - f1[opp[j], n]  # f^c_j(x) - f_k(x, t+1)
+        dF -= e * ub
+        dT -= e * np.cross(l, ub)
+    assert np.abs(dT).max() > 1e-4 and np.abs(dF).max() > 1e-4
+    assert np.abs((Fg - Fp)[0] - dF).max() <= 1e-12
+    assert np.abs((Tg - Tp)[0] - dT).max() <= 1e-12
