@@ -10,6 +10,13 @@ cross-section A_p whose piston moves at v_p.
   cylinder and lattice (the face plane, shared by both, counted half), the
   lattice ends at the cylinder density, and that density is the closed form
   M / (V_lattice - A_p / 2 + V_0 - A_p H_p).
+* A uniform flow along the face under a lid moving with it, piston at rest,
+  is a fixed point: the face's five unknown populations carry the node's own
+  tangential state, so its redistribution returns f^eq(1, u0).  A reading
+  that filled them from the cylinder at rest (w rho) would take the
+  tangential momentum of populations 7, 9, 15, 17 out of the face's velocity
+  and break the fixed point.  (Own post- against pre-collision values, and
+  rho^{n+1} against rho* in the velocity, coincide in this state.)
 """
 import numpy as np
 import pytest
@@ -66,3 +73,14 @@ def test_slow_stroke_conserves_mass_and_reaches_the_closed_form_density(vp):
     closed = M0 / (NX * NY * NZ - 0.5 * A + V0 - A * H)
     assert abs(rho - closed) <= 1e-4 * closed
     assert (rho > 1.0) == (vp > 0)
+
+
+def test_uniform_tangential_flow_under_a_comoving_lid_is_a_fixed_point():
+    u0 = np.array([0.04, -0.02, 0.0])
+    o = oracle.Oracle(NX, NY, NZ, tau0=0.6, cs=0.15, u_hi=tuple(u0), zieb=dict(area=A, volume=V0, vp=0.0))
+    f = np.broadcast_to(oracle.feq(1.0, u0)[:, None, None, None], (19, NZ, NY, NX)).copy()
+    o.set_populations(f)
+    o.step(30)
+    assert np.abs(o.populations() - f).max() <= 1e-14
+    rho, H, vf = o.zieb_state()
+    assert rho == 1.0 and H == 0.0 and abs(vf) <= 1e-14
