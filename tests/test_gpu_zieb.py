@@ -51,6 +51,21 @@ def test_rest_state_stays_exact():
     assert z[0] == 1.0 and z[1] == 0.0 and z[2] == 0.0
 
 
+def test_uniform_tangential_flow_under_a_comoving_lid_stays_put():
+    """The oracle's fixed point (a uniform flow along the face, the lid moving
+    with it, the piston at rest) holds on the GPU to FP32 rounding."""
+    shape = (24, 20, 16)
+    A = shape[0] * shape[1]
+    u0 = (0.04, -0.02, 0.0)
+    lat, _ = pair(shape, dict(area=A, volume=30.0 * A, vp=0.0), tau0=0.6, cs=0.15, u_hi=u0)
+    f = np.broadcast_to(oracle.feq(1.0, np.array(u0))[:, None, None, None], (19,) + shape[::-1]).copy()
+    lat.set_populations(f)
+    lat.step(30)
+    assert np.abs(lat.populations() - f).max() <= 1e-6
+    z = lat.zieb_state()
+    assert abs(z[0] - 1.0) <= 1e-6 and z[1] == 0.0 and abs(z[2]) <= 1e-6
+
+
 def test_piston_stroke_matches_the_oracle():
     """A piston stroke against the oracle.  Parity unpinned for part of one
     reading: the five populations that enter from the cylinder take the
