@@ -40,12 +40,39 @@ __device__ __forceinline__ float dist2(float dx, float dy, float dz) {
 __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
 // Offset of periodic coordinate x from base b, folded into [-n/2, n/2).
+// Every caller passes a node coordinate x in [0, n) and the floor b of a
+// centre in [0, n] (positions are wrapped into the box after each move),
+// so x - b lies in [-n, n) and one conditional add replaces the remainder.
 __device__ __forceinline__ int fold(int x, int b, int n) {
-    int d = (x - b) % n;
+    int d = x - b;
     if (d < 0) d += n;
     if (2 * d >= n) d -= n;
     return d;
 }
+
+// Offsets (ox, oy, oz) in [0, B)^3 of box index t = ox + B (oy + B oz),
+// advanced by a fixed stride with carries (one division per thread at the
+// start, none per step).
+struct BoxWalk {
+    int ox, oy, oz, sx, sy, sz, B;
+    __device__ __forceinline__ BoxWalk(int t, int stride, int b) : B(b) {
+        ox = t % B;
+        oy = (t / B) % B;
+        oz = t / (B * B);
+        sx = stride % B;
+        sy = (stride / B) % B;
+        sz = stride / (B * B);
+    }
+    __device__ __forceinline__ void next() {
+        ox += sx;
+        int c = ox >= B;
+        if (c) ox -= B;
+        oy += sy + c;
+        c = oy >= B;
+        if (c) oy -= B;
+        oz += sz + c;
+    }
+};
 
 // Half width of the box (around floor(X)) holding every node inside a sphere
 // of FP32 radius R: offsets lie in [-ceil(R) + 1, ceil(R)].
@@ -67,11 +94,10 @@ __device__ __forceinline__ void add_moment(double *acc, double sign, float lx, f
     for (int a = 0; a < 6; ++a) acc[a] = sign > 0.0 ? __dadd_rn(acc[a], m[a]) : __dsub_rn(acc[a], m[a]);
 }
 
-// Node of box offset t (of the (2e+1)^3 box around floor(X_p)) if sphere p
+// Node at offset (ox, oy, oz) from floor(X_p) (each in [-e, e]) if sphere p
 // wins it, else -1.
 __device__ __forceinline__ int mark_node(const Lat &L, const SFrame &F, const SFrame *nf, const int *nid,
-                                         const int cnt, const int p, const int e, const int B, const int t) {
-    const int oz = t / (B * B) - e, oy = (t / B) % B - e, ox = t % B - e;
+                                         const int cnt, const int p, const int ox, const int oy, const int oz) {
     const int z = F.b[2] + oz;
     if (z < 0 || z >= L.nz) return -1;
     const float d2 = dist2(rel(ox, F.fr[0]), rel(oy, F.fr[1]), rel(oz, F.fr[2]));
@@ -104,8 +130,9 @@ __device__ __forceinline__ void mark_body(const Lat &L, const Parts &pt, const S
     const SFrame F = fcur[p];
     __syncthreads();
     const int e = ext_of(F.R), B = 2 * e + 1, B3 = B * B * B;
-    for (int t = threadIdx.x; t < B3; t += blockDim.x) {
-        const int n = mark_node(L, F, nf, nid, cnt, p, e, B, t);
+    BoxWalk w(threadIdx.x, blockDim.x, B);
+    for (int t = threadIdx.x; t < B3; t += blockDim.x, w.next()) {
+        const int n = mark_node(L, F, nf, nid, cnt, p, w.ox - e, w.oy - e, w.oz - e);
         if (n < 0) continue;
         flag[n] = cur;
         owner[n] = p;
@@ -154,7 +181,7 @@ __device__ __forceinline__ void mark_corr_body(const Lat &L, const Parts &pt, co
         }
         __syncthreads();
         for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-            const int n = mark_node(L, F, nf, nid, cnt, p, e, B, t);
+            const int n = mark_node(L, F, nf, nid, cnt, p, t % B - e, (t / B) % B - e, t / (B * B) - e);
             if (n < 0) continue;
             if (prev[t - t0] == 0) clist[atomicAdd(&ccount, 1)] = n;
             flag[n] = cur;
@@ -223,8 +250,11 @@ __device__ __forceinline__ void mark_corr_body(const Lat &L, const Parts &pt, co
 #endif
 constexpr int kGeomThreads = LBM_GEOM_THREADS;
 
+// The plain forms are bounded so that the CTAs of a few thousand spheres
+// are resident at once (one wave): 32 registers for the marks, 40 for the
+// refill.
 template <typename T, bool CORR>
-__global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
+__global__ void __launch_bounds__(CORR ? 256 : kGeomThreads, CORR ? 4 : 2048 / kGeomThreads) k_mark(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
                                               uint8_t *__restrict__ flag, int32_t *__restrict__ owner,
                                               const T *__restrict__ f, const int P, const int corr,
                                               const uint8_t cur) {
@@ -235,7 +265,7 @@ __global__ void __launch_bounds__(256) k_mark(const Lat L, const Parts pt, const
 // Batched: instance blockIdx.y at step parity sp (also the population
 // parity); block (0, i) also clears the instance's link / refill counters.
 template <typename T, bool CORR>
-__global__ void __launch_bounds__(256) k_mark_b(const Inst *__restrict__ I, const int sp) {
+__global__ void __launch_bounds__(256, CORR ? 4 : 8) k_mark_b(const Inst *__restrict__ I, const int sp) {
     const Inst &a = I[blockIdx.y];
     if (blockIdx.x == 0 && threadIdx.x < 2) a.ctr[threadIdx.x] = 0ull;
     if ((int)blockIdx.x >= a.pt.np) return;
@@ -265,15 +295,34 @@ __device__ __forceinline__ void refill_body(const Lat &L, const SFrame *__restri
     const int bx = Fp.b[0], by = Fp.b[1], bz = Fp.b[2];
     if (threadIdx.x == 0) count = 0;
     __syncthreads();
-    for (int t = threadIdx.x; t < B * B * B; t += blockDim.x) {
-        const int z = bz + t / (B * B) - e;
-        if (z < 0 || z >= L.nz) continue;
-        const int y = wrapi(by + (t / B) % B - e, L.ny), x = wrapi(bx + t % B - e, L.nx);
-        const int n = x + L.nx * (y + L.ny * z);
-        if (flag[n] != prev_mark || owner[n] != p) continue;
-        const int k = atomicAdd(&count, 1);
-        if (k < kRefillCap) list[k] = n;
-        else atomicOr(status, ST_TILE);
+    // the box is scanned kScanBatch offsets per thread at a time, their
+    // flags and owners loaded together (one memory round trip per batch)
+    constexpr int kScanBatch = 4;
+    const int B3 = B * B * B;
+    BoxWalk w(threadIdx.x, blockDim.x, B);
+    for (int t0 = threadIdx.x; t0 < B3; t0 += kScanBatch * blockDim.x) {
+        int n[kScanBatch];
+#pragma unroll
+        for (int j = 0; j < kScanBatch; ++j) {
+            const int z = bz + w.oz - e;
+            const bool in = t0 + j * (int)blockDim.x < B3 && z >= 0 && z < L.nz;
+            n[j] = in ? wrapi(bx + w.ox - e, L.nx) + L.nx * (wrapi(by + w.oy - e, L.ny) + L.ny * z) : -1;
+            w.next();
+        }
+        uint8_t fl[kScanBatch];
+        int32_t ow[kScanBatch];
+#pragma unroll
+        for (int j = 0; j < kScanBatch; ++j) {
+            fl[j] = n[j] >= 0 ? flag[n[j]] : 0;
+            ow[j] = n[j] >= 0 ? owner[n[j]] : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < kScanBatch; ++j) {
+            if (fl[j] != prev_mark || ow[j] != p) continue;  // prev_mark is 1 or 3, never the 0 of a skipped offset
+            const int k = atomicAdd(&count, 1);
+            if (k < kRefillCap) list[k] = n[j];
+            else atomicOr(status, ST_TILE);
+        }
     }
     __syncthreads();
     if constexpr (CORR) {
@@ -316,12 +365,15 @@ __device__ __forceinline__ void refill_body(const Lat &L, const SFrame *__restri
             if (zz >= 0 && zz < L.nz) {
                 const int yy = wrapi(y + rcy(lane), L.ny), xx = wrapi(x + rcx(lane), L.nx);
                 const int m = xx + L.nx * (yy + L.ny * zz);
-                if (flag[m] == 0) {
-                    const Nbr nb(L, xx, yy);
-                    const long long sm = m + L.plane;
-                    float v[Q];
+                // the neighbour's populations are loaded with its flag (every
+                // node has its 19 slots), and summed only if it is fluid
+                const uint8_t fm = flag[m];
+                const Nbr nb(L, xx, yy);
+                const long long sm = m + L.plane;
+                float v[Q];
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) v[i] = Store<T>::ld(f + in_slot(L, nb, P, i, sm));
+                for (int i = 0; i < Q; ++i) v[i] = Store<T>::ld(f + in_slot(L, nb, P, i, sm));
+                if (fm == 0) {
 #pragma unroll
                     for (int i = 0; i < Q; ++i) dr += v[i];
                     ok = 1;
@@ -373,7 +425,7 @@ __device__ __forceinline__ void refill_body(const Lat &L, const SFrame *__restri
 }
 
 template <typename T, bool CORR>
-__global__ void __launch_bounds__(256, 4) k_refill(const Lat L, const SFrame *__restrict__ fcur,
+__global__ void __launch_bounds__(CORR ? 256 : kGeomThreads, CORR ? 4 : 1280 / kGeomThreads) k_refill(const Lat L, const SFrame *__restrict__ fcur,
                                                 const SFrame *__restrict__ fprev, T *__restrict__ f,
                                                 uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
                                                 const int P, unsigned long long *__restrict__ ctr,
@@ -383,7 +435,7 @@ __global__ void __launch_bounds__(256, 4) k_refill(const Lat L, const SFrame *__
 
 // Batched: instance blockIdx.y; parity P is also the step parity.
 template <typename T, bool CORR>
-__global__ void __launch_bounds__(256, 4) k_refill_b(const Inst *__restrict__ I, const int P) {
+__global__ void __launch_bounds__(256, CORR ? 4 : 5) k_refill_b(const Inst *__restrict__ I, const int P) {
     const Inst &a = I[blockIdx.y];
     if ((int)blockIdx.x >= a.pt.np) return;
     refill_body<T, CORR>(a.L, a.pt.frame[P], a.pt.frame[P ^ 1], (T *)a.f, a.flag, a.owner, P, a.ctr, a.status,
