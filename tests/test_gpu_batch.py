@@ -162,3 +162,34 @@ def test_full_sweep_batch_members_match_standalone_runs():
             assert np.array_equal(m.forces()[0], a.forces()[0])
         a.close()
     batch.close()
+
+
+@pytest.mark.parametrize("box,precision", [((520, 14, 10), "fp32"), ((301, 14, 12), "bf16")])
+def test_rows_of_several_blocks_bitwise(box, precision):
+    """Rows longer than one block of the single-instance collide (256-node
+    row segments, the last one ragged; odd nx takes the one-node kernel in
+    16-bit storage) against the batched kernels, which walk the nodes in
+    flat chunks, bitwise, with spheres across the segment joints and the
+    periodic seam, and a moving lid."""
+    L = lbm()
+    nx, ny, nz = box
+    far = 511.3 if nx > 512 else nx - 6.0  # a third joint, else a sphere near the row's end
+    X = np.array([[255.6, ny / 2, nz / 2], [1.2, ny / 2 - 0.3, nz / 2 + 0.4], [far, ny / 2 + 0.2, nz / 2 - 0.3]])
+    V = np.tile([[0.02, -0.005, 0.003]], (len(X), 1))
+    R = np.full(len(X), 3.0)
+    kw = dict(tau0=0.6, cs=0.15, g=(3e-6, 0.0, 0.0), u_hi=(0.03, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8,
+              dem_substeps=16, max_particles=len(X), max_radius=3.0, precision=precision)
+    batch = L.Batch([dict(nx=nx, ny=ny, nz=nz, **kw)])
+    alone = L.Lattice(nx, ny, nz, **kw)
+    for lat in (batch.members[0], alone):
+        lat.set_particles(X, V=V, R=R)
+    for n in (1, 2, 7):
+        batch.step(n)
+        alone.step(n)
+        batch.sync()
+        m = batch.members[0]
+        assert np.array_equal(m.owner(), alone.owner())
+        assert np.array_equal(m.populations(), alone.populations())
+        assert np.array_equal(m.forces()[0], alone.forces()[0])
+    alone.close()
+    batch.close()
