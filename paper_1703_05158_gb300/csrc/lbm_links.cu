@@ -8,11 +8,17 @@ namespace lbm {
 
 // GI: compiled with the Galilean-invariant momentum exchange (taken where
 // the handle asks for it).
+// The link kernel waits on scattered DRAM accesses: five resident CTAs per
+// SM (48 registers, a few bytes of spills) with two links per thread in
+// flight keep more of them outstanding than four CTAs at 64 registers with
+// three (0.114 against 0.117 ms per launch on 2000 spheres; six CTAs at 40
+// registers spill more and lose).  A thread's links, and so the sums, are
+// in the same order for any batch.
 #ifndef LBM_LINK_MINB
-#define LBM_LINK_MINB 4  // resident CTAs per SM the register budget is set for (64 registers)
+#define LBM_LINK_MINB 5  // resident CTAs per SM the register budget is set for
 #endif
 #ifndef LBM_LINK_BATCH
-#define LBM_LINK_BATCH 3  // links per thread whose populations are loaded together (no spills at 64)
+#define LBM_LINK_BATCH 2  // links per thread whose populations are loaded together
 #endif
 
 template <typename T, bool GI>
