@@ -639,7 +639,7 @@ int serial_step_launches(lbm_s *h) {
     if (!rc) rc = ok(cudaEventRecord(h->ev_nbr, h->side));
     if (!rc) rc = launch_refill(h, P);
     if (!rc) rc = launch_stream_collide(h, P);
-    if (!rc) rc = launch_links(h, P);
+    if (!rc) rc = launch_links(h, P, true);
     if (!rc && h->zieb) rc = launch_zieb(h, P);
     if (!rc) rc = ok(cudaStreamWaitEvent(h->stream, h->ev_nbr, 0));
     if (!rc) rc = launch_dem(h);

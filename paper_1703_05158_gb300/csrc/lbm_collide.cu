@@ -28,6 +28,9 @@ namespace lbm {
 template <int ODD, typename T>
 __global__ void __launch_bounds__(256, 4) k_stream_collide(const Lat L, const Phys ph, T *__restrict__ f,
                                                         uint8_t *__restrict__ flag, int *__restrict__ status) {
+    // a programmatic dependent (the link kernel) may launch once every block
+    // has started; it waits for this grid's completion before its reads
+    asm volatile("griddepcontrol.launch_dependents;");
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= L.nx) return;
@@ -137,6 +140,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_collide_batch_tab(const __grid_co
 template <int ODD, typename T>
 __global__ void __launch_bounds__(128, 8) k_stream_collide2(const Lat L, const Phys ph, T *__restrict__ f,
                                                             uint8_t *__restrict__ flag, int *__restrict__ status) {
+    asm volatile("griddepcontrol.launch_dependents;");  // as in k_stream_collide
     const int xp = blockIdx.x * blockDim.x + threadIdx.x;
     if (xp >= (L.nx >> 1)) return;
     sc_pair<ODD, T>(L, ph, f, flag, status, xp, blockIdx.y, blockIdx.z);

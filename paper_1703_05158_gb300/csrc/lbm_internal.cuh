@@ -381,7 +381,11 @@ int launch_zieb(lbm_s *h, int P);  // ZIEB face after the step of parity P
 int launch_wait_probe(lbm_s *h);   // a bounded device wait that runs out (self-test)
 int launch_mark(lbm_s *h, int P, int corr);  // corr: momentum correction of the covered nodes
 int launch_refill(lbm_s *h, int parity);
-int launch_links(lbm_s *h, int parity);
+// after_collide: launched as a programmatic dependent of the collide kernel
+// just before it on the stream (its node codes and link list, which read
+// only the marks, overlap the collide's last blocks; the populations are
+// read after the collide grid has completed).
+int launch_links(lbm_s *h, int parity, bool after_collide = false);
 int launch_neighbours(lbm_s *h, int force, cudaStream_t stream = nullptr);
 int launch_contact(lbm_s *h);
 int launch_dem(lbm_s *h);

@@ -83,27 +83,43 @@ int links_setup(int ext, int cap) {
 
 template <typename T, bool GI>
 static void links_launch(lbm_s *h, int parity, size_t smem, const SFrame *fcur, int ext, unsigned mB, unsigned mB2,
-                         int cap) {
-    k_links<T, GI><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, fcur, (T *)h->f, h->flag, h->owner, parity, ext,
-                                                       mB, mB2, cap, h->status, h->ctr);
+                         int cap, bool pdl) {
+    if (!pdl) {
+        k_links<T, GI><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, fcur, (T *)h->f, h->flag, h->owner, parity,
+                                                           ext, mB, mB2, cap, h->status, h->ctr);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(h->pt.np);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_links<T, GI>, h->L, h->pt, fcur, (T *)h->f, (uint8_t *)h->flag,
+                       (const int32_t *)h->owner, parity, ext, mB, mB2, cap, h->status, h->ctr);
 }
 
 template <typename T>
 static void links_launch_t(lbm_s *h, int parity, size_t smem, const SFrame *fcur, int ext, unsigned mB, unsigned mB2,
-                           int cap) {
-    if (h->pt.gimea) links_launch<T, true>(h, parity, smem, fcur, ext, mB, mB2, cap);
-    else links_launch<T, false>(h, parity, smem, fcur, ext, mB, mB2, cap);
+                           int cap, bool pdl) {
+    if (h->pt.gimea) links_launch<T, true>(h, parity, smem, fcur, ext, mB, mB2, cap, pdl);
+    else links_launch<T, false>(h, parity, smem, fcur, ext, mB, mB2, cap, pdl);
 }
 
-int launch_links(lbm_s *h, int parity) {
+int launch_links(lbm_s *h, int parity, bool after_collide) {
     const int ext = h->tile_ext, cap = h->link_cap;
     const size_t smem = link_smem(ext, cap);
     const SFrame *fcur = h->pt.frame[h->steps & 1];
     const unsigned B = 2u * ext + 1u, mB = 0xFFFFFFFFu / B + 1u, mB2 = 0xFFFFFFFFu / (B * B) + 1u;
+    const bool pdl = after_collide;
     switch (h->precision) {
-        case LBM_FP32: links_launch_t<float>(h, parity, smem, fcur, ext, mB, mB2, cap); break;
-        case LBM_BF16_DEV: links_launch_t<__nv_bfloat16>(h, parity, smem, fcur, ext, mB, mB2, cap); break;
-        case LBM_FP16_DEV: links_launch_t<__half>(h, parity, smem, fcur, ext, mB, mB2, cap); break;
+        case LBM_FP32: links_launch_t<float>(h, parity, smem, fcur, ext, mB, mB2, cap, pdl); break;
+        case LBM_BF16_DEV: links_launch_t<__nv_bfloat16>(h, parity, smem, fcur, ext, mB, mB2, cap, pdl); break;
+        case LBM_FP16_DEV: links_launch_t<__half>(h, parity, smem, fcur, ext, mB, mB2, cap, pdl); break;
         default: return LBM_ERR_ARG;
     }
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;

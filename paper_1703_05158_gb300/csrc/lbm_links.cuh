@@ -425,6 +425,13 @@ __device__ __forceinline__ void links_body(const Lat &L, const Parts &pt, const 
     const SFrame Fr = fcur[p];
     link_codes(L, Fr.b, flag, owner, p, tl, SolidOf{0}, sh.code);
     const int total = link_enumerate(sh, tl, cap, status);
+    // Launched as a programmatic dependent of the collide, the CTA may start
+    // while the collide's last blocks run: the codes and the list read only
+    // the marks (a refilled node's flag turns from 2 to 0 in the collide,
+    // fluid either way), the populations only after the collide grid has
+    // completed and its writes are visible.  In an ordinary launch this
+    // wait returns at once.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     LinkAcc acc;
     link_apply<T, GI, BATCH, CG>(L, pt, Fr, f, P, tl, total,
                                  [&](int l, int &t, int &j, float &q, int &br) {
