@@ -25,20 +25,30 @@ template <typename T, bool GI>
 __global__ void __launch_bounds__(256, LBM_LINK_MINB) k_links(const Lat L, const Parts pt, const SFrame *__restrict__ fcur,
                                                T *__restrict__ f,
                                                uint8_t *__restrict__ flag, const int32_t *__restrict__ owner,
-                                               const int P, const int ext, const unsigned mB, const unsigned mB2,
-                                               const int cap, int *__restrict__ status,
+                                               const int P, const int ext, const int cap, int *__restrict__ status,
                                                unsigned long long *__restrict__ ctr) {
-    links_body<T, GI, LBM_LINK_BATCH>(L, pt, fcur, f, flag, owner, P, ext, mB, mB2, cap, status, ctr, blockIdx.x);
+    links_body<T, GI, LBM_LINK_BATCH>(L, pt, fcur, f, flag, owner, P, ext, cap, status, ctr, blockIdx.x);
 }
 
 // Batched: instance blockIdx.y; parity P is also the step parity.
+// The batched form (its instance read through a pointer takes more
+// registers): 4 CTAs per SM at 64 registers with two links in flight took
+// the 64-member sweep from 3.846 to 3.407 ms per step against 3 CTAs at 80
+// registers with six (3.482 with three links at 4 CTAs, 3.435 at 5 CTAs
+// and 48 registers, which spill 136 bytes).
+#ifndef LBM_LINK_B_MINB
+#define LBM_LINK_B_MINB 4
+#endif
+#ifndef LBM_LINK_B_BATCH
+#define LBM_LINK_B_BATCH 2
+#endif
 template <typename T, bool GI>
-__global__ void __launch_bounds__(256, 3) k_links_b(const Inst *__restrict__ I, const int P, const int ext,
-                                                 const unsigned mB, const unsigned mB2, const int cap) {
+__global__ void __launch_bounds__(256, LBM_LINK_B_MINB) k_links_b(const Inst *__restrict__ I, const int P,
+                                                                  const int ext, const int cap) {
     const Inst &a = I[blockIdx.y];
     if ((int)blockIdx.x >= a.pt.np) return;
-    links_body<T, GI>(a.L, a.pt, a.pt.frame[P], (T *)a.f, a.flag, a.owner, P, ext, mB, mB2, cap, a.status, a.ctr,
-                      blockIdx.x);
+    links_body<T, GI, LBM_LINK_B_BATCH>(a.L, a.pt, a.pt.frame[P], (T *)a.f, a.flag, a.owner, P, ext, cap, a.status,
+                                        a.ctr, blockIdx.x);
 }
 
 int link_capacity(double max_radius) {
@@ -82,11 +92,10 @@ int links_setup(int ext, int cap) {
 }
 
 template <typename T, bool GI>
-static void links_launch(lbm_s *h, int parity, size_t smem, const SFrame *fcur, int ext, unsigned mB, unsigned mB2,
-                         int cap, bool pdl) {
+static void links_launch(lbm_s *h, int parity, size_t smem, const SFrame *fcur, int ext, int cap, bool pdl) {
     if (!pdl) {
         k_links<T, GI><<<h->pt.np, 256, smem, h->stream>>>(h->L, h->pt, fcur, (T *)h->f, h->flag, h->owner, parity,
-                                                           ext, mB, mB2, cap, h->status, h->ctr);
+                                                           ext, cap, h->status, h->ctr);
         return;
     }
     cudaLaunchConfig_t cfg = {};
@@ -100,26 +109,24 @@ static void links_launch(lbm_s *h, int parity, size_t smem, const SFrame *fcur, 
     cfg.attrs = at;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, k_links<T, GI>, h->L, h->pt, fcur, (T *)h->f, (uint8_t *)h->flag,
-                       (const int32_t *)h->owner, parity, ext, mB, mB2, cap, h->status, h->ctr);
+                       (const int32_t *)h->owner, parity, ext, cap, h->status, h->ctr);
 }
 
 template <typename T>
-static void links_launch_t(lbm_s *h, int parity, size_t smem, const SFrame *fcur, int ext, unsigned mB, unsigned mB2,
-                           int cap, bool pdl) {
-    if (h->pt.gimea) links_launch<T, true>(h, parity, smem, fcur, ext, mB, mB2, cap, pdl);
-    else links_launch<T, false>(h, parity, smem, fcur, ext, mB, mB2, cap, pdl);
+static void links_launch_t(lbm_s *h, int parity, size_t smem, const SFrame *fcur, int ext, int cap, bool pdl) {
+    if (h->pt.gimea) links_launch<T, true>(h, parity, smem, fcur, ext, cap, pdl);
+    else links_launch<T, false>(h, parity, smem, fcur, ext, cap, pdl);
 }
 
 int launch_links(lbm_s *h, int parity, bool after_collide) {
     const int ext = h->tile_ext, cap = h->link_cap;
     const size_t smem = link_smem(ext, cap);
     const SFrame *fcur = h->pt.frame[h->steps & 1];
-    const unsigned B = 2u * ext + 1u, mB = 0xFFFFFFFFu / B + 1u, mB2 = 0xFFFFFFFFu / (B * B) + 1u;
     const bool pdl = after_collide;
     switch (h->precision) {
-        case LBM_FP32: links_launch_t<float>(h, parity, smem, fcur, ext, mB, mB2, cap, pdl); break;
-        case LBM_BF16_DEV: links_launch_t<__nv_bfloat16>(h, parity, smem, fcur, ext, mB, mB2, cap, pdl); break;
-        case LBM_FP16_DEV: links_launch_t<__half>(h, parity, smem, fcur, ext, mB, mB2, cap, pdl); break;
+        case LBM_FP32: links_launch_t<float>(h, parity, smem, fcur, ext, cap, pdl); break;
+        case LBM_BF16_DEV: links_launch_t<__nv_bfloat16>(h, parity, smem, fcur, ext, cap, pdl); break;
+        case LBM_FP16_DEV: links_launch_t<__half>(h, parity, smem, fcur, ext, cap, pdl); break;
         default: return LBM_ERR_ARG;
     }
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
@@ -130,23 +137,22 @@ int links_setup_batch(int ext, int cap) { return links_setup(ext, cap); }
 // A batch with any member on the Galilean-invariant exchange takes the GI
 // kernels; each instance still follows its own setting.
 template <typename T>
-static void links_launch_batch(const lbm_batch_s *b, int P, size_t smem, int ext, unsigned mB, unsigned mB2, int cap) {
+static void links_launch_batch(const lbm_batch_s *b, int P, size_t smem, int ext, int cap) {
     bool gi = false;
     for (int i = 0; i < b->n; ++i) gi = gi || b->m[i]->pt.gimea != 0;
     const dim3 grid(b->max_np, b->n);
-    if (gi) k_links_b<T, true><<<grid, 256, smem, b->stream>>>(b->dinst, P, ext, mB, mB2, cap);
-    else k_links_b<T, false><<<grid, 256, smem, b->stream>>>(b->dinst, P, ext, mB, mB2, cap);
+    if (gi) k_links_b<T, true><<<grid, 256, smem, b->stream>>>(b->dinst, P, ext, cap);
+    else k_links_b<T, false><<<grid, 256, smem, b->stream>>>(b->dinst, P, ext, cap);
 }
 
 int launch_links_batch(const lbm_batch_s *b, int P) {
     if (b->max_np == 0) return LBM_OK;
     const int ext = b->ext, cap = b->cap;
     const size_t smem = link_smem(ext, cap);
-    const unsigned B = 2u * ext + 1u, mB = 0xFFFFFFFFu / B + 1u, mB2 = 0xFFFFFFFFu / (B * B) + 1u;
     switch (b->precision) {
-        case LBM_FP32: links_launch_batch<float>(b, P, smem, ext, mB, mB2, cap); break;
-        case LBM_BF16_DEV: links_launch_batch<__nv_bfloat16>(b, P, smem, ext, mB, mB2, cap); break;
-        case LBM_FP16_DEV: links_launch_batch<__half>(b, P, smem, ext, mB, mB2, cap); break;
+        case LBM_FP32: links_launch_batch<float>(b, P, smem, ext, cap); break;
+        case LBM_BF16_DEV: links_launch_batch<__nv_bfloat16>(b, P, smem, ext, cap); break;
+        case LBM_FP16_DEV: links_launch_batch<__half>(b, P, smem, ext, cap); break;
         default: return LBM_ERR_ARG;
     }
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;

@@ -416,13 +416,20 @@ template <typename T, bool GI, int BATCH = 6, bool CG = false>
 __device__ __forceinline__ void links_body(const Lat &L, const Parts &pt, const SFrame *__restrict__ fcur,
                                            T *__restrict__ f, const uint8_t *__restrict__ flag,
                                            const int32_t *__restrict__ owner, const int P, const int ext,
-                                           const unsigned mB, const unsigned mB2, const int cap,
-                                           int *__restrict__ status, unsigned long long *__restrict__ ctr,
-                                           const int p) {
+                                           const int cap, int *__restrict__ status,
+                                           unsigned long long *__restrict__ ctr, const int p) {
     extern __shared__ unsigned char smem[];
-    const Tile tl(ext, mB, mB2);
-    const LinkShared sh(smem, cap, tl.B3);
     const SFrame Fr = fcur[p];
+    // The sphere's own tile: its solid nodes lie within ceil(R) of floor(X)
+    // (the marks' box), their links' fluid nodes x = s - c_j and x - c_j
+    // within two more.  ext (shared memory is sized for it) bounds it; a
+    // small sphere among large ones scans only its own box.  Nodes are
+    // listed in (z, y, x) order whatever the extent, so the link list, and
+    // every sum over it, is the same for any extent that holds the sphere.
+    const int e = min(ext, (int)ceilf(Fr.R) + 2);
+    const unsigned B = 2u * (unsigned)e + 1u;
+    const Tile tl(e, 0xFFFFFFFFu / B + 1u, 0xFFFFFFFFu / (B * B) + 1u);
+    const LinkShared sh(smem, cap, tl.B3);
     link_codes(L, Fr.b, flag, owner, p, tl, SolidOf{0}, sh.code);
     const int total = link_enumerate(sh, tl, cap, status);
     // Launched as a programmatic dependent of the collide, the CTA may start
