@@ -373,6 +373,9 @@ __device__ __forceinline__ int ld_volatile(const int *p) { return *(const volati
 
 // Returns false (and sets the timeout status) if the other blocks did not
 // arrive within ~2^22 polls, or if another block already gave up.
+#ifndef LBM_BAR_SLEEP_NS
+#define LBM_BAR_SLEEP_NS 32  // pause between polls
+#endif
 __device__ bool grid_barrier(unsigned *bar, unsigned target, int *status) {
     __shared__ int ok;
     __syncthreads();
@@ -387,7 +390,9 @@ __device__ bool grid_barrier(unsigned *bar, unsigned target, int *status) {
                 good = 0;
                 break;
             }
-            __nanosleep(32);
+#if LBM_BAR_SLEEP_NS > 0
+            __nanosleep(LBM_BAR_SLEEP_NS);
+#endif
         }
         __threadfence();
         ok = good;
@@ -714,7 +719,10 @@ __global__ void __launch_bounds__(kDemThreads, 1) k_dem_cluster(const Lat L, con
     dem_cluster_body<FRIC, false>(L, pt, fnext, sp, status);
 }
 
-constexpr int kDemGridThreads = 64;  // threads per CTA of the grid form
+#ifndef LBM_DEM_GRID_THREADS
+#define LBM_DEM_GRID_THREADS 64
+#endif
+constexpr int kDemGridThreads = LBM_DEM_GRID_THREADS;  // threads per CTA of the grid form
 // sphere count from which the automatic choice takes the grid form: one
 // cluster then holds two or more spheres per thread (measured: 8136 spheres
 // with friction, DEM 0.31 ms per step in the cluster, 0.14 ms in the grid)
