@@ -150,8 +150,9 @@ typedef struct {
 
 /* Allocate a simulation and set the fluid to rest (f = w, rho = 1, u = 0)
  * with no spheres.  *out receives the handle.  LBM_ERR_ARG on an invalid
- * parameter (tau0 <= 1/2, a wall velocity with a z component, a box that
- * cannot hold a sphere of max_radius, ...), LBM_ERR_UNSUPPORTED for
+ * parameter (tau0 <= 1/2, a wall velocity with a z component, with spheres
+ * an nx or ny below 2 (ceil(max_radius) + 3) + 1, so that a sphere's link
+ * tile does not wrap onto itself, ...), LBM_ERR_UNSUPPORTED for
  * periodic_z != 0, LBM_ERR_NOMEM / LBM_ERR_CUDA on device failure. */
 int lbm_create(const lbm_params *params, lbm_handle *out);
 
@@ -316,10 +317,9 @@ typedef struct lbm_batch_s *lbm_batch;
 /* Create count >= 1 members.  Members run the serial order with one DEM
  * cluster each: their schedule and dem_mode fields are not used.  LBM_ERR_ARG
  * if the params differ in device, precision or stream or one is invalid (as
- * lbm_create), LBM_ERR_UNSUPPORTED if the DEM cluster cannot hold the largest
- * max_particles, a member has a ZIEB face, or a member with spheres has nx or
- * ny below 2 (ceil(r) + 2) + 3 for r the largest max_radius of the batch (the
- * link kernel tiles every member's spheres with the batch's largest tile). */
+ * lbm_create, whose box rule each member meets for its own max_radius),
+ * LBM_ERR_UNSUPPORTED if the DEM cluster cannot hold the largest
+ * max_particles or a member has a ZIEB face. */
 int lbm_batch_create(const lbm_params *params, int32_t count, lbm_batch *out);
 
 /* Destroy the batch and its members (synchronises the stream first). */

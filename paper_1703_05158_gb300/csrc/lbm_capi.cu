@@ -1173,17 +1173,10 @@ int lbm_batch_create(const lbm_params *params, int32_t count, lbm_batch *out) {
         if (params[i].device != params[0].device || params[i].precision != params[0].precision ||
             params[i].cuda_stream != params[0].cuda_stream)
             return LBM_ERR_ARG;
-    // The batched link kernel tiles the spheres of every member with the
-    // largest extent; each member with spheres needs that tile to fit its
-    // periodic box without wrapping onto itself (the rule lbm_create applies
-    // to a lattice alone, with the batch's extent).
-    int ext_max = 0;
-    for (int i = 0; i < count; ++i)
-        if (params[i].max_particles > 0 && params[i].max_radius > 0.0 && params[i].max_radius <= 16.0)
-            ext_max = std::max(ext_max, (int)std::ceil(params[i].max_radius) + 2);
-    for (int i = 0; i < count; ++i)
-        if (params[i].max_particles > 0 && (params[i].nx < 2 * ext_max + 3 || params[i].ny < 2 * ext_max + 3))
-            return LBM_ERR_UNSUPPORTED;
+    // Each link CTA scans its own sphere's tile (extent ceil(R) + 2, within
+    // that of its member's max_radius), which the member's own box rule in
+    // lbm_create keeps from wrapping onto itself; only the link kernel's
+    // shared memory is sized for the batch's largest tile.
     lbm_batch_s *b = new (std::nothrow) lbm_batch_s();
     if (!b) return LBM_ERR_NOMEM;
     b->device = params[0].device;

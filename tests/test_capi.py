@@ -132,12 +132,13 @@ def test_binding_structs_match_the_header_layout(tmp_path):
 
 def test_link_tile_decode_by_multiply_high_is_exact_for_every_allowed_radius():
     """The link kernel splits a tile index t < B^3 into (x, y, z) with
-    __umulhi(t, 2^32 / B + 1) in place of t / B (B = 2 ext + 1, ext =
-    ceil(max_radius) + 2); check the quotients for every t and every radius
-    the ABI accepts (max_radius <= 16), and that the kernel still uses this
-    form.  The 16-bit list of a sphere's own tile nodes needs B^3 <= 2^16."""
-    src = open(os.path.join(ROOT, "paper_1703_05158_gb300", "csrc", "lbm_links.cu")).read()
-    assert src.count("mB = 0xFFFFFFFFu / B + 1u, mB2 = 0xFFFFFFFFu / (B * B) + 1u") == 2
+    __umulhi(t, 2^32 / B + 1) in place of t / B (B = 2 e + 1, e = ceil(R) + 2
+    for the CTA's sphere of radius R, at most that of max_radius); check the
+    quotients for every t and every extent a radius the ABI accepts gives
+    (R <= 16), and that the kernel still uses this form.  The 16-bit list of
+    a sphere's own tile nodes needs B^3 <= 2^16."""
+    src = open(os.path.join(ROOT, "paper_1703_05158_gb300", "csrc", "lbm_links.cuh")).read()
+    assert src.count("Tile tl(e, 0xFFFFFFFFu / B + 1u, 0xFFFFFFFFu / (B * B) + 1u)") == 1
     for R in range(1, 17):
         B = 2 * (R + 2) + 1
         B2 = B * B
@@ -148,23 +149,6 @@ def test_link_tile_decode_by_multiply_high_is_exact_for_every_allowed_radius():
         assert np.array_equal(z, t // np.uint64(B2))
         r = t - z * np.uint64(B2)
         assert np.array_equal((r * np.uint64(mB)) >> np.uint64(32), r // np.uint64(B))
-
-
-def test_batch_rejects_a_member_box_narrower_than_the_shared_link_tile():
-    """Alone, a 20 x 20 box takes spheres up to radius 4 (tile 2 (4 + 2) + 3
-    = 15 nodes); batched with a radius-8 member, whose tile of 23 nodes the
-    link kernel uses for every member, it is refused before any device
-    work.  A member without spheres is not tiled and stays accepted."""
-    small = lbm.make_params(20, 20, 16, 0.8, max_particles=2, max_radius=4.0)
-    large = lbm.make_params(64, 64, 32, 0.8, max_particles=2, max_radius=8.0)
-    with pytest.raises(lbm.LbmError) as e:
-        lbm.lbm_batch_create([small, large])
-    assert e.value.code == lbm.LBM_ERR_UNSUPPORTED
-    fluid_only = lbm.make_params(20, 20, 16, 0.8)
-    try:  # passes the check; creating the members then needs a device
-        lbm.lbm_batch_destroy(lbm.lbm_batch_create([fluid_only, large]))
-    except lbm.LbmError as e:
-        assert e.code != lbm.LBM_ERR_UNSUPPORTED
 
 
 def _channel_params(**kw):

@@ -193,3 +193,34 @@ def test_rows_of_several_blocks_bitwise(box, precision):
         assert np.array_equal(m.forces()[0], alone.forces()[0])
     alone.close()
     batch.close()
+
+
+def test_small_box_beside_a_large_sphere_member_bitwise():
+    """A 20 x 20 box with spheres up to radius 4 (its own link tile 2 (4 + 2)
+    + 1 = 13 nodes wide, 15 with the wrap margin) batched with a member of
+    radius-8 spheres (tile 21 nodes, wider than the small box): every link
+    CTA scans its own sphere's tile, so the small member is accepted and
+    both step bitwise as alone."""
+    L = lbm()
+    kw = dict(tau0=0.7, cs=0.12, g=(2e-6, 0.0, 0.0), rho_s=2.5, kn=1e3, restitution=0.8, dem_substeps=16)
+    cases = [((20, 20, 16), 4.0, np.array([[5.2, 6.1, 7.3], [14.6, 13.8, 8.4]]), np.array([3.5, 4.0])),
+             ((64, 64, 32), 8.0, np.array([[20.3, 30.2, 15.6], [45.1, 33.7, 16.2]]), np.array([7.0, 8.0]))]
+    cfgs = [dict(nx=b[0], ny=b[1], nz=b[2], max_particles=2, max_radius=r, **kw) for b, r, _, _ in cases]
+    batch = L.Batch(cfgs)
+    alone = [L.Lattice(*b, max_particles=2, max_radius=r, **kw) for b, r, _, _ in cases]
+    V = np.array([[0.01, -0.004, 0.002], [-0.006, 0.003, -0.001]])
+    for m, a, (_, _, X, R) in zip(batch.members, alone, cases):
+        m.set_particles(X, V=V, R=R)
+        a.set_particles(X, V=V, R=R)
+    for n in (1, 2, 9):
+        batch.step(n)
+        for a in alone:
+            a.step(n)
+        batch.sync()
+        for m, a in zip(batch.members, alone):
+            assert np.array_equal(m.owner(), a.owner())
+            assert np.array_equal(m.populations(), a.populations())
+            assert np.array_equal(m.forces()[0], a.forces()[0])
+    for a in alone:
+        a.close()
+    batch.close()
