@@ -261,8 +261,12 @@ __device__ __forceinline__ void warp_add(double v, double *dst) {
 // nodes of one x row; grid (ceil(nx / kChanTx), ny, nz), so that (x, y, z)
 // come from the block and thread indices without integer division.
 constexpr int kChanTx = 128;
+// Resident blocks per SM of k_chan_adj: 10 (48 registers, a few hundred
+// bytes of spills to L1) waits out more of its latency than 8 at 64
+// registers without spills (reverse sweep 87.7 against 89.1 ms per gradient
+// of 500 steps; 12 blocks at 40 registers 88.2).
 #ifndef LBM_CHAN_ADJ_MINB
-#define LBM_CHAN_ADJ_MINB 8  // resident blocks per SM of k_chan_adj (register budget 64)
+#define LBM_CHAN_ADJ_MINB 10
 #endif
 
 // Row neighbours of (y, z): y periodic; z - 1 and z + 1 clamped into the
