@@ -268,6 +268,13 @@ constexpr int kChanTx = 128;
 #ifndef LBM_CHAN_ADJ_MINB
 #define LBM_CHAN_ADJ_MINB 10
 #endif
+// Resident blocks per SM of k_chan_step (the forward and the reverse
+// sweep's recompute): 12 at 40 registers, 110.6 ms per gradient against
+// 112.1 at 8 (64 registers) and 111.3 at 10; 16 (32 registers) spills
+// heavily and took 129 ms.
+#ifndef LBM_CHAN_STEP_MINB
+#define LBM_CHAN_STEP_MINB 12
+#endif
 
 // Row neighbours of (y, z): y periodic; z - 1 and z + 1 clamped into the
 // box (a pull from outside the box is replaced by the bounce-back of the cut
@@ -340,7 +347,7 @@ __device__ __forceinline__ int extra_index(const ChanGeo &G) {
 // the populations of the node's cut links (bounce-back; Eq. 19 with q from
 // the geometry, walls and plate q = 1/2).
 template <bool PULL>
-__global__ void __launch_bounds__(kChanTx, 8) k_chan_step(const ChanGeo G, const Phys ph, const float u_peak,
+__global__ void __launch_bounds__(kChanTx, LBM_CHAN_STEP_MINB) k_chan_step(const ChanGeo G, const Phys ph, const float u_peak,
                                                        const float *__restrict__ Gin, const float *__restrict__ fin,
                                                        float *__restrict__ frec, float *__restrict__ Gout,
                                                        double *__restrict__ drag, int *__restrict__ status) {
