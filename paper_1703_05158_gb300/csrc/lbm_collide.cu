@@ -24,9 +24,20 @@
 
 namespace lbm {
 
-// Every fluid node, one thread each, one block per row segment.
+// Every fluid node, one thread each, one block per row segment.  Resident
+// blocks per SM: the even parity fits 48 registers without spills and at 5
+// blocks keeps more loads in flight (FP32 collide 0.435 -> 0.422 ms per
+// step over both parities; 6 blocks at 40 registers spill and lose); the
+// odd parity's shifted addressing needs 64 (at 48 it spills 112 bytes and
+// the step's collide took 0.477 ms).
+#ifndef LBM_SC_MINB_EVEN
+#define LBM_SC_MINB_EVEN 5
+#endif
+#ifndef LBM_SC_MINB_ODD
+#define LBM_SC_MINB_ODD 4
+#endif
 template <int ODD, typename T>
-__global__ void __launch_bounds__(256, 4) k_stream_collide(const Lat L, const Phys ph, T *__restrict__ f,
+__global__ void __launch_bounds__(256, ODD ? LBM_SC_MINB_ODD : LBM_SC_MINB_EVEN) k_stream_collide(const Lat L, const Phys ph, T *__restrict__ f,
                                                         uint8_t *__restrict__ flag, int *__restrict__ status) {
     // a programmatic dependent (the link kernel) may launch once every block
     // has started; it waits for this grid's completion before its reads
