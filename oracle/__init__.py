@@ -18,7 +18,10 @@ face's rest state, face density and mass balance of a piston stroke, and
 for the Galilean-invariant exchange its reduction to Eqs. 25, 26 at rest and
 its extra force on a translating sphere (the velocity times the fluid mass
 the moving bounce-back creates).  The coupled free-sphere trajectory itself
-has no closed form: parity unpinned beyond those invariants.  The
+has no closed form: its transient is unpinned beyond those invariants; its
+steady state is pinned by Galilean invariance (a free sphere's terminal
+velocity under a constant force against the drag on the same sphere held
+fixed in the co-moving frame, tests/test_oracle_galilean.py).  The
 Galilean-invariant extra term is pinned in force (a translating sphere:
 the fluid mass the moving bounce-back creates) and in force and torque (a
 sphere spinning in place: the term formed from the streamed populations).

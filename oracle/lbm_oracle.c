@@ -38,7 +38,9 @@
  *
  * Readings of passages the paper leaves open are marked "reading:".
  * Parity pins: every function below is pinned by tests in tests/ except the
- * full coupled moving-sphere trajectory, which has no closed form.
+ * transient of the full coupled moving-sphere trajectory, which has no
+ * closed form; its steady state is pinned by Galilean invariance (a free
+ * sphere's terminal velocity against the drag in the co-moving frame).
  */
 #include <math.h>
 #include <stdint.h>
