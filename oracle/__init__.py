@@ -68,48 +68,77 @@ _lib = None
 def _load():
     global _lib
     if _lib is None:
-        path = _build.build()
-        lib = ctypes.CDLL(path)
-        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
-        lib.orc_create.restype = vp
-        lib.orc_create.argtypes = [ctypes.POINTER(OrcParams)]
-        lib.orc_destroy.argtypes = [vp]
-        lib.orc_set_particles.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp, ctypes.c_void_p]
-        lib.orc_set_populations.argtypes = [vp, dp]
-        lib.orc_get_populations.argtypes = [vp, dp]
-        lib.orc_step.argtypes = [vp, ctypes.c_int]
-        lib.orc_forces.argtypes = [vp, dp, dp]
-        lib.orc_contact_forces.argtypes = [vp, dp]
-        lib.orc_contact_torques.argtypes = [vp, dp]
-        lib.orc_contact_overflow.restype = ctypes.c_int
-        lib.orc_contact_overflow.argtypes = [vp]
-        lib.orc_zieb_state.argtypes = [vp, dp]
-        lib.orc_zieb_set_piston.argtypes = [vp, ctypes.c_double]
-        lib.orc_particles.argtypes = [vp, dp, dp, dp]
-        lib.orc_fields.argtypes = [vp, dp, dp]
-        lib.orc_tau_eff.argtypes = [vp, dp]
-        lib.orc_owner.argtypes = [vp, ip]
-        lib.orc_links.restype = ctypes.c_long
-        lib.orc_links.argtypes = [vp, ctypes.c_long, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                  ctypes.c_void_p]
-        lib.orc_refilled.restype = ctypes.c_long
-        lib.orc_refilled.argtypes = [vp]
-        lib.orc_step_count.restype = ctypes.c_long
-        lib.orc_step_count.argtypes = [vp]
-        lib.orc_tables.argtypes = [ip, ip, ip, dp, ip]
-        lib.orc_feq.argtypes = [ctypes.c_double, dp, dp]
-        lib.orc_refill_only.argtypes = [vp]
-        lib.orc_set_load.argtypes = [vp, ctypes.c_void_p, ctypes.c_void_p]
-        lib.orc_plate_drag.restype = ctypes.c_double
-        lib.orc_plate_drag.argtypes = [vp]
-        lib.orc_channel_violation.restype = ctypes.c_int
-        lib.orc_channel_violation.argtypes = [vp]
-        lib.chan_run.restype = ctypes.c_int
-        lib.chan_run.argtypes = [ctypes.POINTER(ChanParams), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
-                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                 ctypes.c_void_p, ctypes.c_void_p]
-        _lib = lib
+        _lib = _bind(ctypes.CDLL(_build.build()))
     return _lib
+
+
+class Planted:
+    """Context in which new Oracle objects run a modified oracle: the text of
+    lbm_oracle.c with a mistake planted in it, compiled into ``path`` (a test
+    checks that its pins catch the mistake).  The library is restored on
+    exit."""
+
+    def __init__(self, oracle_source, path):
+        self.lib = _bind(ctypes.CDLL(_build.build_variant(oracle_source, path)))
+
+    def __enter__(self):
+        global _lib
+        self.saved, _lib = _load(), self.lib
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def source():
+    """The text of lbm_oracle.c (for planting a mistake in a copy)."""
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "lbm_oracle.c")) as fh:
+        return fh.read()
+
+
+def _bind(lib):
+    """Declare the oracle's entry points on a loaded library."""
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    lib.orc_create.restype = vp
+    lib.orc_create.argtypes = [ctypes.POINTER(OrcParams)]
+    lib.orc_destroy.argtypes = [vp]
+    lib.orc_set_particles.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp, ctypes.c_void_p]
+    lib.orc_set_populations.argtypes = [vp, dp]
+    lib.orc_get_populations.argtypes = [vp, dp]
+    lib.orc_step.argtypes = [vp, ctypes.c_int]
+    lib.orc_forces.argtypes = [vp, dp, dp]
+    lib.orc_contact_forces.argtypes = [vp, dp]
+    lib.orc_contact_torques.argtypes = [vp, dp]
+    lib.orc_contact_overflow.restype = ctypes.c_int
+    lib.orc_contact_overflow.argtypes = [vp]
+    lib.orc_zieb_state.argtypes = [vp, dp]
+    lib.orc_zieb_set_piston.argtypes = [vp, ctypes.c_double]
+    lib.orc_particles.argtypes = [vp, dp, dp, dp]
+    lib.orc_fields.argtypes = [vp, dp, dp]
+    lib.orc_tau_eff.argtypes = [vp, dp]
+    lib.orc_owner.argtypes = [vp, ip]
+    lib.orc_links.restype = ctypes.c_long
+    lib.orc_links.argtypes = [vp, ctypes.c_long, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p]
+    lib.orc_refilled.restype = ctypes.c_long
+    lib.orc_refilled.argtypes = [vp]
+    lib.orc_step_count.restype = ctypes.c_long
+    lib.orc_step_count.argtypes = [vp]
+    lib.orc_tables.argtypes = [ip, ip, ip, dp, ip]
+    lib.orc_feq.argtypes = [ctypes.c_double, dp, dp]
+    lib.orc_refill_only.argtypes = [vp]
+    lib.orc_set_load.argtypes = [vp, ctypes.c_void_p, ctypes.c_void_p]
+    lib.orc_plate_drag.restype = ctypes.c_double
+    lib.orc_plate_drag.argtypes = [vp]
+    lib.orc_channel_violation.restype = ctypes.c_int
+    lib.orc_channel_violation.argtypes = [vp]
+    lib.chan_run.restype = ctypes.c_int
+    lib.chan_run.argtypes = [ctypes.POINTER(ChanParams), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_void_p, ctypes.c_void_p]
+    return lib
 
 
 def _dp(a):

@@ -25,5 +25,19 @@ def build(force=False):
     return LIB
 
 
+def build_variant(oracle_source, out):
+    """Compile ``oracle_source`` (the text of a modified lbm_oracle.c, for a
+    test that plants a mistake) with the channel oracle into ``out``, with the
+    flags of build(); return its path."""
+    out = str(out)
+    src = out + ".c"
+    with open(src, "w") as fh:
+        fh.write(oracle_source)
+    cmd = ["gcc", "-std=gnu11", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-I", HERE, src, SRCS[1], "-o", out, "-lm"]
+    subprocess.check_call(cmd)
+    return out
+
+
 if __name__ == "__main__":
     print(build(force=True))
