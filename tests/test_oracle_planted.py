@@ -1,0 +1,53 @@
+"""Planted mistakes: each case plants one plausible error in a copy of the
+oracle (a dropped factor or term, a wrong sign, transposed weights) and
+checks that the pin named beside it fails on that copy, while it passes on
+the oracle itself (its own test file).  The copies are compiled for the
+test and run through ``oracle.Planted``; the oracle is never modified."""
+import numpy as np
+import pytest
+
+import oracle
+import test_oracle_dem
+import test_oracle_drag
+import test_oracle_flows
+import test_oracle_galilean
+import test_oracle_invariants
+import test_oracle_lattice
+
+CASES = [
+    # Guo et al. source without its (1 - 1/(2 tau)) factor (Sect. 2.2)
+    ("guo_factor", "+ (1.0 - 0.5 / tau) * src;", "+ src;",
+     lambda t: test_oracle_flows.test_poiseuille_exact_at_magic_tau()),
+    # velocity without the half-force shift (Eq. 6 with the body force)
+    ("half_force_shift", "u[0] = mx / r + 0.5 * s->p.g[0];", "u[0] = mx / r;",
+     lambda t: test_oracle_invariants.test_body_force_momentum_per_step()),
+    # Smagorinsky relaxation time without the sqrt(2) of |S| (Eq. 18)
+    ("smagorinsky_sqrt2", "18.0 * sqrt(2.0) * C * C * Q", "18.0 * C * C * Q",
+     lambda t: test_oracle_flows.test_smagorinsky_eddy_viscosity_in_uniform_shear()),
+    # equilibrium with a wrong second-order coefficient (Eq. 9)
+    ("feq_quadratic", "4.5 * cu * cu", "3.0 * cu * cu",
+     lambda t: test_oracle_lattice.test_equilibrium_moments(t, 1.03, (0.04, -0.02, 0.01))),
+    # moving-wall term of Eq. 21 with the wrong sign (halfway walls take the q >= 1/2 branch)
+    ("wall_term_sign", "+ 3.0 / q * s->w[j] * cku;", "- 3.0 / q * s->w[j] * cku;",
+     lambda t: test_oracle_flows.test_couette_linear_profile()),
+    # momentum exchange with f_k subtracted instead of added (Eq. 25)
+    ("exchange_sign", "double m = s->fc[(long)j * s->N + n] + s->fn[(long)k * s->N + n];",
+     "double m = s->fc[(long)j * s->N + n] - s->fn[(long)k * s->N + n];",
+     lambda t: test_oracle_drag.test_momentum_balance_at_steady_state()),
+    # normal damping coefficient missing its factor 2 (Eq. 1)
+    ("damping_factor", "return -2.0 * le * sqrt(meff * s->p.kn)", "return -le * sqrt(meff * s->p.kn)",
+     lambda t: test_oracle_dem.test_restitution_and_contact_time((4.0, 4.0))),
+    # interpolation weights of the q < 1/2 branch of Eq. 19 transposed
+    ("interpolation_weights", "return 2.0 * q * fcj + (1.0 - 2.0 * q) * s->fc[(long)j * s->N + nb] + dw;",
+     "return (1.0 - 2.0 * q) * fcj + 2.0 * q * s->fc[(long)j * s->N + nb] + dw;",
+     lambda t: test_oracle_galilean.test_free_sphere_terminal_velocity_balances_the_co_moving_fixed_drag()),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pin", CASES, ids=[c[0] for c in CASES])
+def test_planted_mistake_fails_its_pin(name, old, new, pin, d3q19, tmp_path):
+    src = oracle.source()
+    assert src.count(old) == 1, name
+    with oracle.Planted(src.replace(old, new), tmp_path / (name + ".so")):
+        with pytest.raises(AssertionError):
+            pin(d3q19)
