@@ -98,6 +98,22 @@ def test_overlap_tie_break():
     assert np.array_equal(owner >= 0, ina | inb)
 
 
+def test_exact_ties_go_to_the_smaller_index():
+    """Two equal spheres whose centres are mirror images across the node
+    plane x = 10: every node of that plane inside both is at the same FP32
+    distance from either centre, an exact tie of the keys |x - X| - R, and
+    belongs to the sphere of smaller index whichever order they are given in."""
+    R = 2.75
+    for first, second in (((8.0, 8.5, 8.25), (12.0, 8.5, 8.25)), ((12.0, 8.5, 8.25), (8.0, 8.5, 8.25))):
+        o = oracle.Oracle(22, 17, 16, tau0=0.8)
+        o.set_particles([first, second], R=[R, R])
+        owner = o.owner()
+        both = exact_inside(o.shape, first, R) & exact_inside(o.shape, second, R)
+        tied = np.argwhere(both)
+        assert len(tied) > 0 and (tied[:, 2] == 10).all()
+        assert (owner[both] == 0).all()
+
+
 def test_refill_of_uncovered_nodes():
     """Shift a sphere by a prescribed motion; every node uncovered gets the
     equilibrium at the mean density of its neighbours fluid before and after,

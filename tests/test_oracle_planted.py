@@ -10,6 +10,7 @@ import oracle
 import test_oracle_dem
 import test_oracle_drag
 import test_oracle_flows
+import test_oracle_geometry
 import test_oracle_galilean
 import test_oracle_invariants
 import test_oracle_lattice
@@ -41,6 +42,26 @@ CASES = [
     ("interpolation_weights", "return 2.0 * q * fcj + (1.0 - 2.0 * q) * s->fc[(long)j * s->N + nb] + dw;",
      "return (1.0 - 2.0 * q) * fcj + 2.0 * q * s->fc[(long)j * s->N + nb] + dw;",
      lambda t: test_oracle_galilean.test_free_sphere_terminal_velocity_balances_the_co_moving_fixed_drag()),
+    # inside test |x - X|^2 <= R^2 instead of the strict < (Sect. 2.3)
+    ("inside_not_strict", "if (!(d2 < R2)) continue;", "if (!(d2 <= R2)) continue;",
+     lambda t: test_oracle_geometry.test_node_count_of_centred_spheres()),
+    # exact overlap ties going to the larger sphere index
+    ("tie_break", "if (key < s->key[n]) {", "if (key <= s->key[n]) {",
+     lambda t: test_oracle_geometry.test_exact_ties_go_to_the_smaller_index()),
+    # overlap decided by the distance to the centre, the radius left out of the key
+    ("key_without_radius", "float key = sqrtf(d2) - Rf;", "float key = sqrtf(d2);",
+     lambda t: test_oracle_geometry.test_overlap_tie_break()),
+    # link fraction from the wrong root (sign of b)
+    ("link_fraction_root", "float q = c0 / (-b + sqrtf(disc));", "float q = c0 / (b + sqrtf(disc));",
+     lambda t: test_oracle_geometry.test_cut_links_and_fractions_brute_force()),
+    # refill at the spin velocity only, the sphere's translation dropped
+    ("refill_velocity", "double us[3] = {V[0] + (W[1] * l[2] - W[2] * l[1]),",
+     "double us[3] = {(W[1] * l[2] - W[2] * l[1]),",
+     lambda t: test_oracle_geometry.test_refill_of_uncovered_nodes()),
+    # refill density averaged also over neighbours that were solid before
+    ("refill_neighbours", "if (s->owner_prev[m] >= 0 || s->owner[m] >= 0) continue;",
+     "if (s->owner[m] >= 0) continue;",
+     lambda t: test_oracle_geometry.test_refill_of_uncovered_nodes()),
 ]
 
 
