@@ -281,6 +281,24 @@ def test_no_particles_and_capacity_errors():
     assert lat.info()["steps"] == 3
 
 
+def test_exact_overlap_ties_match_the_oracle():
+    """Mirror-image equal spheres: the nodes of the plane between them tie
+    exactly (the same FP32 key from either centre) and go to the smaller
+    index in the library as in the oracle, in either order, before and after
+    a step."""
+    R = 2.75
+    for first, second in (((8.0, 8.5, 8.25), (12.0, 8.5, 8.25)), ((12.0, 8.5, 8.25), (8.0, 8.5, 8.25))):
+        parts = dict(X=np.array([first, second]), V=np.zeros((2, 3)), R=np.array([R, R]),
+                     fixed=np.array([1, 1], dtype=np.uint8))
+        lat, orc = make_pair((22, 17, 16), parts=parts, tau0=0.8)
+        assert np.array_equal(lat.owner(), orc.owner())
+        assert ((orc.owner() == 0) & (np.arange(22)[None, None, :] == 10)).any()
+        lat.step(1)
+        orc.step(1)
+        assert np.array_equal(lat.owner(), orc.owner())
+        lat.close()
+
+
 def test_largest_lattice_and_the_index_limit():
     """Populations are addressed with 32-bit element offsets: a box whose
     19 slot arrays (with the two wall planes and padding) reach 2^31
