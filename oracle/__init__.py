@@ -73,13 +73,14 @@ def _load():
 
 
 class Planted:
-    """Context in which new Oracle objects run a modified oracle: the text of
-    lbm_oracle.c with a mistake planted in it, compiled into ``path`` (a test
+    """Context in which new Oracle objects (and the channel oracle) run a
+    modified oracle: the text of lbm_oracle.c, and optionally of
+    channel_oracle.c, with a mistake planted, compiled into ``path`` (a test
     checks that its pins catch the mistake).  The library is restored on
     exit."""
 
-    def __init__(self, oracle_source, path):
-        self.lib = _bind(ctypes.CDLL(_build.build_variant(oracle_source, path)))
+    def __init__(self, oracle_source, path, channel_source=None):
+        self.lib = _bind(ctypes.CDLL(_build.build_variant(oracle_source, path, channel_source)))
 
     def __enter__(self):
         global _lib
@@ -92,9 +93,10 @@ class Planted:
         return False
 
 
-def source():
-    """The text of lbm_oracle.c (for planting a mistake in a copy)."""
-    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "lbm_oracle.c")) as fh:
+def source(name="lbm_oracle.c"):
+    """The text of one of the oracle's C files (for planting a mistake in a
+    copy)."""
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), name)) as fh:
         return fh.read()
 
 

@@ -25,16 +25,21 @@ def build(force=False):
     return LIB
 
 
-def build_variant(oracle_source, out):
+def build_variant(oracle_source, out, channel_source=None):
     """Compile ``oracle_source`` (the text of a modified lbm_oracle.c, for a
-    test that plants a mistake) with the channel oracle into ``out``, with the
+    test that plants a mistake) with the channel oracle (``channel_source``,
+    a modified channel_oracle.c, or the file itself) into ``out``, with the
     flags of build(); return its path."""
     out = str(out)
-    src = out + ".c"
-    with open(src, "w") as fh:
-        fh.write(oracle_source)
+    srcs = [out + ".lbm.c", out + ".chan.c"]
+    if channel_source is None:
+        with open(SRCS[1]) as fh:
+            channel_source = fh.read()
+    for path, text in zip(srcs, (oracle_source, channel_source)):
+        with open(path, "w") as fh:
+            fh.write(text)
     cmd = ["gcc", "-std=gnu11", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-I", HERE, src, SRCS[1], "-o", out, "-lm"]
+           "-I", HERE] + srcs + ["-o", out, "-lm"]
     subprocess.check_call(cmd)
     return out
 

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
+import test_oracle_channel
 import test_oracle_dem
 import test_oracle_drag
 import test_oracle_flows
@@ -88,3 +89,23 @@ def test_planted_mistake_fails_its_pin(name, old, new, pin, d3q19, tmp_path):
     with oracle.Planted(src.replace(old, new), tmp_path / (name + ".so")):
         with pytest.raises(AssertionError):
             pin(d3q19)
+
+
+# the differentiation form's tangent-linear (dual-number) arithmetic
+CHANNEL_CASES = [
+    # derivative of sqrt without its factor 1/2 (the Smagorinsky time's Q and root)
+    ("dsqrt", "dual r = {s, s > 0.0 ? a.d / (2.0 * s) : 0.0};", "dual r = {s, s > 0.0 ? a.d / s : 0.0};", 2),
+    # quotient rule with the wrong sign
+    ("ddiv", "(a.d * b.v - a.v * b.d) / (b.v * b.v)", "(a.d * b.v + a.v * b.d) / (b.v * b.v)", 0),
+    # product rule missing one term
+    ("dmul", "dual r = {a.v * b.v, a.d * b.v + a.v * b.d};", "dual r = {a.v * b.v, a.d * b.v};", 1),
+]
+
+
+@pytest.mark.parametrize("name,old,new,k", CHANNEL_CASES, ids=[c[0] for c in CHANNEL_CASES])
+def test_planted_derivative_mistake_fails_the_central_difference_pin(name, old, new, k, tmp_path):
+    chan = oracle.source("channel_oracle.c")
+    assert chan.count(old) == 1, name
+    with oracle.Planted(oracle.source(), tmp_path / (name + ".so"), channel_source=chan.replace(old, new)):
+        with pytest.raises(AssertionError):
+            test_oracle_channel.test_tangent_linear_matches_central_differences(k)
