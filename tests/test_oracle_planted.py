@@ -16,6 +16,8 @@ import test_oracle_geometry
 import test_oracle_galilean
 import test_oracle_invariants
 import test_oracle_lattice
+import test_oracle_mea
+import test_oracle_zieb
 
 CASES = [
     # Guo et al. source without its (1 - 1/(2 tau)) factor (Sect. 2.2)
@@ -79,6 +81,20 @@ CASES = [
     # Coulomb cap without mu (Eq. 3)
     ("coulomb_cap", "double cap = s->p.mu * (fn > 0.0 ? fn : 0.0);", "double cap = (fn > 0.0 ? fn : 0.0);",
      lambda t: test_oracle_friction.test_sliding_sphere_decelerates_at_mu_g_then_rolls(0.5)),
+    # momentum correction: a covered node's momentum taken from its sphere instead of given to it
+    ("correction_sign", "add_momentum(s, p, l, m, 1.0);", "add_momentum(s, p, l, m, -1.0);",
+     lambda t: test_oracle_invariants.test_momentum_correction_conserves_total_momentum()),
+    # Galilean-invariant exchange with its extra term's sign flipped
+    ("gi_sign", "for (int a = 0; a < 3; ++a) dP[a] -= e * ub[a];", "for (int a = 0; a < 3; ++a) dP[a] += e * ub[a];",
+     lambda t: test_oracle_mea.test_extra_force_of_a_translating_sphere_is_its_velocity_times_the_created_mass()),
+    # ZIEB cylinder density (Eq. 8) with the exponent's sign flipped
+    ("zieb_exponent", "exp((P->zieb_vp * A - s->zvf * A) / (P->zieb_volume - A * s->zH))",
+     "exp((s->zvf * A - P->zieb_vp * A) / (P->zieb_volume - A * s->zH))",
+     lambda t: test_oracle_zieb.test_slow_stroke_conserves_mass_and_reaches_the_closed_form_density(0.0025)),
+    # ZIEB density fix (Eq. 9) that drops the normal population instead of completing it (the
+    # face still holds rho^{n+1}, its inflow velocity and so the cylinder's mass balance go wrong)
+    ("zieb_fix", "f[12] = rho1 - (rstar - f[12]);", "f[12] = rho1 - rstar;",
+     lambda t: test_oracle_zieb.test_slow_stroke_conserves_mass_and_reaches_the_closed_form_density(0.0025)),
 ]
 
 
