@@ -9,6 +9,7 @@ by a prescribed motion.
 import itertools
 
 import numpy as np
+import pytest
 
 import oracle
 
@@ -114,13 +115,15 @@ def test_exact_ties_go_to_the_smaller_index():
         assert (owner[both] == 0).all()
 
 
-def test_refill_of_uncovered_nodes():
+@pytest.mark.parametrize("Om", [(0.0, 0.0, 0.0), (0.01, -0.02, 0.015)])
+def test_refill_of_uncovered_nodes(Om):
     """Shift a sphere by a prescribed motion; every node uncovered gets the
     equilibrium at the mean density of its neighbours fluid before and after,
-    and at the surface velocity of the sphere (Sect. 2.3, solid equilibrium)."""
-    X0, R, V = np.array([10.25, 9.5, 9.75]), 3.5, np.array([0.75, 0.0, 0.0])
+    and at the surface velocity of the sphere, u_s = V + Om x (x - X) with X
+    the new centre (Sect. 2.3, solid equilibrium)."""
+    X0, R, V, Om = np.array([10.25, 9.5, 9.75]), 3.5, np.array([0.75, 0.0, 0.0]), np.array(Om)
     o = oracle.Oracle(22, 20, 20, tau0=0.7, cs=0.1, g=(1e-4, 0, 0))
-    o.set_particles([X0], V=[V], R=[R], fixed=[1])
+    o.set_particles([X0], V=[V], Om=[Om], R=[R], fixed=[1])
     o.step(1)
     X1 = o.particles()[0][0]
     assert np.array_equal(X1, X0 + V)
@@ -142,7 +145,7 @@ def test_refill_of_uncovered_nodes():
             yy, xx = (y + C[i, 1]) % ny, (x + C[i, 0]) % nx
             if not before[zz, yy, xx] and not after[zz, yy, xx]:
                 rhos.append(f_before[:, zz, yy, xx].sum())
-        expect = oracle.feq(np.mean(rhos), V)
+        expect = oracle.feq(np.mean(rhos), V + np.cross(Om, np.array([x, y, z]) - X1))
         assert np.allclose(f[:, z, y, x], expect, rtol=0, atol=1e-15)
     # nodes not uncovered are untouched
     keep = ~uncovered & ~after

@@ -61,11 +61,15 @@ CASES = [
     # refill at the spin velocity only, the sphere's translation dropped
     ("refill_velocity", "double us[3] = {V[0] + (W[1] * l[2] - W[2] * l[1]),",
      "double us[3] = {(W[1] * l[2] - W[2] * l[1]),",
-     lambda t: test_oracle_geometry.test_refill_of_uncovered_nodes()),
+     lambda t: test_oracle_geometry.test_refill_of_uncovered_nodes((0.0, 0.0, 0.0))),
+    # refill surface velocity with the rotation's cross product reversed, (x - X) x Om
+    ("refill_rotation", "double us[3] = {V[0] + (W[1] * l[2] - W[2] * l[1]),",
+     "double us[3] = {V[0] - (W[1] * l[2] - W[2] * l[1]),",
+     lambda t: test_oracle_geometry.test_refill_of_uncovered_nodes((0.01, -0.02, 0.015))),
     # refill density averaged also over neighbours that were solid before
     ("refill_neighbours", "if (s->owner_prev[m] >= 0 || s->owner[m] >= 0) continue;",
      "if (s->owner[m] >= 0) continue;",
-     lambda t: test_oracle_geometry.test_refill_of_uncovered_nodes()),
+     lambda t: test_oracle_geometry.test_refill_of_uncovered_nodes((0.0, 0.0, 0.0))),
     # moment of inertia of a shell (2/3 m R^2) in place of the solid sphere's
     ("inertia", "double I = 0.4 * m * s->R[a] * s->R[a];", "double I = (2.0 / 3.0) * m * s->R[a] * s->R[a];",
      lambda t: test_oracle_dem.test_external_load_constant_acceleration()),
