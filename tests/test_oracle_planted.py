@@ -39,6 +39,9 @@ CASES = [
     ("exchange_sign", "double m = s->fc[(long)j * s->N + n] + s->fn[(long)k * s->N + n];",
      "double m = s->fc[(long)j * s->N + n] - s->fn[(long)k * s->N + n];",
      lambda t: test_oracle_drag.test_momentum_balance_at_steady_state()),
+    # torque (Eq. 26) with the arm and the momentum transposed in one component, dP x l
+    ("torque_cross", "T[0] += l[1] * dP[2] - l[2] * dP[1];", "T[0] += l[2] * dP[1] - l[1] * dP[2];",
+     lambda t: test_oracle_drag.test_torque_spinning_sphere()),
     # normal damping coefficient missing its factor 2 (Eq. 1)
     ("damping_factor", "return -2.0 * le * sqrt(meff * s->p.kn)", "return -le * sqrt(meff * s->p.kn)",
      lambda t: test_oracle_dem.test_restitution_and_contact_time((4.0, 4.0))),
