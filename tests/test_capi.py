@@ -237,3 +237,19 @@ def test_per_sphere_capacities_hold_sampled_worst_cases_up_to_radius_16():
                 most_uncovered = max(most_uncovered, int((inside & (((g - X - d) ** 2).sum(1) >= R * R)).sum()))
         assert most_links < cap, (R, most_links, cap)
         assert most_uncovered < refill_cap, (R, most_uncovered)
+
+
+def test_a_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """Without the compiled library the binding raises, whether asked to load
+    it as built or through an entry point that builds first: there is no CPU
+    fallback behind it."""
+    from paper_1703_05158_gb300 import build as bld
+
+    absent = str(tmp_path / "absent.so")
+    monkeypatch.setattr(lbm, "_lib", None)
+    monkeypatch.setattr(bld, "LIB", absent)
+    with pytest.raises(RuntimeError, match="missing"):
+        lbm.load(build=False)
+    monkeypatch.setattr(bld, "build", lambda *a, **k: absent)
+    with pytest.raises(RuntimeError, match="missing"):
+        lbm.lbm_error_string(0)
