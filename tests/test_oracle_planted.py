@@ -26,6 +26,12 @@ CASES = [
     # velocity without the half-force shift (Eq. 6 with the body force)
     ("half_force_shift", "u[0] = mx / r + 0.5 * s->p.g[0];", "u[0] = mx / r;",
      lambda t: test_oracle_invariants.test_body_force_momentum_per_step()),
+    # BGK relaxation with tau0 in place of the node's tau* (the eddy viscosity computed, then unused)
+    ("relax_tau0", "= fi - (fi - e) / tau +", "= fi - (fi - e) / s->p.tau0 +",
+     lambda t: test_oracle_flows.test_smagorinsky_eddy_viscosity_in_uniform_shear()),
+    # q >= 1/2 branch of Eq. 19 with the second weight's sign flipped
+    ("q_ge_half_weight", "+ (2.0 * q - 1.0) / (2.0 * q) * fck", "+ (1.0 - 2.0 * q) / (2.0 * q) * fck",
+     lambda t: test_oracle_geometry.test_bounce_back_reads_the_fictitious_node()),
     # Smagorinsky relaxation time without the sqrt(2) of |S| (Eq. 18)
     ("smagorinsky_sqrt2", "18.0 * sqrt(2.0) * C * C * Q", "18.0 * C * C * Q",
      lambda t: test_oracle_flows.test_smagorinsky_eddy_viscosity_in_uniform_shear()),
