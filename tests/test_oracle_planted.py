@@ -120,21 +120,27 @@ def test_planted_mistake_fails_its_pin(name, old, new, pin, d3q19, tmp_path):
             pin(d3q19)
 
 
-# the differentiation form's tangent-linear (dual-number) arithmetic
+# the differentiation form: its tangent-linear (dual-number) arithmetic and its inlet
 CHANNEL_CASES = [
     # derivative of sqrt without its factor 1/2 (the Smagorinsky time's Q and root)
-    ("dsqrt", "dual r = {s, s > 0.0 ? a.d / (2.0 * s) : 0.0};", "dual r = {s, s > 0.0 ? a.d / s : 0.0};", 2),
+    ("dsqrt", "dual r = {s, s > 0.0 ? a.d / (2.0 * s) : 0.0};", "dual r = {s, s > 0.0 ? a.d / s : 0.0};",
+     lambda: test_oracle_channel.test_tangent_linear_matches_central_differences(2)),
     # quotient rule with the wrong sign
-    ("ddiv", "(a.d * b.v - a.v * b.d) / (b.v * b.v)", "(a.d * b.v + a.v * b.d) / (b.v * b.v)", 0),
+    ("ddiv", "(a.d * b.v - a.v * b.d) / (b.v * b.v)", "(a.d * b.v + a.v * b.d) / (b.v * b.v)",
+     lambda: test_oracle_channel.test_tangent_linear_matches_central_differences(0)),
     # product rule missing one term
-    ("dmul", "dual r = {a.v * b.v, a.d * b.v + a.v * b.d};", "dual r = {a.v * b.v, a.d * b.v};", 1),
+    ("dmul", "dual r = {a.v * b.v, a.d * b.v + a.v * b.d};", "dual r = {a.v * b.v, a.d * b.v};",
+     lambda: test_oracle_channel.test_tangent_linear_matches_central_differences(1)),
+    # inlet profile u_peak 2 zh (1 - zh): half the prescribed flux
+    ("inlet_profile", "dscale(s->theta[0], 4.0 * zh * (1.0 - zh))", "dscale(s->theta[0], 2.0 * zh * (1.0 - zh))",
+     lambda: test_oracle_channel.test_mass_flux_is_the_same_through_every_plane_at_steady_state()),
 ]
 
 
-@pytest.mark.parametrize("name,old,new,k", CHANNEL_CASES, ids=[c[0] for c in CHANNEL_CASES])
-def test_planted_derivative_mistake_fails_the_central_difference_pin(name, old, new, k, tmp_path):
+@pytest.mark.parametrize("name,old,new,pin", CHANNEL_CASES, ids=[c[0] for c in CHANNEL_CASES])
+def test_planted_channel_mistake_fails_its_pin(name, old, new, pin, tmp_path):
     chan = oracle.source("channel_oracle.c")
     assert chan.count(old) == 1, name
     with oracle.Planted(oracle.source(), tmp_path / (name + ".so"), channel_source=chan.replace(old, new)):
         with pytest.raises(AssertionError):
-            test_oracle_channel.test_tangent_linear_matches_central_differences(k)
+            pin()
