@@ -48,6 +48,10 @@ CASES = [
     # torque (Eq. 26) with the arm and the momentum transposed in one component, dP x l
     ("torque_cross", "T[0] += l[1] * dP[2] - l[2] * dP[1];", "T[0] += l[2] * dP[1] - l[1] * dP[2];",
      lambda t: test_oracle_drag.test_torque_spinning_sphere()),
+    # sphere-sphere spring at half its stiffness (Eq. 1): the contact lasts sqrt(2) longer
+    ("contact_stiffness", "double fn = P->kn * delta - gamma_n(s, meff) * vn;",
+     "double fn = 0.5 * P->kn * delta - gamma_n(s, meff) * vn;",
+     lambda t: test_oracle_dem.test_restitution_and_contact_time((4.0, 4.0))),
     # normal damping coefficient missing its factor 2 (Eq. 1)
     ("damping_factor", "return -2.0 * le * sqrt(meff * s->p.kn)", "return -le * sqrt(meff * s->p.kn)",
      lambda t: test_oracle_dem.test_restitution_and_contact_time((4.0, 4.0))),
